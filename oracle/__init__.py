@@ -1,0 +1,16 @@
+"""FP64 CPU oracle for the sequential Metropolis Monte Carlo (arXiv:1602.05716).
+
+TEST INFRASTRUCTURE: only tests/, __graft_entry__.smoke() and bench.py's CPU
+baseline / reference legs import this package.  The product library never
+does.  The C source (mco.c) cites the paper section each function follows.
+
+Parity status: every function here is pinned by a CPU test against something
+other than itself (cuRAND's host Philox stream, math.log, closed-form 2- and
+3-ion energies, brute-force energy differences, the exact confined-pair
+distance distribution, the ideal-gas limit and the Debye-Hueckel limiting law).
+"""
+from .oracle import (OracleChain, build, lib, philox4x32_10, move_draws, log_L, total_energy,
+                     RECORD_DTYPE, ACCEPT, REJECT_METROPOLIS, REJECT_OVERLAP, REJECT_WALL)
+
+__all__ = ["OracleChain", "build", "lib", "philox4x32_10", "move_draws", "log_L", "total_energy",
+           "RECORD_DTYPE", "ACCEPT", "REJECT_METROPOLIS", "REJECT_OVERLAP", "REJECT_WALL"]

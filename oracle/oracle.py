@@ -1,0 +1,201 @@
+"""ctypes binding of the FP64 CPU oracle (mco.c).  Test infrastructure only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = None
+
+ACCEPT, REJECT_METROPOLIS, REJECT_OVERLAP, REJECT_WALL = 0, 1, 2, 3
+
+RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("dE", np.float64),
+                         ("a", np.float32, (3,)), ("pad", np.float32)])
+
+
+def build() -> str:
+    """Compile mco.c with gcc: -O2, no FP contraction, no fast-math, OpenMP for the chunk sums."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_HERE, "mco.c")]
+    out = os.path.join(_BUILD, "libmco.so")
+    if not os.path.exists(out) or os.path.getmtime(out) < max(os.path.getmtime(s) for s in srcs):
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                               "-fPIC", "-shared", *srcs, "-o", out + ".tmp", "-lm"])
+        os.replace(out + ".tmp", out)
+    return out
+
+
+def lib():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    L = ctypes.CDLL(build())
+    vp, i64, u64, u32, dbl, ci = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                  ctypes.c_double, ctypes.c_int)
+    L.mco_philox4x32_10.argtypes = [vp, vp, vp]
+    L.mco_philox4x32_10.restype = None
+    L.mco_move_draws.argtypes = [u64, u32, u64, u32, vp]
+    L.mco_move_draws.restype = None
+    L.mco_log.argtypes = [dbl]
+    L.mco_log.restype = dbl
+    L.mco_set_threads.argtypes = [ci]
+    L.mco_set_threads.restype = None
+    L.mco_get_threads.restype = ci
+    L.mco_create.argtypes = [vp, vp, i64, dbl, dbl, dbl, dbl, u64, u32, ctypes.POINTER(vp)]
+    L.mco_create.restype = ci
+    L.mco_destroy.argtypes = [vp]
+    L.mco_destroy.restype = None
+    L.mco_sweep.argtypes = [vp, i64]
+    L.mco_sweep.restype = ci
+    L.mco_partial_sweep.argtypes = [vp, i64]
+    L.mco_partial_sweep.restype = ci
+    L.mco_energy.argtypes = [vp, vp, vp]
+    L.mco_energy.restype = ci
+    L.mco_total_energy_of.argtypes = [vp, vp, i64, dbl]
+    L.mco_total_energy_of.restype = dbl
+    L.mco_gr_histogram.argtypes = [vp, ci, dbl, dbl, vp]
+    L.mco_gr_histogram.restype = ci
+    L.mco_get_positions.argtypes = [vp, vp]
+    L.mco_get_positions.restype = ci
+    L.mco_set_positions.argtypes = [vp, vp]
+    L.mco_set_positions.restype = ci
+    L.mco_stats.argtypes = [vp, vp]
+    L.mco_stats.restype = ci
+    L.mco_set_counters.argtypes = [vp, u64, dbl]
+    L.mco_set_counters.restype = ci
+    L.mco_set_record.argtypes = [vp, vp, i64]
+    L.mco_set_record.restype = ci
+    L.mco_record_len.argtypes = [vp]
+    L.mco_record_len.restype = i64
+    L.mco_delta_e.argtypes = [vp, i64, vp, ctypes.POINTER(ci)]
+    L.mco_delta_e.restype = dbl
+    _LIB = L
+    return L
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().mco_philox4x32_10(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def move_draws(seed: int, chain: int, m: int, purpose: int = 0) -> np.ndarray:
+    out = np.zeros(4, dtype=np.uint32)
+    lib().mco_move_draws(seed, chain, m, purpose, out.ctypes.data)
+    return out
+
+
+def log_L(u: float) -> float:
+    return lib().mco_log(float(u))
+
+
+def total_energy(pos: np.ndarray, q: np.ndarray, l_B: float) -> float:
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    qd = np.ascontiguousarray(q, dtype=np.float64)
+    return lib().mco_total_energy_of(pos.ctypes.data, qd.ctypes.data, int(qd.shape[0]), float(l_B))
+
+
+class OracleChain:
+    """One sequential Metropolis chain, FP64 canonical arithmetic (mco_* API)."""
+
+    def __init__(self, pos, q, sigma, l_B, R, half_width, seed, chain_id=0, threads=None):
+        L = lib()
+        if threads is not None:
+            L.mco_set_threads(int(threads))
+        self._pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1, 3)
+        self._q = np.ascontiguousarray(q, dtype=np.float32)
+        self.n = int(self._q.shape[0])
+        h = ctypes.c_void_p()
+        rc = L.mco_create(self._pos.ctypes.data, self._q.ctypes.data, self.n, float(sigma), float(l_B),
+                          float(R), float(half_width), int(seed), int(chain_id), ctypes.byref(h))
+        if rc != 0:
+            raise ValueError(f"mco_create failed with code {rc}")
+        self._h = h
+        self._rec = None
+        self.l_B = float(l_B)
+
+    @classmethod
+    def from_chain(cls, ch, threads=None):
+        return cls(ch.pos, ch.q, ch.sigma, ch.l_B, ch.R, ch.half_width, ch.seed, ch.chain_id, threads=threads)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mco_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n: int = 1):
+        rc = lib().mco_sweep(self._h, int(n))
+        if rc != 0:
+            raise RuntimeError(f"mco_sweep: {rc}")
+
+    def partial_sweep(self, n_moves: int):
+        rc = lib().mco_partial_sweep(self._h, int(n_moves))
+        if rc != 0:
+            raise RuntimeError(f"mco_partial_sweep: {rc}")
+
+    def energy(self, recompute: bool = True):
+        led = ctypes.c_double()
+        rec = ctypes.c_double()
+        lib().mco_energy(self._h, ctypes.byref(led), ctypes.byref(rec) if recompute else None)
+        return led.value, (rec.value if recompute else None)
+
+    def positions(self) -> np.ndarray:
+        out = np.zeros((self.n, 3), dtype=np.float32)
+        lib().mco_get_positions(self._h, out.ctypes.data)
+        return out
+
+    def set_positions(self, pos):
+        p = np.ascontiguousarray(pos, dtype=np.float32)
+        rc = lib().mco_set_positions(self._h, p.ctypes.data)
+        if rc != 0:
+            raise ValueError(f"mco_set_positions: {rc}")
+
+    def stats(self) -> dict:
+        out = np.zeros(5, dtype=np.uint64)
+        lib().mco_stats(self._h, out.ctypes.data)
+        return dict(sweep=int(out[0]), accept=int(out[1]), rej_metropolis=int(out[2]),
+                    rej_overlap=int(out[3]), rej_wall=int(out[4]))
+
+    def set_counters(self, sweep: int, ledger: float):
+        lib().mco_set_counters(self._h, int(sweep), float(ledger))
+
+    def gr_histogram(self, n_bins=400, r_max=8.0, wall_margin=0.0, counts=None) -> np.ndarray:
+        if counts is None:
+            counts = np.zeros((3, n_bins), dtype=np.uint64)
+        rc = lib().mco_gr_histogram(self._h, int(n_bins), float(r_max), float(wall_margin), counts.ctypes.data)
+        if rc != 0:
+            raise RuntimeError(f"mco_gr_histogram: {rc}")
+        return counts
+
+    def record(self, cap: int | None):
+        """Start recording per-move records (cap entries); None stops."""
+        if cap is None:
+            lib().mco_set_record(self._h, None, 0)
+            self._rec = None
+            return
+        self._rec = np.zeros(int(cap), dtype=RECORD_DTYPE)
+        lib().mco_set_record(self._h, self._rec.ctypes.data, int(cap))
+
+    def records(self) -> np.ndarray:
+        if self._rec is None:
+            return np.zeros(0, dtype=RECORD_DTYPE)
+        n = lib().mco_record_len(self._h)
+        return self._rec[:n].copy()
+
+    def delta_e(self, i: int, a) -> tuple[float, bool]:
+        aa = np.ascontiguousarray(a, dtype=np.float32)
+        ovl = ctypes.c_int()
+        de = lib().mco_delta_e(self._h, int(i), aa.ctypes.data, ctypes.byref(ovl))
+        return de, bool(ovl.value)
