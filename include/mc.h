@@ -1,0 +1,199 @@
+/*
+ * mc.h -- C ABI of the GB300 sequential-Metropolis library (libmcgb300.so).
+ *
+ * The library runs the canonical Metropolis Monte Carlo of primitive-model
+ * electrolytes of Liang, Xing & Li (arXiv:1602.05716): ions are hard spheres
+ * of diameter sigma carrying integer valences q, interacting by the bare
+ * Coulomb potential l_B q_i q_j / r in units of k_B T (l_B = Bjerrum length),
+ * no cutoff and no periodic images, confined by a hard spherical wall of
+ * radius R (Sec. 5.2).  One sweep ("Monte Carlo cycle") tries every ion once
+ * in ascending index order (Sec. 2, sequential updating scheme); each trial
+ * move draws a displacement uniform in a cube of half-width h (Algorithm 1),
+ * computes the exact O(N) energy change
+ *     dE = l_B q_i sum_{j != i} q_j (1/|x'_i - x_j| - 1/|x_i - x_j|)
+ * against the current positions of all other ions (Sec. 2, the Delta E_ij
+ * table), rejects on hard-core overlap (Sec. 3.3) or the wall, and accepts
+ * when the uniform draw u satisfies u < exp(-dE) (Algorithm 4, Eq.
+ * trial-outcome).
+ *
+ * Decisions and positions are bit-identical to the FP64 CPU oracle that uses
+ * the same Philox4x32-10 stream keyed by (seed, chain) with counter = move
+ * index; the GPU computes pair terms in FP32 and recomputes a move's dE in the
+ * oracle's FP64 arithmetic whenever the FP32 value lies inside its proven
+ * error bound of the acceptance threshold.
+ *
+ * Conventions for every call:
+ *  - Return 0 (MC_OK) on success, a negative MC_ERR_* code otherwise; the
+ *    message of the last failure on the calling thread is mc_last_error().
+ *  - Host pointers are read (or written) only during the call; the caller
+ *    keeps ownership.  Positions are float32, packed xyz (3 floats per ion),
+ *    ion-major; valences are float32 (integer values).
+ *  - A handle owns its device memory and a CUDA stream; calls on one handle
+ *    must not run concurrently from several host threads.
+ *  - After MC_ERR_TIMEOUT or MC_ERR_CUDA from a sweep the handle is poisoned
+ *    (every later call but mc_destroy/mc_last_error returns MC_ERR_POISONED);
+ *    the device itself stays usable for other handles.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_OK 0
+#define MC_ERR_INVALID (-1)      /* bad argument (NULL pointer, N < 1, sigma <= 0, ...) */
+#define MC_ERR_OVERLAP_INIT (-2) /* input configuration overlaps or leaves the wall */
+#define MC_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define MC_ERR_TIMEOUT (-4)      /* a bounded device-side wait expired */
+#define MC_ERR_OOM (-5)          /* device or host allocation failed */
+#define MC_ERR_POISONED (-6)     /* handle unusable after an earlier TIMEOUT/CUDA error */
+
+typedef struct mc_system *mc_handle;
+
+/* One chain's inputs (mc_create_batch).  pos_xyz: n*3 floats; q: n floats. */
+typedef struct {
+    const float *pos_xyz;
+    const float *q;
+    int64_t n;
+    double sigma;      /* hard-core diameter */
+    double l_B;        /* Bjerrum length, in units of length (same as sigma) */
+    double R;          /* radius of the hard spherical wall; centres stay within R - sigma/2 */
+    double half_width; /* h: trial displacement uniform in [-h, h)^3 */
+    uint64_t seed;     /* Philox key (low 32 bits) and counter word 3 (high 32 bits) */
+    uint32_t chain_id; /* Philox key word 1 */
+} mc_chain_desc;
+
+/* Counters of one chain since creation (mc_stats). */
+typedef struct {
+    uint64_t sweeps;         /* completed sweeps */
+    uint64_t accepts;        /* accepted moves */
+    uint64_t rej_metropolis; /* rejected by u >= exp(-dE) */
+    uint64_t rej_overlap;    /* rejected by hard-core overlap */
+    uint64_t rej_wall;       /* rejected by the wall */
+    uint64_t guard_fp64;     /* moves decided by the FP64 recomputation */
+    uint64_t decided_interval; /* moves decided before the outcomes of earlier moves of their group were known */
+    uint64_t reserved[9];
+} mc_stats_t;
+
+/* Per-move validation record (mc_record_enable / mc_record_read). */
+typedef struct {
+    uint64_t m;     /* move index = sweep * N + i */
+    int32_t i;      /* ion */
+    int32_t outcome; /* 0 accept, 1 Metropolis reject, 2 overlap, 3 wall */
+    double dE;      /* dE used for the ledger / decision (FP64 value when tier == 4); NaN if not evaluated */
+    double dE32;    /* dE from the FP32 pair sums (NaN when not evaluated) */
+    double scale;   /* l_B |q_i| sum_j |q_j| (1/r' + 1/r): the error-bound scale */
+    int32_t tier;   /* 0 decided from an interval, 1 from the exact FP32 sum, 4 by the FP64 recomputation */
+    int32_t pad;
+} mc_record;
+
+/* Create a single chain (a batch of one).  Copies pos_xyz (n*3) and q (n) to
+ * the device, validates that every centre lies within R - sigma/2 and no two
+ * centres are closer than sigma (MC_ERR_OVERLAP_INIT otherwise), and computes
+ * the initial energy for the ledger.  Sec. 3.1 (float4 x,y,z,valence layout),
+ * Sec. 5.2 (spherical hard wall).                                            */
+int mc_create(const float *pos_xyz, const float *q, int64_t n, double sigma, double l_B, double R,
+              double half_width, uint64_t seed, uint32_t chain_id, mc_handle *out);
+
+/* Create n_chains independent chains (uneven N allowed) swept together by one
+ * persistent launch.  Chains are addressed by index 0..n_chains-1 below.
+ * The paper runs one independent simulation per GPU (Sec. 5.2); here many
+ * independent chains share one GPU.                                          */
+int mc_create_batch(const mc_chain_desc *descs, int n_chains, mc_handle *out);
+
+/* Run n_sweeps sweeps of every chain of the handle (Sec. 2; Algorithms 1-5
+ * describe the paper's GPU schedule, which this launch replaces by its own).
+ * Blocks until done; returns MC_ERR_TIMEOUT if a device-side wait expired.  */
+int mc_sweep(mc_handle h, int64_t n_sweeps);
+
+/* Enqueue n_sweeps sweeps on the handle's stream and return; errors surface
+ * at the next mc_synchronize.                                               */
+int mc_sweep_async(mc_handle h, int64_t n_sweeps);
+int mc_synchronize(mc_handle h);
+
+/* Use the caller's CUDA stream (a cudaStream_t passed as void*); NULL reverts
+ * to the handle's own stream.                                                */
+int mc_set_stream(mc_handle h, void *cuda_stream);
+
+/* Energy of chain `chain`: *ledger = initial energy + sum of accepted dE (FP64
+ * running ledger); *recomputed (nullable) = l_B sum_{i<j} q_i q_j / r_ij of the
+ * current configuration, FP32 pair terms with FP64 row sums (the drift check).
+ * Sec. 5.2 monitors the total energy to judge equilibration.                */
+int mc_energy(mc_handle h, int chain, double *ledger, double *recomputed);
+
+/* Pair-distance histogram behind g_{++}, g_{+-}, g_{--} (Sec. 5.2, Fig. PCF).
+ * For every ion i with |r_i| <= R - sigma/2 - wall_margin (all ions when
+ * wall_margin <= 0) and every j != i: bin = floor(r_ij / (r_max / n_bins)),
+ * counted when bin < n_bins.  counts has 3*n_bins entries (class-major:
+ * 0 = both valences > 0, 1 = mixed, 2 = both < 0) and is ADDED to (caller-
+ * owned, accumulate over calls).  r_ij is the FP64 distance of the FP32
+ * centres, so counts are exact integers.                                     */
+int mc_gr_histogram(mc_handle h, int chain, int n_bins, double r_max, double wall_margin, uint64_t *counts);
+
+/* Copy chain positions to / from a caller buffer of n*3 floats.  Setting
+ * validates like mc_create (MC_ERR_OVERLAP_INIT).                           */
+int mc_get_positions(mc_handle h, int chain, float *pos_xyz);
+int mc_set_positions(mc_handle h, int chain, const float *pos_xyz);
+
+/* Checkpoint: positions (n*3 floats), completed sweeps, energy ledger and
+ * counters.  Restoring them (with the same seed/chain id) resumes the chain
+ * bit-identically, because every random draw is keyed by the move index.    */
+int mc_get_state(mc_handle h, int chain, float *pos_xyz, uint64_t *sweeps, double *ledger, mc_stats_t *stats);
+int mc_set_state(mc_handle h, int chain, const float *pos_xyz, uint64_t sweeps, double ledger,
+                 const mc_stats_t *stats);
+
+/* Counters of chain `chain` (accepts, rejects by cause, FP64 guard count). */
+int mc_stats(mc_handle h, int chain, mc_stats_t *out);
+
+/* Number of chains and N of a chain. */
+int mc_num_chains(mc_handle h);
+int64_t mc_num_ions(mc_handle h, int chain);
+
+/* Validation mode: record the first `cap` moves of later sweeps of chain
+ * `chain` (record index = sweeps since enabling * N + i).  cap = 0 disables. */
+int mc_record_enable(mc_handle h, int chain, int64_t cap);
+/* Copy up to cap records; returns the number copied (>= 0) or an error. */
+int64_t mc_record_read(mc_handle h, int chain, mc_record *out, int64_t cap);
+
+/* Options (mc_set_option):
+ *  MC_OPT_GUARD_MODE   0 = FP32 with proven error band (default),
+ *                      1 = recompute every evaluated move in FP64,
+ *                      2 = decide from FP32 alone (band 0; test of the band only)
+ *  MC_OPT_TIMEOUT_MS   bound of every device-side wait (default 4000)
+ *  MC_OPT_CTAS         persistent CTAs per launch (0 = one per resident slot)
+ *  MC_OPT_SKIP_PUBLISH fault injection: the work item with this index never
+ *                      publishes its result (waiters time out); -1 = off
+ *  MC_OPT_USE_GRAPH    1 = capture each distinct sweep count in a CUDA graph
+ *                      and replay it (default 1), 0 = plain launches        */
+#define MC_OPT_GUARD_MODE 1
+#define MC_OPT_TIMEOUT_MS 2
+#define MC_OPT_CTAS 3
+#define MC_OPT_SKIP_PUBLISH 4
+#define MC_OPT_USE_GRAPH 5
+int mc_set_option(mc_handle h, int option, int64_t value);
+
+/* Free all device and host memory of the handle. */
+void mc_destroy(mc_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mc_last_error(void);
+
+/* Device information for roofline reporting: SM count, max SM clock (kHz). */
+int mc_device_info(int *sm_count, int *sm_clock_khz, int *cc_major, int *cc_minor);
+
+/* Test hook: Philox4x32-10 of the library's device code and of cuRAND's
+ * curand_Philox4x32_10 for n (counter, key) pairs; ctr: n*4, key: n*2,
+ * out_lib / out_curand: n*4 (all host arrays).                               */
+int mc_test_philox(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out_lib, uint32_t *out_curand);
+
+/* Test hook: the library's device FP64 logarithm L(u) for n values. */
+int mc_test_log(const double *u, int64_t n, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

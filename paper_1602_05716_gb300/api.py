@@ -1,0 +1,237 @@
+"""ctypes binding of libmcgb300.so (include/mc.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ERR_INVALID, ERR_OVERLAP_INIT, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_POISONED = -1, -2, -3, -4, -5, -6
+OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH = 1, 2, 3, 4, 5
+
+RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("dE", np.float64),
+                         ("dE32", np.float64), ("scale", np.float64), ("tier", np.int32), ("pad", np.int32)])
+
+_STATS_FIELDS = ["sweeps", "accepts", "rej_metropolis", "rej_overlap", "rej_wall", "guard_fp64",
+                 "decided_interval"]
+
+
+class MCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("pos_xyz", ctypes.c_void_p), ("q", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("sigma", ctypes.c_double), ("l_B", ctypes.c_double), ("R", ctypes.c_double),
+                ("half_width", ctypes.c_double), ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in _STATS_FIELDS] + [("reserved", ctypes.c_uint64 * 9)]
+
+
+_LIB = None
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    return _build.build(verbose=verbose, force=force)
+
+
+def lib():
+    """Load the in-tree CUDA library; raises if it has not been built (no fallback exists)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"{_build.LIB} is missing: run paper_1602_05716_gb300.build() "
+                          "(nvcc for sm_103a); there is no CPU fallback")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, u64, u32, dbl, ci = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                  ctypes.c_double, ctypes.c_int)
+    sig = {
+        "mc_create": ([vp, vp, i64, dbl, dbl, dbl, dbl, u64, u32, ctypes.POINTER(vp)], ci),
+        "mc_create_batch": ([ctypes.POINTER(_Desc), ci, ctypes.POINTER(vp)], ci),
+        "mc_sweep": ([vp, i64], ci),
+        "mc_sweep_async": ([vp, i64], ci),
+        "mc_synchronize": ([vp], ci),
+        "mc_set_stream": ([vp, vp], ci),
+        "mc_energy": ([vp, ci, vp, vp], ci),
+        "mc_gr_histogram": ([vp, ci, ci, dbl, dbl, vp], ci),
+        "mc_get_positions": ([vp, ci, vp], ci),
+        "mc_set_positions": ([vp, ci, vp], ci),
+        "mc_get_state": ([vp, ci, vp, vp, vp, vp], ci),
+        "mc_set_state": ([vp, ci, vp, u64, dbl, vp], ci),
+        "mc_stats": ([vp, ci, vp], ci),
+        "mc_num_chains": ([vp], ci),
+        "mc_num_ions": ([vp, ci], i64),
+        "mc_record_enable": ([vp, ci, i64], ci),
+        "mc_record_read": ([vp, ci, vp, i64], i64),
+        "mc_set_option": ([vp, ci, i64], ci),
+        "mc_destroy": ([vp], None),
+        "mc_last_error": ([], ctypes.c_char_p),
+        "mc_device_info": ([vp, vp, vp, vp], ci),
+        "mc_test_philox": ([vp, vp, i64, vp, vp], ci),
+        "mc_test_log": ([vp, i64, vp], ci),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = L
+    return L
+
+
+def _check(rc: int):
+    if rc < 0:
+        raise MCError(rc, lib().mc_last_error().decode(errors="replace"))
+    return rc
+
+
+def device_info() -> dict:
+    sm, clk, ma, mi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().mc_device_info(ctypes.byref(sm), ctypes.byref(clk), ctypes.byref(ma), ctypes.byref(mi)))
+    return dict(sm_count=sm.value, sm_clock_khz=clk.value, cc=(ma.value, mi.value))
+
+
+def test_philox(ctr: np.ndarray, key: np.ndarray):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    n = ctr.shape[0]
+    a = np.zeros((n, 4), np.uint32)
+    b = np.zeros((n, 4), np.uint32)
+    _check(lib().mc_test_philox(ctr.ctypes.data, key.ctypes.data, n, a.ctypes.data, b.ctypes.data))
+    return a, b
+
+
+def test_log(u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros_like(u)
+    _check(lib().mc_test_log(u.ctypes.data, u.shape[0], out.ctypes.data))
+    return out
+
+
+class System:
+    """A set of independent chains swept together (mc_create / mc_create_batch)."""
+
+    def __init__(self, chains):
+        """chains: iterable of objects with pos (N,3) float32, q (N,) float32, sigma, l_B, R, half_width,
+        seed, chain_id (e.g. inputs.Chain)."""
+        L = lib()
+        chains = list(chains)
+        self._keep = []
+        descs = (_Desc * len(chains))()
+        for k, c in enumerate(chains):
+            p = np.ascontiguousarray(c.pos, dtype=np.float32).reshape(-1, 3)
+            q = np.ascontiguousarray(c.q, dtype=np.float32)
+            self._keep += [p, q]
+            descs[k] = _Desc(p.ctypes.data, q.ctypes.data, q.shape[0], float(c.sigma), float(c.l_B), float(c.R),
+                             float(c.half_width), int(c.seed), int(c.chain_id))
+        h = ctypes.c_void_p()
+        _check(L.mc_create_batch(descs, len(chains), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+        self.n = [int(L.mc_num_ions(h, k)) for k in range(len(chains))]
+
+    @classmethod
+    def single(cls, pos, q, sigma, l_B, R, half_width, seed, chain_id=0):
+        class _C:
+            pass
+        c = _C()
+        c.pos, c.q, c.sigma, c.l_B, c.R, c.half_width, c.seed, c.chain_id = (pos, q, sigma, l_B, R, half_width,
+                                                                              seed, chain_id)
+        return cls([c])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def sweep(self, n: int = 1):
+        _check(lib().mc_sweep(self._h, int(n)))
+
+    def sweep_async(self, n: int = 1):
+        _check(lib().mc_sweep_async(self._h, int(n)))
+
+    def synchronize(self):
+        _check(lib().mc_synchronize(self._h))
+
+    def set_stream(self, stream_ptr: int | None):
+        _check(lib().mc_set_stream(self._h, stream_ptr))
+
+    def set_option(self, opt: int, value: int):
+        _check(lib().mc_set_option(self._h, int(opt), int(value)))
+
+    def energy(self, chain: int = 0, recompute: bool = True):
+        led = ctypes.c_double()
+        rec = ctypes.c_double()
+        _check(lib().mc_energy(self._h, chain, ctypes.byref(led), ctypes.byref(rec) if recompute else None))
+        return led.value, (rec.value if recompute else None)
+
+    def positions(self, chain: int = 0) -> np.ndarray:
+        out = np.zeros((self.n[chain], 3), np.float32)
+        _check(lib().mc_get_positions(self._h, chain, out.ctypes.data))
+        return out
+
+    def set_positions(self, pos, chain: int = 0):
+        p = np.ascontiguousarray(pos, dtype=np.float32)
+        _check(lib().mc_set_positions(self._h, chain, p.ctypes.data))
+
+    def stats(self, chain: int = 0) -> dict:
+        s = _Stats()
+        _check(lib().mc_stats(self._h, chain, ctypes.byref(s)))
+        return {f: int(getattr(s, f)) for f in _STATS_FIELDS}
+
+    def get_state(self, chain: int = 0) -> dict:
+        pos = np.zeros((self.n[chain], 3), np.float32)
+        sw = ctypes.c_uint64()
+        led = ctypes.c_double()
+        st = _Stats()
+        _check(lib().mc_get_state(self._h, chain, pos.ctypes.data, ctypes.byref(sw), ctypes.byref(led),
+                                  ctypes.byref(st)))
+        return dict(pos=pos, sweeps=sw.value, ledger=led.value, stats={f: int(getattr(st, f)) for f in _STATS_FIELDS})
+
+    def set_state(self, state: dict, chain: int = 0):
+        p = np.ascontiguousarray(state["pos"], dtype=np.float32)
+        st = _Stats()
+        for f in _STATS_FIELDS:
+            setattr(st, f, int(state["stats"].get(f, 0)))
+        _check(lib().mc_set_state(self._h, chain, p.ctypes.data, int(state["sweeps"]), float(state["ledger"]),
+                                  ctypes.byref(st)))
+
+    def gr_histogram(self, chain: int = 0, n_bins: int = 400, r_max: float = 8.0, wall_margin: float = 0.0,
+                     counts: np.ndarray | None = None) -> np.ndarray:
+        if counts is None:
+            counts = np.zeros((3, n_bins), np.uint64)
+        _check(lib().mc_gr_histogram(self._h, chain, int(n_bins), float(r_max), float(wall_margin),
+                                     counts.ctypes.data))
+        return counts
+
+    def record_enable(self, cap: int, chain: int = 0):
+        _check(lib().mc_record_enable(self._h, chain, int(cap)))
+        self._rec_cap = int(cap)
+
+    def records(self, chain: int = 0) -> np.ndarray:
+        cap = getattr(self, "_rec_cap", 0)
+        out = np.zeros(cap, RECORD_DTYPE)
+        n = _check(lib().mc_record_read(self._h, chain, out.ctypes.data, cap))
+        return out[:n]

@@ -1,0 +1,192 @@
+// mc_device.cuh -- device building blocks of the sm_103a sequential-Metropolis
+// path: the Philox4x32-10 stream, the FP64 logarithm of the acceptance test,
+// the FP64 canonical pair term, and the structures shared by the kernels and
+// the host runtime.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcg {
+
+// ---------------------------------------------------------------------------
+// Work decomposition.  A "group" is S consecutive ions of one chain; a work
+// item ("ticket") is one group at one sweep.  A CTA of T threads owns the S
+// trial moves of its group.
+constexpr int S = 128;          // moves per group
+constexpr int T = 256;          // threads per CTA
+constexpr int ETA = T / (S / 2);  // threads per pair of moves (column slices)
+constexpr int CS = S + 8;       // row stride of the correction matrix (floats)
+constexpr int CHUNK = 1024;     // canonical FP64 summation chunk
+constexpr int WORDS = S / 32;   // 32-move flag words per group
+
+// Outcome codes (same meaning as the records of the C ABI).
+constexpr int OUT_ACCEPT = 0;
+constexpr int OUT_METROPOLIS = 1;
+constexpr int OUT_OVERLAP = 2;
+constexpr int OUT_WALL = 3;
+
+// Error codes written by the kernel into Ctl::err.
+constexpr int KERR_TIMEOUT = 1;
+constexpr int KERR_PROTOCOL = 2;
+
+struct MoveRec {
+    unsigned long long m;
+    int i;
+    int outcome;
+    double dE;
+    double dE32;
+    double scale;
+    int tier;
+    int pad;
+};
+
+// Per-chain device descriptor (read-only during a launch).
+struct ChainDev {
+    float4 *pos;                  // N_pad entries: x, y, z, valence (Sec. 3.1's float4 layout)
+    unsigned long long *flags;    // per 32-ion word: ((sweep+1) << 32) | accept bits
+    double *ledger;               // running energy
+    unsigned long long *ledger_seq;  // groups folded into the ledger (absolute stream index)
+    unsigned long long *stats;    // 8 counters
+    unsigned long long *sweep;    // completed sweeps (absolute)
+    MoveRec *rec;                 // validation records or nullptr
+    unsigned long long rec_sweep0;  // sweep at which recording started
+    long long rec_cap;
+    int N;
+    int B;                        // groups: ceil(N / S)
+    float D;                      // fl32(2h)
+    float sig2_lo;                // FP32 squared distances below this certainly overlap
+    float sig2_hi;                // ... above this certainly do not; in between FP64 decides
+    float pad_f;
+    double sig2;                  // sigma^2
+    double lB;                    // Bjerrum length
+    double Rc2;                   // (R - sigma/2)^2
+    unsigned key0, key1, ctr3;    // Philox key (seed_lo, chain_id), counter word 3 (seed_hi)
+    unsigned pad;
+};
+
+struct Ticket {
+    int chain;
+    int g;
+    int s_rel;
+    int pad;
+};
+
+struct Ctl {
+    unsigned int ticket;          // next work item
+    int err;                      // KERR_*
+    int abort;                    // set on any error: every CTA leaves
+    int guard_mode;               // 0 band, 1 always FP64, 2 never
+    long long timeout_ns;
+    long long skip_ticket;        // fault injection (-1 off)
+    unsigned long long err_info;  // where a wait gave up
+};
+
+// Counter slots of ChainDev::stats.
+constexpr int CNT_ACCEPT = 0, CNT_METRO = 1, CNT_OVERLAP = 2, CNT_WALL = 3, CNT_FP64 = 4, CNT_INTERVAL = 5;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): two 32x32 multiplies per round with
+// the published multipliers; key bumped by the published Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Draws of move m: counter (m_lo, m_hi, purpose, seed_hi), key (seed_lo, chain).
+__device__ __forceinline__ uint4 move_draws(const ChainDev &ch, unsigned long long m, unsigned purpose)
+{
+    return philox4x32_10(make_uint4((unsigned)m, (unsigned)(m >> 32), purpose, ch.ctr3), make_uint2(ch.key0, ch.key1));
+}
+
+// Trial position: x'_k = fl32(x_k + fl32((u_k - 1/2) D)), u_k = (w_k >> 8) 2^-24
+// (Algorithm 1: displacement (u - 0.5) D added to the old coordinate).
+__device__ __forceinline__ float trial_coord(float x, unsigned w, float D)
+{
+    const float u = __uint2float_rn(w >> 8) * 0x1p-24f;
+    return __fadd_rn(x, __fmul_rn(__fsub_rn(u, 0.5f), D));
+}
+
+// ---------------------------------------------------------------------------
+// L(u): natural logarithm in FP64 from IEEE +, -, *, / only, so that every
+// implementation of the same steps returns the same double.  Reduction
+// u = f 2^e with f in [sqrt(1/2), sqrt(2)); ln f = 2 atanh(s) with
+// s = (f - 1)/(f + 1) summed as 2 s (1 + z/3 + ... + z^10/21), z = s^2
+// (Abramowitz & Stegun 4.1.27); ln 2 split into a 32-bit head and a tail.
+__device__ __forceinline__ double series_log(double u)
+{
+    int e;
+    double f = frexp(u, &e);
+    if (f < 0.70710678118654752440) {
+        f = __dmul_rn(f, 2.0);
+        e -= 1;
+    }
+    const double s = __ddiv_rn(__dsub_rn(f, 1.0), __dadd_rn(f, 1.0));
+    const double z = __dmul_rn(s, s);
+    double p = __ddiv_rn(1.0, 21.0);
+#pragma unroll
+    for (int k = 9; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, z), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    const double lnf = __dmul_rn(__dmul_rn(2.0, s), p);
+    const double de = (double)e;
+    return __dadd_rn(__dmul_rn(de, 0.693147180601954460144042968750),
+                     __dadd_rn(__dmul_rn(de, -4.2009150726810847291823431924e-11), lnf));
+}
+
+// FP64 squared distance of two FP32 points, in the order ((dx^2 + dy^2) + dz^2).
+__device__ __forceinline__ double d2_fp64(float ax, float ay, float az, float bx, float by, float bz)
+{
+    const double dx = __dsub_rn((double)ax, (double)bx);
+    const double dy = __dsub_rn((double)ay, (double)by);
+    const double dz = __dsub_rn((double)az, (double)bz);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// FP64 pair term q_j (1/|a - y| - 1/|b - y|) with IEEE sqrt and division.
+__device__ __forceinline__ double term_fp64(float4 a, float4 b, float4 y, bool &ovl, double sig2)
+{
+    const double d2n = d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z);
+    const double d2o = d2_fp64(b.x, b.y, b.z, y.x, y.y, y.z);
+    ovl = d2n < sig2;
+    const double rn = __ddiv_rn(1.0, __dsqrt_rn(d2n));
+    const double ro = __ddiv_rn(1.0, __dsqrt_rn(d2o));
+    return __dmul_rn((double)y.w, __dsub_rn(rn, ro));
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Release / acquire accesses at GPU scope for the inter-CTA protocol.
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace mcg

@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded inputs.
+
+Bar: accept/reject decisions and positions bit-identical (integer-valued outcomes, FP32 coordinates that
+must match exactly); per-move dE error of the FP32 path <= 1e-6 of l_B |q_i| sum_j |q_j| (1/r' + 1/r);
+histogram counts bit-identical; energies within the FP32 pair-term tolerance stated per test.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+THREADS = min(16, os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1602_05716_gb300 as p
+    p.build()
+    p.lib()
+    return p
+
+
+def _pair(ch, **kw):
+    import paper_1602_05716_gb300 as p
+    return p.System([ch]), oracle.OracleChain.from_chain(ch, threads=THREADS)
+
+
+def test_philox_matches_curand_and_oracle(pkg):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [0, 0, 7, 0]]
+    key[:4] = [[0, 0], [0xFFFFFFFF] * 2, [5, 6], [0, 0]]
+    mine, cur = pkg.test_philox(ctr, key)
+    assert (mine == cur).all()
+    for k in range(0, 4096, 97):
+        assert (oracle.philox4x32_10(ctr[k], key[k]) == mine[k]).all()
+
+
+def test_device_log_bit_identical_to_oracle(pkg):
+    rng = np.random.default_rng(2)
+    ks = np.concatenate([rng.integers(1, 1 << 24, 50000), [1, 2, 3, (1 << 24) - 1, 1 << 23, 11863283, 11863284]])
+    u = ks.astype(np.float64) * 2.0 ** -24
+    got = pkg.test_log(u)
+    ref = np.array([oracle.log_L(x) for x in u])
+    assert (got.view(np.uint64) == ref.view(np.uint64)).all()
+
+
+def _compare_records(gr, orc, N, lB_q_tol=1e-6):
+    assert len(gr) == len(orc)
+    assert (gr["m"] == orc["m"]).all()
+    assert (gr["outcome"] == orc["outcome"]).all(), np.nonzero(gr["outcome"] != orc["outcome"])[0][:10]
+    ev = (orc["outcome"] == oracle.ACCEPT) | (orc["outcome"] == oracle.REJECT_METROPOLIS)
+    # tier-4 moves carry the oracle's FP64 value exactly
+    t4 = ev & (gr["tier"] == 4)
+    assert (gr["dE"][t4] == orc["dE"][t4]).all()
+    # FP32 values: error relative to the bound scale (BJ target 1e-6)
+    ok32 = ev & np.isfinite(gr["dE32"])
+    err = np.abs(gr["dE32"][ok32] - orc["dE"][ok32]) / np.maximum(gr["scale"][ok32], 1e-300)
+    if err.size:
+        assert err.max() <= lB_q_tol, err.max()
+    return err
+
+
+@pytest.mark.parametrize("n,two_one,phi,sweeps", [(2, False, 0.05, 30), (3, True, 0.05, 30), (33, False, 0.1, 20),
+                                                  (128, False, 0.15, 10), (129, True, 0.15, 10),
+                                                  (257, False, 0.2, 8), (300, True, 0.25, 6), (700, False, 0.2, 3)])
+def test_trajectory_bit_identical_small(pkg, n, two_one, phi, sweeps):
+    """Several tiles and a ragged tail: decisions, positions and counters identical to the oracle."""
+    ch = inputs.small_chain(n, phi=phi, seed=100 + n, two_one=two_one, half_width=0.4)
+    gs, oc = _pair(ch)
+    gs.record_enable(sweeps * n)
+    oc.record(sweeps * n)
+    for _ in range(sweeps):
+        gs.sweep(1)
+        oc.sweep(1)
+        assert (gs.positions() == oc.positions()).all()
+    _compare_records(gs.records(), oc.records(), n)
+    sg, so = gs.stats(), oc.stats()
+    for k_g, k_o in [("accepts", "accept"), ("rej_metropolis", "rej_metropolis"), ("rej_overlap", "rej_overlap"),
+                     ("rej_wall", "rej_wall")]:
+        assert sg[k_g] == so[k_o], (k_g, sg, so)
+    led_g, rec_g = gs.energy()
+    led_o, rec_o = oc.energy()
+    scale = max(1.0, abs(rec_o))
+    assert abs(led_g - led_o) < 1e-6 * scale * max(1, n / 100)
+    assert abs(rec_g - rec_o) < 1e-5 * scale
+
+
+def test_plain_n256_full_run(pkg):
+    """The N=256 1:1 workload (phi 0.10, l_B 0.7, h 0.5) for all 2000 sweeps: identical final positions."""
+    ch = inputs.workload("plain_n256").chains[0]
+    gs, oc = _pair(ch)
+    gs.sweep(ch.sweeps)
+    oc.sweep(ch.sweeps)
+    assert (gs.positions() == oc.positions()).all()
+    sg, so = gs.stats(), oc.stats()
+    assert sg["accepts"] == so["accept"] and sg["rej_overlap"] == so["rej_overlap"]
+    led_g, _ = gs.energy(recompute=False)
+    led_o, rec_o = oc.energy()
+    assert abs(led_g - rec_o) < 1e-6 * max(1.0, abs(rec_o)) * 50
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_guard_modes(pkg, mode):
+    """Mode 1 recomputes every evaluated move in FP64 (band = infinity): must equal the oracle.  Mode 2 decides in
+    FP32 alone (band = 0): may differ only on moves the band would have sent to FP64 -- counted, expected rare."""
+    ch = inputs.small_chain(300, phi=0.2, seed=7, two_one=True)
+    gs, oc = _pair(ch)
+    gs.set_option(pkg.OPT_GUARD_MODE, mode)
+    gs.record_enable(300 * 4)
+    oc.record(300 * 4)
+    gs.sweep(4)
+    oc.sweep(4)
+    gr, orc = gs.records(), oc.records()
+    if mode == 1:
+        assert (gs.positions() == oc.positions()).all()
+        assert (gr["outcome"] == orc["outcome"]).all()
+        ev = (orc["outcome"] == 0) | (orc["outcome"] == 1)
+        assert (gr["dE"][ev] == orc["dE"][ev]).all()
+    else:
+        diff = int((gr["outcome"] != orc["outcome"]).sum())
+        assert diff <= 3, diff
+
+
+def test_large_chain_prefix(pkg):
+    """The N=16383 2:1 workload (phi 0.20, h 0.3): the first two sweeps bit-identical, in the production launch."""
+    ch = inputs.workload("plain_n16383").chains[0]
+    gs, oc = _pair(ch)
+    n = ch.n
+    gs.record_enable(2 * n)
+    oc.record(2 * n)
+    gs.sweep(2)
+    oc.sweep(2)
+    assert (gs.positions() == oc.positions()).all()
+    err = _compare_records(gs.records(), oc.records(), n)
+    print("max relative dE error", err.max() if err.size else 0.0)
+
+
+def test_energy_and_histogram_match_oracle(pkg):
+    ch = inputs.small_chain(900, phi=0.2, seed=31, two_one=True)
+    gs, oc = _pair(ch)
+    gs.sweep(3)
+    oc.sweep(3)
+    assert (gs.positions() == oc.positions()).all()
+    _, rec_g = gs.energy()
+    _, rec_o = oc.energy()
+    assert abs(rec_g - rec_o) < 1e-5 * max(1.0, abs(rec_o))
+    for margin in (0.0, 2.0):
+        hg = gs.gr_histogram(0, 400, 8.0, margin)
+        ho = oc.gr_histogram(400, 8.0, margin)
+        assert (hg == ho).all()
+
+
+def test_checkpoint_resume_bit_identical(pkg):
+    ch = inputs.small_chain(400, phi=0.2, seed=41)
+    import paper_1602_05716_gb300 as p
+    a = p.System([ch])
+    a.sweep(5)
+    st = a.get_state()
+    a.sweep(6)
+    ref = a.positions()
+    b = p.System([ch])
+    b.set_state(st)
+    b.sweep(6)
+    assert (b.positions() == ref).all()
+    assert b.stats()["accepts"] == a.stats()["accepts"]
+
+
+def test_batch_equals_single(pkg):
+    import paper_1602_05716_gb300 as p
+    chains = [inputs.small_chain(n, phi=0.15, seed=200 + n, two_one=(n % 2 == 1), chain_id=k)
+              for k, n in enumerate([64, 300, 1000, 129])]
+    batch = p.System(chains)
+    batch.sweep(4)
+    for k, ch in enumerate(chains):
+        single = p.System([ch])
+        single.sweep(4)
+        assert (batch.positions(k) == single.positions()).all()
+
+
+def test_bounded_wait_fault_injection(pkg):
+    """A work item that never publishes: every waiter gives up after the timeout, the call returns
+    MC_ERR_TIMEOUT, the handle is poisoned and the device stays usable."""
+    import paper_1602_05716_gb300 as p
+    ch = inputs.small_chain(600, phi=0.15, seed=5)
+    s = p.System([ch])
+    s.set_option(p.OPT_TIMEOUT_MS, 300)
+    s.set_option(p.OPT_SKIP_PUBLISH, 3)
+    with pytest.raises(p.MCError) as ei:
+        s.sweep(2)
+    assert ei.value.code == p.ERR_TIMEOUT
+    with pytest.raises(p.MCError) as ei:
+        s.sweep(1)
+    assert ei.value.code == p.ERR_POISONED
+    s.close()
+    t = p.System([ch])
+    t.sweep(2)
+    o = oracle.OracleChain.from_chain(ch)
+    o.sweep(2)
+    assert (t.positions() == o.positions()).all()
+
+
+def test_create_rejects_invalid(pkg):
+    import paper_1602_05716_gb300 as p
+    pos = np.array([[0, 0, 0], [0.5, 0, 0]], np.float32)
+    with pytest.raises(p.MCError) as ei:
+        p.System.single(pos, np.array([1, -1], np.float32), 1.0, 0.7, 3.0, 0.5, 0)
+    assert ei.value.code == p.ERR_OVERLAP_INIT
+    pos = np.array([[0, 0, 0], [2.9, 0, 0]], np.float32)
+    with pytest.raises(p.MCError) as ei:
+        p.System.single(pos, np.array([1, -1], np.float32), 1.0, 0.7, 3.0, 0.5, 0)
+    assert ei.value.code == p.ERR_OVERLAP_INIT
+    with pytest.raises(p.MCError) as ei:
+        p.System.single(np.zeros((1, 3), np.float32), np.ones(1, np.float32), -1.0, 0.7, 3.0, 0.5, 0)
+    assert ei.value.code == p.ERR_INVALID
