@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Throughput of the exact sequential Metropolis path on GB300 (moves/s and G pair-evals/s).
+
+Workload (default): N = 16383 ions of a 2:1 primitive-model electrolyte (5461 x +2, 10922 x -1), sigma = 1,
+l_B = 0.7, hard sphere at volume fraction 0.20, displacement half-width 0.3, 500 sweeps = 50 steps of 10
+sweeps.  One step is one launch of the persistent sweep kernel (all trial moves of 10 sweeps: random draws,
+trial positions, wall test, FP32 pair sums, FP64 guard, decisions, position updates, ledger).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line (rank 0).  With --gpus N > 1 (launched by torch.distributed.run) every rank runs an
+independent replica chain (chain id = rank; no data-path collective: the path does not shard) and the value
+is the moves of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MC trial moves/s and G pair-evals/s per GB300 vs plain exact FP64-guarded path"
+SWEEP_SOURCES = ["paper_1602_05716_gb300/csrc/mc_sweep.cu", "paper_1602_05716_gb300/csrc/mc_device.cuh"]
+
+# ALU roofline of the pair term ("Roofline"): per pair-eval two MUFU reciprocal square roots and
+# 14 FP32-pipe operations (6 differences, 6 multiply/fma for the two squared distances, 1 difference of the
+# inverse distances, 1 fma into the sum).  Unit rates per SM per clock on sm_103: FP32 lanes 128; MUFU rsqrt
+# MUFU_RSQ_PER_CLK (measured by the throughput probe recorded in profiles/alu_throughput_probe.md).
+FP32_PER_CLK = 128.0
+MUFU_RSQ_PER_CLK = 16.0
+ALG_FP32_PER_PAIR = 14.0
+RSQ_PER_PAIR = 2.0
+
+
+def peak_pairs_per_clk_sm() -> float:
+    return min(MUFU_RSQ_PER_CLK / RSQ_PER_PAIR, FP32_PER_CLK / ALG_FP32_PER_PAIR)
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per launch of the sweep kernel from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = data.get(workload)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_step")
+
+
+def peaks_file() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        self.idx = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max_sum(t_local: float, moves_local: float, world: int, device=None):
+    """(max time over ranks, total moves over ranks); plain values at world size 1."""
+    if world == 1:
+        return t_local, moves_local
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    mm = torch.tensor([moves_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(mm, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(mm.item())
+
+
+def cpu_baseline(chain, min_seconds: float = 8.0, max_sweeps: int = 20, threads: int | None = None) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: whole sweeps of the same starting configuration."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    oc = oracle.OracleChain.from_chain(chain, threads=threads)
+    t0 = time.perf_counter()
+    sweeps = 0
+    while sweeps < max_sweeps:
+        oc.sweep(1)
+        sweeps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    moves = sweeps * chain.n
+    return {"value": moves / dt, "unit": "moves/s", "cores": threads, "kind": "oracle",
+            "sample": f"{sweeps} full sweeps ({moves} moves, {sweeps * chain.pair_evals_per_sweep:.3g} pair-evals) of "
+                      f"the same N={chain.n} chain from its initial configuration, {dt:.2f} s wall, FP64 canonical "
+                      f"oracle with chunk-parallel sums on {threads} threads",
+            "pair_evals_per_s": sweeps * chain.pair_evals_per_sweep / dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import inputs
+    ch = inputs.workload(args.workload).chains[0]
+    import oracle
+    threads = os.cpu_count() or 1
+    oc = oracle.OracleChain.from_chain(ch, threads=threads)
+    # each step: a bounded sample of the workload (a fixed number of moves), sized so K+W steps end in minutes
+    moves_per_step = max(1, min(ch.n, int(args.ref_moves_per_step)))
+    for _ in range(args.warmup):
+        oc.partial_sweep(moves_per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oc.partial_sweep(moves_per_step)
+    dt = time.perf_counter() - t0
+    value = args.steps * moves_per_step / dt
+    sample = (f"{args.steps} steps x {moves_per_step} moves (prefix of a sweep) of the N={ch.n} chain, FP64 oracle "
+              f"on {threads} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": ch.n},
+            "gpair_evals_per_s": value * (ch.n - 1) / 1e9,
+            "cpu_baseline": {"value": value, "unit": "moves/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import inputs
+    import paper_1602_05716_gb300 as pkg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.build()
+    wl = inputs.workload(args.workload)
+    base = wl.chains[0]
+    if len(wl.chains) != 1:
+        raise SystemExit("bench.py times single-chain workloads; use the batch benchmark for batches")
+    import copy
+    ch = copy.copy(base)
+    ch.chain_id = base.chain_id + rank  # independent replica per rank
+    sps = args.sweeps_per_step
+    n = ch.n
+    moves_per_step = n * sps
+    pairs_per_step = n * (n - 1) * sps
+
+    stream = torch.cuda.Stream()
+    flush = torch.empty(max(1, args.flush_mb) * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        sysm = pkg.System([ch])
+        sysm.set_stream(stream.cuda_stream)
+        for _ in range(args.warmup):
+            flush.zero_()
+            sysm.sweep_async(sps)
+        stream.synchronize()
+        sysm.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            w0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.zero_()  # L2 flush between timed steps (default 512 MiB > 129 MB L2), outside the events
+                ev[k][0].record(stream)
+                sysm.sweep_async(sps)
+                ev[k][1].record(stream)
+            stream.synchronize()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - w0
+        sysm.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1000.0
+    t_max, moves_total = reduce_max_sum(t_local, float(moves_per_step * args.steps), world,
+                                        device=torch.device("cuda", local))
+    if world > 1:
+        torch.distributed.barrier()
+    stats = sysm.stats()
+    led, rec = sysm.energy()
+    value = moves_total / t_max
+    pair_rate = value * (n - 1)
+
+    # roofline of the dominant kernel (the persistent sweep kernel: one launch per step)
+    info = pkg.device_info()
+    peaks = peaks_file()
+    max_mhz = float(peaks.get("sm_max_mhz") or info["sm_clock_khz"] / 1000.0)
+    peak = info["sm_count"] * peak_pairs_per_clk_sm() * max_mhz * 1e6
+    mean_step_s = statistics.mean(step_ms) / 1000.0
+    achieved = pairs_per_step / mean_step_s
+    csum = clk.summary()
+    load_mhz = csum.get("sm_mhz")
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-evals/s",
+            "frac": achieved / peak, "traffic": measured_traffic(args.workload),
+            "peak_basis": f"{info['sm_count']} SMs x min(MUFU rsqrt {MUFU_RSQ_PER_CLK:g}/clk / 2 per pair, FP32 "
+                          f"{FP32_PER_CLK:g}/clk / {ALG_FP32_PER_PAIR:g} per pair) x {max_mhz:g} MHz (max SM clock)",
+            "frac_at_load_clock": (achieved / (peak * load_mhz / max_mhz)) if load_mhz else None,
+            "kernel": "mcg::sweep_kernel (one launch per step, timed by CUDA events on its stream)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "N": n, "sweeps_per_step": sps,
+                       "sweeps_timed": sps * args.steps, "phi": ch.phi, "l_B": ch.l_B, "half_width": ch.half_width,
+                       "l2": f"flushed between steps ({args.flush_mb} MiB device write outside the timed events)",
+                       "parallelism": f"replicas x{world}"},
+            "gpair_evals_per_s": pair_rate / 1e9,
+            "roofline": roof,
+            "clocks": csum,
+            "gpu_launches": 2 * args.steps,
+            "accept_rate": stats["accepts"] / max(1, n * stats["sweeps"]),
+            "fp64_guard_per_move": stats["guard_fp64"] / max(1, n * stats["sweeps"]),
+            "interval_decided_per_move": stats["decided_interval"] / max(1, n * stats["sweeps"]),
+            "energy": {"ledger": led, "recomputed": rec, "drift": led - rec},
+            "wall_s": wall}
+
+    # end to end through the C ABI with host buffers: upload positions, sweep, read positions + ledger back
+    if not args.no_e2e:
+        import ctypes
+        L = pkg.lib()
+        host = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+        host.copy_(torch.from_numpy(sysm.positions()))
+        led_h = ctypes.c_double()
+        e2e_t = []
+        for k in range(args.warmup + args.steps):
+            stream.synchronize()
+            t0 = time.perf_counter()
+            rc = L.mc_set_positions(sysm.handle, 0, ctypes.c_void_p(host.data_ptr()))
+            rc = rc or L.mc_sweep(sysm.handle, sps)
+            rc = rc or L.mc_get_positions(sysm.handle, 0, ctypes.c_void_p(host.data_ptr()))
+            rc = rc or L.mc_energy(sysm.handle, 0, ctypes.byref(led_h), None)
+            dt = time.perf_counter() - t0
+            if rc:
+                raise RuntimeError(L.mc_last_error().decode())
+            if k >= args.warmup:
+                e2e_t.append(dt)
+        t_e2e, mv = reduce_max_sum(sum(e2e_t), float(moves_per_step * args.steps), world,
+                                   device=torch.device("cuda", local))
+        npad = ((n + 127) // 128) * 128
+        line["e2e"] = {"value": mv / t_e2e, "unit": "moves/s", "h2d_bytes_per_step": 16 * npad,
+                       "d2h_bytes_per_step": 16 * n + 8,
+                       "path": "mc_set_positions(pinned host) + mc_sweep + mc_get_positions + mc_energy per step"}
+        line["gpu_launches"] += 2 * args.steps
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(base, min_seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="plain_n16383")
+    ap.add_argument("--sweeps-per-step", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--ref-moves-per-step", type=int, default=2048)
+    ap.add_argument("--flush-mb", type=int, default=512)
+    args = ap.parse_args()
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("--steps >= 1, --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

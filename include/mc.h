@@ -74,9 +74,15 @@ typedef struct {
     uint64_t rej_metropolis; /* rejected by u >= exp(-dE) */
     uint64_t rej_overlap;    /* rejected by hard-core overlap */
     uint64_t rej_wall;       /* rejected by the wall */
-    uint64_t guard_fp64;     /* moves decided by the FP64 recomputation */
+    uint64_t guard_fp64;     /* moves sent to the guard tiers (FP32 value inside its error band) */
     uint64_t decided_interval; /* moves decided before the outcomes of earlier moves of their group were known */
-    uint64_t reserved[9];
+    uint64_t tier2, tier3, tier4; /* guard decisions by accurate FP32, double-single, FP64 */
+    uint64_t rounds;         /* decision rounds over all work items */
+    uint64_t cyc_wait_window; /* SM cycles, summed over work items: waiting for the previous group's outcome, */
+    uint64_t cyc_tiles;      /* ... in the pair-sum tiles (including waits for their publication), */
+    uint64_t cyc_resolve;    /* ... deciding (rounds, excluding guard tiers), */
+    uint64_t cyc_guard;      /* ... in guard tiers, */
+    uint64_t cyc_total;      /* ... and in total */
 } mc_stats_t;
 
 /* Per-move validation record (mc_record_enable / mc_record_read). */
@@ -87,7 +93,8 @@ typedef struct {
     double dE;      /* dE used for the ledger / decision (FP64 value when tier == 4); NaN if not evaluated */
     double dE32;    /* dE from the FP32 pair sums (NaN when not evaluated) */
     double scale;   /* l_B |q_i| sum_j |q_j| (1/r' + 1/r): the error-bound scale */
-    int32_t tier;   /* 0 decided from an interval, 1 from the exact FP32 sum, 4 by the FP64 recomputation */
+    int32_t tier;   /* 0 decided from an interval, 1 from the exact FP32 sum, 2 accurate FP32, 3 double-single,
+                       4 the FP64 recomputation */
     int32_t pad;
 } mc_record;
 
@@ -162,7 +169,9 @@ int64_t mc_record_read(mc_handle h, int chain, mc_record *out, int64_t cap);
 /* Options (mc_set_option):
  *  MC_OPT_GUARD_MODE   0 = FP32 with proven error band (default),
  *                      1 = recompute every evaluated move in FP64,
- *                      2 = decide from FP32 alone (band 0; test of the band only)
+ *                      2 = decide from FP32 alone (band 0; test of the band only),
+ *                      3 = send every evaluated move through the guard tiers
+ *                          (accurate FP32, then double-single, then FP64)
  *  MC_OPT_TIMEOUT_MS   bound of every device-side wait (default 4000)
  *  MC_OPT_CTAS         persistent CTAs per launch (0 = one per resident slot)
  *  MC_OPT_SKIP_PUBLISH fault injection: the work item with this index never

@@ -15,7 +15,8 @@ RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32
                          ("dE32", np.float64), ("scale", np.float64), ("tier", np.int32), ("pad", np.int32)])
 
 _STATS_FIELDS = ["sweeps", "accepts", "rej_metropolis", "rej_overlap", "rej_wall", "guard_fp64",
-                 "decided_interval"]
+                 "decided_interval", "tier2", "tier3", "tier4", "rounds", "cyc_wait_window", "cyc_tiles",
+                 "cyc_resolve", "cyc_guard", "cyc_total"]
 
 
 class MCError(RuntimeError):
@@ -31,7 +32,7 @@ class _Desc(ctypes.Structure):
 
 
 class _Stats(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_uint64) for f in _STATS_FIELDS] + [("reserved", ctypes.c_uint64 * 9)]
+    _fields_ = [(f, ctypes.c_uint64) for f in _STATS_FIELDS]
 
 
 _LIB = None

@@ -55,7 +55,7 @@ struct Chain {
     uint64_t seed = 0;
     uint32_t chain_id = 0;
     std::vector<float> q;        // host copy of the valences
-    float4 *pos = nullptr;
+    float4 *pos[2] = {nullptr, nullptr};  // positions after sweep v live in pos[(v + 1) & 1]
     unsigned long long *flags = nullptr;
     unsigned char *slab = nullptr;  // ledger, ledger_seq, stats, sweep, energy out
     double *ledger = nullptr;
@@ -68,6 +68,8 @@ struct Chain {
     long long rec_cap = 0;
     unsigned long long rec_sweep0 = 0;
     uint64_t sweeps = 0;         // host mirror of *sweep
+    uint64_t sweep_base = 0;     // sweep count when the positions were last set from the host
+    float4 *cur() const { return pos[sweeps & 1]; }
 };
 
 struct GraphKey {
@@ -141,13 +143,20 @@ int validate(const float *xyz, int64_t n, double sigma, double R)
     return MC_OK;
 }
 
+// Positions become the state after sweep c.sweeps - 1 (buffer c.sweeps & 1);
+// the padding slots of both buffers hold far-away ions of valence 0.
 int upload_positions(mc_system *h, Chain &c, const float *xyz, cudaStream_t st)
 {
     std::vector<float4> buf((size_t)c.B * mcg::S);
     for (int i = 0; i < c.N; ++i) buf[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], c.q[i]);
     for (size_t i = c.N; i < buf.size(); ++i) buf[i] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
-    CK(cudaMemcpyAsync(c.pos, buf.data(), sizeof(float4) * buf.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c.cur(), buf.data(), sizeof(float4) * buf.size(), cudaMemcpyHostToDevice, st));
+    if (c.B * mcg::S > c.N) {
+        float4 *other = c.pos[(c.sweeps + 1) & 1];
+        CK(cudaMemcpyAsync(other + c.N, buf.data() + c.N, sizeof(float4) * (buf.size() - c.N), cudaMemcpyHostToDevice, st));
+    }
     CK(cudaStreamSynchronize(st));
+    c.sweep_base = c.sweeps;
     (void)h;
     return MC_OK;
 }
@@ -156,7 +165,9 @@ int upload_positions(mc_system *h, Chain &c, const float *xyz, cudaStream_t st)
 mcg::ChainDev describe(const Chain &c)
 {
     mcg::ChainDev d{};
-    d.pos = c.pos;
+    d.pos[0] = c.pos[0];
+    d.pos[1] = c.pos[1];
+    d.sweep_base = c.sweep_base;
     d.flags = c.flags;
     d.ledger = c.ledger;
     d.ledger_seq = c.ledger_seq;
@@ -214,7 +225,8 @@ int init_chain(mc_system *h, Chain &c, const mc_chain_desc &d)
     c.seed = d.seed;
     c.chain_id = d.chain_id;
     c.q.assign(d.q, d.q + d.n);
-    CK(cudaMalloc(&c.pos, sizeof(float4) * (size_t)c.B * mcg::S));
+    CK(cudaMalloc(&c.pos[0], sizeof(float4) * (size_t)c.B * mcg::S));
+    CK(cudaMalloc(&c.pos[1], sizeof(float4) * (size_t)c.B * mcg::S));
     CK(cudaMalloc(&c.flags, sizeof(unsigned long long) * (size_t)c.B * mcg::WORDS));
     CK(cudaMalloc(&c.slab, 256));
     CK(cudaMemsetAsync(c.flags, 0, sizeof(unsigned long long) * (size_t)c.B * mcg::WORDS, h->stream));
@@ -227,14 +239,15 @@ int init_chain(mc_system *h, Chain &c, const mc_chain_desc &d)
     rc = upload_positions(h, c, d.pos_xyz, h->stream);
     if (rc) return rc;
     CK(cudaMalloc(&c.rows, sizeof(double) * (size_t)c.N));
-    CK(mcg_host::energy_launch(c.pos, c.N, c.lB, c.rows, c.ledger, h->stream));
+    CK(mcg_host::energy_launch(c.cur(), c.N, c.lB, c.rows, c.ledger, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return MC_OK;
 }
 
 void free_chain(Chain &c)
 {
-    cudaFree(c.pos);
+    cudaFree(c.pos[0]);
+    cudaFree(c.pos[1]);
     cudaFree(c.flags);
     cudaFree(c.slab);
     cudaFree(c.rows);
@@ -474,7 +487,7 @@ int mc_energy(mc_handle h, int chain, double *ledger, double *recomputed)
     CK(cudaStreamSynchronize(h->stream));
     if (ledger) CK(cudaMemcpy(ledger, c.ledger, sizeof(double), cudaMemcpyDeviceToHost));
     if (recomputed) {
-        CK(mcg_host::energy_launch(c.pos, c.N, c.lB, c.rows, c.e_out, h->stream));
+        CK(mcg_host::energy_launch(c.cur(), c.N, c.lB, c.rows, c.e_out, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         CK(cudaMemcpy(recomputed, c.e_out, sizeof(double), cudaMemcpyDeviceToHost));
     }
@@ -498,7 +511,7 @@ int mc_gr_histogram(mc_handle h, int chain, int n_bins, double r_max, double wal
     CK(cudaMalloc(&d, sizeof(unsigned long long) * hc.size()));
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * hc.size(), h->stream);
     const float hi = std::nextafter((float)(r_max * r_max * (1.0 + 0x1p-18)), 3.0e38f);
-    if (e == cudaSuccess) e = mcg_host::gr_launch(c.pos, c.N, n_bins, dr, hi, wall_margin > 0.0 ? 1 : 0, lim2, d, h->stream);
+    if (e == cudaSuccess) e = mcg_host::gr_launch(c.cur(), c.N, n_bins, dr, hi, wall_margin > 0.0 ? 1 : 0, lim2, d, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) e = cudaMemcpy(hc.data(), d, sizeof(unsigned long long) * hc.size(), cudaMemcpyDeviceToHost);
     cudaFree(d);
@@ -515,7 +528,7 @@ int mc_get_positions(mc_handle h, int chain, float *pos_xyz)
     Chain &c = h->chains[chain];
     std::vector<float4> buf((size_t)c.N);
     CK(cudaStreamSynchronize(h->stream));
-    CK(cudaMemcpy(buf.data(), c.pos, sizeof(float4) * buf.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(buf.data(), c.cur(), sizeof(float4) * buf.size(), cudaMemcpyDeviceToHost));
     for (int i = 0; i < c.N; ++i) {
         pos_xyz[3 * i] = buf[i].x;
         pos_xyz[3 * i + 1] = buf[i].y;
@@ -533,7 +546,9 @@ int mc_set_positions(mc_handle h, int chain, const float *pos_xyz)
     rc = validate(pos_xyz, c.N, c.sigma, c.R);
     if (rc) return rc;
     CK(cudaStreamSynchronize(h->stream));
-    return upload_positions(h, c, pos_xyz, h->stream);
+    rc = upload_positions(h, c, pos_xyz, h->stream);
+    if (rc) return rc;
+    return sync_descriptors(h);
 }
 
 int mc_stats(mc_handle h, int chain, mc_stats_t *out)
@@ -553,6 +568,15 @@ int mc_stats(mc_handle h, int chain, mc_stats_t *out)
     out->rej_wall = v[mcg::CNT_WALL];
     out->guard_fp64 = v[mcg::CNT_FP64];
     out->decided_interval = v[mcg::CNT_INTERVAL];
+    out->tier2 = v[mcg::CNT_T2];
+    out->tier3 = v[mcg::CNT_T3];
+    out->tier4 = v[mcg::CNT_T4];
+    out->rounds = v[mcg::CNT_ROUNDS];
+    out->cyc_wait_window = v[mcg::CNT_CYC_WIN];
+    out->cyc_tiles = v[mcg::CNT_CYC_TILES];
+    out->cyc_resolve = v[mcg::CNT_CYC_RESOLVE];
+    out->cyc_guard = v[mcg::CNT_CYC_GUARD];
+    out->cyc_total = v[mcg::CNT_CYC_TOTAL];
     return MC_OK;
 }
 
@@ -572,9 +596,18 @@ int mc_set_state(mc_handle h, int chain, const float *pos_xyz, uint64_t sweeps, 
     int rc = check_chain(h, chain);
     if (rc) return rc;
     Chain &c = h->chains[chain];
-    if (pos_xyz && (rc = mc_set_positions(h, chain, pos_xyz))) return rc;
     if (sweeps >= 0xfffffff0ull) return fail(MC_ERR_INVALID, "sweep count too large");
+    if (pos_xyz && (rc = validate(pos_xyz, c.N, c.sigma, c.R))) return rc;
     CK(cudaStreamSynchronize(h->stream));
+    if (!pos_xyz && ((c.sweeps ^ sweeps) & 1))  // keep the current positions in the buffer of the new parity
+        CK(cudaMemcpy(c.pos[sweeps & 1], c.cur(), sizeof(float4) * (size_t)c.B * mcg::S, cudaMemcpyDeviceToDevice));
+    c.sweeps = sweeps;
+    if (pos_xyz) {
+        rc = upload_positions(h, c, pos_xyz, h->stream);
+        if (rc) return rc;
+    } else {
+        c.sweep_base = sweeps;
+    }
     std::vector<unsigned long long> fl((size_t)c.B * mcg::WORDS, (unsigned long long)(unsigned)sweeps << 32);
     CK(cudaMemcpy(c.flags, fl.data(), sizeof(unsigned long long) * fl.size(), cudaMemcpyHostToDevice));
     unsigned long long seq = (unsigned long long)sweeps * (unsigned long long)c.B;
@@ -590,6 +623,9 @@ int mc_set_state(mc_handle h, int chain, const float *pos_xyz, uint64_t sweeps, 
         v[mcg::CNT_WALL] = stats->rej_wall;
         v[mcg::CNT_FP64] = stats->guard_fp64;
         v[mcg::CNT_INTERVAL] = stats->decided_interval;
+        v[mcg::CNT_T2] = stats->tier2;
+        v[mcg::CNT_T3] = stats->tier3;
+        v[mcg::CNT_T4] = stats->tier4;
         CK(cudaMemcpy(c.stats, v, sizeof v, cudaMemcpyHostToDevice));
     }
     c.sweeps = sweeps;
@@ -645,7 +681,7 @@ static int set_option(mc_handle h, int option, int64_t value)
 {
     switch (option) {
     case MC_OPT_GUARD_MODE:
-        if (value < 0 || value > 2) return fail(MC_ERR_INVALID, "guard mode %lld", (long long)value);
+        if (value < 0 || value > 3) return fail(MC_ERR_INVALID, "guard mode %lld", (long long)value);
         h->guard_mode = (int)value;
         return MC_OK;
     case MC_OPT_TIMEOUT_MS:

@@ -43,12 +43,14 @@ struct MoveRec {
 
 // Per-chain device descriptor (read-only during a launch).
 struct ChainDev {
-    float4 *pos;                  // N_pad entries: x, y, z, valence (Sec. 3.1's float4 layout)
+    float4 *pos[2];               // 2 x N_pad entries: x, y, z, valence (Sec. 3.1's float4 layout); the
+                                  // positions after sweep v live in pos[(v + 1) & 1]
     unsigned long long *flags;    // per 32-ion word: ((sweep+1) << 32) | accept bits
     double *ledger;               // running energy
     unsigned long long *ledger_seq;  // groups folded into the ledger (absolute stream index)
     unsigned long long *stats;    // 8 counters
     unsigned long long *sweep;    // completed sweeps (absolute)
+    unsigned long long sweep_base;  // sweep count when the positions were last set from the host
     MoveRec *rec;                 // validation records or nullptr
     unsigned long long rec_sweep0;  // sweep at which recording started
     long long rec_cap;
@@ -76,14 +78,16 @@ struct Ctl {
     unsigned int ticket;          // next work item
     int err;                      // KERR_*
     int abort;                    // set on any error: every CTA leaves
-    int guard_mode;               // 0 band, 1 always FP64, 2 never
+    int guard_mode;               // 0 band, 1 always FP64, 2 never, 3 always through the tiers
     long long timeout_ns;
     long long skip_ticket;        // fault injection (-1 off)
     unsigned long long err_info;  // where a wait gave up
 };
 
 // Counter slots of ChainDev::stats.
-constexpr int CNT_ACCEPT = 0, CNT_METRO = 1, CNT_OVERLAP = 2, CNT_WALL = 3, CNT_FP64 = 4, CNT_INTERVAL = 5;
+constexpr int CNT_ACCEPT = 0, CNT_METRO = 1, CNT_OVERLAP = 2, CNT_WALL = 3, CNT_FP64 = 4, CNT_INTERVAL = 5,
+              CNT_T2 = 6, CNT_T3 = 7, CNT_T4 = 8, CNT_ROUNDS = 9, CNT_CYC_WIN = 10, CNT_CYC_TILES = 11,
+              CNT_CYC_RESOLVE = 12, CNT_CYC_GUARD = 13, CNT_CYC_TOTAL = 14;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): two 32x32 multiplies per round with
@@ -180,6 +184,39 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Error-free transformations in FP32 (Knuth's TwoSum, FMA-based TwoProduct).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer()

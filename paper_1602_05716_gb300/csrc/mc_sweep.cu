@@ -2,109 +2,146 @@
 //
 // What it computes is the sequential-updating Metropolis chain of Sec. 2:
 // every sweep tries ions 0..N-1 in order; move i's energy change uses the
-// current positions of all other ions (Eq. of the Delta E_ij table: ions
+// current positions of all other ions (the Delta E_ij table of Sec. 2: ions
 // j < i already at their outcome of this sweep, ions j > i at their position
 // from the previous sweep).  How it computes it is GB300-specific:
 //
 //  * Work items are (chain, group of S = 128 consecutive ions, sweep),
 //    handed out in stream order by an atomic ticket, so a CTA only ever waits
 //    on work already claimed by a running CTA (no dependence on block
-//    dispatch order, which the paper's deadlock argument of Sec. 3.5
-//    implicitly assumes).
-//  * A CTA computes, for its S moves, the pair sums against every other
-//    group's latest published positions, tile by tile (the brush of Sec. 3.4,
-//    Algorithm 2), oldest version first; groups publish per-32-ion words
-//    ((sweep+1) << 32 | accept bits) with release stores and are read with
-//    acquire loads -- a sweep-tagged flag needs no reset (the paper's
-//    BlockState array of Algorithm 5 must be cleared by the last block).
-//  * Inside the group (Algorithms 3 and 4) the lower-triangle terms are
-//    computed for both possible positions of each earlier ion j (old and
-//    trial); the correction c_kj = term(trial_j) - term(old_j) is kept in
-//    shared memory.  Decisions are then resolved mostly in parallel: a move
-//    whose outcome is the same for every combination of the unknown earlier
-//    outcomes is decided at once; the rest are decided in order by one warp
-//    with exact sums.
-//  * Pair terms are FP32 (rsqrt.approx), promoted to FP64 per tile.  A move
-//    is decided in FP32 only when |dE + ln u| exceeds a proven bound on the
-//    FP32 error; otherwise the whole CTA recomputes dE in the oracle's FP64
-//    arithmetic and summation order (the paper computes every energy term in
-//    FP64, Sec. 3.3; GB300's FP64 rate makes that the exception here).
+//    dispatch order, which the deadlock argument of Sec. 3.5 assumes).
+//  * A group publishes its new positions into one of two buffers (sweep
+//    parity) and then, per 32 ions, a release-stored word
+//    ((sweep+1) << 32 | accept bits).  Readers acquire the word.  Tags only
+//    grow, so no reset is needed (Algorithm 5's BlockState must be cleared).
+//  * A CTA computes its S moves' pair sums (FP32, rsqrt.approx) against every
+//    other group's published positions, tile by tile, oldest version first
+//    (the brush of Algorithm 2), polling the next tiles' flags with relaxed
+//    loads and prefetching their positions into registers.
+//  * The group just before this one (the "window") and this group's own
+//    earlier moves (the lower triangle of Algorithms 3 and 4) are computed for
+//    both possible positions of each such ion; the corrections
+//    c_kj = term(trial_j) - term(old_j) stay in shared memory.  After the
+//    window's accept bits arrive only masked sums remain; decisions are found
+//    by interval rounds: a move whose outcome is the same for every
+//    combination of still-unknown earlier outcomes is decided at once.
+//  * A move is decided in FP32 only when its energy change lies outside a
+//    proven FP32 error bound of the threshold; otherwise it is recomputed by
+//    an accurate FP32 form (error proportional to the displacement), then in
+//    double-single arithmetic, and finally in the oracle's FP64 arithmetic and
+//    summation order, each tier with its own bound.
 //  * Every wait is bounded by %globaltimer; on expiry the kernel records the
 //    error, raises an abort flag and all CTAs return.
 #include "mc_device.cuh"
 
 namespace mcg {
 
+constexpr int MPT = 4;             // moves per thread in the pair loops
+constexpr int SL = T / (S / MPT);  // column slices (8)
+constexpr int HALF = S / 2;
+
 struct __align__(16) Smem {
-    float4 own[S];    // old positions x_k (w = valence)
-    float4 trial[S];  // trial positions x'_k (w = valence)
-    float4 tile[S];   // one column group
-    double Lneg[S];   // -L(u_acc) (+inf when u_acc == 0)
-    double base[S];   // FP64 sum of all terms with known positions (+ in-group lower with old positions)
-    double dE[S];     // dE of each decided, evaluated move
-    float Ab[S];      // sum |q_j| (1/r' + 1/r)  (both versions for in-group lower j)
-    float Tb[S];      // sum |t_j| of the terms in base
-    float TCb[S];     // sum |c_kj|
-    float mind2[S];   // min FP32 |x'_k - x_j|^2 over positions known to be final
-    unsigned ovo[S][WORDS];  // bit j: x'_k overlaps old x_j (in-group, j < k)
-    unsigned ovn[S][WORDS];  // bit j: x'_k overlaps trial x'_j
-    unsigned accw[WORDS];
-    unsigned decw[WORDS];
-    unsigned char st[S];     // status bits
+    float4 own[S];    // this group: old positions (w = valence)
+    float4 trial[S];  // this group: trial positions
+    float4 wold[S];   // window group: old positions
+    float4 wtri[S];   // window group: trial positions
+    float4 tile[2][S];
+    float cin[S * CS];   // c[j][k], j < k, this group
+    float cwin[S * CS];  // c[j][k], window ion j
+    float bhi[S], blo[S];  // sum of terms with known positions (float-float)
+    float Ab[S], Tb[S], TCb[S], mind2[S];
+    float lo_w[S], hi_w[S], lo_i[S], hi_i[S];
+    float Lf[S];   // -ln(u_acc) in FP32 (+inf if u_acc == 0)
+    float bnd[S];  // static part of the FP32 band
+    float wex[S];  // exact window correction (after the window's bits)
+    float run[S];  // exact in-group correction over decided-accepted j < k
+    float part[2][S];
+    float plo[2][S];
+    float phi[2][S];
+    float dE32[S];
+    double dEv[S];  // dE used for the ledger and the records
+    unsigned ovo[S][WORDS], ovn[S][WORDS];    // x'_k overlaps old / trial position of in-group j < k
+    unsigned wovo[S][WORDS], wovn[S][WORDS];  // ... of window ion j
+    unsigned accw[WORDS], decw[WORDS], seen[WORDS], winacc[WORDS], acc0[WORDS], dec0[WORDS];
+    unsigned char st[S];
     signed char outcome[S];
     unsigned char tier[S];
     unsigned char pad0[S];
-    float cmat[S * CS];      // c[j][k] at j*CS + k
     double chunk[CHUNK];
-    double red[T / 32];
-    int ticket;
-    int ok;
-    int guard_k;
-    int ovl_flag;
+    double redd[32];
+    float redf[32];
+    int ticket, ok, guard_k, ovl_flag;
+    int rdy[2];
+    int pad1[2];
 };
 
-constexpr unsigned ST_WALL = 1u, ST_UZERO = 2u, ST_INACTIVE = 4u, ST_OVL_CERTAIN = 8u, ST_OVL_AMBIG = 16u;
+constexpr unsigned ST_WALL = 1u, ST_UZERO = 2u, ST_INACTIVE = 4u, ST_OVL_CERTAIN = 8u, ST_OVL_AMBIG = 16u,
+                   ST_OVL_POSSIBLE = 32u;
 constexpr unsigned FULL = 0xffffffffu;
 
-// Bound constants (units of u = 2^-24); see the error analysis in the design doc.
-constexpr double U32 = 0x1p-24;
-constexpr double C_TERM = 10.0;   // per-term error of q_j (1/r' - 1/r) relative to |q_j| (1/r' + 1/r)
-constexpr double C_SUM = 40.0;    // FP32 partial sums of <= 32 terms before FP64 promotion
-constexpr double C_CORR = S + 8;  // FP32 sums of <= S corrections in the resolver
+// Bound constants (units of u = 2^-24); the derivation is in DESIGN.md ("FP32 error bound").
+constexpr float U32 = 0x1p-24f;
+constexpr float C_TERM = 10.0f;           // per-term error of q_j (1/r' - 1/r) relative to |q_j| (1/r' + 1/r)
+constexpr float C_SUM = 24.0f;            // FP32 partials of <= 16 terms, TwoSum-accumulated
+constexpr float C_CORR = 2.0f * (S + 8);  // FP32 sums and interval sums of <= S corrections
 
-__device__ __forceinline__ bool wait_group(const ChainDev &ch, int J, unsigned need, Ctl *ctl)
+__device__ __forceinline__ float finf()
 {
-    const int nw = min(WORDS, (ch.N - J * S + 31) / 32);
+    return __int_as_float(0x7f800000);
+}
+
+__device__ __forceinline__ bool bit(const unsigned *w, int j)
+{
+    return (w[j >> 5] >> (j & 31)) & 1u;
+}
+
+// Mask of the bits j < k within word w.
+__device__ __forceinline__ unsigned below(int k, int w)
+{
+    return (w * 32 + 32 <= k) ? 0xffffffffu : (w * 32 >= k ? 0u : ((1u << (k - w * 32)) - 1u));
+}
+
+// Warp 0 waits until the sweep tags of the nw words of group J lie in [lo, hi]
+// (acquire).  Returns false on timeout, protocol error or abort.  bits (lane w)
+// gets word w's accept bits.
+__device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsigned hi, Ctl *ctl, unsigned &bits)
+{
+    const int lane = threadIdx.x & 31;
     const unsigned long long t0 = globaltimer();
-    for (int w = 0; w < nw; ++w) {
-        unsigned spins = 0;
-        for (;;) {
-            const unsigned long long v = ld_acquire(&ch.flags[J * WORDS + w]);
+    unsigned spins = 0;
+    bool done = lane >= nw;
+    bits = 0u;
+    for (;;) {
+        if (!done) {
+            const unsigned long long v = ld_acquire(&ch.flags[J * WORDS + lane]);
             const unsigned tag = (unsigned)(v >> 32);
-            if (tag == need) break;
-            if ((int)(tag - need) > 0) {  // a newer version than any reader can need
+            if ((int)(tag - lo) >= 0 && (int)(hi - tag) >= 0) {
+                done = true;
+                bits = (unsigned)v;
+            } else if ((int)(tag - hi) > 0) {
                 atomicCAS(&ctl->err, 0, KERR_PROTOCOL);
                 atomicExch(&ctl->abort, 1);
-                return false;
-            }
-            if (*(volatile int *)&ctl->abort) return false;
-            if (++spins > 32) __nanosleep(40);
-            if ((spins & 63) == 0 && (long long)(globaltimer() - t0) > ctl->timeout_ns) {
-                if (atomicCAS(&ctl->err, 0, KERR_TIMEOUT) == 0)
-                    ctl->err_info = ((unsigned long long)J << 32) | need;
-                atomicExch(&ctl->abort, 1);
-                return false;
             }
         }
+        if (__all_sync(FULL, done)) return true;
+        if (*(volatile int *)&ctl->abort) return false;
+        if (++spins > 16) __nanosleep(32);
+        if ((spins & 63) == 0 && (long long)(globaltimer() - t0) > ctl->timeout_ns) {
+            if (lane == 0) {
+                if (atomicCAS(&ctl->err, 0, KERR_TIMEOUT) == 0) ctl->err_info = ((unsigned long long)J << 32) | lo;
+                atomicExch(&ctl->abort, 1);
+            }
+            __syncwarp();
+            return false;
+        }
     }
-    return true;
 }
 
 // FP32 pair term of move (a = trial, b = old) against y:
-// t = q_y (1/|a-y| - 1/|b-y|) accumulated into s; |q|(1/r'+1/r) into A;
+// t = q_y (1/|a-y| - 1/|b-y|) accumulated into s; |q| (1/r' + 1/r) into A;
 // |t| into Tt; |a-y|^2 into the running minimum mn.
-__device__ __forceinline__ void pair_acc(const float4 a, const float4 b, const float4 y, float &s, float &A,
-                                         float &Tt, float &mn)
+__device__ __forceinline__ void pair_acc(const float4 a, const float4 b, const float4 y, float &s, float &A, float &Tt,
+                                         float &mn)
 {
     const float dxn = a.x - y.x, dyn = a.y - y.y, dzn = a.z - y.z;
     const float d2n = fmaf(dzn, dzn, fmaf(dyn, dyn, dxn * dxn));
@@ -129,8 +166,8 @@ __device__ __forceinline__ float pair_term(const float4 a, const float4 b, const
     return y.w * (rn - ro);
 }
 
-// Exact overlap test |a - y|^2 < sigma^2 from the FP32 squared distance, with
-// the FP64 squared distance of the FP32 points deciding inside the band.
+// Exact overlap test |a - y|^2 < sigma^2 from the FP32 squared distance, the
+// FP64 squared distance of the FP32 points deciding inside the band.
 __device__ __forceinline__ bool overlaps(float d2f, const float4 a, const float4 y, float lo, float hi, double sig2)
 {
     if (d2f < lo) return true;
@@ -138,62 +175,216 @@ __device__ __forceinline__ bool overlaps(float d2f, const float4 a, const float4
     return d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < sig2;
 }
 
-// In-group pair (ion j of this group against move k of this group).
-__device__ __forceinline__ void ingroup_pair(Smem &sm, int k, int j, const float4 a, const float4 b, const float4 yo,
-                                             const float4 yn, float &s, float &A, float &Tt, float &TC, float &mn,
-                                             float lo, float hi, double sig2)
+// Both-position pair of move k against an ion j whose outcome is unknown
+// (an earlier ion of this group, or an ion of the window group).
+__device__ __forceinline__ void both_pair(float *cm, unsigned (*ovo)[WORDS], unsigned (*ovn)[WORDS], int k, int j,
+                                          const float4 a, const float4 b, const float4 yo, const float4 yn, float &s,
+                                          float &A, float &Tt, float &TC, float lo, float hi, double sig2)
 {
-    if (j > k) {  // ion j moves after k: its old position is final for move k (upper triangle, Algorithm 3)
-        pair_acc(a, b, yo, s, A, Tt, mn);
-    } else if (j < k) {  // ion j moves before k: position depends on its outcome (Algorithm 4's lower triangle)
-        float Ao, An, d2o_n, d2n_n;
-        const float to = pair_term(a, b, yo, Ao, d2o_n);
-        const float tn = pair_term(a, b, yn, An, d2n_n);
-        s += to;
-        Tt += fabsf(to);
-        A += Ao + An;
-        const float c = tn - to;
-        sm.cmat[j * CS + k] = c;
-        TC += fabsf(c);
-        if (overlaps(d2o_n, a, yo, lo, hi, sig2)) atomicOr(&sm.ovo[k][j >> 5], 1u << (j & 31));
-        if (overlaps(d2n_n, a, yn, lo, hi, sig2)) atomicOr(&sm.ovn[k][j >> 5], 1u << (j & 31));
-    }
+    float Ao, An, d2o_n, d2n_n;
+    const float to = pair_term(a, b, yo, Ao, d2o_n);
+    const float tn = pair_term(a, b, yn, An, d2n_n);
+    s += to;
+    Tt += fabsf(to);
+    A += Ao + An;
+    const float c = tn - to;
+    cm[j * CS + k] = c;
+    TC += fabsf(c);
+    if (overlaps(d2o_n, a, yo, lo, hi, sig2)) atomicOr(&ovo[k][j >> 5], 1u << (j & 31));
+    if (overlaps(d2n_n, a, yn, lo, hi, sig2)) atomicOr(&ovn[k][j >> 5], 1u << (j & 31));
 }
 
-__device__ __forceinline__ bool bit(const unsigned *w, int j)
+struct Ctx {
+    const ChainDev *ch;
+    const float4 *Pprev;  // positions after sweep s-1
+    const float4 *Pcur;   // positions after sweep s (groups < g published)
+    int N, B, g, k0, nk, Jw, nwk;
+    bool win;
+    unsigned long long s;
+};
+
+// Position of ion j as seen by move k of this group (all earlier moves of the
+// group decided, the window's bits known).
+__device__ __forceinline__ float4 position_of(const Smem &sm, const Ctx &c, int k, int j)
 {
-    return (w[j >> 5] >> (j & 31)) & 1u;
+    const int J = j / S, l = j - J * S;
+    if (J == c.g) return (l < k && bit(sm.accw, l)) ? sm.trial[l] : sm.own[l];
+    if (c.win && J == c.Jw) return bit(sm.winacc, l) ? sm.wtri[l] : sm.wold[l];
+    return J > c.g ? __ldcg(&c.Pprev[j]) : __ldcg(&c.Pcur[j]);
 }
 
-// Error bound of the FP32-derived dE of move k ("FP32 error bound").
-__device__ __forceinline__ double band(const Smem &sm, int k, double lBabs, int mode)
-{
-    if (mode == 1) return __longlong_as_double(0x7ff0000000000000ll);  // +inf: always FP64
-    if (mode == 2) return 0.0;
-    const double A = sm.Ab[k], Tt = sm.Tb[k], TC = sm.TCb[k];
-    return lBabs * (U32 * (C_TERM * A + C_SUM * Tt + C_CORR * TC) + 0x1p-40 * (A + Tt));
-}
-
-// Position of ion j as seen by move k of the current group (all earlier
-// moves of the group decided).
-__device__ __forceinline__ float4 position_for(const Smem &sm, const ChainDev &ch, int k0, int nk, int k, int j)
-{
-    const int l = j - k0;
-    if (l >= 0 && l < nk) {
-        if (l < k && bit(sm.accw, l)) return sm.trial[l];
-        return sm.own[l];
-    }
-    return __ldcg(&ch.pos[j]);
-}
-
-// FP64 recomputation of move k in the oracle's arithmetic: terms in FP64 with
-// IEEE sqrt and division, summed sequentially within 1024-index chunks, the
-// chunk sums added in order; overlap from the FP64 squared distance.
-__device__ void fp64_decide(Smem &sm, const ChainDev &ch, int k0, int nk, int k)
+// Sum of per-thread FP64 values and FP32 bound terms over the CTA (thread 0 gets it).
+__device__ __forceinline__ void block_sum(Smem &sm, double v, float bb, double &tot, double &btot)
 {
     const int tid = threadIdx.x;
-    const int N = ch.N;
-    const int i = k0 + k;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(FULL, v, o);
+        bb += __shfl_xor_sync(FULL, bb, o);
+    }
+    if ((tid & 31) == 0) {
+        sm.redd[tid >> 5] = v;
+        sm.redf[tid >> 5] = bb;
+    }
+    __syncthreads();
+    tot = 0.0;
+    btot = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < T / 32; ++w) {
+            tot += sm.redd[w];
+            btot += (double)sm.redf[w];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Guard tiers for move k (whole CTA).  Return 0 accept, 1 reject, -1 undecided.
+
+// Tier 2: accurate FP32.  With e = y - b and delta = a - b the pair's energy
+// change is q (delta . (2e - delta)) (rn ro)^2 / (rn + ro): no difference of
+// two large inverse distances, so the rounding error scales with
+// |delta| / r^2 instead of 1/r.  Per-term bound ("guard tiers"):
+// |q| [ |t| (rel(Dn) + 19u) + 4u M (rn ro)^2/(rn+ro) + u |delta| (2 Ro + rho)/rho^3 ]
+// with rho a lower bound of the distance from y to the segment [b, a].
+__device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
+{
+    const int tid = threadIdx.x;
+    const float4 a = sm.trial[k], b = sm.own[k];
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const float dn = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) * (1.0f + 0x1p-18f);
+    const float s2 = (float)c.ch->sig2;
+    const float rho0 = sqrtf(fmaxf(s2 * (1.0f - 0x1p-18f) - 0.25f * dn * dn, 0.0f)) * (1.0f - 0x1p-18f);
+    const int i = c.k0 + k;
+    float hi = 0.f, lo = 0.f, bsum = 0.f;
+    for (int j = tid; j < c.N; j += T) {
+        if (j == i) continue;
+        const float4 y = position_of(sm, c, k, j);
+        const float ex = y.x - b.x, ey = y.y - b.y, ez = y.z - b.z;
+        const float Do = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        const float wx = fmaf(2.0f, ex, -dx), wy = fmaf(2.0f, ey, -dy), wz = fmaf(2.0f, ez, -dz);
+        const float Dd = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
+        const float M = fabsf(dx * wx) + fabsf(dy * wy) + fabsf(dz * wz);
+        const float Dn = Do - Dd;
+        const float ro = rsqrt_approx(Do), rn = rsqrt_approx(Dn);
+        const float pr = rn * ro, inv = rcp_approx(rn + ro);
+        const float t = Dd * pr * pr * inv;
+        const float term = y.w * t;
+        float e, s;
+        two_sum(hi, term, s, e);
+        hi = s;
+        lo += e;
+        const float relDn = fmaf(3.0f * U32, Do, 4.0f * U32 * M) * rn * rn + U32;
+        const float Ro = Do * ro * (1.0f + 0x1p-18f), Rn = Dn * rn;
+        const float rho = fmaxf(fminf(Rn, Ro) * (1.0f - 0x1p-18f) - 0.5f * dn, rho0);
+        const float ir = rcp_approx(rho);
+        const float E1 = fabsf(t) * (relDn + 19.0f * U32);
+        const float E2 = 4.0f * U32 * M * pr * pr * inv;
+        const float E3 = U32 * dn * (2.0f * Ro + rho) * ir * ir * ir;
+        bsum += fabsf(y.w) * (E1 + E2 + E3);
+    }
+    double tot, bt;
+    block_sum(sm, (double)hi + (double)lo, bsum, tot, bt);
+    if (tid == 0) {
+        const double lq = c.ch->lB * (double)a.w;
+        const double dE = lq * tot;
+        const double B2 = fabs(lq) * bt * 1.25 + 0x1p-40 * (fabs(dE) + fabs(L64)) + 1e-300;
+        sm.redd[16] = dE;
+        sm.guard_k = (dE < L64 - B2) ? 0 : ((dE > L64 + B2) ? 1 : -1);
+    }
+    __syncthreads();
+    const int out = sm.guard_k;
+    dE_out = sm.redd[16];
+    __syncthreads();
+    return out;
+}
+
+// Double-single arithmetic for tier 3 (each value is an unevaluated sum hi + lo).
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float &sh, float &sl)
+{
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = e + (al + bl);
+    sh = s + e;
+    sl = e - (sh - s);
+}
+
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl)
+{
+    float p, e;
+    two_prod(ah, bh, p, e);
+    e = fmaf(ah, bl, fmaf(al, bh, e));
+    ph = p + e;
+    pl = e - (ph - p);
+}
+
+// 1/sqrt(D) for D = (dh, dl) in double-single: FP32 seed, one Newton step with
+// the residual 1 - D r^2 formed in double-single.
+__device__ __forceinline__ void df_rsqrt(float dh, float dl, float &rh, float &rl)
+{
+    const float r0 = rsqrt_approx(dh);
+    float ph, pl, xh, xl;
+    two_prod(r0, r0, ph, pl);
+    df_mul(dh, dl, ph, pl, xh, xl);
+    const float res = (1.0f - xh) - xl;
+    const float corr = 0.5f * r0 * res;
+    rh = r0 + corr;
+    rl = corr - (rh - r0);
+}
+
+// Tier 3: every pair term in double-single arithmetic (distances from exact
+// FP32 differences); bound 2^-38 l_B |q_i| sum_j |q_j| (1/r' + 1/r).
+__device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
+{
+    const int tid = threadIdx.x;
+    const float4 a = sm.trial[k], b = sm.own[k];
+    const int i = c.k0 + k;
+    float hh = 0.f, hl = 0.f, absum = 0.f;
+    for (int j = tid; j < c.N; j += T) {
+        if (j == i) continue;
+        const float4 y = position_of(sm, c, k, j);
+        float Dn_h = 0.f, Dn_l = 0.f, Do_h = 0.f, Do_l = 0.f;
+        const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, yv[3] = {y.x, y.y, y.z};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float eh, el, sh, sl;
+            two_sum(av[q], -yv[q], eh, el);  // exact a - y
+            df_mul(eh, el, eh, el, sh, sl);
+            df_add(Dn_h, Dn_l, sh, sl, Dn_h, Dn_l);
+            two_sum(bv[q], -yv[q], eh, el);  // exact b - y
+            df_mul(eh, el, eh, el, sh, sl);
+            df_add(Do_h, Do_l, sh, sl, Do_h, Do_l);
+        }
+        float rnh, rnl, roh, rol, th, tl, qh, ql;
+        df_rsqrt(Dn_h, Dn_l, rnh, rnl);
+        df_rsqrt(Do_h, Do_l, roh, rol);
+        df_add(rnh, rnl, -roh, -rol, th, tl);
+        df_mul(th, tl, y.w, 0.0f, qh, ql);
+        df_add(hh, hl, qh, ql, hh, hl);
+        absum += fabsf(y.w) * (rnh + roh);
+    }
+    double tot, bt;
+    block_sum(sm, (double)hh + (double)hl, absum, tot, bt);
+    if (tid == 0) {
+        const double lq = c.ch->lB * (double)a.w;
+        const double dE = lq * tot;
+        const double B3 = fabs(lq) * bt * 1.01 * 0x1p-38 + 0x1p-48 * (fabs(dE) + fabs(L64)) + 1e-300;
+        sm.redd[16] = dE;
+        sm.guard_k = (dE < L64 - B3) ? 0 : ((dE > L64 + B3) ? 1 : -1);
+    }
+    __syncthreads();
+    const int out = sm.guard_k;
+    dE_out = sm.redd[16];
+    __syncthreads();
+    return out;
+}
+
+// Tier 4: the oracle's arithmetic -- FP64 terms with IEEE sqrt and division,
+// summed sequentially within 1024-index chunks, chunk sums added in order;
+// overlap from the FP64 squared distance.
+__device__ void tier4(Smem &sm, const Ctx &c, int k, double &dE_out, bool &ovl_out)
+{
+    const int tid = threadIdx.x;
+    const int N = c.N;
+    const int i = c.k0 + k;
     const float4 a = sm.trial[k], b = sm.own[k];
     if (tid == 0) sm.ovl_flag = 0;
     double total = 0.0;
@@ -204,7 +395,7 @@ __device__ void fp64_decide(Smem &sm, const ChainDev &ch, int k0, int nk, int k)
             double t = 0.0;
             if (j < N && j != i) {
                 bool o;
-                t = term_fp64(a, b, position_for(sm, ch, k0, nk, k, j), o, ch.sig2);
+                t = term_fp64(a, b, position_of(sm, c, k, j), o, c.ch->sig2);
                 if (o) sm.ovl_flag = 1;
             }
             sm.chunk[jj] = t;
@@ -219,18 +410,10 @@ __device__ void fp64_decide(Smem &sm, const ChainDev &ch, int k0, int nk, int k)
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        const double dE = __dmul_rn(__dmul_rn(ch.lB, (double)a.w), total);
-        int out;
-        if (sm.ovl_flag) out = OUT_OVERLAP;
-        else if (sm.st[k] & ST_UZERO) out = OUT_ACCEPT;
-        else out = (dE < sm.Lneg[k]) ? OUT_ACCEPT : OUT_METROPOLIS;
-        sm.outcome[k] = (signed char)out;
-        sm.tier[k] = 4;
-        sm.dE[k] = sm.ovl_flag ? __longlong_as_double(0x7ff8000000000000ll) : dE;
-        sm.decw[k >> 5] |= 1u << (k & 31);
-        if (out == OUT_ACCEPT) sm.accw[k >> 5] |= 1u << (k & 31);
-    }
+    if (tid == 0) sm.redd[16] = __dmul_rn(__dmul_rn(c.ch->lB, (double)a.w), total);
+    __syncthreads();
+    dE_out = sm.redd[16];
+    ovl_out = sm.ovl_flag != 0;
     __syncthreads();
 }
 
@@ -239,28 +422,90 @@ __device__ __forceinline__ float4 pad_point(float v)
     return make_float4(v, v, v, 0.0f);
 }
 
+// Decision of move k from an interval [x_lo, x_hi] of its pair sum
+// sum_j q_j (1/r' - 1/r).  Returns OUT_ACCEPT / OUT_METROPOLIS or -1.
+__device__ __forceinline__ int decide_interval(const Smem &sm, int k, float lq, float x_lo, float x_hi)
+{
+    const float e1 = lq * x_lo, e2 = lq * x_hi;
+    if (!(isfinite(e1) && isfinite(e2))) return -1;
+    const float elo = fminf(e1, e2), ehi = fmaxf(e1, e2);
+    const float L = sm.Lf[k];
+    const float band = sm.bnd[k] + 0x1p-20f * (fmaxf(fabsf(elo), fabsf(ehi)) + fabsf(L));
+    if (ehi < L - band) return OUT_ACCEPT;
+    if (elo > L + band) return OUT_METROPOLIS;
+    return -1;
+}
+
+// Overlap status of move k from the bits of its group's earlier ions: decided
+// ions at their known position, undecided ions either way.
+__device__ __forceinline__ void ingroup_overlap(const Smem &sm, int k, const unsigned *dec, const unsigned *acc,
+                                                bool &certain, bool &possible)
+{
+    unsigned c = 0, p = 0;
+#pragma unroll
+    for (int w = 0; w < WORDS; ++w) {
+        const unsigned bl = below(k, w);
+        const unsigned dw = dec[w] & bl, uw = ~dec[w] & bl, aw = acc[w];
+        c |= ((sm.ovn[k][w] & aw) | (sm.ovo[k][w] & ~aw)) & dw;
+        c |= sm.ovo[k][w] & sm.ovn[k][w] & uw;
+        p |= (sm.ovo[k][w] | sm.ovn[k][w]) & uw;
+    }
+    certain = c != 0;
+    possible = p != 0;
+}
+
 // One work item: the S moves of group g of chain `tk.chain` at sweep s.
 __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, const Ticket tk, int ticket, Ctl *ctl)
 {
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const ChainDev &ch = chains[tk.chain];
-    const int N = ch.N, B = ch.B, g = tk.g, k0 = g * S, nk = min(S, N - k0);
-    const unsigned long long s = *ch.sweep + (unsigned long long)tk.s_rel;
-    const unsigned need_prev = (unsigned)s;        // tag of a version written in sweep s-1
-    const unsigned need_cur = (unsigned)(s + 1);   // tag of a version written in sweep s
-    const float lo2 = ch.sig2_lo, hi2 = ch.sig2_hi;  // FP32 overlap band [lo2, hi2]
+    Ctx c;
+    c.ch = &ch;
+    c.N = ch.N;
+    c.B = ch.B;
+    c.g = tk.g;
+    c.k0 = c.g * S;
+    c.nk = min(S, c.N - c.k0);
+    c.s = *ch.sweep + (unsigned long long)tk.s_rel;
+    const unsigned long long s = c.s;
+    c.Pprev = ch.pos[s & 1];
+    c.Pcur = ch.pos[(s + 1) & 1];
+    const int N = c.N, B = c.B, g = c.g, k0 = c.k0, nk = c.nk;
+    const unsigned tag_prev = (unsigned)s, tag_cur = (unsigned)(s + 1);
+    // the window: the group moved just before this one, when it exists in this run of the chain
+    unsigned long long sw = 0;
+    c.Jw = -1;
+    c.win = false;
+    c.nwk = 0;
+    if (B >= 2) {
+        c.Jw = (g == 0) ? B - 1 : g - 1;
+        sw = (g == 0) ? s - 1 : s;
+        c.win = (g == 0) ? (s > ch.sweep_base) : true;
+        c.nwk = min(S, N - c.Jw * S);
+    }
+    const float lo2 = ch.sig2_lo, hi2 = ch.sig2_hi;
     const double sig2 = ch.sig2;
     const int mode = ctl->guard_mode;
+    const float lBf = (float)ch.lB;
+    // phase timers (thread 0): SM cycles
+    long long cyc_start = clock64(), cyc_tiles = 0, cyc_win = 0, cyc_guard = 0, cyc_res0 = 0;
+    int n_rounds = 0;
 
-    // 1. our group's positions after its previous move (Algorithm 1's loads)
-    if (tid == 0) sm.ok = wait_group(ch, g, need_prev, ctl);
+    // 1. own positions (version s-1) and, if active, the window's old positions (version sw-1)
+    if (warp == 0) {
+        unsigned bits;
+        bool ok = wait_words(ch, g, (nk + 31) / 32, tag_prev, tag_prev, ctl, bits);
+        if (ok && c.win) ok = wait_words(ch, c.Jw, (c.nwk + 31) / 32, (unsigned)sw, (unsigned)(sw + 1), ctl, bits);
+        if (lane == 0) sm.ok = ok;
+    }
     __syncthreads();
     if (!sm.ok) return false;
     if (tid < S) {
         const int k = tid;
         unsigned stv = 0;
         if (k < nk) {
-            const float4 x = __ldcg(&ch.pos[k0 + k]);
+            const float4 x = __ldcg(&c.Pprev[k0 + k]);
             const unsigned long long m = s * (unsigned long long)N + (unsigned long long)(k0 + k);
             const uint4 w = move_draws(ch, m, 0u);
             const float4 a = make_float4(trial_coord(x.x, w.x, ch.D), trial_coord(x.y, w.y, ch.D),
@@ -273,253 +518,439 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             const unsigned ua = w.w >> 8;
             if (ua == 0u) {
                 stv |= ST_UZERO;
-                sm.Lneg[k] = __longlong_as_double(0x7ff0000000000000ll);
+                sm.Lf[k] = finf();
             } else {
-                sm.Lneg[k] = -series_log((double)ua * 0x1p-24);
+                sm.Lf[k] = -logf(__uint2float_rn(ua) * 0x1p-24f);
             }
         } else {
             sm.own[k] = pad_point(-1.0e6f);
             sm.trial[k] = pad_point(-1.0e6f);
-            sm.Lneg[k] = 0.0;
+            sm.Lf[k] = 0.f;
             stv = ST_INACTIVE;
+        }
+        if (c.win && k < c.nwk) {
+            const int jg = c.Jw * S + k;
+            const float4 x = __ldcg(&ch.pos[sw & 1][jg]);
+            const unsigned long long m = sw * (unsigned long long)N + (unsigned long long)jg;
+            const uint4 w = move_draws(ch, m, 0u);
+            sm.wold[k] = x;
+            sm.wtri[k] = make_float4(trial_coord(x.x, w.x, ch.D), trial_coord(x.y, w.y, ch.D),
+                                     trial_coord(x.z, w.z, ch.D), x.w);
         }
         sm.st[k] = (unsigned char)stv;
         sm.outcome[k] = -1;
         sm.tier[k] = 0;
-        sm.dE[k] = __longlong_as_double(0x7ff8000000000000ll);
+        sm.dEv[k] = 0.0;
 #pragma unroll
         for (int w = 0; w < WORDS; ++w) {
             sm.ovo[k][w] = 0u;
             sm.ovn[k][w] = 0u;
+            sm.wovo[k][w] = 0u;
+            sm.wovn[k][w] = 0u;
         }
     }
     if (tid < WORDS) {
         sm.accw[tid] = 0u;
         sm.decw[tid] = 0u;
+        sm.seen[tid] = 0u;
+        sm.winacc[tid] = 0u;
     }
     __syncthreads();
 
-    // 2. pair sums: thread (p, r) owns moves p and p + S/2, column slice r
-    const int p = tid / ETA, r = tid % ETA;
-    const int kA = p, kB = p + S / 2;
-    const float4 aA = sm.trial[kA], bA = sm.own[kA], aB = sm.trial[kB], bB = sm.own[kB];
-    float sA = 0.f, sB = 0.f, AA = 0.f, AB = 0.f, TA = 0.f, TB = 0.f, CA = 0.f, CB = 0.f;
-    float mA = __int_as_float(0x7f800000), mB = __int_as_float(0x7f800000);
-    double SA = 0.0, SB = 0.0;
-
-    // 2a. in-group block (Algorithms 3 and 4): upper triangle final, lower triangle both ways
-    for (int j = r; j < nk; j += ETA) {
-        const float4 yo = sm.own[j], yn = sm.trial[j];
-        if (kA < nk) ingroup_pair(sm, kA, j, aA, bA, yo, yn, sA, AA, TA, CA, mA, lo2, hi2, sig2);
-        if (kB < nk) ingroup_pair(sm, kB, j, aB, bB, yo, yn, sB, AB, TB, CB, mB, lo2, hi2, sig2);
+    // 2. pair sums.  Thread (p, r): moves p + 32 m (m = 0..3), column slice r of 8.
+    const int p = tid / SL, r = tid % SL;
+    float4 a[MPT], b[MPT];
+    float sA[MPT], hA[MPT], lA[MPT], AA[MPT], TA[MPT], CA[MPT], mA[MPT];
+#pragma unroll
+    for (int m = 0; m < MPT; ++m) {
+        a[m] = sm.trial[p + 32 * m];
+        b[m] = sm.own[p + 32 * m];
+        sA[m] = hA[m] = lA[m] = AA[m] = TA[m] = CA[m] = 0.f;
+        mA[m] = finf();
     }
-    SA += (double)sA;
-    SB += (double)sB;
-    sA = sB = 0.f;
+    auto promote = [&]() {
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            float s2, e;
+            two_sum(hA[m], sA[m], s2, e);
+            hA[m] = s2;
+            lA[m] += e;
+            sA[m] = 0.f;
+        }
+    };
 
-    // 2b. every other group, oldest published version first (Algorithm 2 per guest group, Algorithm 5's order)
-    for (int step = 1; step < B; ++step) {
-        const int J = (g + step) % B;
-        const unsigned need = (J > g) ? need_prev : need_cur;
-        if (tid == 0) sm.ok = wait_group(ch, J, need, ctl);
+    // 2a. this group: upper triangle final (Algorithm 3), lower triangle both ways (Algorithm 4)
+    for (int j = r; j < nk; j += SL) {
+        const float4 yo = sm.own[j], yn = sm.trial[j];
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            const int k = p + 32 * m;
+            if (k >= nk || j == k) continue;
+            if (j > k) pair_acc(a[m], b[m], yo, sA[m], AA[m], TA[m], mA[m]);
+            else both_pair(sm.cin, sm.ovo, sm.ovn, k, j, a[m], b[m], yo, yn, sA[m], AA[m], TA[m], CA[m], lo2, hi2, sig2);
+        }
+    }
+    promote();
+    // 2b. the window group, both ways
+    if (c.win) {
+        for (int j = r; j < c.nwk; j += SL) {
+            const float4 yo = sm.wold[j], yn = sm.wtri[j];
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                const int k = p + 32 * m;
+                if (k >= nk) continue;
+                both_pair(sm.cwin, sm.wovo, sm.wovn, k, j, a[m], b[m], yo, yn, sA[m], AA[m], TA[m], CA[m], lo2, hi2,
+                          sig2);
+            }
+        }
+        promote();
+    }
+
+    // 2c. every other group, oldest published version first (Algorithm 2 per guest group):
+    // J = g+1 .. B-1 (version s-1), then J = 0 .. g-1 (version s), the window excluded.
+    auto tile_J = [&](int i) -> int {
+        int J = (g + 1 + i) % B;
+        if (c.win && J == c.Jw) return -1;  // never reached: the window is the last in this order
+        return J;
+    };
+    const int ntl = (B - 1) - (c.win ? 1 : 0);
+    auto tile_tag = [&](int J) -> unsigned { return J > g ? tag_prev : tag_cur; };
+    auto tile_src = [&](int J) -> const float4 * { return (J > g ? c.Pprev : c.Pcur) + (size_t)J * S; };
+    auto tile_words = [&](int J) -> int { return (min(S, N - J * S) + 31) / 32; };
+    if (ntl > 0) {
+        const int J0 = tile_J(0);
+        if (warp == 0) {
+            unsigned bits;
+            const bool ok = wait_words(ch, J0, tile_words(J0), tile_tag(J0), tile_tag(J0), ctl, bits);
+            if (lane == 0) sm.ok = ok;
+        }
         __syncthreads();
         if (!sm.ok) return false;
-        if (tid < S) {
-            const int idx = J * S + tid;
-            sm.tile[tid] = (idx < N) ? __ldcg(&ch.pos[idx]) : pad_point(1.0e6f);
+        if (tid < S) sm.tile[0][tid] = __ldcg(&tile_src(J0)[tid]);
+        if (warp == 0) {  // is tile 1 published already?
+            bool ok = false;
+            if (ntl > 1) {
+                const int J1 = tile_J(1);
+                const int nw = tile_words(J1);
+                bool mine = true;
+                if (lane < nw) mine = (unsigned)(ld_relaxed(&ch.flags[J1 * WORDS + lane]) >> 32) == tile_tag(J1);
+                ok = __all_sync(FULL, mine);
+            }
+            if (lane == 0) {
+                if (ok) fence_acq_rel();
+                sm.rdy[1] = ok;
+            }
         }
-        __syncthreads();
-#pragma unroll 8
-        for (int jj = 0; jj < S / ETA; ++jj) {
-            const float4 y = sm.tile[jj * ETA + r];
-            pair_acc(aA, bA, y, sA, AA, TA, mA);
-            pair_acc(aB, bB, y, sB, AB, TB, mB);
-        }
-        SA += (double)sA;
-        SB += (double)sB;
-        sA = sB = 0.f;
         __syncthreads();
     }
-
-    // 2c. combine the ETA column slices
+    const long long cyc_t0 = clock64();
+    int Jn = ntl > 1 ? tile_J(1) : -1;   // tile i+1
+    int Jnn = ntl > 2 ? tile_J(2) : -1;  // tile i+2
+    for (int i = 0; i < ntl; ++i) {
+        const int cur = i & 1;
+        const bool pf = (i + 1 < ntl) && sm.rdy[(i + 1) & 1];
+        float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pf && tid < S) pre = __ldcg(&tile_src(Jn)[tid]);
+        unsigned long long pv = 0;
+        const int nwnn = (Jnn >= 0) ? tile_words(Jnn) : 0;
+        if (warp == 0 && lane < nwnn) pv = ld_relaxed(&ch.flags[Jnn * WORDS + lane]);
+#pragma unroll 4
+        for (int jj = 0; jj < S / SL; ++jj) {
+            const float4 y = sm.tile[cur][jj * SL + r];
 #pragma unroll
-    for (int o = 1; o < ETA; o <<= 1) {
-        SA += __shfl_xor_sync(FULL, SA, o);
-        SB += __shfl_xor_sync(FULL, SB, o);
-        AA += __shfl_xor_sync(FULL, AA, o);
-        AB += __shfl_xor_sync(FULL, AB, o);
-        TA += __shfl_xor_sync(FULL, TA, o);
-        TB += __shfl_xor_sync(FULL, TB, o);
-        CA += __shfl_xor_sync(FULL, CA, o);
-        CB += __shfl_xor_sync(FULL, CB, o);
-        mA = fminf(mA, __shfl_xor_sync(FULL, mA, o));
-        mB = fminf(mB, __shfl_xor_sync(FULL, mB, o));
+            for (int m = 0; m < MPT; ++m) pair_acc(a[m], b[m], y, sA[m], AA[m], TA[m], mA[m]);
+        }
+        promote();
+        if (pf && tid < S) sm.tile[cur ^ 1][tid] = pre;
+        if (warp == 0 && Jnn >= 0) {
+            const bool ok = __all_sync(FULL, lane >= nwnn || (unsigned)(pv >> 32) == tile_tag(Jnn));
+            if (lane == 0) {
+                if (ok) fence_acq_rel();
+                sm.rdy[i & 1] = ok;  // slot of tile i+2
+            }
+        }
+        __syncthreads();
+        if (i + 1 < ntl && !pf) {  // the next tile was not published in time: wait for it now
+            if (warp == 0) {
+                unsigned bits;
+                const bool ok = wait_words(ch, Jn, tile_words(Jn), tile_tag(Jn), tile_tag(Jn), ctl, bits);
+                if (lane == 0) sm.ok = ok;
+            }
+            __syncthreads();
+            if (!sm.ok) return false;
+            if (tid < S) sm.tile[cur ^ 1][tid] = __ldcg(&tile_src(Jn)[tid]);
+            __syncthreads();
+        }
+        Jn = Jnn;
+        Jnn = (i + 3 < ntl) ? tile_J(i + 3) : -1;
+    }
+    cyc_tiles = clock64() - cyc_t0;
+
+    // 2d. combine the 8 column slices
+#pragma unroll
+    for (int o = 1; o < SL; o <<= 1) {
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            const float h2 = __shfl_xor_sync(FULL, hA[m], o), l2 = __shfl_xor_sync(FULL, lA[m], o);
+            float s2, e;
+            two_sum(hA[m], h2, s2, e);
+            hA[m] = s2;
+            lA[m] = lA[m] + l2 + e;
+            AA[m] += __shfl_xor_sync(FULL, AA[m], o);
+            TA[m] += __shfl_xor_sync(FULL, TA[m], o);
+            CA[m] += __shfl_xor_sync(FULL, CA[m], o);
+            mA[m] = fminf(mA[m], __shfl_xor_sync(FULL, mA[m], o));
+        }
     }
     if (r == 0) {
-        // FP32 accumulations of the bound quantities are inflated by 2^-10 (>= their own rounding error)
-        sm.base[kA] = SA;
-        sm.Ab[kA] = AA * (1.0f + 0x1p-10f);
-        sm.Tb[kA] = TA * (1.0f + 0x1p-10f);
-        sm.TCb[kA] = CA * (1.0f + 0x1p-10f);
-        sm.mind2[kA] = mA;
-        sm.base[kB] = SB;
-        sm.Ab[kB] = AB * (1.0f + 0x1p-10f);
-        sm.Tb[kB] = TB * (1.0f + 0x1p-10f);
-        sm.TCb[kB] = CB * (1.0f + 0x1p-10f);
-        sm.mind2[kB] = mB;
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            const int k = p + 32 * m;
+            sm.bhi[k] = hA[m];
+            sm.blo[k] = lA[m];
+            sm.Ab[k] = AA[m] * (1.0f + 0x1p-10f);
+            sm.Tb[k] = TA[m] * (1.0f + 0x1p-10f);
+            sm.TCb[k] = CA[m] * (1.0f + 0x1p-10f);
+            sm.mind2[k] = mA[m];
+        }
     }
     __syncthreads();
 
-    // 3. decisions.  3a: moves decided without any in-group dependence.
+    // 3. per-move preparation: interval sums of the corrections (threads < S: this
+    // group, threads >= S: the window), overlap status, static band.
+    {
+        const int k = tid & (S - 1), h = tid >> 7;
+        float lo = 0.f, hi = 0.f;
+        if (h == 0) {
+            for (int j = 0; j < k; ++j) {
+                const float cv = sm.cin[j * CS + k];
+                lo += fminf(cv, 0.f);
+                hi += fmaxf(cv, 0.f);
+            }
+            sm.lo_i[k] = lo;
+            sm.hi_i[k] = hi;
+        } else {
+            if (c.win)
+                for (int j = 0; j < c.nwk; ++j) {
+                    const float cv = sm.cwin[j * CS + k];
+                    lo += fminf(cv, 0.f);
+                    hi += fmaxf(cv, 0.f);
+                }
+            sm.lo_w[k] = lo;
+            sm.hi_w[k] = hi;
+        }
+    }
     if (tid < S) {
         const int k = tid;
         unsigned stv = sm.st[k];
-        bool dec = false;
-        if (stv & ST_INACTIVE) {
-            dec = true;
-        } else if (stv & ST_WALL) {
-            dec = true;
-            sm.outcome[k] = OUT_WALL;
-        } else {
+        if (!(stv & (ST_INACTIVE | ST_WALL))) {
             const float m2 = sm.mind2[k];
             if (m2 < lo2) stv |= ST_OVL_CERTAIN;
-            else if (!(m2 > hi2)) stv |= ST_OVL_AMBIG;  // inside the band (or NaN): FP64 decides
-            sm.st[k] = (unsigned char)stv;
-            if (stv & ST_OVL_CERTAIN) {
-                dec = true;
-                sm.outcome[k] = OUT_OVERLAP;
+            else if (!(m2 > hi2)) stv |= ST_OVL_AMBIG;
+            unsigned any = 0, both = 0;
+#pragma unroll
+            for (int w = 0; w < WORDS; ++w) {
+                any |= sm.ovo[k][w] | sm.ovn[k][w] | sm.wovo[k][w] | sm.wovn[k][w];
+                both |= (sm.ovo[k][w] & sm.ovn[k][w]) | (sm.wovo[k][w] & sm.wovn[k][w]);
             }
+            if (both) stv |= ST_OVL_CERTAIN;
+            else if (any) stv |= ST_OVL_POSSIBLE;
+            sm.st[k] = (unsigned char)stv;
         }
-        const unsigned bal = __ballot_sync(FULL, dec);
-        if ((tid & 31) == 0) sm.decw[tid >> 5] = bal;
+        const float lqa = fabsf(lBf * sm.own[k].w);
+        sm.bnd[k] = (mode == 1 || mode == 3) ? finf()
+                              : (mode == 2 ? 0.f
+                                           : lqa * (U32 * (C_TERM * sm.Ab[k] + C_SUM * sm.Tb[k] + C_CORR * sm.TCb[k]) +
+                                                    0x1p-36f * (sm.Ab[k] + sm.Tb[k])));
+        sm.run[k] = 0.f;
+        sm.wex[k] = 0.f;
     }
     __syncthreads();
 
-    // 3b: moves whose outcome is the same for every combination of the
-    // undecided earlier outcomes of the group (interval over the corrections).
+    // 4. round 0: moves decided whatever the window and this group's earlier moves do
     if (tid < S) {
         const int k = tid;
-        bool dec = bit(sm.decw, k);
-        if (!dec && !(sm.st[k] & ST_OVL_AMBIG)) {
-            float lo = 0.f, hi = 0.f;
-            bool ovl_c = false, ovl_p = false;
-            for (int j = 0; j < k; ++j) {
-                if (bit(sm.decw, j)) {  // decided so far means rejected: old position
-                    ovl_c |= bit(sm.ovo[k], j);
-                } else {
-                    const float c = sm.cmat[j * CS + k];
-                    lo += fminf(c, 0.f);
-                    hi += fmaxf(c, 0.f);
-                    const bool bo = bit(sm.ovo[k], j), bn = bit(sm.ovn[k], j);
-                    if (bo && bn) ovl_c = true;
-                    else if (bo || bn) ovl_p = true;
-                }
-            }
-            if (ovl_c) {
-                dec = true;
-                sm.outcome[k] = OUT_OVERLAP;
-            } else if (!ovl_p) {
-                if (sm.st[k] & ST_UZERO) {
-                    dec = true;
-                    sm.outcome[k] = OUT_ACCEPT;
-                } else if (mode != 1) {
-                    const double lq = __dmul_rn(ch.lB, (double)sm.own[k].w);
-                    const double e1 = lq * (sm.base[k] + (double)lo), e2 = lq * (sm.base[k] + (double)hi);
-                    const double bnd = band(sm, k, fabs(lq), mode) + 0x1p-50 * (fabs(e1) + fabs(e2) + fabs(sm.Lneg[k]));
-                    if (isfinite(e1) && isfinite(e2)) {
-                        const double elo = e1 < e2 ? e1 : e2, ehi = e1 < e2 ? e2 : e1;
-                        if (ehi < sm.Lneg[k] - bnd) {
-                            dec = true;
-                            sm.outcome[k] = OUT_ACCEPT;
-                        } else if (elo > sm.Lneg[k] + bnd) {
-                            dec = true;
-                            sm.outcome[k] = OUT_METROPOLIS;
-                        }
-                    }
-                }
+        const unsigned stv = sm.st[k];
+        int out = -1;
+        if (stv & ST_INACTIVE) out = 4;
+        else if (stv & ST_WALL) out = OUT_WALL;
+        else if (stv & ST_OVL_CERTAIN) out = OUT_OVERLAP;
+        else if (!(stv & (ST_OVL_POSSIBLE | ST_OVL_AMBIG))) {
+            if (stv & ST_UZERO) out = OUT_ACCEPT;
+            else {
+                const float lq = lBf * sm.own[k].w;
+                const float base = sm.bhi[k] + sm.blo[k];
+                out = decide_interval(sm, k, lq, base + (sm.lo_w[k] + sm.lo_i[k]), base + (sm.hi_w[k] + sm.hi_i[k]));
             }
         }
-        const unsigned bal = __ballot_sync(FULL, dec);
-        const unsigned acc = __ballot_sync(FULL, dec && sm.outcome[k] == OUT_ACCEPT);
-        if ((tid & 31) == 0) {
-            sm.decw[tid >> 5] = bal;
-            sm.accw[tid >> 5] = acc;
+        if (out >= 0 && out <= 3) sm.outcome[k] = (signed char)out;
+        const unsigned dec = __ballot_sync(FULL, out >= 0);
+        const unsigned acc = __ballot_sync(FULL, out == OUT_ACCEPT);
+        if (lane == 0) {
+            sm.decw[warp] = dec;
+            sm.accw[warp] = acc;
+        }
+    }
+
+    // 5. the window's outcome (the critical wait), then its exact correction sums
+    const long long cyc_w0 = clock64();
+    if (c.win) {
+        if (warp == 0) {
+            unsigned bits;
+            const int nw = (c.nwk + 31) / 32;
+            const bool ok = wait_words(ch, c.Jw, nw, (unsigned)(sw + 1), (unsigned)(sw + 1), ctl, bits);
+            if (lane < WORDS) sm.winacc[lane] = (lane < nw) ? bits : 0u;
+            if (lane == 0) sm.ok = ok;
+        }
+        __syncthreads();
+        if (!sm.ok) return false;
+        cyc_win = clock64() - cyc_w0;
+        {
+            const int k = tid & (S - 1), h = tid >> 7;
+            float sx = 0.f;
+            const unsigned wa0 = sm.winacc[2 * h], wa1 = sm.winacc[2 * h + 1];
+#pragma unroll 16
+            for (int jj = 0; jj < HALF; ++jj) {
+                const unsigned wb = jj < 32 ? wa0 : wa1;
+                const float cv = sm.cwin[(h * HALF + jj) * CS + k];
+                sx += ((wb >> (jj & 31)) & 1u) ? cv : 0.f;
+            }
+            sm.part[h][k] = sx;
+        }
+        __syncthreads();
+        if (tid < S) {
+            const int k = tid;
+            sm.wex[k] = sm.part[0][k] + sm.part[1][k];
+            unsigned wo = 0;  // the window's overlap is now exact
+#pragma unroll
+            for (int w = 0; w < WORDS; ++w) wo |= (sm.wovn[k][w] & sm.winacc[w]) | (sm.wovo[k][w] & ~sm.winacc[w]);
+            unsigned stv = sm.st[k];
+            if (wo) stv |= ST_OVL_CERTAIN;
+            sm.st[k] = (unsigned char)stv;
         }
     }
     __syncthreads();
-    // moves settled in 3b (not rejected by wall/overlap before any dependence) are "interval" decisions
-    // 3c: the rest in order, one warp, exact sums; FP64 for moves inside the band.
+
+    // 6. rounds over this group's earlier moves: exact sums over decided ones,
+    // intervals over undecided ones.  The first undecided move has only decided
+    // predecessors after at most one more round; if it is still inside its band
+    // it goes to the guard tiers.
+    cyc_res0 = clock64();
     for (;;) {
-        if (tid < 32) {
-            const int lane = tid;
-            int k = 0;
-            int guard = -1;
-            for (;;) {
-                // next undecided move
-                int nxt = -1;
-#pragma unroll
-                for (int w = 0; w < WORDS; ++w) {
-                    const unsigned und = ~sm.decw[w];
-                    if (nxt < 0 && und) nxt = w * 32 + __ffs(und) - 1;
-                }
-                if (nxt < 0 || nxt >= nk) break;
-                k = nxt;
-                float part = 0.f;
-                for (int j = lane; j < k; j += 32)
-                    if (bit(sm.accw, j)) part += sm.cmat[j * CS + k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-                if (lane == 0) {
-                    bool ovl = false;
-#pragma unroll
-                    for (int w = 0; w < WORDS; ++w) {
-                        const unsigned below = (w * 32 + 32 <= k) ? FULL : (w * 32 >= k ? 0u : ((1u << (k - w * 32)) - 1u));
-                        ovl |= ((sm.ovn[k][w] & sm.accw[w]) | (sm.ovo[k][w] & ~sm.accw[w])) & below;
-                    }
-                    int out = -1;
-                    double dE = __longlong_as_double(0x7ff8000000000000ll);
-                    if (ovl) {
-                        out = OUT_OVERLAP;
-                    } else if (sm.st[k] & ST_OVL_AMBIG) {
-                        out = -2;  // exact overlap needs FP64
-                    } else {
-                        const double lq = __dmul_rn(ch.lB, (double)sm.own[k].w);
-                        dE = lq * (sm.base[k] + (double)part);
-                        if (sm.st[k] & ST_UZERO) {
-                            out = OUT_ACCEPT;
-                        } else {
-                            const double bnd = band(sm, k, fabs(lq), mode) + 0x1p-50 * (fabs(dE) + fabs(sm.Lneg[k]));
-                            if (dE < sm.Lneg[k] - bnd) out = OUT_ACCEPT;
-                            else if (dE > sm.Lneg[k] + bnd) out = OUT_METROPOLIS;
-                            else out = -2;
-                        }
-                    }
-                    if (out == -2) {
-                        guard = k;
-                    } else {
-                        sm.outcome[k] = (signed char)out;
-                        sm.tier[k] = 1;
-                        sm.dE[k] = dE;
-                        sm.decw[k >> 5] |= 1u << (k & 31);
-                        if (out == OUT_ACCEPT) sm.accw[k >> 5] |= 1u << (k & 31);
-                    }
-                }
-                guard = __shfl_sync(FULL, guard, 0);
-                __syncwarp();
-                if (guard >= 0) break;
-            }
-            if (lane == 0) sm.guard_k = guard;
+        ++n_rounds;
+        if (tid < WORDS) {
+            sm.acc0[tid] = sm.accw[tid];
+            sm.dec0[tid] = sm.decw[tid];
         }
         __syncthreads();
-        const int gk = sm.guard_k;
-        if (gk < 0) break;
-        fp64_decide(sm, ch, k0, nk, gk);
+        {  // partial sums over j in half h of [0, k)
+            const int k = tid & (S - 1), h = tid >> 7;
+            float sx = 0.f, lo = 0.f, hi = 0.f;
+            if (!bit(sm.dec0, k)) {
+                const int j0 = h * HALF, j1 = min(k, j0 + HALF);
+                for (int j = j0; j < j1; ++j) {
+                    const unsigned bm = 1u << (j & 31);
+                    const unsigned wd = sm.dec0[j >> 5], wa = sm.acc0[j >> 5], ws = sm.seen[j >> 5];
+                    const float cv = sm.cin[j * CS + k];
+                    if (wa & ~ws & bm) sx += cv;
+                    else if (!(wd & bm)) {
+                        lo += fminf(cv, 0.f);
+                        hi += fmaxf(cv, 0.f);
+                    }
+                }
+            }
+            sm.part[h][k] = sx;
+            sm.plo[h][k] = lo;
+            sm.phi[h][k] = hi;
+        }
+        __syncthreads();
+        if (tid < S) {
+            const int k = tid;
+            int out = -1;
+            if (!bit(sm.dec0, k)) {
+                const float run = sm.run[k] + (sm.part[0][k] + sm.part[1][k]);
+                sm.run[k] = run;
+                const float lo = sm.plo[0][k] + sm.plo[1][k], hi = sm.phi[0][k] + sm.phi[1][k];
+                const unsigned stv = sm.st[k];
+                bool ov_c, ov_p;
+                ingroup_overlap(sm, k, sm.dec0, sm.acc0, ov_c, ov_p);
+                bool unknown = false;
+#pragma unroll
+                for (int w = 0; w < WORDS; ++w) unknown |= (~sm.dec0[w] & below(k, w)) != 0u;
+                if ((stv & ST_OVL_CERTAIN) || ov_c) out = OUT_OVERLAP;
+                else if (!ov_p && !(stv & ST_OVL_AMBIG)) {
+                    if (stv & ST_UZERO) out = OUT_ACCEPT;
+                    else {
+                        const float lq = lBf * sm.own[k].w;
+                        const float base = sm.bhi[k] + (sm.blo[k] + (sm.wex[k] + run));
+                        out = decide_interval(sm, k, lq, base + lo, base + hi);
+                    }
+                }
+                if (out >= 0) {
+                    sm.outcome[k] = (signed char)out;
+                    sm.tier[k] = unknown ? 0 : 1;
+                }
+            }
+            const unsigned dec = __ballot_sync(FULL, out >= 0);
+            const unsigned acc = __ballot_sync(FULL, out == OUT_ACCEPT);
+            if (lane == 0) {
+                sm.seen[warp] = sm.acc0[warp];
+                sm.decw[warp] |= dec;
+                sm.accw[warp] |= acc;
+            }
+        }
+        __syncthreads();
+        int first = -1;
+#pragma unroll
+        for (int w = 0; w < WORDS; ++w) {
+            const unsigned und = ~sm.decw[w];
+            if (first < 0 && und) first = w * 32 + __ffs(und) - 1;
+        }
+        if (first < 0 || first >= nk) break;
+        bool exact = true;  // were all predecessors of `first` decided when this round started?
+#pragma unroll
+        for (int w = 0; w < WORDS; ++w) exact &= (~sm.dec0[w] & below(first, w)) == 0u;
+        if (!exact) continue;
+        // guard tiers on move k = first: exact FP32 value was inside its band (or overlap was ambiguous)
+        const long long cyc_g0 = clock64();
+        const int k = first;
+        const unsigned stv = sm.st[k];
+        const unsigned ua = move_draws(ch, s * (unsigned long long)N + (unsigned long long)(k0 + k), 0u).w >> 8;
+        const double L64 = (ua == 0u) ? 0.0 : -series_log((double)ua * 0x1p-24);
+        double dE = 0.0;
+        int res = -1, tier = 2;
+        if (!(stv & ST_OVL_AMBIG) && mode != 1) {
+            res = tier2(sm, c, k, L64, dE);
+            if (res < 0) {
+                tier = 3;
+                res = tier3(sm, c, k, L64, dE);
+            }
+        }
+        if (res < 0) {
+            bool ovl = false;
+            tier = 4;
+            tier4(sm, c, k, dE, ovl);
+            if (ovl) res = 2;
+            else if (ua == 0u) res = 0;
+            else res = (dE < L64) ? 0 : 1;
+        }
+        if (tid == 0) {
+            const int out = res == 0 ? OUT_ACCEPT : (res == 1 ? OUT_METROPOLIS : OUT_OVERLAP);
+            sm.outcome[k] = (signed char)out;
+            sm.tier[k] = (unsigned char)tier;
+            sm.dEv[k] = dE;
+            sm.decw[k >> 5] |= 1u << (k & 31);
+            if (out == OUT_ACCEPT) sm.accw[k >> 5] |= 1u << (k & 31);
+        }
+        __syncthreads();
+        cyc_guard += clock64() - cyc_g0;
     }
+    const long long cyc_resolve = clock64() - cyc_res0 - cyc_guard;
 
-    // 4. publish: final positions, then the sweep-tagged words with the accept bits
+    // 7. publish: final positions (version s), then the sweep-tagged words with the accept bits
     if (tid < nk) {
         const bool acc = bit(sm.accw, tid);
-        __stcg(&ch.pos[k0 + tid], acc ? sm.trial[tid] : sm.own[tid]);
+        __stcg(&ch.pos[(s + 1) & 1][k0 + tid], acc ? sm.trial[tid] : sm.own[tid]);
     }
     __syncthreads();
     const bool publish = (long long)ticket != ctl->skip_ticket;
@@ -527,35 +958,39 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         __threadfence();
         const int nw = (nk + 31) / 32;
         for (int w = 0; w < nw; ++w)
-            st_release(&ch.flags[g * WORDS + w], ((unsigned long long)need_cur << 32) | sm.accw[w]);
+            st_release(&ch.flags[g * WORDS + w], ((unsigned long long)tag_cur << 32) | sm.accw[w]);
     }
 
-    // 5. bookkeeping off the critical path: dE of moves decided by interval, ledger, counters, records
+    // 8. off the critical path: FP32 dE of every evaluated move, ledger, counters, records
+    {
+        const int k = tid & (S - 1), h = tid >> 7;
+        float sx = 0.f;
+        const int j0 = h * HALF, j1 = min(k, j0 + HALF);
+        for (int j = j0; j < j1; ++j)
+            if (bit(sm.accw, j)) sx += sm.cin[j * CS + k];
+        sm.part[h][k] = sx;
+    }
+    __syncthreads();
     double mydE = 0.0;
-    if (tid < nk) {
+    if (tid < S) {
         const int k = tid;
         const int out = sm.outcome[k];
-        const bool need_sum = (out == OUT_ACCEPT || out == OUT_METROPOLIS) && sm.tier[k] == 0 &&
-                              !(sm.st[k] & ST_UZERO);
-        const bool acc_uzero = (out == OUT_ACCEPT) && sm.tier[k] == 0 && (sm.st[k] & ST_UZERO);
-        if (need_sum || acc_uzero || (ch.rec && out != OUT_WALL && out != OUT_OVERLAP && sm.tier[k] != 4)) {
-            float part = 0.f;
-            for (int j = 0; j < k; ++j)
-                if (bit(sm.accw, j)) part += sm.cmat[j * CS + k];
-            const double lq = __dmul_rn(ch.lB, (double)sm.own[k].w);
-            if (sm.tier[k] == 0) sm.dE[k] = lq * (sm.base[k] + (double)part);
+        float d32 = __int_as_float(0x7fc00000);
+        if (k < nk && (out == OUT_ACCEPT || out == OUT_METROPOLIS)) {
+            const float lq = lBf * sm.own[k].w;
+            d32 = lq * (sm.bhi[k] + (sm.blo[k] + (sm.wex[k] + (sm.part[0][k] + sm.part[1][k]))));
+            if (sm.tier[k] <= 1) sm.dEv[k] = (double)d32;
         }
-        if (out == OUT_ACCEPT) mydE = sm.dE[k];
+        sm.dE32[k] = d32;
+        if (k < nk && out == OUT_ACCEPT) mydE = sm.dEv[k];
     }
-    // deterministic block sum of the accepted dE (fixed tree order)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mydE += __shfl_xor_sync(FULL, mydE, o);
-    if ((tid & 31) == 0) sm.red[tid >> 5] = mydE;
+    if (lane == 0) sm.redd[warp] = mydE;
     __syncthreads();
     if (tid == 0 && publish) {
         double gsum = 0.0;
-        for (int w = 0; w < T / 32; ++w) gsum += sm.red[w];
-        // fold into the chain ledger in stream order
+        for (int w = 0; w < T / 32; ++w) gsum += sm.redd[w];
         const unsigned long long me = s * (unsigned long long)B + (unsigned long long)g;
         const unsigned long long t0 = globaltimer();
         unsigned spins = 0;
@@ -565,7 +1000,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 ok = false;
                 break;
             }
-            if (++spins > 32) __nanosleep(40);
+            if (++spins > 16) __nanosleep(32);
             if ((spins & 63) == 0 && (long long)(globaltimer() - t0) > ctl->timeout_ns) {
                 atomicCAS(&ctl->err, 0, KERR_TIMEOUT);
                 atomicExch(&ctl->abort, 1);
@@ -580,27 +1015,36 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         }
         sm.ok = ok ? 1 : 0;
     }
-    if (tid < 32) {
-        // counters by outcome
-        unsigned cnt[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = tid; k < nk; k += 32) {
+    if (warp == 0) {
+        unsigned cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = lane; k < nk; k += 32) {
             const int out = sm.outcome[k];
             if (out >= 0 && out <= 3) cnt[out]++;
-            if (sm.tier[k] == 4) cnt[4]++;
+            if (sm.tier[k] >= 2) cnt[4]++;
             if (sm.tier[k] == 0 && (out == OUT_ACCEPT || out == OUT_METROPOLIS)) cnt[5]++;
+            if (sm.tier[k] >= 2) cnt[4 + sm.tier[k]]++;
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
+        for (int q = 0; q < 9; ++q) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt[c] += __shfl_xor_sync(FULL, cnt[c], o);
+            for (int o = 16; o > 0; o >>= 1) cnt[q] += __shfl_xor_sync(FULL, cnt[q], o);
         }
-        if (tid == 0) {
+        if (lane == 0) {
             atomicAdd(&ch.stats[CNT_ACCEPT], (unsigned long long)cnt[OUT_ACCEPT]);
             atomicAdd(&ch.stats[CNT_METRO], (unsigned long long)cnt[OUT_METROPOLIS]);
             atomicAdd(&ch.stats[CNT_OVERLAP], (unsigned long long)cnt[OUT_OVERLAP]);
             atomicAdd(&ch.stats[CNT_WALL], (unsigned long long)cnt[OUT_WALL]);
             atomicAdd(&ch.stats[CNT_FP64], (unsigned long long)cnt[4]);
             atomicAdd(&ch.stats[CNT_INTERVAL], (unsigned long long)cnt[5]);
+            atomicAdd(&ch.stats[CNT_T2], (unsigned long long)cnt[6]);
+            atomicAdd(&ch.stats[CNT_T3], (unsigned long long)cnt[7]);
+            atomicAdd(&ch.stats[CNT_T4], (unsigned long long)cnt[8]);
+            atomicAdd(&ch.stats[CNT_ROUNDS], (unsigned long long)n_rounds);
+            atomicAdd(&ch.stats[CNT_CYC_WIN], (unsigned long long)cyc_win);
+            atomicAdd(&ch.stats[CNT_CYC_TILES], (unsigned long long)cyc_tiles);
+            atomicAdd(&ch.stats[CNT_CYC_RESOLVE], (unsigned long long)cyc_resolve);
+            atomicAdd(&ch.stats[CNT_CYC_GUARD], (unsigned long long)cyc_guard);
+            atomicAdd(&ch.stats[CNT_CYC_TOTAL], (unsigned long long)(clock64() - cyc_start));
         }
     }
     if (ch.rec && s >= ch.rec_sweep0 && tid < nk) {
@@ -613,18 +1057,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             rc.outcome = sm.outcome[k];
             rc.tier = sm.tier[k];
             rc.pad = 0;
-            const double lq = __dmul_rn(ch.lB, (double)sm.own[k].w);
-            rc.scale = fabs(lq) * (double)sm.Ab[k];
+            rc.scale = fabs(ch.lB * (double)sm.own[k].w) * (double)sm.Ab[k];
             const int out = sm.outcome[k];
-            rc.dE = (out == OUT_ACCEPT || out == OUT_METROPOLIS) ? sm.dE[k] : __longlong_as_double(0x7ff8000000000000ll);
-            double d32 = __longlong_as_double(0x7ff8000000000000ll);
-            if (out == OUT_ACCEPT || out == OUT_METROPOLIS) {
-                float part = 0.f;
-                for (int j = 0; j < k; ++j)
-                    if (bit(sm.accw, j)) part += sm.cmat[j * CS + k];
-                d32 = lq * (sm.base[k] + (double)part);
-            }
-            rc.dE32 = d32;
+            const bool ev = out == OUT_ACCEPT || out == OUT_METROPOLIS;
+            rc.dE = ev ? sm.dEv[k] : __longlong_as_double(0x7ff8000000000000ll);
+            rc.dE32 = ev ? (double)sm.dE32[k] : __longlong_as_double(0x7ff8000000000000ll);
             ch.rec[idx] = rc;
         }
     }
@@ -632,7 +1069,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     return sm.ok != 0;
 }
 
-__global__ void __launch_bounds__(T, 2)
+__global__ void __launch_bounds__(T, 1)
 sweep_kernel(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sched, int n_tickets, Ctl *ctl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

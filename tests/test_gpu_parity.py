@@ -107,10 +107,12 @@ def test_plain_n256_full_run(pkg):
     assert abs(led_g - rec_o) < 1e-6 * max(1.0, abs(rec_o)) * 50
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_guard_modes(pkg, mode):
-    """Mode 1 recomputes every evaluated move in FP64 (band = infinity): must equal the oracle.  Mode 2 decides in
-    FP32 alone (band = 0): may differ only on moves the band would have sent to FP64 -- counted, expected rare."""
+    """Mode 1 recomputes every evaluated move in FP64 (band = infinity): must equal the oracle.  Mode 3 sends every
+    evaluated move through the accurate-FP32 and double-single tiers before FP64: must equal the oracle, and the
+    dE of those tiers must be within 1e-9 of the oracle's.  Mode 2 decides in FP32 alone (band = 0): may differ
+    only on moves the band would have sent to a guard tier -- counted, expected rare."""
     ch = inputs.small_chain(300, phi=0.2, seed=7, two_one=True)
     gs, oc = _pair(ch)
     gs.set_option(pkg.OPT_GUARD_MODE, mode)
@@ -124,6 +126,18 @@ def test_guard_modes(pkg, mode):
         assert (gr["outcome"] == orc["outcome"]).all()
         ev = (orc["outcome"] == 0) | (orc["outcome"] == 1)
         assert (gr["dE"][ev] == orc["dE"][ev]).all()
+    elif mode == 3:
+        assert (gs.positions() == oc.positions()).all()
+        assert (gr["outcome"] == orc["outcome"]).all()
+        ev = (orc["outcome"] == 0) | (orc["outcome"] == 1)
+        tiers = gr["tier"][ev]
+        assert (tiers >= 2).all() and (tiers == 2).sum() > 0
+        err = np.abs(gr["dE"][ev] - orc["dE"][ev]) / gr["scale"][ev]
+        # accurate FP32 (tier 2): error far below the FP32 band; double-single (tier 3): ~2^-38; FP64: exact
+        assert err[tiers == 2].max() <= 1e-7, err[tiers == 2].max()
+        if (tiers == 3).any():
+            assert err[tiers == 3].max() <= 1e-10
+        assert (err[tiers == 4] == 0).all()
     else:
         diff = int((gr["outcome"] != orc["outcome"]).sum())
         assert diff <= 3, diff
