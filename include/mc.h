@@ -83,6 +83,7 @@ typedef struct {
     uint64_t cyc_resolve;    /* ... deciding (rounds, excluding guard tiers), */
     uint64_t cyc_guard;      /* ... in guard tiers, */
     uint64_t cyc_total;      /* ... and in total */
+    uint64_t cyc_tier[3];    /* SM cycles in guard tiers 2, 3 and 4 */
 } mc_stats_t;
 
 /* Per-move validation record (mc_record_enable / mc_record_read). */
@@ -165,6 +166,20 @@ int64_t mc_num_ions(mc_handle h, int chain);
 int mc_record_enable(mc_handle h, int chain, int64_t cap);
 /* Copy up to cap records; returns the number copied (>= 0) or an error. */
 int64_t mc_record_read(mc_handle h, int chain, mc_record *out, int64_t cap);
+
+/* Work-item timeline (profiling): for each (sweep, group of 128 ions) of
+ * chain `chain` after enabling, %globaltimer nanoseconds at which the work
+ * item started, had everything but the previous group's outcome, observed
+ * that outcome, finished deciding, published its own outcome, and published
+ * its new positions.                                                        */
+typedef struct {
+    uint64_t item; /* sweep * groups + group */
+    uint64_t t_start, t_ready, t_window, t_resolved, t_published;
+    uint64_t n_guard; /* 1 if a guard tier ran */
+    uint64_t t_positions; /* ... and published its new positions */
+} mc_trace_rec;
+int mc_trace_enable(mc_handle h, int chain, int64_t cap);
+int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
 
 /* Options (mc_set_option):
  *  MC_OPT_GUARD_MODE   0 = FP32 with proven error band (default),

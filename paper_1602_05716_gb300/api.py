@@ -14,9 +14,13 @@ OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH = 1, 2
 RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("dE", np.float64),
                          ("dE32", np.float64), ("scale", np.float64), ("tier", np.int32), ("pad", np.int32)])
 
+TRACE_DTYPE = np.dtype([("item", np.uint64), ("t_start", np.uint64), ("t_ready", np.uint64),
+                        ("t_window", np.uint64), ("t_resolved", np.uint64), ("t_published", np.uint64),
+                        ("n_guard", np.uint64), ("t_positions", np.uint64)])
+
 _STATS_FIELDS = ["sweeps", "accepts", "rej_metropolis", "rej_overlap", "rej_wall", "guard_fp64",
                  "decided_interval", "tier2", "tier3", "tier4", "rounds", "cyc_wait_window", "cyc_tiles",
-                 "cyc_resolve", "cyc_guard", "cyc_total"]
+                 "cyc_resolve", "cyc_guard", "cyc_total", "cyc_tier2", "cyc_tier3", "cyc_tier4"]
 
 
 class MCError(RuntimeError):
@@ -71,6 +75,8 @@ def lib():
         "mc_num_ions": ([vp, ci], i64),
         "mc_record_enable": ([vp, ci, i64], ci),
         "mc_record_read": ([vp, ci, vp, i64], i64),
+        "mc_trace_enable": ([vp, ci, i64], ci),
+        "mc_trace_read": ([vp, ci, vp, i64], i64),
         "mc_set_option": ([vp, ci, i64], ci),
         "mc_destroy": ([vp], None),
         "mc_last_error": ([], ctypes.c_char_p),
@@ -230,6 +236,16 @@ class System:
     def record_enable(self, cap: int, chain: int = 0):
         _check(lib().mc_record_enable(self._h, chain, int(cap)))
         self._rec_cap = int(cap)
+
+    def trace_enable(self, cap: int, chain: int = 0):
+        _check(lib().mc_trace_enable(self._h, chain, int(cap)))
+        self._trace_cap = int(cap)
+
+    def trace(self, chain: int = 0) -> np.ndarray:
+        cap = getattr(self, "_trace_cap", 0)
+        out = np.zeros(cap, TRACE_DTYPE)
+        n = _check(lib().mc_trace_read(self._h, chain, out.ctypes.data, cap))
+        return out[:n]
 
     def records(self, chain: int = 0) -> np.ndarray:
         cap = getattr(self, "_rec_cap", 0)

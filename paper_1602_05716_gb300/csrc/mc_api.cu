@@ -57,6 +57,7 @@ struct Chain {
     std::vector<float> q;        // host copy of the valences
     float4 *pos[2] = {nullptr, nullptr};  // positions after sweep v live in pos[(v + 1) & 1]
     unsigned long long *flags = nullptr;
+    unsigned long long *bits = nullptr;
     unsigned char *slab = nullptr;  // ledger, ledger_seq, stats, sweep, energy out
     double *ledger = nullptr;
     unsigned long long *ledger_seq = nullptr;
@@ -66,6 +67,8 @@ struct Chain {
     double *rows = nullptr;      // energy scratch (lazy)
     mcg::MoveRec *rec = nullptr;
     long long rec_cap = 0;
+    mcg::TraceRec *trace = nullptr;
+    long long trace_cap = 0;
     unsigned long long rec_sweep0 = 0;
     uint64_t sweeps = 0;         // host mirror of *sweep
     uint64_t sweep_base = 0;     // sweep count when the positions were last set from the host
@@ -169,11 +172,14 @@ mcg::ChainDev describe(const Chain &c)
     d.pos[1] = c.pos[1];
     d.sweep_base = c.sweep_base;
     d.flags = c.flags;
+    d.bits = c.bits;
     d.ledger = c.ledger;
     d.ledger_seq = c.ledger_seq;
     d.stats = c.stats;
     d.sweep = c.sweep;
     d.rec = c.rec;
+    d.trace = c.trace;
+    d.trace_cap = c.trace_cap;
     d.rec_sweep0 = c.rec_sweep0;
     d.rec_cap = c.rec_cap;
     d.N = c.N;
@@ -228,14 +234,16 @@ int init_chain(mc_system *h, Chain &c, const mc_chain_desc &d)
     CK(cudaMalloc(&c.pos[0], sizeof(float4) * (size_t)c.B * mcg::S));
     CK(cudaMalloc(&c.pos[1], sizeof(float4) * (size_t)c.B * mcg::S));
     CK(cudaMalloc(&c.flags, sizeof(unsigned long long) * (size_t)c.B * mcg::WORDS));
-    CK(cudaMalloc(&c.slab, 256));
+    CK(cudaMalloc(&c.bits, sizeof(unsigned long long) * (size_t)c.B * mcg::WORDS));
+    CK(cudaMalloc(&c.slab, 64 + 8 * mcg::NCOUNTERS));
     CK(cudaMemsetAsync(c.flags, 0, sizeof(unsigned long long) * (size_t)c.B * mcg::WORDS, h->stream));
-    CK(cudaMemsetAsync(c.slab, 0, 256, h->stream));
+    CK(cudaMemsetAsync(c.bits, 0, sizeof(unsigned long long) * (size_t)c.B * mcg::WORDS, h->stream));
+    CK(cudaMemsetAsync(c.slab, 0, 64 + 8 * mcg::NCOUNTERS, h->stream));
     c.ledger = (double *)c.slab;
     c.ledger_seq = (unsigned long long *)(c.slab + 8);
     c.sweep = (unsigned long long *)(c.slab + 16);
     c.e_out = (double *)(c.slab + 24);
-    c.stats = (unsigned long long *)(c.slab + 64);  // 16 counters
+    c.stats = (unsigned long long *)(c.slab + 64);  // NCOUNTERS counters
     rc = upload_positions(h, c, d.pos_xyz, h->stream);
     if (rc) return rc;
     CK(cudaMalloc(&c.rows, sizeof(double) * (size_t)c.N));
@@ -249,9 +257,11 @@ void free_chain(Chain &c)
     cudaFree(c.pos[0]);
     cudaFree(c.pos[1]);
     cudaFree(c.flags);
+    cudaFree(c.bits);
     cudaFree(c.slab);
     cudaFree(c.rows);
     cudaFree(c.rec);
+    cudaFree(c.trace);
     c = Chain();
 }
 
@@ -557,7 +567,7 @@ int mc_stats(mc_handle h, int chain, mc_stats_t *out)
     if (rc) return rc;
     if (!out) return fail(MC_ERR_INVALID, "NULL output");
     Chain &c = h->chains[chain];
-    unsigned long long v[16];
+    unsigned long long v[mcg::NCOUNTERS];
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaMemcpy(v, c.stats, sizeof v, cudaMemcpyDeviceToHost));
     std::memset(out, 0, sizeof *out);
@@ -577,6 +587,9 @@ int mc_stats(mc_handle h, int chain, mc_stats_t *out)
     out->cyc_resolve = v[mcg::CNT_CYC_RESOLVE];
     out->cyc_guard = v[mcg::CNT_CYC_GUARD];
     out->cyc_total = v[mcg::CNT_CYC_TOTAL];
+    out->cyc_tier[0] = v[mcg::CNT_CYC_T2];
+    out->cyc_tier[1] = v[mcg::CNT_CYC_T3];
+    out->cyc_tier[2] = v[mcg::CNT_CYC_T4];
     return MC_OK;
 }
 
@@ -610,13 +623,14 @@ int mc_set_state(mc_handle h, int chain, const float *pos_xyz, uint64_t sweeps, 
     }
     std::vector<unsigned long long> fl((size_t)c.B * mcg::WORDS, (unsigned long long)(unsigned)sweeps << 32);
     CK(cudaMemcpy(c.flags, fl.data(), sizeof(unsigned long long) * fl.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.bits, fl.data(), sizeof(unsigned long long) * fl.size(), cudaMemcpyHostToDevice));
     unsigned long long seq = (unsigned long long)sweeps * (unsigned long long)c.B;
     unsigned long long sw = sweeps;
     CK(cudaMemcpy(c.ledger, &ledger, sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c.ledger_seq, &seq, sizeof seq, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c.sweep, &sw, sizeof sw, cudaMemcpyHostToDevice));
     if (stats) {
-        unsigned long long v[16] = {};
+        unsigned long long v[mcg::NCOUNTERS] = {};
         v[mcg::CNT_ACCEPT] = stats->accepts;
         v[mcg::CNT_METRO] = stats->rej_metropolis;
         v[mcg::CNT_OVERLAP] = stats->rej_overlap;
@@ -662,6 +676,38 @@ int mc_record_enable(mc_handle h, int chain, int64_t cap)
     }
     c.rec_sweep0 = c.sweeps;
     return sync_descriptors(h);
+}
+
+int mc_trace_enable(mc_handle h, int chain, int64_t cap)
+{
+    int rc = check_chain(h, chain);
+    if (rc) return rc;
+    if (cap < 0) return fail(MC_ERR_INVALID, "cap < 0");
+    Chain &c = h->chains[chain];
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(c.trace);
+    c.trace = nullptr;
+    c.trace_cap = 0;
+    if (cap > 0) {
+        CK(cudaMalloc(&c.trace, sizeof(mcg::TraceRec) * (size_t)cap));
+        CK(cudaMemset(c.trace, 0, sizeof(mcg::TraceRec) * (size_t)cap));
+        c.trace_cap = cap;
+    }
+    c.rec_sweep0 = c.sweeps;
+    return sync_descriptors(h);
+}
+
+int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap)
+{
+    int rc = check_chain(h, chain);
+    if (rc) return rc;
+    Chain &c = h->chains[chain];
+    if (!out || cap < 0) return fail(MC_ERR_INVALID, "bad trace buffer");
+    static_assert(sizeof(mc_trace_rec) == sizeof(mcg::TraceRec), "trace layout");
+    const int64_t n = std::min<int64_t>(cap, c.trace_cap);
+    CK(cudaStreamSynchronize(h->stream));
+    if (n > 0) CK(cudaMemcpy(out, c.trace, sizeof(mc_trace_rec) * (size_t)n, cudaMemcpyDeviceToHost));
+    return n;
 }
 
 int64_t mc_record_read(mc_handle h, int chain, mc_record *out, int64_t cap)

@@ -41,17 +41,28 @@ struct MoveRec {
     int pad;
 };
 
+// Per-work-item timeline (mc_trace_enable): %globaltimer nanoseconds.
+struct TraceRec {
+    unsigned long long item;   // absolute stream index sweep * B + group
+    unsigned long long t_start, t_ready, t_window, t_resolved, t_published;
+    unsigned long long n_guard;
+    unsigned long long t_positions;
+};
+
 // Per-chain device descriptor (read-only during a launch).
 struct ChainDev {
     float4 *pos[2];               // 2 x N_pad entries: x, y, z, valence (Sec. 3.1's float4 layout); the
                                   // positions after sweep v live in pos[(v + 1) & 1]
-    unsigned long long *flags;    // per 32-ion word: ((sweep+1) << 32) | accept bits
+    unsigned long long *flags;    // per 32-ion word: ((sweep+1) << 32) | accept bits, released after the positions
+    unsigned long long *bits;     // per 32-ion word: the same value, stored as soon as the outcomes are known
     double *ledger;               // running energy
     unsigned long long *ledger_seq;  // groups folded into the ledger (absolute stream index)
     unsigned long long *stats;    // 8 counters
     unsigned long long *sweep;    // completed sweeps (absolute)
     unsigned long long sweep_base;  // sweep count when the positions were last set from the host
     MoveRec *rec;                 // validation records or nullptr
+    TraceRec *trace;              // work-item timeline or nullptr
+    long long trace_cap;
     unsigned long long rec_sweep0;  // sweep at which recording started
     long long rec_cap;
     int N;
@@ -87,7 +98,9 @@ struct Ctl {
 // Counter slots of ChainDev::stats.
 constexpr int CNT_ACCEPT = 0, CNT_METRO = 1, CNT_OVERLAP = 2, CNT_WALL = 3, CNT_FP64 = 4, CNT_INTERVAL = 5,
               CNT_T2 = 6, CNT_T3 = 7, CNT_T4 = 8, CNT_ROUNDS = 9, CNT_CYC_WIN = 10, CNT_CYC_TILES = 11,
-              CNT_CYC_RESOLVE = 12, CNT_CYC_GUARD = 13, CNT_CYC_TOTAL = 14;
+              CNT_CYC_RESOLVE = 12, CNT_CYC_GUARD = 13, CNT_CYC_TOTAL = 14, CNT_CYC_T2 = 15, CNT_CYC_T3 = 16,
+              CNT_CYC_T4 = 17;
+constexpr int NCOUNTERS = 24;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): two 32x32 multiplies per round with
@@ -191,6 +204,11 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ void fence_acq_rel()

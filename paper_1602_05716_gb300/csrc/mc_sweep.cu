@@ -56,6 +56,7 @@ struct __align__(16) Smem {
     float wex[S];  // exact window correction (after the window's bits)
     float run[S];  // exact in-group correction over decided-accepted j < k
     float part[2][S];
+    float wpart[2][S];
     float plo[2][S];
     float phi[2][S];
     float dE32[S];
@@ -104,8 +105,10 @@ __device__ __forceinline__ unsigned below(int k, int w)
 // Warp 0 waits until the sweep tags of the nw words of group J lie in [lo, hi]
 // (acquire).  Returns false on timeout, protocol error or abort.  bits (lane w)
 // gets word w's accept bits.
-__device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsigned hi, Ctl *ctl, unsigned &bits)
+__device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsigned hi, Ctl *ctl, unsigned &bits,
+                           bool sleep = true, bool outcome_words = false)
 {
+    const unsigned long long *words = outcome_words ? ch.bits : ch.flags;
     const int lane = threadIdx.x & 31;
     const unsigned long long t0 = globaltimer();
     unsigned spins = 0;
@@ -113,7 +116,8 @@ __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsig
     bits = 0u;
     for (;;) {
         if (!done) {
-            const unsigned long long v = ld_acquire(&ch.flags[J * WORDS + lane]);
+            const unsigned long long v = outcome_words ? ld_relaxed(&words[J * WORDS + lane])
+                                                       : ld_acquire(&words[J * WORDS + lane]);
             const unsigned tag = (unsigned)(v >> 32);
             if ((int)(tag - lo) >= 0 && (int)(hi - tag) >= 0) {
                 done = true;
@@ -124,8 +128,9 @@ __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsig
             }
         }
         if (__all_sync(FULL, done)) return true;
-        if (*(volatile int *)&ctl->abort) return false;
-        if (++spins > 16) __nanosleep(32);
+        ++spins;
+        if (spins > 16 && sleep) __nanosleep(32);
+        if ((spins & 31) == 0 && *(volatile int *)&ctl->abort) return false;
         if ((spins & 63) == 0 && (long long)(globaltimer() - t0) > ctl->timeout_ns) {
             if (lane == 0) {
                 if (atomicCAS(&ctl->err, 0, KERR_TIMEOUT) == 0) ctl->err_info = ((unsigned long long)J << 32) | lo;
@@ -213,6 +218,50 @@ __device__ __forceinline__ float4 position_of(const Smem &sm, const Ctx &c, int 
     return J > c.g ? __ldcg(&c.Pprev[j]) : __ldcg(&c.Pcur[j]);
 }
 
+// Guard tiers stage the positions seen by move k in blocks of GSTAGE ions,
+// reusing the window-correction matrix (dead once the window's sums are
+// formed): branch-free 16-byte loads of every ion's published position, then
+// this group's and the window group's ions patched from shared memory.  The
+// callers skip ion k itself and the padding beyond N by index.
+constexpr int GSTAGE = 2048;
+static_assert(GSTAGE * 16 + GSTAGE * 8 <= S * CS * 4, "guard staging fits in the window matrix");
+
+__device__ __forceinline__ float4 *stage_buf(Smem &sm)
+{
+    return reinterpret_cast<float4 *>(sm.cwin);
+}
+
+__device__ __forceinline__ double *stage_terms(Smem &sm)
+{
+    return reinterpret_cast<double *>(reinterpret_cast<float4 *>(sm.cwin) + GSTAGE);
+}
+
+__device__ void stage_positions(Smem &sm, const Ctx &c, int k, int j0)
+{
+    float4 *buf = stage_buf(sm);
+    const int tid = threadIdx.x;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < GSTAGE / T; ++u) {
+        const int t = u * T + tid, j = j0 + t;
+        const float4 *src = ((j >> 7) > c.g) ? c.Pprev : c.Pcur;
+        buf[t] = (j < c.N) ? __ldcg(&src[j]) : make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+    }
+    __syncthreads();
+    if (tid < S) {
+        const int l = tid;
+        int t = c.k0 + l - j0;
+        if (t >= 0 && t < GSTAGE && l < c.nk) {
+            buf[t] = (l < k && bit(sm.accw, l)) ? sm.trial[l] : sm.own[l];
+        }
+        if (c.win && l < c.nwk) {
+            t = c.Jw * S + l - j0;
+            if (t >= 0 && t < GSTAGE) buf[t] = bit(sm.winacc, l) ? sm.wtri[l] : sm.wold[l];
+        }
+    }
+    __syncthreads();
+}
+
 // Sum of per-thread FP64 values and FP32 bound terms over the CTA (thread 0 gets it).
 __device__ __forceinline__ void block_sum(Smem &sm, double v, float bb, double &tot, double &btot)
 {
@@ -255,9 +304,14 @@ __device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
     const float rho0 = sqrtf(fmaxf(s2 * (1.0f - 0x1p-18f) - 0.25f * dn * dn, 0.0f)) * (1.0f - 0x1p-18f);
     const int i = c.k0 + k;
     float hi = 0.f, lo = 0.f, bsum = 0.f;
-    for (int j = tid; j < c.N; j += T) {
-        if (j == i) continue;
-        const float4 y = position_of(sm, c, k, j);
+    const float4 *buf = stage_buf(sm);
+    for (int j0 = 0; j0 < c.N; j0 += GSTAGE) {
+      stage_positions(sm, c, k, j0);
+#pragma unroll 2
+      for (int u = 0; u < GSTAGE / T; ++u) {
+        const int j = j0 + u * T + tid;
+        if (j >= c.N || j == i) continue;
+        const float4 y = buf[u * T + tid];
         const float ex = y.x - b.x, ey = y.y - b.y, ez = y.z - b.z;
         const float Do = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float wx = fmaf(2.0f, ex, -dx), wy = fmaf(2.0f, ey, -dy), wz = fmaf(2.0f, ez, -dz);
@@ -280,6 +334,7 @@ __device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
         const float E2 = 4.0f * U32 * M * pr * pr * inv;
         const float E3 = U32 * dn * (2.0f * Ro + rho) * ir * ir * ir;
         bsum += fabsf(y.w) * (E1 + E2 + E3);
+      }
     }
     double tot, bt;
     block_sum(sm, (double)hi + (double)lo, bsum, tot, bt);
@@ -338,9 +393,13 @@ __device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
     const float4 a = sm.trial[k], b = sm.own[k];
     const int i = c.k0 + k;
     float hh = 0.f, hl = 0.f, absum = 0.f;
-    for (int j = tid; j < c.N; j += T) {
-        if (j == i) continue;
-        const float4 y = position_of(sm, c, k, j);
+    const float4 *buf = stage_buf(sm);
+    for (int j0 = 0; j0 < c.N; j0 += GSTAGE) {
+      stage_positions(sm, c, k, j0);
+      for (int u = 0; u < GSTAGE / T; ++u) {
+        const int j = j0 + u * T + tid;
+        if (j >= c.N || j == i) continue;
+        const float4 y = buf[u * T + tid];
         float Dn_h = 0.f, Dn_l = 0.f, Do_h = 0.f, Do_l = 0.f;
         const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, yv[3] = {y.x, y.y, y.z};
 #pragma unroll
@@ -360,6 +419,7 @@ __device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
         df_mul(th, tl, y.w, 0.0f, qh, ql);
         df_add(hh, hl, qh, ql, hh, hl);
         absum += fabsf(y.w) * (rnh + roh);
+      }
     }
     double tot, bt;
     block_sum(sm, (double)hh + (double)hl, absum, tot, bt);
@@ -386,28 +446,40 @@ __device__ void tier4(Smem &sm, const Ctx &c, int k, double &dE_out, bool &ovl_o
     const int N = c.N;
     const int i = c.k0 + k;
     const float4 a = sm.trial[k], b = sm.own[k];
+    const float4 *buf = stage_buf(sm);
+    double *terms = stage_terms(sm);
     if (tid == 0) sm.ovl_flag = 0;
     double total = 0.0;
-    for (int c0 = 0; c0 < N; c0 += CHUNK) {
-        __syncthreads();
-        for (int jj = tid; jj < CHUNK; jj += T) {
-            const int j = c0 + jj;
-            double t = 0.0;
+    for (int j0 = 0; j0 < N; j0 += GSTAGE) {
+        stage_positions(sm, c, k, j0);
+        for (int u = 0; u < GSTAGE / T; ++u) {
+            const int t = u * T + tid;
+            const int j = j0 + t;
+            const float4 y = buf[t];
+            double v = 0.0;
             if (j < N && j != i) {
                 bool o;
-                t = term_fp64(a, b, position_of(sm, c, k, j), o, c.ch->sig2);
+                v = term_fp64(a, b, y, o, c.ch->sig2);
                 if (o) sm.ovl_flag = 1;
             }
-            sm.chunk[jj] = t;
+            terms[t] = v;
         }
         __syncthreads();
-        if (tid == 0) {
-            const int len = min(CHUNK, N - c0);
+        // each 1024-ion chunk is summed sequentially by its own thread (chunks are independent)
+        if (tid < GSTAGE / CHUNK) {
+            const int cb = j0 + tid * CHUNK;
             double s = 0.0;
-            for (int jj = 0; jj < len; ++jj)
-                if (c0 + jj != i) s = __dadd_rn(s, sm.chunk[jj]);
-            total = __dadd_rn(total, s);
+            if (cb < N) {
+                const int len = min(CHUNK, N - cb);
+                for (int jj = 0; jj < len; ++jj)
+                    if (cb + jj != i) s = __dadd_rn(s, terms[tid * CHUNK + jj]);
+            }
+            sm.redd[tid] = s;
         }
+        __syncthreads();
+        if (tid == 0)
+            for (int q = 0; q < GSTAGE / CHUNK; ++q)
+                if (j0 + q * CHUNK < N) total = __dadd_rn(total, sm.redd[q]);
     }
     __syncthreads();
     if (tid == 0) sm.redd[16] = __dmul_rn(__dmul_rn(c.ch->lB, (double)a.w), total);
@@ -454,6 +526,38 @@ __device__ __forceinline__ void ingroup_overlap(const Smem &sm, int k, const uns
     possible = p != 0;
 }
 
+// Partial sums of the decision rounds, two threads per move (half h of the
+// earlier moves j in [64h, 64h + 64)): corrections of ions accepted since the
+// last round (exact) and min/max sums over undecided ions (interval).  Uses
+// the snapshot words acc0/dec0 and the words seen by the last round.
+__device__ __forceinline__ void partial_pass(Smem &sm)
+{
+    const int tid = threadIdx.x;
+    const int k = tid & (S - 1), h = tid >> 7;
+    float sx = 0.f, lo = 0.f, hi = 0.f;
+    if (!bit(sm.dec0, k)) {
+        const int w0 = 2 * h, w1 = 2 * h + 1;
+        const unsigned na0 = sm.acc0[w0] & ~sm.seen[w0] & below(k, w0), na1 = sm.acc0[w1] & ~sm.seen[w1] & below(k, w1);
+        const unsigned un0 = ~sm.dec0[w0] & below(k, w0), un1 = ~sm.dec0[w1] & below(k, w1);
+        if (na0 | na1 | un0 | un1) {
+            const float *col = &sm.cin[(h * HALF) * CS + k];
+#pragma unroll
+            for (int jj = 0; jj < HALF; ++jj) {
+                const unsigned na = jj < 32 ? na0 : na1, un = jj < 32 ? un0 : un1;
+                const unsigned bm = 1u << (jj & 31);
+                const float cv = col[jj * CS];
+                sx += (na & bm) ? cv : 0.f;
+                lo += (un & bm) ? fminf(cv, 0.f) : 0.f;
+                hi += (un & bm) ? fmaxf(cv, 0.f) : 0.f;
+            }
+        }
+    }
+    sm.part[h][k] = sx;
+    sm.plo[h][k] = lo;
+    sm.phi[h][k] = hi;
+    __syncthreads();
+}
+
 // One work item: the S moves of group g of chain `tk.chain` at sweep s.
 __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, const Ticket tk, int ticket, Ctl *ctl)
 {
@@ -490,6 +594,9 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     const float lBf = (float)ch.lB;
     // phase timers (thread 0): SM cycles
     long long cyc_start = clock64(), cyc_tiles = 0, cyc_win = 0, cyc_guard = 0, cyc_res0 = 0;
+    long long cyc_t[3] = {0, 0, 0};
+    const unsigned long long gt_start = globaltimer();
+    unsigned long long gt_ready = 0, gt_window = 0, gt_resolved = 0, gt_pub = 0;
     int n_rounds = 0;
 
     // 1. own positions (version s-1) and, if active, the window's old positions (version sw-1)
@@ -606,6 +713,31 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         promote();
     }
 
+    // 2b'. interval sums of the corrections (threads < S: this group, threads >= S: the window);
+    // needs only the two passes above, so it runs before the tiles
+    __syncthreads();
+    {
+        const int k = tid & (S - 1), h = tid >> 7;
+        float lo = 0.f, hi = 0.f;
+        if (h == 0) {
+            for (int j = 0; j < k; ++j) {
+                const float cv = sm.cin[j * CS + k];
+                lo += fminf(cv, 0.f);
+                hi += fmaxf(cv, 0.f);
+            }
+            sm.lo_i[k] = lo;
+            sm.hi_i[k] = hi;
+        } else {
+            if (c.win)
+                for (int j = 0; j < c.nwk; ++j) {
+                    const float cv = sm.cwin[j * CS + k];
+                    lo += fminf(cv, 0.f);
+                    hi += fmaxf(cv, 0.f);
+                }
+            sm.lo_w[k] = lo;
+            sm.hi_w[k] = hi;
+        }
+    }
     // 2c. every other group, oldest published version first (Algorithm 2 per guest group):
     // J = g+1 .. B-1 (version s-1), then J = 0 .. g-1 (version s), the window excluded.
     auto tile_J = [&](int i) -> int {
@@ -716,30 +848,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     }
     __syncthreads();
 
-    // 3. per-move preparation: interval sums of the corrections (threads < S: this
-    // group, threads >= S: the window), overlap status, static band.
-    {
-        const int k = tid & (S - 1), h = tid >> 7;
-        float lo = 0.f, hi = 0.f;
-        if (h == 0) {
-            for (int j = 0; j < k; ++j) {
-                const float cv = sm.cin[j * CS + k];
-                lo += fminf(cv, 0.f);
-                hi += fmaxf(cv, 0.f);
-            }
-            sm.lo_i[k] = lo;
-            sm.hi_i[k] = hi;
-        } else {
-            if (c.win)
-                for (int j = 0; j < c.nwk; ++j) {
-                    const float cv = sm.cwin[j * CS + k];
-                    lo += fminf(cv, 0.f);
-                    hi += fmaxf(cv, 0.f);
-                }
-            sm.lo_w[k] = lo;
-            sm.hi_w[k] = hi;
-        }
-    }
+    // 3. per-move preparation: overlap status and static band.
     if (tid < S) {
         const int k = tid;
         unsigned stv = sm.st[k];
@@ -792,41 +901,50 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         }
     }
 
-    // 5. the window's outcome (the critical wait), then its exact correction sums
+    // 5. first in-group partial pass (needs only round 0's decisions), then the window's outcome (the
+    // critical wait) and its exact correction sums.
+    __syncthreads();
+    if (tid < WORDS) {
+        sm.acc0[tid] = sm.accw[tid];
+        sm.dec0[tid] = sm.decw[tid];
+    }
+    __syncthreads();
+    partial_pass(sm);
+    gt_ready = globaltimer();
     const long long cyc_w0 = clock64();
     if (c.win) {
         if (warp == 0) {
             unsigned bits;
             const int nw = (c.nwk + 31) / 32;
-            const bool ok = wait_words(ch, c.Jw, nw, (unsigned)(sw + 1), (unsigned)(sw + 1), ctl, bits);
+            const bool ok = wait_words(ch, c.Jw, nw, (unsigned)(sw + 1), (unsigned)(sw + 1), ctl, bits, false, true);
             if (lane < WORDS) sm.winacc[lane] = (lane < nw) ? bits : 0u;
             if (lane == 0) sm.ok = ok;
         }
         __syncthreads();
         if (!sm.ok) return false;
         cyc_win = clock64() - cyc_w0;
+        gt_window = globaltimer();
         {
             const int k = tid & (S - 1), h = tid >> 7;
             float sx = 0.f;
             const unsigned wa0 = sm.winacc[2 * h], wa1 = sm.winacc[2 * h + 1];
+            const float *col = &sm.cwin[(h * HALF) * CS + k];
 #pragma unroll 16
             for (int jj = 0; jj < HALF; ++jj) {
                 const unsigned wb = jj < 32 ? wa0 : wa1;
-                const float cv = sm.cwin[(h * HALF + jj) * CS + k];
+                const float cv = col[jj * CS];
                 sx += ((wb >> (jj & 31)) & 1u) ? cv : 0.f;
             }
-            sm.part[h][k] = sx;
+            sm.wpart[h][k] = sx;
         }
         __syncthreads();
         if (tid < S) {
             const int k = tid;
-            sm.wex[k] = sm.part[0][k] + sm.part[1][k];
+            sm.wex[k] = sm.wpart[0][k] + sm.wpart[1][k];
             unsigned wo = 0;  // the window's overlap is now exact
 #pragma unroll
             for (int w = 0; w < WORDS; ++w) wo |= (sm.wovn[k][w] & sm.winacc[w]) | (sm.wovo[k][w] & ~sm.winacc[w]);
-            unsigned stv = sm.st[k];
-            if (wo) stv |= ST_OVL_CERTAIN;
-            sm.st[k] = (unsigned char)stv;
+            if (wo) sm.st[k] = (unsigned char)(sm.st[k] | ST_OVL_CERTAIN);
         }
     }
     __syncthreads();
@@ -838,32 +956,6 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     cyc_res0 = clock64();
     for (;;) {
         ++n_rounds;
-        if (tid < WORDS) {
-            sm.acc0[tid] = sm.accw[tid];
-            sm.dec0[tid] = sm.decw[tid];
-        }
-        __syncthreads();
-        {  // partial sums over j in half h of [0, k)
-            const int k = tid & (S - 1), h = tid >> 7;
-            float sx = 0.f, lo = 0.f, hi = 0.f;
-            if (!bit(sm.dec0, k)) {
-                const int j0 = h * HALF, j1 = min(k, j0 + HALF);
-                for (int j = j0; j < j1; ++j) {
-                    const unsigned bm = 1u << (j & 31);
-                    const unsigned wd = sm.dec0[j >> 5], wa = sm.acc0[j >> 5], ws = sm.seen[j >> 5];
-                    const float cv = sm.cin[j * CS + k];
-                    if (wa & ~ws & bm) sx += cv;
-                    else if (!(wd & bm)) {
-                        lo += fminf(cv, 0.f);
-                        hi += fmaxf(cv, 0.f);
-                    }
-                }
-            }
-            sm.part[h][k] = sx;
-            sm.plo[h][k] = lo;
-            sm.phi[h][k] = hi;
-        }
-        __syncthreads();
         if (tid < S) {
             const int k = tid;
             int out = -1;
@@ -910,55 +1002,86 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         bool exact = true;  // were all predecessors of `first` decided when this round started?
 #pragma unroll
         for (int w = 0; w < WORDS; ++w) exact &= (~sm.dec0[w] & below(first, w)) == 0u;
-        if (!exact) continue;
-        // guard tiers on move k = first: exact FP32 value was inside its band (or overlap was ambiguous)
-        const long long cyc_g0 = clock64();
-        const int k = first;
-        const unsigned stv = sm.st[k];
-        const unsigned ua = move_draws(ch, s * (unsigned long long)N + (unsigned long long)(k0 + k), 0u).w >> 8;
-        const double L64 = (ua == 0u) ? 0.0 : -series_log((double)ua * 0x1p-24);
-        double dE = 0.0;
-        int res = -1, tier = 2;
-        if (!(stv & ST_OVL_AMBIG) && mode != 1) {
-            res = tier2(sm, c, k, L64, dE);
-            if (res < 0) {
-                tier = 3;
-                res = tier3(sm, c, k, L64, dE);
+        if (exact) {
+            // guard tiers on move k = first: exact FP32 value was inside its band (or overlap was ambiguous)
+            const long long cyc_g0 = clock64();
+            const int k = first;
+            const unsigned stv = sm.st[k];
+            const unsigned ua = move_draws(ch, s * (unsigned long long)N + (unsigned long long)(k0 + k), 0u).w >> 8;
+            const double L64 = (ua == 0u) ? 0.0 : -series_log((double)ua * 0x1p-24);
+            double dE = 0.0;
+            int res = -1, tier = 2;
+            if (!(stv & ST_OVL_AMBIG) && mode != 1) {
+                long long q0 = clock64();
+                res = tier2(sm, c, k, L64, dE);
+                cyc_t[0] += clock64() - q0;
+                if (res < 0) {
+                    tier = 3;
+                    q0 = clock64();
+                    res = tier3(sm, c, k, L64, dE);
+                    cyc_t[1] += clock64() - q0;
+                }
             }
+            if (res < 0) {
+                bool ovl = false;
+                tier = 4;
+                const long long q0 = clock64();
+                tier4(sm, c, k, dE, ovl);
+                cyc_t[2] += clock64() - q0;
+                if (ovl) res = 2;
+                else if (ua == 0u) res = 0;
+                else res = (dE < L64) ? 0 : 1;
+            }
+            if (tid == 0) {
+                const int out = res == 0 ? OUT_ACCEPT : (res == 1 ? OUT_METROPOLIS : OUT_OVERLAP);
+                sm.outcome[k] = (signed char)out;
+                sm.tier[k] = (unsigned char)tier;
+                sm.dEv[k] = dE;
+                sm.decw[k >> 5] |= 1u << (k & 31);
+                if (out == OUT_ACCEPT) sm.accw[k >> 5] |= 1u << (k & 31);
+            }
+            __syncthreads();
+            cyc_guard += clock64() - cyc_g0;
         }
-        if (res < 0) {
-            bool ovl = false;
-            tier = 4;
-            tier4(sm, c, k, dE, ovl);
-            if (ovl) res = 2;
-            else if (ua == 0u) res = 0;
-            else res = (dE < L64) ? 0 : 1;
-        }
-        if (tid == 0) {
-            const int out = res == 0 ? OUT_ACCEPT : (res == 1 ? OUT_METROPOLIS : OUT_OVERLAP);
-            sm.outcome[k] = (signed char)out;
-            sm.tier[k] = (unsigned char)tier;
-            sm.dEv[k] = dE;
-            sm.decw[k >> 5] |= 1u << (k & 31);
-            if (out == OUT_ACCEPT) sm.accw[k >> 5] |= 1u << (k & 31);
+        if (tid < WORDS) {
+            sm.acc0[tid] = sm.accw[tid];
+            sm.dec0[tid] = sm.decw[tid];
         }
         __syncthreads();
-        cyc_guard += clock64() - cyc_g0;
+        partial_pass(sm);
     }
     const long long cyc_resolve = clock64() - cyc_res0 - cyc_guard;
+    gt_resolved = globaltimer();
 
-    // 7. publish: final positions (version s), then the sweep-tagged words with the accept bits
+    // 7. publish: the outcome words first (the next group holds both candidate positions and needs only
+    // these bits), then the final positions (version s) and their release-stored words.
+    const bool publish = (long long)ticket != ctl->skip_ticket;
+    if (warp == 0 && publish && lane < (nk + 31) / 32)
+        st_relaxed(&ch.bits[g * WORDS + lane], ((unsigned long long)tag_cur << 32) | sm.accw[lane]);
+    gt_pub = globaltimer();
     if (tid < nk) {
         const bool acc = bit(sm.accw, tid);
         __stcg(&ch.pos[(s + 1) & 1][k0 + tid], acc ? sm.trial[tid] : sm.own[tid]);
     }
     __syncthreads();
-    const bool publish = (long long)ticket != ctl->skip_ticket;
-    if (tid == 0 && publish) {
-        __threadfence();
-        const int nw = (nk + 31) / 32;
-        for (int w = 0; w < nw; ++w)
-            st_release(&ch.flags[g * WORDS + w], ((unsigned long long)tag_cur << 32) | sm.accw[w]);
+    if (warp == 0 && publish && lane < (nk + 31) / 32)  // release after the barrier: orders every thread's stores
+        st_release(&ch.flags[g * WORDS + lane], ((unsigned long long)tag_cur << 32) | sm.accw[lane]);
+    const unsigned long long gt_posp = globaltimer();
+    if (tid == 0 && ch.trace) {
+        const unsigned long long item = s * (unsigned long long)B + (unsigned long long)g;
+        const unsigned long long idx = item - ch.rec_sweep0 * (unsigned long long)B;
+        if (item >= ch.rec_sweep0 * (unsigned long long)B && idx < (unsigned long long)ch.trace_cap) {
+            TraceRec tr;
+            tr.item = item;
+            tr.t_start = gt_start;
+            tr.t_ready = gt_ready;
+            tr.t_window = gt_window;
+            tr.t_resolved = gt_resolved;
+            tr.t_published = gt_pub;
+            tr.n_guard = (unsigned long long)(cyc_guard > 0);
+            tr.t_positions = gt_posp;
+            ch.trace[idx] = tr;
+        }
     }
 
     // 8. off the critical path: FP32 dE of every evaluated move, ledger, counters, records
@@ -1045,6 +1168,9 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             atomicAdd(&ch.stats[CNT_CYC_RESOLVE], (unsigned long long)cyc_resolve);
             atomicAdd(&ch.stats[CNT_CYC_GUARD], (unsigned long long)cyc_guard);
             atomicAdd(&ch.stats[CNT_CYC_TOTAL], (unsigned long long)(clock64() - cyc_start));
+            atomicAdd(&ch.stats[CNT_CYC_T2], (unsigned long long)cyc_t[0]);
+            atomicAdd(&ch.stats[CNT_CYC_T3], (unsigned long long)cyc_t[1]);
+            atomicAdd(&ch.stats[CNT_CYC_T4], (unsigned long long)cyc_t[2]);
         }
     }
     if (ch.rec && s >= ch.rec_sweep0 && tid < nk) {
