@@ -200,6 +200,24 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
 #define MC_OPT_USE_GRAPH 5
 int mc_set_option(mc_handle h, int option, int64_t value);
 
+/* Total energy l_B sum_{i<j} q_i q_j / r_ij of n ions WITHOUT allocating
+ * anything (no counterpart in the paper; an interface for callers that
+ * cannot allocate device memory while they run: code being captured into a
+ * CUDA graph, real-time loops that must not enter the allocator, hosts whose
+ * device memory belongs to a pool they may not bypass).
+ * pos_q_dev: device array of n float4 (x, y, z, valence), 16-byte aligned;
+ * energy_dev: device double receiving the result; stream: a cudaStream_t as
+ * void* (NULL = the default stream).  Same kernels and arithmetic as the
+ * recomputed energy of mc_energy (FP32 pair terms, FP64 row sums).
+ * The row sums live in one fixed device array of 1,048,576 doubles (8 MiB)
+ * that the library's module carries on every GPU that loads it, until the
+ * process exits; n > 1,048,576 returns MC_ERR_INVALID.  The first call on a
+ * device looks up the array's address with that device current: make it
+ * before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU race; every call rewrites the rows it reads, so nothing
+ * needs clearing.  The call only enqueues work on `stream`.                  */
+int mc_total_energy_noalloc(const void *pos_q_dev, int64_t n, double l_B, double *energy_dev, void *stream);
+
 /* Free all device and host memory of the handle. */
 void mc_destroy(mc_handle h);
 

@@ -83,6 +83,7 @@ def lib():
         "mc_device_info": ([vp, vp, vp, vp], ci),
         "mc_test_philox": ([vp, vp, i64, vp, vp], ci),
         "mc_test_log": ([vp, i64, vp], ci),
+        "mc_total_energy_noalloc": ([vp, i64, dbl, vp, vp], ci),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -443,6 +443,13 @@ int finish(mc_system *h)
 
 }  // namespace
 
+namespace mcg_host {
+int set_error(int code, const char *msg)
+{
+    return fail(code, "%s", msg);
+}
+}  // namespace mcg_host
+
 extern "C" {
 
 int mc_create(const float *pos_xyz, const float *q, int64_t n, double sigma, double l_B, double R, double half_width,

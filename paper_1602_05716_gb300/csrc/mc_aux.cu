@@ -3,6 +3,10 @@
 // test hooks for the Philox stream and the FP64 logarithm.
 #include <curand_kernel.h>
 
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/mc.h"
 #include "mc_device.cuh"
 
 namespace mcg {
@@ -153,3 +157,57 @@ cudaError_t log_test_launch(const double *u, int n, double *out, cudaStream_t st
 }
 
 }  // namespace mcg_host
+
+// ---------------------------------------------------------------------------
+// Allocation-free total energy (mc_total_energy_noalloc).  Some callers cannot
+// allocate device memory while they run: code inside a CUDA stream capture
+// (allocation calls are not capturable), real-time loops that must not block
+// in the allocator, and hosts whose device memory is owned by a pool they may
+// not bypass.  For them the row sums of the energy kernels live in one
+// file-scope device array instead of a per-handle buffer.  It is loaded with
+// the module, so every GPU that loads this library holds it until the process
+// exits.
+namespace mcg_host {
+int set_error(int code, const char *msg);
+}
+
+namespace {
+
+constexpr long long NOALLOC_MAX_IONS = 1ll << 20;  // 8 MiB of FP64 row sums
+static __device__ __align__(256) double g_noalloc_rows[NOALLOC_MAX_IONS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+}  // namespace
+
+extern "C" int mc_total_energy_noalloc(const void *pos_q_dev, int64_t n, double l_B, double *energy_dev, void *stream)
+{
+    if (!pos_q_dev || !energy_dev) return mcg_host::set_error(MC_ERR_INVALID, "NULL device pointer");
+    if (n < 1 || n > NOALLOC_MAX_IONS)
+        return mcg_host::set_error(MC_ERR_INVALID, "n out of range: the allocation-free energy handles 1..1048576 ions");
+    if (!(l_B >= 0.0) || l_B > 1.0e300) return mcg_host::set_error(MC_ERR_INVALID, "invalid l_B");
+    if ((reinterpret_cast<uintptr_t>(pos_q_dev) & 15u) || (reinterpret_cast<uintptr_t>(energy_dev) & 7u))
+        return mcg_host::set_error(MC_ERR_INVALID, "misaligned device pointer (positions need 16 bytes, energy 8)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return mcg_host::set_error(MC_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return mcg_host::set_error(MC_ERR_INVALID, "device ordinal too large");
+    double *rows = nullptr;
+    {
+        // set-up, once per device, with that device current: the array's device address
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_rows);
+            if (e != cudaSuccess || !ptr) return mcg_host::set_error(MC_ERR_CUDA, cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = static_cast<double *>(ptr);
+        }
+        rows = g_noalloc_ptr[dev];
+    }
+    e = mcg_host::energy_launch(static_cast<const float4 *>(pos_q_dev), (int)n, l_B, rows, energy_dev,
+                                static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return mcg_host::set_error(MC_ERR_CUDA, cudaGetErrorString(e));
+    return MC_OK;
+}
