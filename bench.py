@@ -53,17 +53,18 @@ def source_hash() -> str:
 
 
 def measured_traffic(workload: str):
-    """DRAM bytes per launch of the sweep kernel from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per step of the sweep kernel from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", f"sweep_kernel_{workload}.md")
     try:
         with open(path) as f:
-            data = json.load(f)
-    except (OSError, ValueError):
+            for line in f:
+                if line.startswith("traffic_bytes_per_step:"):
+                    parts = line.split()
+                    if parts[3] == source_hash():
+                        return int(parts[1])
+    except (OSError, ValueError, IndexError):
         return None
-    ent = data.get(workload)
-    if not ent or ent.get("source_hash") != source_hash():
-        return None
-    return ent.get("dram_bytes_per_step")
+    return None
 
 
 def peaks_file() -> dict:
