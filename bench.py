@@ -150,25 +150,44 @@ def reduce_max_sum(t_local: float, moves_local: float, world: int, device=None):
     return float(tt.item()), float(mm.item())
 
 
-def cpu_baseline(chain, min_seconds: float = 8.0, max_sweeps: int = 20, threads: int | None = None) -> dict:
-    """The FP64 oracle, as it stands, on the host cores: whole sweeps of the same starting configuration."""
+def cpu_baseline(chains, min_seconds: float = 8.0, max_sweeps: int = 20, threads: int | None = None) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: whole sweeps of the workload's chains (round-robin,
+    one sweep each in turn) from their initial configurations, until the time budget is spent."""
     import oracle
     threads = threads or os.cpu_count() or 1
-    oc = oracle.OracleChain.from_chain(chain, threads=threads)
+    ocs = [oracle.OracleChain.from_chain(c, threads=threads) for c in chains]
     t0 = time.perf_counter()
-    sweeps = 0
-    while sweeps < max_sweeps:
-        oc.sweep(1)
+    moves = pairs = sweeps = 0
+    k = 0
+    while sweeps < max_sweeps * len(chains):
+        c = chains[k % len(chains)]
+        ocs[k % len(chains)].sweep(1)
+        moves += c.n
+        pairs += c.pair_evals_per_sweep
         sweeps += 1
+        k += 1
         if time.perf_counter() - t0 >= min_seconds:
             break
     dt = time.perf_counter() - t0
-    moves = sweeps * chain.n
+    what = (f"the N={chains[0].n} chain" if len(chains) == 1 else
+            f"{min(sweeps, len(chains))} of the {len(chains)} chains in turn")
     return {"value": moves / dt, "unit": "moves/s", "cores": threads, "kind": "oracle",
-            "sample": f"{sweeps} full sweeps ({moves} moves, {sweeps * chain.pair_evals_per_sweep:.3g} pair-evals) of "
-                      f"the same N={chain.n} chain from its initial configuration, {dt:.2f} s wall, FP64 canonical "
-                      f"oracle with chunk-parallel sums on {threads} threads",
-            "pair_evals_per_s": sweeps * chain.pair_evals_per_sweep / dt}
+            "sample": f"{sweeps} full sweeps ({moves} moves, {pairs:.3g} pair-evals) of {what} from the initial "
+                      f"configuration, {dt:.2f} s wall, FP64 canonical oracle with chunk-parallel sums on "
+                      f"{threads} threads",
+            "pair_evals_per_s": pairs / dt}
+
+
+def replica_chains(chains, rank: int):
+    """Independent replicas: every rank runs the workload's chains with chain ids shifted by rank * len(chains)
+    (a new Philox key, hence an independent trajectory)."""
+    import copy
+    out = []
+    for c in chains:
+        d = copy.copy(c)
+        d.chain_id = c.chain_id + rank * len(chains)
+        out.append(d)
+    return out
 
 
 def run_reference(args):
@@ -216,22 +235,18 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pkg.build()
     wl = inputs.workload(args.workload)
-    base = wl.chains[0]
-    if len(wl.chains) != 1:
-        raise SystemExit("bench.py times single-chain workloads; use the batch benchmark for batches")
-    import copy
-    ch = copy.copy(base)
-    ch.chain_id = base.chain_id + rank  # independent replica per rank
+    chains = replica_chains(wl.chains, rank)
     sps = args.sweeps_per_step
-    n = ch.n
+    n = sum(c.n for c in chains)
     moves_per_step = n * sps
-    pairs_per_step = n * (n - 1) * sps
+    pairs_per_step = sum(c.n * (c.n - 1) for c in chains) * sps
 
     stream = torch.cuda.Stream()
     flush = torch.empty(max(1, args.flush_mb) * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
-        sysm = pkg.System([ch])
+        sysm = pkg.System(chains)
         sysm.set_stream(stream.cuda_stream)
+        tuned = sysm.autotune(2) if len(chains) > 1 else None
         for _ in range(args.warmup):
             flush.zero_()
             sysm.sweep_async(sps)
@@ -258,10 +273,11 @@ def run_ours(args):
                                         device=torch.device("cuda", local))
     if world > 1:
         torch.distributed.barrier()
-    stats = sysm.stats()
-    led, rec = sysm.energy()
+    stats = {k: sum(sysm.stats(i)[k] for i in range(len(chains))) for k in sysm.stats(0)}
+    energies = [sysm.energy(i) for i in range(len(chains))]
+    led, rec = energies[0]
     value = moves_total / t_max
-    pair_rate = value * (n - 1)
+    pair_rate = pairs_per_step * args.steps * (moves_total / (moves_per_step * args.steps)) / t_max
 
     # roofline of the dominant kernel (the persistent sweep kernel: one launch per step)
     info = pkg.device_info()
@@ -282,35 +298,46 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "N": n, "sweeps_per_step": sps,
-                       "sweeps_timed": sps * args.steps, "phi": ch.phi, "l_B": ch.l_B, "half_width": ch.half_width,
+            "config": {"workload": args.workload, "chains": len(chains), "N": n if len(chains) > 1 else chains[0].n,
+                       "sweeps_per_step": sps, "sweeps_timed": sps * args.steps,
+                       "phi": chains[0].phi if len(chains) == 1 else "U[0.01,0.30]",
+                       "l_B": chains[0].l_B if len(chains) == 1 else "U[0.5,2.0]",
+                       "half_width": chains[0].half_width,
                        "l2": f"flushed between steps ({args.flush_mb} MiB device write outside the timed events)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "autotune": tuned},
             "gpair_evals_per_s": pair_rate / 1e9,
             "roofline": roof,
             "clocks": csum,
             "gpu_launches": 2 * args.steps,
-            "accept_rate": stats["accepts"] / max(1, n * stats["sweeps"]),
-            "fp64_guard_per_move": stats["guard_fp64"] / max(1, n * stats["sweeps"]),
-            "interval_decided_per_move": stats["decided_interval"] / max(1, n * stats["sweeps"]),
-            "energy": {"ledger": led, "recomputed": rec, "drift": led - rec},
+            "accept_rate": stats["accepts"] / max(1, n * stats["sweeps"] // len(chains)),
+            "guard_per_move": stats["guard_fp64"] / max(1, n * stats["sweeps"] // len(chains)),
+            "guard_tiers_2_3_4": [stats["tier2"], stats["tier3"], stats["tier4"]],
+            "interval_decided_per_move": stats["decided_interval"] / max(1, n * stats["sweeps"] // len(chains)),
+            "energy": {"ledger": led, "recomputed": rec, "drift": led - rec,
+                       "max_abs_drift_over_chains": max(abs(a - b) for a, b in energies)},
             "wall_s": wall}
 
     # end to end through the C ABI with host buffers: upload positions, sweep, read positions + ledger back
     if not args.no_e2e:
         import ctypes
         L = pkg.lib()
-        host = torch.empty((n, 3), dtype=torch.float32).pin_memory()
-        host.copy_(torch.from_numpy(sysm.positions()))
+        hosts = []
+        for i in range(len(chains)):
+            hb = torch.empty((chains[i].n, 3), dtype=torch.float32).pin_memory()
+            hb.copy_(torch.from_numpy(sysm.positions(i)))
+            hosts.append(hb)
         led_h = ctypes.c_double()
         e2e_t = []
         for k in range(args.warmup + args.steps):
             stream.synchronize()
             t0 = time.perf_counter()
-            rc = L.mc_set_positions(sysm.handle, 0, ctypes.c_void_p(host.data_ptr()))
+            rc = 0
+            for i, hb in enumerate(hosts):
+                rc = rc or L.mc_set_positions(sysm.handle, i, ctypes.c_void_p(hb.data_ptr()))
             rc = rc or L.mc_sweep(sysm.handle, sps)
-            rc = rc or L.mc_get_positions(sysm.handle, 0, ctypes.c_void_p(host.data_ptr()))
-            rc = rc or L.mc_energy(sysm.handle, 0, ctypes.byref(led_h), None)
+            for i, hb in enumerate(hosts):
+                rc = rc or L.mc_get_positions(sysm.handle, i, ctypes.c_void_p(hb.data_ptr()))
+                rc = rc or L.mc_energy(sysm.handle, i, ctypes.byref(led_h), None)
             dt = time.perf_counter() - t0
             if rc:
                 raise RuntimeError(L.mc_last_error().decode())
@@ -318,14 +345,14 @@ def run_ours(args):
                 e2e_t.append(dt)
         t_e2e, mv = reduce_max_sum(sum(e2e_t), float(moves_per_step * args.steps), world,
                                    device=torch.device("cuda", local))
-        npad = ((n + 127) // 128) * 128
+        npad = sum(((c.n + 127) // 128) * 128 for c in chains)
         line["e2e"] = {"value": mv / t_e2e, "unit": "moves/s", "h2d_bytes_per_step": 16 * npad,
-                       "d2h_bytes_per_step": 16 * n + 8,
+                       "d2h_bytes_per_step": 16 * n + 8 * len(chains),
                        "path": "mc_set_positions(pinned host) + mc_sweep + mc_get_positions + mc_energy per step"}
         line["gpu_launches"] += 2 * args.steps
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(base, min_seconds=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(wl.chains, min_seconds=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -336,7 +363,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None, help="default: the workload's sweeps / sweeps-per-step")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain_n16383")
@@ -347,6 +374,9 @@ def main():
     ap.add_argument("--ref-moves-per-step", type=int, default=2048)
     ap.add_argument("--flush-mb", type=int, default=512)
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = {"plain_n256": 200, "plain_n16383": 50, "batch64": 20, "da_n65536": 10,
+                      "large_n1048576": 1}.get(args.workload, 50)
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("--steps >= 1, --warmup >= 0")
     if args.impl == "reference":

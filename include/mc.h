@@ -192,13 +192,25 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
  *  MC_OPT_SKIP_PUBLISH fault injection: the work item with this index never
  *                      publishes its result (waiters time out); -1 = off
  *  MC_OPT_USE_GRAPH    1 = capture each distinct sweep count in a CUDA graph
- *                      and replay it (default 1), 0 = plain launches        */
+ *                      and replay it (default 1), 0 = plain launches
+ *  MC_OPT_POLICY       order of the work items of a batch: 0 = one group of
+ *                      every chain in turn (default), 1 = sweep-synchronous */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3
 #define MC_OPT_SKIP_PUBLISH 4
 #define MC_OPT_USE_GRAPH 5
+#define MC_OPT_POLICY 6
 int mc_set_option(mc_handle h, int option, int64_t value);
+int mc_get_option(mc_handle h, int option, int64_t *value);
+
+/* Autotuner for batches: times trial_sweeps sweeps for every candidate work
+ * order (MC_OPT_POLICY) and persistent CTA count (all resident slots, 3/4,
+ * 1/2), keeps the fastest in the handle and restores every chain's state,
+ * so the trajectories are unchanged.  Outputs (nullable): the chosen policy,
+ * CTA count and its trial time in ms.  The paper tunes block size and
+ * threads per particle by hand (Sec. 4, Table Para).                        */
+int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t *best_ctas, double *best_ms);
 
 /* Total energy l_B sum_{i<j} q_i q_j / r_ij of n ions WITHOUT allocating
  * anything (no counterpart in the paper; an interface for callers that

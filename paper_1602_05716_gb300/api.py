@@ -9,7 +9,7 @@ import numpy as np
 from . import build as _build
 
 ERR_INVALID, ERR_OVERLAP_INIT, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_POISONED = -1, -2, -3, -4, -5, -6
-OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH = 1, 2, 3, 4, 5
+OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH, OPT_POLICY = 1, 2, 3, 4, 5, 6
 
 RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("dE", np.float64),
                          ("dE32", np.float64), ("scale", np.float64), ("tier", np.int32), ("pad", np.int32)])
@@ -78,6 +78,8 @@ def lib():
         "mc_trace_enable": ([vp, ci, i64], ci),
         "mc_trace_read": ([vp, ci, vp, i64], i64),
         "mc_set_option": ([vp, ci, i64], ci),
+        "mc_get_option": ([vp, ci, vp], ci),
+        "mc_autotune": ([vp, i64, vp, vp, vp], ci),
         "mc_destroy": ([vp], None),
         "mc_last_error": ([], ctypes.c_char_p),
         "mc_device_info": ([vp, vp, vp, vp], ci),
@@ -188,6 +190,16 @@ class System:
 
     def set_option(self, opt: int, value: int):
         _check(lib().mc_set_option(self._h, int(opt), int(value)))
+
+    def get_option(self, opt: int) -> int:
+        v = ctypes.c_int64()
+        _check(lib().mc_get_option(self._h, int(opt), ctypes.byref(v)))
+        return v.value
+
+    def autotune(self, trial_sweeps: int = 2) -> dict:
+        pol, ctas, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().mc_autotune(self._h, int(trial_sweeps), ctypes.byref(pol), ctypes.byref(ctas), ctypes.byref(ms)))
+        return dict(policy=pol.value, ctas=ctas.value, trial_ms=ms.value)
 
     def energy(self, chain: int = 0, recompute: bool = True):
         led = ctypes.c_double()

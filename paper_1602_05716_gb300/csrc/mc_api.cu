@@ -78,7 +78,11 @@ struct Chain {
 struct GraphKey {
     long long n;
     int grid;
-    bool operator<(const GraphKey &o) const { return n < o.n || (n == o.n && grid < o.grid); }
+    int policy;
+    bool operator<(const GraphKey &o) const
+    {
+        return n != o.n ? n < o.n : (grid != o.grid ? grid < o.grid : policy < o.policy);
+    }
 };
 
 }  // namespace
@@ -97,8 +101,9 @@ struct mc_system {
     int ctas_override = 0;
     long long skip_ticket = -1;
     int use_graph = 1;
+    int policy = 0;  // ticket order: 0 group round-robin over chains, 1 sweep-synchronous
     int sm_count = 0, occ = 0;
-    std::map<long long, std::pair<mcg::Ticket *, int>> scheds;  // n_sweeps -> device schedule
+    std::map<std::pair<long long, int>, std::pair<mcg::Ticket *, int>> scheds;  // (n_sweeps, policy) -> schedule
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
 
@@ -330,7 +335,7 @@ int create_common(const mc_chain_desc *descs, int n_chains, mc_handle *out)
 // groups in stream order (sweep-major, group-minor).
 int schedule_for(mc_system *h, long long n, mcg::Ticket **d, int *count)
 {
-    auto it = h->scheds.find(n);
+    auto it = h->scheds.find({n, h->policy});
     if (it != h->scheds.end()) {
         *d = it->second.first;
         *count = it->second.second;
@@ -344,16 +349,28 @@ int schedule_for(mc_system *h, long long n, mcg::Ticket **d, int *count)
     }
     if (total > (1ll << 31) - 1) return fail(MC_ERR_INVALID, "too many work items (%lld); sweep in smaller batches", total);
     t.reserve((size_t)total);
-    for (long long step = 0; step < longest; ++step)
-        for (size_t ci = 0; ci < h->chains.size(); ++ci) {
-            const Chain &c = h->chains[ci];
-            if (step < (long long)c.B * n)
-                t.push_back(mcg::Ticket{(int)ci, (int)(step % c.B), (int)(step / c.B), 0});
-        }
+    if (h->policy == 0) {
+        // one group of every chain in turn: every chain advances at the same rate in groups
+        for (long long step = 0; step < longest; ++step)
+            for (size_t ci = 0; ci < h->chains.size(); ++ci) {
+                const Chain &c = h->chains[ci];
+                if (step < (long long)c.B * n)
+                    t.push_back(mcg::Ticket{(int)ci, (int)(step % c.B), (int)(step / c.B), 0});
+            }
+    } else {
+        // sweep-synchronous: all chains' sweep s before sweep s + 1, groups interleaved within a sweep, so
+        // large chains (more groups per sweep) get proportionally more work items early
+        int maxB = 0;
+        for (auto &c : h->chains) maxB = std::max(maxB, c.B);
+        for (long long sw = 0; sw < n; ++sw)
+            for (int g = 0; g < maxB; ++g)
+                for (size_t ci = 0; ci < h->chains.size(); ++ci)
+                    if (g < h->chains[ci].B) t.push_back(mcg::Ticket{(int)ci, g, (int)sw, 0});
+    }
     mcg::Ticket *dp = nullptr;
     CK(cudaMalloc(&dp, sizeof(mcg::Ticket) * t.size()));
     CK(cudaMemcpy(dp, t.data(), sizeof(mcg::Ticket) * t.size(), cudaMemcpyHostToDevice));
-    h->scheds[n] = {dp, (int)t.size()};
+    h->scheds[{n, h->policy}] = {dp, (int)t.size()};
     *d = dp;
     *count = (int)t.size();
     return MC_OK;
@@ -378,7 +395,7 @@ int enqueue_sweeps(mc_system *h, long long n)
     const int grid = grid_for(h);
     const int nch = (int)h->chains.size();
     if (h->use_graph) {
-        GraphKey key{n, grid};
+        GraphKey key{n, grid, h->policy};
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             cudaGraph_t g = nullptr;
@@ -751,6 +768,10 @@ static int set_option(mc_handle h, int option, int64_t value)
     case MC_OPT_USE_GRAPH:
         h->use_graph = value ? 1 : 0;
         return MC_OK;
+    case MC_OPT_POLICY:
+        if (value < 0 || value > 1) return fail(MC_ERR_INVALID, "policy %lld", (long long)value);
+        h->policy = (int)value;
+        return MC_OK;
     default:
         return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
@@ -764,6 +785,86 @@ int mc_set_option(mc_handle h, int option, int64_t value)
     rc = set_option(h, option, value);
     write_ctl(h);
     return rc;
+}
+
+int mc_get_option(mc_handle h, int option, int64_t *value)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!value) return fail(MC_ERR_INVALID, "NULL output");
+    switch (option) {
+    case MC_OPT_GUARD_MODE: *value = h->guard_mode; return MC_OK;
+    case MC_OPT_TIMEOUT_MS: *value = h->timeout_ms; return MC_OK;
+    case MC_OPT_CTAS: *value = h->ctas_override > 0 ? h->ctas_override : grid_for(h); return MC_OK;
+    case MC_OPT_SKIP_PUBLISH: *value = h->skip_ticket; return MC_OK;
+    case MC_OPT_USE_GRAPH: *value = h->use_graph; return MC_OK;
+    case MC_OPT_POLICY: *value = h->policy; return MC_OK;
+    default: return fail(MC_ERR_INVALID, "unknown option %d", option);
+    }
+}
+
+// Autotuner: time trial launches of every candidate (ticket order x CTA count)
+// on a saved copy of every chain's state, keep the fastest, restore the state.
+int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t *best_ctas, double *best_ms)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (trial_sweeps < 1) return fail(MC_ERR_INVALID, "trial_sweeps < 1");
+    CK(cudaStreamSynchronize(h->stream));
+    // save
+    struct Saved {
+        std::vector<float> pos;
+        uint64_t sweeps;
+        double ledger;
+        mc_stats_t st;
+    };
+    std::vector<Saved> saved(h->chains.size());
+    for (size_t i = 0; i < h->chains.size(); ++i) {
+        saved[i].pos.resize((size_t)h->chains[i].N * 3);
+        rc = mc_get_state(h, (int)i, saved[i].pos.data(), &saved[i].sweeps, &saved[i].ledger, &saved[i].st);
+        if (rc) return rc;
+    }
+    const int full = std::max(1, grid_for(h));
+    const int old_policy = h->policy, old_ctas = h->ctas_override;
+    std::vector<int> ctas = {full, std::max(1, (3 * full) / 4), std::max(1, full / 2)};
+    double best = 1e300;
+    int bp = old_policy, bc = old_ctas;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int pol = 0; pol < 2 && rc == 0; ++pol)
+        for (int nc : ctas) {
+            h->policy = pol;
+            h->ctas_override = nc;
+            rc = enqueue_sweeps(h, 1);  // warm: schedule and graph built outside the timing
+            if (!rc) rc = finish(h);
+            if (rc) break;
+            cudaEventRecord(e0, h->stream);
+            rc = enqueue_sweeps(h, trial_sweeps);
+            cudaEventRecord(e1, h->stream);
+            if (!rc) rc = finish(h);
+            if (rc) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bp = pol;
+                bc = nc == full ? 0 : nc;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->policy = bp;
+    h->ctas_override = bc;
+    if (rc) return rc;
+    for (size_t i = 0; i < h->chains.size(); ++i) {
+        rc = mc_set_state(h, (int)i, saved[i].pos.data(), saved[i].sweeps, saved[i].ledger, &saved[i].st);
+        if (rc) return rc;
+    }
+    if (best_policy) *best_policy = bp;
+    if (best_ctas) *best_ctas = bc == 0 ? full : bc;
+    if (best_ms) *best_ms = best;
+    return MC_OK;
 }
 
 void mc_destroy(mc_handle h)

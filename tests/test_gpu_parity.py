@@ -234,3 +234,34 @@ def test_create_rejects_invalid(pkg):
     with pytest.raises(p.MCError) as ei:
         p.System.single(np.zeros((1, 3), np.float32), np.ones(1, np.float32), -1.0, 0.7, 3.0, 0.5, 0)
     assert ei.value.code == p.ERR_INVALID
+
+
+def test_autotune_keeps_trajectories(pkg):
+    """The autotuner runs trial sweeps on saved state and restores it: the chains continue exactly as an
+    untuned handle does (and as the oracle does)."""
+    import paper_1602_05716_gb300 as p
+    chains = [inputs.small_chain(n, phi=0.15, seed=300 + n, two_one=(n % 2 == 0), chain_id=k)
+              for k, n in enumerate([200, 700, 129])]
+    tuned = p.System(chains)
+    tuned.sweep(2)
+    info = tuned.autotune(2)
+    assert info["policy"] in (0, 1) and info["ctas"] >= 1
+    tuned.sweep(3)
+    for k, ch in enumerate(chains):
+        o = oracle.OracleChain.from_chain(ch)
+        o.sweep(5)
+        assert (tuned.positions(k) == o.positions()).all()
+        assert tuned.stats(k)["sweeps"] == 5
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_batch_policies_equal(pkg, policy):
+    import paper_1602_05716_gb300 as p
+    chains = [inputs.small_chain(n, phi=0.15, seed=400 + n, chain_id=k) for k, n in enumerate([256, 1000, 64])]
+    s = p.System(chains)
+    s.set_option(p.OPT_POLICY, policy)
+    s.sweep(3)
+    for k, ch in enumerate(chains):
+        o = oracle.OracleChain.from_chain(ch)
+        o.sweep(3)
+        assert (s.positions(k) == o.positions()).all()
