@@ -147,6 +147,7 @@ typedef struct {
     double dE;       /* l_B q_i sum_j q_j (1/r' - 1/r) in k_B T; NaN if not evaluated */
     float a[3];      /* trial position */
     float pad;
+    double scale;    /* l_B |q_i| sum_{j != i} |q_j| (1/r' + 1/r): the scale of the FP32 tolerance; NaN if not evaluated */
 } mco_record;
 
 typedef struct {
@@ -357,6 +358,23 @@ static double canonical_sum(mco_chain *c, int64_t i, const float a[3], const flo
     return total;
 }
 
+/* Scale of the per-move dE tolerance, l_B |q_i| sum_{j != i} |q_j| (1/r' + 1/r),
+ * over the same positions as chunk_terms (FP64, sequential).  Only filled in
+ * records; the decision never reads it.                                     */
+static double move_scale(const mco_chain *c, int64_t i, const float a[3], const float b[3])
+{
+    double s = 0.0;
+    for (int64_t j = 0; j < c->n; ++j) {
+        if (j == i) continue;
+        const float *y = c->x + 3 * j;
+        double dxn = (double)a[0] - (double)y[0], dyn = (double)a[1] - (double)y[1], dzn = (double)a[2] - (double)y[2];
+        double dxo = (double)b[0] - (double)y[0], dyo = (double)b[1] - (double)y[1], dzo = (double)b[2] - (double)y[2];
+        double rn = sqrt((dxn * dxn + dyn * dyn) + dzn * dzn), ro = sqrt((dxo * dxo + dyo * dyo) + dzo * dzo);
+        s += fabs(c->q[j]) * (1.0 / rn + 1.0 / ro);
+    }
+    return c->lB * fabs(c->q[i]) * s;
+}
+
 /* Trial position of move m for ion i (Algorithm 1 with reading R2). Returns
  * the acceptance draw's integer (w3 >> 8).                                   */
 static uint32_t trial(const mco_chain *c, uint64_t m, int64_t i, float a[3])
@@ -424,6 +442,7 @@ static void one_move(mco_chain *c, uint64_t s, int64_t i)
         r->a[1] = a[1];
         r->a[2] = a[2];
         r->pad = 0.0f;
+        r->scale = isnan(dE) ? NAN : move_scale(c, i, a, b);
     }
 }
 

@@ -14,7 +14,7 @@ _LIB = None
 ACCEPT, REJECT_METROPOLIS, REJECT_OVERLAP, REJECT_WALL = 0, 1, 2, 3
 
 RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("dE", np.float64),
-                         ("a", np.float32, (3,)), ("pad", np.float32)])
+                         ("a", np.float32, (3,)), ("pad", np.float32), ("scale", np.float64)])
 
 
 def build() -> str:

@@ -124,6 +124,35 @@ def test_delta_e_is_energy_difference(n, two_one):
     assert checked > 10
 
 
+def test_record_scale_replays_by_brute_force():
+    """The tolerance scale of each record, l_B |q_i| sum_j |q_j| (1/r' + 1/r), equals numpy's on positions
+    rebuilt by replaying the recorded outcomes in order (Sec. 2: j < i already moved); |dE| <= scale."""
+    ch = inputs.small_chain(150, phi=0.1, seed=11, two_one=True)
+    oc = oracle.OracleChain.from_chain(ch)
+    oc.record(2 * ch.n)
+    oc.sweep(2)
+    pos = ch.pos.astype(np.float64).copy()
+    seen = 0
+    for r in oc.records():
+        i = int(r["i"])
+        a = r["a"].astype(np.float64)
+        if r["outcome"] in (oracle.ACCEPT, oracle.REJECT_METROPOLIS):
+            mask = np.arange(ch.n) != i
+            dn = np.sqrt(((a - pos[mask]) ** 2).sum(-1))
+            do = np.sqrt(((pos[i] - pos[mask]) ** 2).sum(-1))
+            q = ch.q.astype(np.float64)
+            ref = float(ch.l_B) * abs(q[i]) * float((np.abs(q[mask]) * (1 / dn + 1 / do)).sum())
+            assert abs(r["scale"] - ref) <= 1e-12 * ref
+            assert abs(r["dE"]) <= r["scale"]
+            seen += 1
+        else:
+            assert np.isnan(r["scale"])
+        if r["outcome"] == oracle.ACCEPT:
+            pos[i] = a
+    assert seen > 60
+    assert (pos.astype(np.float32) == oc.positions()).all()
+
+
 def test_total_energy_matches_numpy():
     ch = inputs.small_chain(300, phi=0.2, seed=5, two_one=True)
     assert abs(oracle.total_energy(ch.pos, ch.q, ch.l_B) - _numpy_energy(ch.pos, ch.q, ch.l_B)) < 1e-10
