@@ -93,7 +93,8 @@ typedef struct {
     int32_t outcome; /* 0 accept, 1 Metropolis reject, 2 overlap, 3 wall */
     double dE;      /* dE used for the ledger / decision (FP64 value when tier == 4); NaN if not evaluated */
     double dE32;    /* dE from the FP32 pair sums (NaN when not evaluated) */
-    double scale;   /* l_B |q_i| sum_j |q_j| (1/r' + 1/r): the error-bound scale */
+    double bound;   /* proven bound of |dE32 - dE_FP64| apart from a relative 2^-20 |dE| (the static band of
+                       the FP32 decision); +inf when a guard mode disabled the band */
     int32_t tier;   /* 0 decided from an interval, 1 from the exact FP32 sum, 2 accurate FP32, 3 double-single,
                        4 the FP64 recomputation */
     int32_t pad;

@@ -12,7 +12,7 @@ ERR_INVALID, ERR_OVERLAP_INIT, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_POISONED = -1
 OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH, OPT_POLICY = 1, 2, 3, 4, 5, 6
 
 RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("dE", np.float64),
-                         ("dE32", np.float64), ("scale", np.float64), ("tier", np.int32), ("pad", np.int32)])
+                         ("dE32", np.float64), ("bound", np.float64), ("tier", np.int32), ("pad", np.int32)])
 
 TRACE_DTYPE = np.dtype([("item", np.uint64), ("t_start", np.uint64), ("t_ready", np.uint64),
                         ("t_window", np.uint64), ("t_resolved", np.uint64), ("t_published", np.uint64),

@@ -196,6 +196,9 @@ mcg::ChainDev describe(const Chain &c)
     // s2 (1 -/+ 2^-19) the FP32 comparison already agrees with FP64.
     d.sig2_lo = std::nextafter((float)(s2 * (1.0 - 0x1p-19)), 0.0f);
     d.sig2_hi = std::nextafter((float)(s2 * (1.0 + 0x1p-19)), 3.0e38f);
+    double qabs = 0.0;
+    for (float v : c.q) qabs += std::fabs((double)v);
+    d.a_max = (float)(2.0 * qabs / (c.sigma * (1.0 - 0x1p-17)) * (1.0 + 0x1p-20));
     d.lB = c.lB;
     const double Rc = c.R - 0.5 * c.sigma;
     d.Rc2 = Rc * Rc;

@@ -36,7 +36,7 @@ struct MoveRec {
     int outcome;
     double dE;
     double dE32;
-    double scale;
+    double bound;  // proven FP32 error bound of dE32 (static part), +inf when the band was disabled
     int tier;
     int pad;
 };
@@ -70,7 +70,7 @@ struct ChainDev {
     float D;                      // fl32(2h)
     float sig2_lo;                // FP32 squared distances below this certainly overlap
     float sig2_hi;                // ... above this certainly do not; in between FP64 decides
-    float pad_f;
+    float a_max;                  // 2 sum_j |q_j| / sigma: bounds sum_j |q_j| (1/r' + 1/r) of a valid move
     double sig2;                  // sigma^2
     double lB;                    // Bjerrum length
     double Rc2;                   // (R - sigma/2)^2
@@ -220,6 +220,22 @@ __device__ __forceinline__ float rcp_approx(float x)
 {
     float r;
     asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Flush-to-zero forms for the pair loop: the same accuracy on normal inputs
+// (inverse distances of ions at least sigma apart inside a finite sphere).
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 

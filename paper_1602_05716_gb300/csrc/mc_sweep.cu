@@ -14,10 +14,12 @@
 //    parity) and then, per 32 ions, a release-stored word
 //    ((sweep+1) << 32 | accept bits).  Readers acquire the word.  Tags only
 //    grow, so no reset is needed (Algorithm 5's BlockState must be cleared).
-//  * A CTA computes its S moves' pair sums (FP32, rsqrt.approx) against every
-//    other group's published positions, tile by tile, oldest version first
-//    (the brush of Algorithm 2), polling the next tiles' flags with relaxed
-//    loads and prefetching their positions into registers.
+//  * A CTA computes its S moves' pair sums against every other group's
+//    published positions, tile by tile, oldest version first (the brush of
+//    Algorithm 2), polling the next tiles' flags with relaxed loads and
+//    prefetching their positions into registers.  Pairs with settled ions use
+//    a cancellation-free FP32 form (error proportional to the displacement over
+//    r^2), so the FP32 band stays narrow as N grows.
 //  * The group just before this one (the "window") and this group's own
 //    earlier moves (the lower triangle of Algorithms 3 and 4) are computed for
 //    both possible positions of each such ion; the corrections
@@ -49,7 +51,7 @@ struct __align__(16) Smem {
     float cin[S * CS];   // c[j][k], j < k, this group
     float cwin[S * CS];  // c[j][k], window ion j
     float bhi[S], blo[S];  // sum of terms with known positions (float-float)
-    float Ab[S], Tb[S], TCb[S], mind2[S];
+    float Ab[S], Tb[S], TCb[S], Pb[S], mind2[S];  // Ab: both-position ions only; Pb: settled ions
     float lo_w[S], hi_w[S], lo_i[S], hi_i[S];
     float Lf[S];   // -ln(u_acc) in FP32 (+inf if u_acc == 0)
     float bnd[S];  // static part of the FP32 band
@@ -72,7 +74,7 @@ struct __align__(16) Smem {
     double redd[32];
     float redf[32];
     int ticket, ok, guard_k, ovl_flag;
-    int rdy[2];
+    int hzs[2];
     int pad1[2];
 };
 
@@ -83,6 +85,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // Bound constants (units of u = 2^-24); the derivation is in DESIGN.md ("FP32 error bound").
 constexpr float U32 = 0x1p-24f;
 constexpr float C_TERM = 10.0f;           // per-term error of q_j (1/r' - 1/r) relative to |q_j| (1/r' + 1/r)
+                                          // (both-position ions, direct form)
 constexpr float C_SUM = 24.0f;            // FP32 partials of <= 16 terms, TwoSum-accumulated
 constexpr float C_CORR = 2.0f * (S + 8);  // FP32 sums and interval sums of <= S corrections
 
@@ -142,22 +145,47 @@ __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsig
     }
 }
 
-// FP32 pair term of move (a = trial, b = old) against y:
-// t = q_y (1/|a-y| - 1/|b-y|) accumulated into s; |q| (1/r' + 1/r) into A;
-// |t| into Tt; |a-y|^2 into the running minimum mn.
-__device__ __forceinline__ void pair_acc(const float4 a, const float4 b, const float4 y, float &s, float &A, float &Tt,
+// Accurate FP32 pair term of move (old b, displacement d = a - b) against an ion y whose position is
+// settled for this move (every other group's tile, and the later ions of this group).  With e = y - b,
+// q_y (1/|a-y| - 1/|b-y|) = q_y Dd (rn ro)^2 / (rn + ro) where Dd = d . (2e - d) = |b-y|^2 - |a-y|^2: no
+// difference of two nearly equal inverse distances, so the rounding error scales with |d| / r^2 instead
+// of 1/r and the FP32 band stays narrow at large N.  Accumulates the term into s, |term| into Tt,
+// |q_y| rn ro into P (the bound's second sum) and the trial's squared distance into the minimum mn.
+__device__ __forceinline__ void pair_far(const float3 b, const float3 d, const float4 y, float &s, float &Tt, float &P,
                                          float &mn)
 {
-    const float dxn = a.x - y.x, dyn = a.y - y.y, dzn = a.z - y.z;
-    const float d2n = fmaf(dzn, dzn, fmaf(dyn, dyn, dxn * dxn));
-    const float dxo = b.x - y.x, dyo = b.y - y.y, dzo = b.z - y.z;
-    const float d2o = fmaf(dzo, dzo, fmaf(dyo, dyo, dxo * dxo));
-    const float rn = rsqrt_approx(d2n), ro = rsqrt_approx(d2o);
-    const float diff = rn - ro;
-    s = fmaf(y.w, diff, s);
-    A = fmaf(fabsf(y.w), rn + ro, A);
-    Tt = fmaf(fabsf(y.w), fabsf(diff), Tt);
-    mn = fminf(mn, d2n);
+    const float ex = y.x - b.x, ey = y.y - b.y, ez = y.z - b.z;
+    const float Do = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+    const float wx = fmaf(2.0f, ex, -d.x), wy = fmaf(2.0f, ey, -d.y), wz = fmaf(2.0f, ez, -d.z);
+    const float Dd = fmaf(d.z, wz, fmaf(d.y, wy, d.x * wx));
+    const float Dn = Do - Dd;
+    const float ro = rsqrt_ftz(Do), rn = rsqrt_ftz(Dn);
+    const float pr = rn * ro;
+    const float t = (Dd * pr) * (pr * rcp_ftz(rn + ro));
+    s = fmaf(y.w, t, s);
+    Tt = fmaf(fabsf(y.w), fabsf(t), Tt);
+    P = fmaf(fabsf(y.w), pr, P);
+    mn = fminf(mn, Dn);
+}
+
+// Bound coefficients of pair_far for a move of length at most dn when every settled ion is at least sp from
+// both the old and the trial position (x = dn / sp).  Following tier 2's per-term bound with
+// Ro <= Rn + dn, M <= dn (Rn + Ro) and rho >= (1 - x/2) min(Rn, Ro):
+//   per term  |err| <= u |q| (kT |t| + kP rn ro),   kT = kD + 20,  kP = (4 + k3) dn,
+//   kD = 3 (1+x)^2 + 4 (2x + x^2) + 1,   k3 = (1+x) (3/g^2 + 2x/g^3),  g = 1 - x/2;
+// the squared distance Dn is within u kO max(Dn, sigma^2) of |a - y|^2, kO = 5 (1+x)^2 + 14x + 8x^2 + 1.
+// Returns false for x >= 1.75, where the move is left to the FP64 tier.
+__device__ __forceinline__ bool far_coeffs(float dn, float sp, float &kT, float &kP, float &kO)
+{
+    const float x = dn / sp * (1.0f + 0x1p-20f);
+    if (!(x < 1.75f)) return false;
+    const float x1 = 1.0f + x, g = 1.0f - 0.5f * x;
+    const float kD = 3.0f * x1 * x1 + 4.0f * x * (2.0f + x) + 1.0f;
+    const float k3 = x1 * (3.0f / (g * g) + 2.0f * x / (g * g * g));
+    kT = (kD + 20.0f) * (1.0f + 0x1p-10f);
+    kP = (4.0f + k3) * dn * (1.0f + 0x1p-10f);
+    kO = (5.0f * x1 * x1 + x * (14.0f + 8.0f * x) + 1.0f) * (1.0f + 0x1p-4f);
+    return true;
 }
 
 __device__ __forceinline__ float pair_term(const float4 a, const float4 b, const float4 y, float &Ay, float &d2n)
@@ -590,6 +618,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     }
     const float lo2 = ch.sig2_lo, hi2 = ch.sig2_hi;
     const double sig2 = ch.sig2;
+    const float s2f = (float)sig2;
+    const float sp = sqrtf(s2f) * (1.0f - 0x1p-17f);  // settled ions of a valid move are at least this far
     const int mode = ctl->guard_mode;
     const float lBf = (float)ch.lB;
     // phase timers (thread 0): SM cycles
@@ -667,12 +697,15 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     // 2. pair sums.  Thread (p, r): moves p + 32 m (m = 0..3), column slice r of 8.
     const int p = tid / SL, r = tid % SL;
     float4 a[MPT], b[MPT];
-    float sA[MPT], hA[MPT], lA[MPT], AA[MPT], TA[MPT], CA[MPT], mA[MPT];
+    float3 b3[MPT], d3[MPT];
+    float sA[MPT], hA[MPT], lA[MPT], AA[MPT], TA[MPT], CA[MPT], PA[MPT], mA[MPT];
 #pragma unroll
     for (int m = 0; m < MPT; ++m) {
         a[m] = sm.trial[p + 32 * m];
         b[m] = sm.own[p + 32 * m];
-        sA[m] = hA[m] = lA[m] = AA[m] = TA[m] = CA[m] = 0.f;
+        b3[m] = make_float3(b[m].x, b[m].y, b[m].z);
+        d3[m] = make_float3(a[m].x - b[m].x, a[m].y - b[m].y, a[m].z - b[m].z);
+        sA[m] = hA[m] = lA[m] = AA[m] = TA[m] = CA[m] = PA[m] = 0.f;
         mA[m] = finf();
     }
     auto promote = [&]() {
@@ -693,7 +726,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         for (int m = 0; m < MPT; ++m) {
             const int k = p + 32 * m;
             if (k >= nk || j == k) continue;
-            if (j > k) pair_acc(a[m], b[m], yo, sA[m], AA[m], TA[m], mA[m]);
+            if (j > k) pair_far(b3[m], d3[m], yo, sA[m], TA[m], PA[m], mA[m]);
             else both_pair(sm.cin, sm.ovo, sm.ovn, k, j, a[m], b[m], yo, yn, sA[m], AA[m], TA[m], CA[m], lo2, hi2, sig2);
         }
     }
@@ -749,72 +782,79 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     auto tile_tag = [&](int J) -> unsigned { return J > g ? tag_prev : tag_cur; };
     auto tile_src = [&](int J) -> const float4 * { return (J > g ? c.Pprev : c.Pcur) + (size_t)J * S; };
     auto tile_words = [&](int J) -> int { return (min(S, N - J * S) + 31) / 32; };
+    const long long cyc_t0 = clock64();
+    // Publication horizon: tiles 0..hz are known to be published and covered by an acquire fence.  Warp 0
+    // polls word 0 of the next 32 tiles (one relaxed load per lane); a single fence covers every newly
+    // confirmed tile, so old versions cost no per-tile synchronisation.  The horizon lives in two slots:
+    // iteration i reads slot i&1 (written before the barrier that ended iteration i-1) and warp 0 writes
+    // slot (i+1)&1, so every thread of an iteration sees the same value.
+    auto advance_horizon = [&](int from) -> int {  // warp 0, all lanes; returns the new horizon
+        const int t = from + 1 + lane;
+        bool ready = false;
+        if (t < ntl) {
+            const int J = tile_J(t);
+            ready = (unsigned)(ld_relaxed(&ch.flags[J * WORDS]) >> 32) == tile_tag(J);
+        }
+        const unsigned bal = __ballot_sync(FULL, ready);
+        const int run = __ffs(~bal) - 1;  // consecutive ready tiles after `from` (-1: all 32)
+        const int hz = min((run < 0) ? from + 32 : from + run, ntl - 1);
+        if (hz > from) fence_acq_rel();
+        return hz;
+    };
     if (ntl > 0) {
-        const int J0 = tile_J(0);
         if (warp == 0) {
-            unsigned bits;
-            const bool ok = wait_words(ch, J0, tile_words(J0), tile_tag(J0), tile_tag(J0), ctl, bits);
-            if (lane == 0) sm.ok = ok;
+            int hz0 = advance_horizon(-1);
+            bool ok = true;
+            if (hz0 < 0) {  // the oldest tile is not published yet: wait for it
+                const int J0 = tile_J(0);
+                unsigned bits;
+                ok = wait_words(ch, J0, tile_words(J0), tile_tag(J0), tile_tag(J0), ctl, bits);
+                hz0 = 0;
+            }
+            if (lane == 0) {
+                sm.ok = ok;
+                sm.hzs[0] = hz0;
+            }
         }
         __syncthreads();
         if (!sm.ok) return false;
-        if (tid < S) sm.tile[0][tid] = __ldcg(&tile_src(J0)[tid]);
-        if (warp == 0) {  // is tile 1 published already?
-            bool ok = false;
-            if (ntl > 1) {
-                const int J1 = tile_J(1);
-                const int nw = tile_words(J1);
-                bool mine = true;
-                if (lane < nw) mine = (unsigned)(ld_relaxed(&ch.flags[J1 * WORDS + lane]) >> 32) == tile_tag(J1);
-                ok = __all_sync(FULL, mine);
-            }
-            if (lane == 0) {
-                if (ok) fence_acq_rel();
-                sm.rdy[1] = ok;
-            }
-        }
+        if (tid < S) sm.tile[0][tid] = __ldcg(&tile_src(tile_J(0))[tid]);
         __syncthreads();
     }
-    const long long cyc_t0 = clock64();
-    int Jn = ntl > 1 ? tile_J(1) : -1;   // tile i+1
-    int Jnn = ntl > 2 ? tile_J(2) : -1;  // tile i+2
     for (int i = 0; i < ntl; ++i) {
         const int cur = i & 1;
-        const bool pf = (i + 1 < ntl) && sm.rdy[(i + 1) & 1];
+        const int hz = sm.hzs[i & 1];
+        const bool pf = (i + 1 < ntl) && (i + 1 <= hz);
+        const int Jn = (i + 1 < ntl) ? tile_J(i + 1) : -1;
         float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
         if (pf && tid < S) pre = __ldcg(&tile_src(Jn)[tid]);
-        unsigned long long pv = 0;
-        const int nwnn = (Jnn >= 0) ? tile_words(Jnn) : 0;
-        if (warp == 0 && lane < nwnn) pv = ld_relaxed(&ch.flags[Jnn * WORDS + lane]);
 #pragma unroll 4
         for (int jj = 0; jj < S / SL; ++jj) {
             const float4 y = sm.tile[cur][jj * SL + r];
 #pragma unroll
-            for (int m = 0; m < MPT; ++m) pair_acc(a[m], b[m], y, sA[m], AA[m], TA[m], mA[m]);
+            for (int m = 0; m < MPT; ++m) pair_far(b3[m], d3[m], y, sA[m], TA[m], PA[m], mA[m]);
         }
         promote();
         if (pf && tid < S) sm.tile[cur ^ 1][tid] = pre;
-        if (warp == 0 && Jnn >= 0) {
-            const bool ok = __all_sync(FULL, lane >= nwnn || (unsigned)(pv >> 32) == tile_tag(Jnn));
-            if (lane == 0) {
-                if (ok) fence_acq_rel();
-                sm.rdy[i & 1] = ok;  // slot of tile i+2
-            }
+        if (warp == 0) {
+            const int nh = (hz < i + 8 && hz < ntl - 1) ? advance_horizon(hz) : hz;
+            if (lane == 0) sm.hzs[(i + 1) & 1] = nh;
         }
         __syncthreads();
-        if (i + 1 < ntl && !pf) {  // the next tile was not published in time: wait for it now
+        if (i + 1 < ntl && !pf) {  // the next tile was not published in time: wait for it now (uniform branch)
             if (warp == 0) {
                 unsigned bits;
                 const bool ok = wait_words(ch, Jn, tile_words(Jn), tile_tag(Jn), tile_tag(Jn), ctl, bits);
-                if (lane == 0) sm.ok = ok;
+                if (lane == 0) {
+                    sm.ok = ok;
+                    sm.hzs[(i + 1) & 1] = max(sm.hzs[(i + 1) & 1], i + 1);
+                }
             }
             __syncthreads();
             if (!sm.ok) return false;
             if (tid < S) sm.tile[cur ^ 1][tid] = __ldcg(&tile_src(Jn)[tid]);
             __syncthreads();
         }
-        Jn = Jnn;
-        Jnn = (i + 3 < ntl) ? tile_J(i + 3) : -1;
     }
     cyc_tiles = clock64() - cyc_t0;
 
@@ -831,6 +871,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             AA[m] += __shfl_xor_sync(FULL, AA[m], o);
             TA[m] += __shfl_xor_sync(FULL, TA[m], o);
             CA[m] += __shfl_xor_sync(FULL, CA[m], o);
+            PA[m] += __shfl_xor_sync(FULL, PA[m], o);
             mA[m] = fminf(mA[m], __shfl_xor_sync(FULL, mA[m], o));
         }
     }
@@ -843,6 +884,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             sm.Ab[k] = AA[m] * (1.0f + 0x1p-10f);
             sm.Tb[k] = TA[m] * (1.0f + 0x1p-10f);
             sm.TCb[k] = CA[m] * (1.0f + 0x1p-10f);
+            sm.Pb[k] = PA[m] * (1.0f + 0x1p-10f);
             sm.mind2[k] = mA[m];
         }
     }
@@ -852,10 +894,20 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     if (tid < S) {
         const int k = tid;
         unsigned stv = sm.st[k];
+        const float4 ak = sm.trial[k], bk = sm.own[k];
+        const float dx = ak.x - bk.x, dy = ak.y - bk.y, dz = ak.z - bk.z;
+        const float dn = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) * (1.0f + 0x1p-18f);
+        float kT = 0.f, kP = 0.f, kO = 0.f;
+        const bool bounded = far_coeffs(dn, sp, kT, kP, kO);
         if (!(stv & (ST_INACTIVE | ST_WALL))) {
+            // the settled ions' squared distances come from pair_far: widen the overlap band to its error
+            const float rel = kO * U32;
+            const float lo2k = fminf(lo2, s2f * (1.0f - rel) * (1.0f - 0x1p-22f));
+            const float hi2k = fmaxf(hi2, s2f * (1.0f + rel) * (1.0f + 0x1p-22f));
             const float m2 = sm.mind2[k];
-            if (m2 < lo2) stv |= ST_OVL_CERTAIN;
-            else if (!(m2 > hi2)) stv |= ST_OVL_AMBIG;
+            if (!bounded) stv |= ST_OVL_AMBIG;
+            else if (m2 < lo2k) stv |= ST_OVL_CERTAIN;
+            else if (!(m2 > hi2k)) stv |= ST_OVL_AMBIG;
             unsigned any = 0, both = 0;
 #pragma unroll
             for (int w = 0; w < WORDS; ++w) {
@@ -867,10 +919,12 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             sm.st[k] = (unsigned char)stv;
         }
         const float lqa = fabsf(lBf * sm.own[k].w);
-        sm.bnd[k] = (mode == 1 || mode == 3) ? finf()
-                              : (mode == 2 ? 0.f
-                                           : lqa * (U32 * (C_TERM * sm.Ab[k] + C_SUM * sm.Tb[k] + C_CORR * sm.TCb[k]) +
-                                                    0x1p-36f * (sm.Ab[k] + sm.Tb[k])));
+        sm.bnd[k] = (mode == 1 || mode == 3 || !bounded)
+                        ? finf()
+                        : (mode == 2 ? 0.f
+                                     : lqa * (U32 * (C_TERM * sm.Ab[k] + (C_SUM + kT) * sm.Tb[k] + kP * sm.Pb[k] +
+                                                     C_CORR * sm.TCb[k]) +
+                                              0x1p-40f * ch.a_max + 0x1p-36f * sm.Tb[k]));
         sm.run[k] = 0.f;
         sm.wex[k] = 0.f;
     }
@@ -1183,7 +1237,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             rc.outcome = sm.outcome[k];
             rc.tier = sm.tier[k];
             rc.pad = 0;
-            rc.scale = fabs(ch.lB * (double)sm.own[k].w) * (double)sm.Ab[k];
+            rc.bound = (double)sm.bnd[k];
             const int out = sm.outcome[k];
             const bool ev = out == OUT_ACCEPT || out == OUT_METROPOLIS;
             rc.dE = ev ? sm.dEv[k] : __longlong_as_double(0x7ff8000000000000ll);

@@ -60,11 +60,17 @@ def _compare_records(gr, orc, N, lB_q_tol=1e-6):
     # tier-4 moves carry the oracle's FP64 value exactly
     t4 = ev & (gr["tier"] == 4)
     assert (gr["dE"][t4] == orc["dE"][t4]).all()
-    # FP32 values: error relative to the bound scale (BJ target 1e-6)
+    # FP32 values: error relative to the oracle's scale l_B |q_i| sum_j |q_j| (1/r' + 1/r) (target 1e-6)
     ok32 = ev & np.isfinite(gr["dE32"])
-    err = np.abs(gr["dE32"][ok32] - orc["dE"][ok32]) / np.maximum(gr["scale"][ok32], 1e-300)
+    diff = np.abs(gr["dE32"][ok32] - orc["dE"][ok32])
+    err = diff / np.maximum(orc["scale"][ok32], 1e-300)
     if err.size:
         assert err.max() <= lB_q_tol, err.max()
+    # ... and within the bound the kernel proved for its FP32 decision
+    bnd = gr["bound"][ok32]
+    fin = np.isfinite(bnd)
+    slack = 2.0 ** -19 * np.abs(orc["dE"][ok32][fin])
+    assert (diff[fin] <= bnd[fin] + slack).all(), np.max((diff[fin] - slack) / bnd[fin])
     return err
 
 
@@ -132,7 +138,7 @@ def test_guard_modes(pkg, mode):
         ev = (orc["outcome"] == 0) | (orc["outcome"] == 1)
         tiers = gr["tier"][ev]
         assert (tiers >= 2).all() and (tiers == 2).sum() > 0
-        err = np.abs(gr["dE"][ev] - orc["dE"][ev]) / gr["scale"][ev]
+        err = np.abs(gr["dE"][ev] - orc["dE"][ev]) / orc["scale"][ev]
         # accurate FP32 (tier 2): error far below the FP32 band; double-single (tier 3): ~2^-38; FP64: exact
         assert err[tiers == 2].max() <= 1e-7, err[tiers == 2].max()
         if (tiers == 3).any():
@@ -265,3 +271,36 @@ def test_batch_policies_equal(pkg, policy):
         o = oracle.OracleChain.from_chain(ch)
         o.sweep(3)
         assert (s.positions(k) == o.positions()).all()
+
+
+def test_large_n1048576_sampled_parity(pkg):
+    """The 2^20-ion 2:1 workload at full size in the production launch: the first 1024 moves of the first sweep
+    (records and positions) against the oracle move by move, then invariants that hold at any size after the
+    full sweep: every ion inside the wall, no two closer than sigma, ledger equal to the recomputed energy."""
+    ch = inputs.workload("large_n1048576").chains[0]
+    import paper_1602_05716_gb300 as p
+    g = p.System([ch])
+    k = 1024
+    g.record_enable(k)
+    g.sweep(1)
+    o = oracle.OracleChain.from_chain(ch, threads=THREADS)
+    o.record(k)
+    o.partial_sweep(k)
+    gr, orc = g.records(), o.records()
+    assert (gr["outcome"] == orc["outcome"]).all()
+    pg = g.positions()
+    assert (pg[:k] == o.positions()[:k]).all()
+    err = _compare_records(gr, orc, ch.n)
+    print("max relative dE error (first 1024 moves)", err.max() if err.size else 0.0)
+    # invariants of the whole configuration after the sweep
+    Rc = ch.R - 0.5
+    x = pg.astype(np.float64)
+    assert ((x ** 2).sum(1) <= Rc * Rc).all()
+    cell = np.floor((x + Rc) / 1.0).astype(np.int64)
+    order = np.lexsort((cell[:, 2], cell[:, 1], cell[:, 0]))
+    from scipy.spatial import cKDTree
+    pairs = cKDTree(x).query_pairs(1.0 - 1e-12)
+    for a, b in pairs:
+        assert ((x[a] - x[b]) ** 2).sum() >= 1.0
+    led, rec = g.energy()
+    assert abs(led - rec) < 1e-5 * abs(rec), (led, rec)
