@@ -84,6 +84,8 @@ typedef struct {
     uint64_t cyc_guard;      /* ... in guard tiers, */
     uint64_t cyc_total;      /* ... and in total */
     uint64_t cyc_tier[3];    /* SM cycles in guard tiers 2, 3 and 4 */
+    uint64_t ovl_scan;       /* exact overlap scans (FP32 minimum inside the overlap band) */
+    uint64_t cyc_ovl_scan;   /* SM cycles in those scans */
 } mc_stats_t;
 
 /* Per-move validation record (mc_record_enable / mc_record_read). */
@@ -96,7 +98,7 @@ typedef struct {
     double bound;   /* proven bound of |dE32 - dE_FP64| apart from a relative 2^-20 |dE| (the static band of
                        the FP32 decision); +inf when a guard mode disabled the band */
     int32_t tier;   /* 0 decided from an interval, 1 from the exact FP32 sum, 2 accurate FP32, 3 double-single,
-                       4 the FP64 recomputation */
+                       4 the FP64 recomputation, 5 overlap found by the exact overlap scan */
     int32_t pad;
 } mc_record;
 

@@ -617,6 +617,8 @@ int mc_stats(mc_handle h, int chain, mc_stats_t *out)
     out->cyc_tier[0] = v[mcg::CNT_CYC_T2];
     out->cyc_tier[1] = v[mcg::CNT_CYC_T3];
     out->cyc_tier[2] = v[mcg::CNT_CYC_T4];
+    out->ovl_scan = v[mcg::CNT_OVL_SCAN];
+    out->cyc_ovl_scan = v[mcg::CNT_CYC_OVL];
     return MC_OK;
 }
 

@@ -99,7 +99,7 @@ struct Ctl {
 constexpr int CNT_ACCEPT = 0, CNT_METRO = 1, CNT_OVERLAP = 2, CNT_WALL = 3, CNT_FP64 = 4, CNT_INTERVAL = 5,
               CNT_T2 = 6, CNT_T3 = 7, CNT_T4 = 8, CNT_ROUNDS = 9, CNT_CYC_WIN = 10, CNT_CYC_TILES = 11,
               CNT_CYC_RESOLVE = 12, CNT_CYC_GUARD = 13, CNT_CYC_TOTAL = 14, CNT_CYC_T2 = 15, CNT_CYC_T3 = 16,
-              CNT_CYC_T4 = 17;
+              CNT_CYC_T4 = 17, CNT_OVL_SCAN = 18, CNT_CYC_OVL = 19;
 constexpr int NCOUNTERS = 24;
 
 // ---------------------------------------------------------------------------

@@ -517,6 +517,37 @@ __device__ void tier4(Smem &sm, const Ctx &c, int k, double &dE_out, bool &ovl_o
     __syncthreads();
 }
 
+// Exact overlap test of move k's trial position against every other ion as move k sees it (all earlier
+// moves of the group decided): an FP32 prefilter (its squared distance errs by at most 5u, far inside
+// 2^-12), then the oracle's FP64 squared distance for the few ions it lets through.  Settles a move whose
+// FP32 minimum fell inside the overlap band at the cost of one pass over the positions, instead of the
+// FP64 tier's full recomputation.
+__device__ bool overlap_exact(Smem &sm, const Ctx &c, int k)
+{
+    const int tid = threadIdx.x;
+    const int i = c.k0 + k;
+    const float4 a = sm.trial[k];
+    const float4 *buf = stage_buf(sm);
+    const double sig2 = c.ch->sig2;
+    const float pre = (float)sig2 * (1.0f + 0x1p-12f);
+    if (tid == 0) sm.ovl_flag = 0;
+    for (int j0 = 0; j0 < c.N; j0 += GSTAGE) {
+        stage_positions(sm, c, k, j0);
+#pragma unroll 4
+        for (int u = 0; u < GSTAGE / T; ++u) {
+            const int t = u * T + tid, j = j0 + t;
+            const float4 y = buf[t];
+            const float dx = a.x - y.x, dy = a.y - y.y, dz = a.z - y.z;
+            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (d2 < pre && j < c.N && j != i && d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < sig2) sm.ovl_flag = 1;
+        }
+    }
+    __syncthreads();
+    const bool o = sm.ovl_flag != 0;
+    __syncthreads();
+    return o;
+}
+
 __device__ __forceinline__ float4 pad_point(float v)
 {
     return make_float4(v, v, v, 0.0f);
@@ -623,7 +654,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     const int mode = ctl->guard_mode;
     const float lBf = (float)ch.lB;
     // phase timers (thread 0): SM cycles
-    long long cyc_start = clock64(), cyc_tiles = 0, cyc_win = 0, cyc_guard = 0, cyc_res0 = 0;
+    long long cyc_start = clock64(), cyc_tiles = 0, cyc_win = 0, cyc_guard = 0, cyc_res0 = 0, cyc_ovl = 0;
+    int n_scan = 0;
     long long cyc_t[3] = {0, 0, 0};
     const unsigned long long gt_start = globaltimer();
     unsigned long long gt_ready = 0, gt_window = 0, gt_resolved = 0, gt_pub = 0;
@@ -1063,36 +1095,53 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             const unsigned stv = sm.st[k];
             const unsigned ua = move_draws(ch, s * (unsigned long long)N + (unsigned long long)(k0 + k), 0u).w >> 8;
             const double L64 = (ua == 0u) ? 0.0 : -series_log((double)ua * 0x1p-24);
-            double dE = 0.0;
-            int res = -1, tier = 2;
-            if (!(stv & ST_OVL_AMBIG) && mode != 1) {
-                long long q0 = clock64();
-                res = tier2(sm, c, k, L64, dE);
-                cyc_t[0] += clock64() - q0;
-                if (res < 0) {
-                    tier = 3;
-                    q0 = clock64();
-                    res = tier3(sm, c, k, L64, dE);
-                    cyc_t[1] += clock64() - q0;
-                }
-            }
-            if (res < 0) {
-                bool ovl = false;
-                tier = 4;
+            if ((stv & ST_OVL_AMBIG) && mode != 1) {
+                // settle the overlap question first; without an overlap the move is decided by the next round
                 const long long q0 = clock64();
-                tier4(sm, c, k, dE, ovl);
-                cyc_t[2] += clock64() - q0;
-                if (ovl) res = 2;
-                else if (ua == 0u) res = 0;
-                else res = (dE < L64) ? 0 : 1;
-            }
-            if (tid == 0) {
-                const int out = res == 0 ? OUT_ACCEPT : (res == 1 ? OUT_METROPOLIS : OUT_OVERLAP);
-                sm.outcome[k] = (signed char)out;
-                sm.tier[k] = (unsigned char)tier;
-                sm.dEv[k] = dE;
-                sm.decw[k >> 5] |= 1u << (k & 31);
-                if (out == OUT_ACCEPT) sm.accw[k >> 5] |= 1u << (k & 31);
+                const bool ov = overlap_exact(sm, c, k);
+                cyc_ovl += clock64() - q0;
+                ++n_scan;
+                if (tid == 0) {
+                    if (ov) {
+                        sm.outcome[k] = (signed char)OUT_OVERLAP;
+                        sm.tier[k] = 5;
+                        sm.decw[k >> 5] |= 1u << (k & 31);
+                    } else {
+                        sm.st[k] = (unsigned char)(stv & ~ST_OVL_AMBIG);
+                    }
+                }
+            } else {
+                double dE = 0.0;
+                int res = -1, tier = 2;
+                if (!(stv & ST_OVL_AMBIG) && mode != 1) {
+                    long long q0 = clock64();
+                    res = tier2(sm, c, k, L64, dE);
+                    cyc_t[0] += clock64() - q0;
+                    if (res < 0) {
+                        tier = 3;
+                        q0 = clock64();
+                        res = tier3(sm, c, k, L64, dE);
+                        cyc_t[1] += clock64() - q0;
+                    }
+                }
+                if (res < 0) {
+                    bool ovl = false;
+                    tier = 4;
+                    const long long q0 = clock64();
+                    tier4(sm, c, k, dE, ovl);
+                    cyc_t[2] += clock64() - q0;
+                    if (ovl) res = 2;
+                    else if (ua == 0u) res = 0;
+                    else res = (dE < L64) ? 0 : 1;
+                }
+                if (tid == 0) {
+                    const int out = res == 0 ? OUT_ACCEPT : (res == 1 ? OUT_METROPOLIS : OUT_OVERLAP);
+                    sm.outcome[k] = (signed char)out;
+                    sm.tier[k] = (unsigned char)tier;
+                    sm.dEv[k] = dE;
+                    sm.decw[k >> 5] |= 1u << (k & 31);
+                    if (out == OUT_ACCEPT) sm.accw[k >> 5] |= 1u << (k & 31);
+                }
             }
             __syncthreads();
             cyc_guard += clock64() - cyc_g0;
@@ -1199,7 +1248,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (out >= 0 && out <= 3) cnt[out]++;
             if (sm.tier[k] >= 2) cnt[4]++;
             if (sm.tier[k] == 0 && (out == OUT_ACCEPT || out == OUT_METROPOLIS)) cnt[5]++;
-            if (sm.tier[k] >= 2) cnt[4 + sm.tier[k]]++;
+            if (sm.tier[k] >= 2 && sm.tier[k] <= 4) cnt[4 + sm.tier[k]]++;
         }
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
@@ -1225,6 +1274,10 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             atomicAdd(&ch.stats[CNT_CYC_T2], (unsigned long long)cyc_t[0]);
             atomicAdd(&ch.stats[CNT_CYC_T3], (unsigned long long)cyc_t[1]);
             atomicAdd(&ch.stats[CNT_CYC_T4], (unsigned long long)cyc_t[2]);
+            if (n_scan) {
+                atomicAdd(&ch.stats[CNT_OVL_SCAN], (unsigned long long)n_scan);
+                atomicAdd(&ch.stats[CNT_CYC_OVL], (unsigned long long)cyc_ovl);
+            }
         }
     }
     if (ch.rec && s >= ch.rec_sweep0 && tid < nk) {
