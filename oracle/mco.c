@@ -170,7 +170,12 @@ typedef struct {
     double *chunk_sum;
     int *chunk_ovl;
     int64_t n_chunks;
+    /* delayed-acceptance surrogate (NULL until mco_set_surrogate) */
+    struct mco_da *da;
 } mco_chain;
+
+static void da_free(struct mco_da *d);
+static void da_regrid(mco_chain *c);
 
 static int nthreads_cfg = 1;
 
@@ -293,6 +298,7 @@ void mco_destroy(mco_chain *c)
     free(c->q);
     free(c->chunk_sum);
     free(c->chunk_ovl);
+    da_free(c->da);
     free(c);
 }
 
@@ -546,6 +552,7 @@ int mco_set_positions(mco_chain *c, const float *pos_xyz)
     if (!c || !pos_xyz) return MCO_ERR_INVALID;
     if (config_valid(pos_xyz, c->n, c->sig2, c->sigma, c->Rc2, c->Rc) != 1) return MCO_ERR_OVERLAP_INIT;
     memcpy(c->x, pos_xyz, sizeof(float) * 3 * (size_t)c->n);
+    da_regrid(c);
     return MCO_OK;
 }
 
@@ -602,4 +609,448 @@ double mco_delta_e(mco_chain *c, int64_t i, const float a[3], int *ovl)
 void mco_move_draws(uint64_t seed, uint32_t chain, uint64_t m, uint32_t purpose, uint32_t w[4])
 {
     move_draws(seed, chain, m, purpose, w);
+}
+
+/* ======================================================================== */
+/* Delayed acceptance with a learned surrogate (a two-stage Metropolis test
+ * in the sense of Christen & Fox, 2005).  The paper's method is the exact
+ * sequential chain of Sec. 2; this variant keeps its stationary distribution
+ * and skips the O(N) sum for moves that a cheap first stage already rejects.
+ * Readings D1-D8 (also listed in the design doc):
+ *
+ *  D1 Surrogate energy of ion i at point p, given the others:
+ *       Et(p) = l_B q_i [phi_near(p) + g(v(p))],
+ *     phi_near(p) = sum q_j / |p - x_j| over counted ions j with
+ *     |p - x_j|^2 < r_c^2 (FP64 from FP32 coordinates, ascending j), and
+ *     g the MLP below.  dEt = Et(x') - Et(x) is exactly antisymmetric.
+ *  D2 Counted ions: all j != i except those tried in the W groups of 128
+ *     ions preceding i's group in sweep order (cyclic over the sweep) and
+ *     the earlier ions of i's own group.  The set depends only on the move
+ *     index, so Et is a function of the current state for every move.
+ *  D3 Features v(p): 32 shell net charges and the radial coordinate.  Feature
+ *     grid: 16^3 cubic cells covering [-R, R]^3; the cell of a point is
+ *     floor((p + R) * 16 / (2R)) per axis in FP32 arithmetic, clamped to
+ *     [0, 15].  Q[c] = summed valence of counted ions in cell c.  The shell of
+ *     a cell at integer offset (dx, dy, dz) from the cell of p is
+ *     floor((e sqrt(n2) - r_c) / Delta), n2 = dx^2 + dy^2 + dz^2, e = 2R/16,
+ *     Delta = (2R - r_c)/32, FP64, clamped to 31; cells closer than r_c are
+ *     left out.  v[k] = F[k] / 16, k < 32; v[32] = |p| / R (FP64).
+ *  D4 g: 33-64-64-1 MLP, SiLU after both hidden layers, BF16 weights; the
+ *     reference arithmetic is FP64 with sequential dot products (bias first),
+ *     silu(z) = z / (1 + exp(-z)) with the exp below.
+ *  D5 Stage 1: a trial that overlaps a counted ion is rejected; otherwise it
+ *     passes iff u1 == 0 or dEt < -L(u1), u1 the acceptance draw of Philox
+ *     purpose 0 (the plain chain's draw).
+ *  D6 Stage 2 (survivors only): the exact sum of the plain chain (overlap
+ *     with any ion rejects); accept iff u2 == 0 or fl(dE - dEt) < -L(u2), u2
+ *     the fourth word of Philox purpose 1.  This is the delayed-acceptance
+ *     ratio min(1, exp(-(dE - dEt))) for an antisymmetric dEt.
+ *  D7 Outcomes: 0 accept, 1 stage-2 reject, 2 overlap, 3 wall, 4 stage-1
+ *     reject.  The ledger adds the exact dE of accepted moves.
+ *  D8 Parameter layout (6401 values): W1[64][33], b1[64], W2[64][64],
+ *     b2[64], W3[64], b3.
+ */
+#define MCO_DA_S 128
+#define MCO_DA_G 16
+#define MCO_DA_NIN 33
+#define MCO_DA_H 64
+#define MCO_DA_NP (MCO_DA_H * MCO_DA_NIN + MCO_DA_H + MCO_DA_H * MCO_DA_H + MCO_DA_H + MCO_DA_H + 1)
+#define MCO_DA_REJECT1 4
+
+struct mco_da {
+    double w[MCO_DA_NP]; /* the BF16 weights, exactly, in FP64 */
+    double rc, rc2;
+    int W;
+    int shell[3 * (MCO_DA_G - 1) * (MCO_DA_G - 1) + 1]; /* shell of a cell offset by its n2, -1 = left out */
+    float Rf, icf;                                    /* feature-cell arithmetic in FP32 */
+    int *cell;                                        /* feature cell of every ion (current position) */
+    int Q[MCO_DA_G * MCO_DA_G * MCO_DA_G];
+    uint64_t n_rej1, n_ovl1, n_ovl2, n_rej2;
+    void *rec;
+    int64_t rec_cap, rec_len;
+};
+
+typedef struct {
+    uint64_t m;
+    int32_t i;
+    int32_t outcome; /* D7 */
+    int32_t stage;   /* 1 if decided by stage 1 (or the wall), 2 if by the exact stage */
+    int32_t pad;
+    double dE;       /* exact dE (NaN unless stage 2 evaluated it) */
+    double dEt;      /* surrogate dEt (NaN unless stage 1 evaluated it) */
+    float a[3];
+    float pad2;
+} mco_da_record;
+
+static void da_free(struct mco_da *d)
+{
+    if (!d) return;
+    free(d->cell);
+    free(d);
+}
+
+/* exp(x) in FP64 from +, -, *, / only (for the SiLU of reading D4, written
+ * so that the reference and a device implementation of the same steps agree
+ * bit for bit).  Method: x = k ln2 + r with k = round-half-even(x / ln2) and
+ * r = (x - k ln2_head) - k ln2_tail (ln2_head has 32 significant bits, so
+ * k ln2_head is exact); exp(r) = 1 + r(1 + r/2(1 + r/3(...(1 + r/20)))) by
+ * nested Horner steps, |r| <= 0.35 so the truncation is below 2^-60; the
+ * result is scaled by 2^k exactly.  exp(x) = 0 below -700 and +inf above
+ * 709 by definition.                                                       */
+double mco_exp(double x)
+{
+    if (x > 709.0) return INFINITY;
+    if (x < -700.0) return 0.0;
+    double kd = nearbyint(x / MCO_LN2_HEAD);
+    double r = (x - kd * MCO_LN2_HEAD) - kd * MCO_LN2_TAIL;
+    double p = 1.0;
+    for (int k = 20; k >= 1; --k) p = 1.0 + (p * r) / (double)k;
+    return ldexp(p, (int)kd);
+}
+
+static double silu64(double z)
+{
+    return z / (1.0 + mco_exp(-z));
+}
+
+/* Reading D4: g(v) with FP64 parameters w (layout D8). */
+double mco_mlp_forward(const double *w, const double v[MCO_DA_NIN])
+{
+    const double *W1 = w, *b1 = W1 + MCO_DA_H * MCO_DA_NIN, *W2 = b1 + MCO_DA_H, *b2 = W2 + MCO_DA_H * MCO_DA_H;
+    const double *W3 = b2 + MCO_DA_H, *b3 = W3 + MCO_DA_H;
+    double h1[MCO_DA_H], h2[MCO_DA_H];
+    for (int o = 0; o < MCO_DA_H; ++o) {
+        double z = b1[o];
+        for (int i = 0; i < MCO_DA_NIN; ++i) z = z + W1[o * MCO_DA_NIN + i] * v[i];
+        h1[o] = silu64(z);
+    }
+    for (int o = 0; o < MCO_DA_H; ++o) {
+        double z = b2[o];
+        for (int i = 0; i < MCO_DA_H; ++i) z = z + W2[o * MCO_DA_H + i] * h1[i];
+        h2[o] = silu64(z);
+    }
+    double g = b3[0];
+    for (int i = 0; i < MCO_DA_H; ++i) g = g + W3[i] * h2[i];
+    return g;
+}
+
+/* Adds scale * d g(v) / d w to grad (backpropagation through D4). */
+static void mlp_grad_acc(const double *w, const double v[MCO_DA_NIN], double scale, double *grad)
+{
+    const double *W1 = w, *b1 = W1 + MCO_DA_H * MCO_DA_NIN, *W2 = b1 + MCO_DA_H, *b2 = W2 + MCO_DA_H * MCO_DA_H;
+    const double *W3 = b2 + MCO_DA_H;
+    double *gW1 = grad, *gb1 = gW1 + MCO_DA_H * MCO_DA_NIN, *gW2 = gb1 + MCO_DA_H, *gb2 = gW2 + MCO_DA_H * MCO_DA_H;
+    double *gW3 = gb2 + MCO_DA_H, *gb3 = gW3 + MCO_DA_H;
+    double z1[MCO_DA_H], h1[MCO_DA_H], z2[MCO_DA_H], h2[MCO_DA_H], d2[MCO_DA_H], d1[MCO_DA_H];
+    for (int o = 0; o < MCO_DA_H; ++o) {
+        double z = b1[o];
+        for (int i = 0; i < MCO_DA_NIN; ++i) z = z + W1[o * MCO_DA_NIN + i] * v[i];
+        z1[o] = z;
+        h1[o] = silu64(z);
+    }
+    for (int o = 0; o < MCO_DA_H; ++o) {
+        double z = b2[o];
+        for (int i = 0; i < MCO_DA_H; ++i) z = z + W2[o * MCO_DA_H + i] * h1[i];
+        z2[o] = z;
+        h2[o] = silu64(z);
+    }
+    /* silu'(z) = s (1 + z (1 - s)), s = 1 / (1 + exp(-z)) */
+    for (int o = 0; o < MCO_DA_H; ++o) {
+        gW3[o] += scale * h2[o];
+        double sg = 1.0 / (1.0 + mco_exp(-z2[o]));
+        d2[o] = scale * W3[o] * (sg * (1.0 + z2[o] * (1.0 - sg)));
+    }
+    gb3[0] += scale;
+    for (int i = 0; i < MCO_DA_H; ++i) d1[i] = 0.0;
+    for (int o = 0; o < MCO_DA_H; ++o) {
+        gb2[o] += d2[o];
+        for (int i = 0; i < MCO_DA_H; ++i) {
+            gW2[o * MCO_DA_H + i] += d2[o] * h1[i];
+            d1[i] += d2[o] * W2[o * MCO_DA_H + i];
+        }
+    }
+    for (int o = 0; o < MCO_DA_H; ++o) {
+        double sg = 1.0 / (1.0 + mco_exp(-z1[o]));
+        double dz = d1[o] * (sg * (1.0 + z1[o] * (1.0 - sg)));
+        gb1[o] += dz;
+        for (int i = 0; i < MCO_DA_NIN; ++i) gW1[o * MCO_DA_NIN + i] += dz * v[i];
+    }
+}
+
+/* Training loss of the surrogate on n pairs (v0 = features at the old position, v1 at the trial, y = the
+ * far part of the exact energy change in units of l_B q_i): mean of (g(v1) - g(v0) - y)^2, and its gradient
+ * with respect to the FP64 parameters (grad may be NULL).                                                 */
+double mco_mlp_loss_grad(const double *w, int64_t n, const double *v0, const double *v1, const double *y,
+                         double *grad)
+{
+    if (grad)
+        for (int k = 0; k < MCO_DA_NP; ++k) grad[k] = 0.0;
+    double loss = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+        double r = (mco_mlp_forward(w, v1 + s * MCO_DA_NIN) - mco_mlp_forward(w, v0 + s * MCO_DA_NIN)) - y[s];
+        loss += r * r;
+        if (grad) {
+            mlp_grad_acc(w, v1 + s * MCO_DA_NIN, 2.0 * r / (double)n, grad);
+            mlp_grad_acc(w, v0 + s * MCO_DA_NIN, -2.0 * r / (double)n, grad);
+        }
+    }
+    return loss / (double)n;
+}
+
+int mco_mlp_nparams(void)
+{
+    return MCO_DA_NP;
+}
+
+static double bf16_to_double(uint16_t b)
+{
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return (double)f;
+}
+
+static int da_cell_axis(const struct mco_da *d, float p)
+{
+    float t = (p + d->Rf) * d->icf;
+    int c = (int)floorf(t);
+    return c < 0 ? 0 : (c > MCO_DA_G - 1 ? MCO_DA_G - 1 : c);
+}
+
+static int da_cell(const struct mco_da *d, const float p[3])
+{
+    return (da_cell_axis(d, p[0]) * MCO_DA_G + da_cell_axis(d, p[1])) * MCO_DA_G + da_cell_axis(d, p[2]);
+}
+
+/* Reading D2: is ion j counted for the move of ion i? */
+static int da_counted(const mco_chain *c, int64_t i, int64_t j)
+{
+    if (j == i) return 0;
+    int64_t B = (c->n + MCO_DA_S - 1) / MCO_DA_S;
+    int64_t gi = i / MCO_DA_S, gj = j / MCO_DA_S;
+    if (gj == gi) return j > i;
+    int64_t back = ((gi - gj) % B + B) % B; /* groups from j's back to i's, 1 .. B-1 */
+    int64_t w = c->da->W < B - 1 ? c->da->W : B - 1;
+    return back > w;
+}
+
+/* Stage-1 quantities of ion i at point p (readings D1-D3): features v, the near-field potential and, when
+ * is_trial, the overlap with a counted ion.                                                              */
+static void da_point(const mco_chain *c, int64_t i, const float p[3], int is_trial, double v[MCO_DA_NIN], double *phi,
+                     int *ovl)
+{
+    struct mco_da *d = c->da;
+    double ph = 0.0;
+    int o = 0;
+    int Q[MCO_DA_G * MCO_DA_G * MCO_DA_G];
+    memcpy(Q, d->Q, sizeof Q);
+    for (int64_t j = 0; j < c->n; ++j) {
+        if (!da_counted(c, i, j)) { /* the grid holds every ion (ion i too): remove the uncounted ones */
+            Q[d->cell[j]] -= (int)c->q[j];
+            continue;
+        }
+        const float *y = c->x + 3 * j;
+        double dx = (double)p[0] - (double)y[0];
+        double dy = (double)p[1] - (double)y[1];
+        double dz = (double)p[2] - (double)y[2];
+        double d2 = (dx * dx + dy * dy) + dz * dz;
+        if (is_trial && d2 < c->sig2) o = 1;
+        if (d2 < d->rc2) ph = ph + c->q[j] / sqrt(d2);
+    }
+    double F[32];
+    for (int k = 0; k < 32; ++k) F[k] = 0.0;
+    int cp = da_cell(d, p);
+    int px = cp / (MCO_DA_G * MCO_DA_G), py = (cp / MCO_DA_G) % MCO_DA_G, pz = cp % MCO_DA_G;
+    for (int cx = 0; cx < MCO_DA_G; ++cx)
+        for (int cy = 0; cy < MCO_DA_G; ++cy)
+            for (int cz = 0; cz < MCO_DA_G; ++cz) {
+                int n2 = (cx - px) * (cx - px) + (cy - py) * (cy - py) + (cz - pz) * (cz - pz);
+                int k = d->shell[n2];
+                if (k >= 0) F[k] += (double)Q[(cx * MCO_DA_G + cy) * MCO_DA_G + cz];
+            }
+    for (int k = 0; k < 32; ++k) v[k] = F[k] * 0.0625;
+    v[32] = sqrt(((double)p[0] * (double)p[0] + (double)p[1] * (double)p[1]) + (double)p[2] * (double)p[2]) / c->R;
+    *phi = ph;
+    if (ovl) *ovl = o;
+}
+
+/* Feature cell of every ion and the net-charge grid of all ions (reading D3). */
+static void da_regrid(mco_chain *c)
+{
+    struct mco_da *d = c->da;
+    if (!d) return;
+    for (int k = 0; k < MCO_DA_G * MCO_DA_G * MCO_DA_G; ++k) d->Q[k] = 0;
+    for (int64_t j = 0; j < c->n; ++j) {
+        d->cell[j] = da_cell(d, c->x + 3 * j);
+        d->Q[d->cell[j]] += (int)c->q[j];
+    }
+}
+
+/* Install the surrogate: n_w = 6401 BF16 weights (layout D8), near-field cutoff r_c, exclusion depth W. */
+int mco_set_surrogate(mco_chain *c, const uint16_t *w_bf16, int64_t n_w, double r_c, int W)
+{
+    if (!c || !w_bf16 || n_w != MCO_DA_NP || !(r_c > 0.0) || W < 0) return MCO_ERR_INVALID;
+    struct mco_da *d = c->da;
+    if (!d) {
+        d = (struct mco_da *)calloc(1, sizeof(struct mco_da));
+        if (!d) return MCO_ERR_OOM;
+        d->cell = (int *)malloc(sizeof(int) * (size_t)c->n);
+        if (!d->cell) {
+            free(d);
+            return MCO_ERR_OOM;
+        }
+        c->da = d;
+    }
+    for (int k = 0; k < MCO_DA_NP; ++k) d->w[k] = bf16_to_double(w_bf16[k]);
+    d->rc = r_c;
+    d->rc2 = r_c * r_c;
+    d->W = W;
+    double e = (2.0 * c->R) / (double)MCO_DA_G, delta = (2.0 * c->R - r_c) / 32.0;
+    for (int n2 = 0; n2 <= 3 * (MCO_DA_G - 1) * (MCO_DA_G - 1); ++n2) {
+        double dist = e * sqrt((double)n2);
+        if (dist < r_c) {
+            d->shell[n2] = -1;
+        } else {
+            double k = floor((dist - r_c) / delta);
+            d->shell[n2] = k > 31.0 ? 31 : (int)k;
+        }
+    }
+    d->Rf = (float)c->R;
+    d->icf = (float)((double)MCO_DA_G / (2.0 * c->R));
+    da_regrid(c);
+    return MCO_OK;
+}
+
+/* One delayed-acceptance move (readings D1-D7). */
+static void one_move_da(mco_chain *c, uint64_t s, int64_t i)
+{
+    struct mco_da *d = c->da;
+    uint64_t m = s * (uint64_t)c->n + (uint64_t)i;
+    float a[3];
+    uint32_t u1 = trial(c, m, i, a);
+    float b[3] = {c->x[3 * i], c->x[3 * i + 1], c->x[3 * i + 2]};
+    int outcome, stage = 1;
+    double dE = NAN, dEt = NAN;
+    double r2 = ((double)a[0] * (double)a[0] + (double)a[1] * (double)a[1]) + (double)a[2] * (double)a[2];
+    if (r2 > c->Rc2) {
+        outcome = MCO_REJECT_WALL;
+    } else {
+        double v1[MCO_DA_NIN], v0[MCO_DA_NIN], phi1, phi0;
+        int ovl1 = 0;
+        da_point(c, i, a, 1, v1, &phi1, &ovl1);
+        if (ovl1) {
+            outcome = MCO_REJECT_OVERLAP;
+            d->n_ovl1++;
+        } else {
+            da_point(c, i, b, 0, v0, &phi0, NULL);
+            dEt = (c->lB * c->q[i]) * ((phi1 + mco_mlp_forward(d->w, v1)) - (phi0 + mco_mlp_forward(d->w, v0)));
+            if (!metropolis_accept(dEt, u1)) {
+                outcome = MCO_DA_REJECT1;
+                d->n_rej1++;
+            } else {
+                stage = 2;
+                int ovl = 0;
+                double total = canonical_sum(c, i, a, b, &ovl);
+                if (ovl) {
+                    outcome = MCO_REJECT_OVERLAP;
+                    d->n_ovl2++;
+                } else {
+                    dE = (c->lB * c->q[i]) * total;
+                    uint32_t w2[4];
+                    move_draws(c->seed, c->chain, m, 1u, w2);
+                    outcome = metropolis_accept(dE - dEt, w2[3] >> 8) ? MCO_ACCEPT : MCO_REJECT_METROPOLIS;
+                    if (outcome == MCO_REJECT_METROPOLIS) d->n_rej2++;
+                }
+            }
+        }
+    }
+    if (outcome == MCO_ACCEPT) {
+        int cn = da_cell(d, a);
+        d->Q[d->cell[i]] -= (int)c->q[i];
+        d->Q[cn] += (int)c->q[i];
+        d->cell[i] = cn;
+        c->x[3 * i] = a[0];
+        c->x[3 * i + 1] = a[1];
+        c->x[3 * i + 2] = a[2];
+        c->ledger = c->ledger + dE;
+        c->n_accept++;
+    } else if (outcome == MCO_REJECT_METROPOLIS || outcome == MCO_DA_REJECT1) {
+        c->n_rej_metropolis++;
+    } else if (outcome == MCO_REJECT_OVERLAP) {
+        c->n_rej_overlap++;
+    } else {
+        c->n_rej_wall++;
+    }
+    if (d->rec && d->rec_len < d->rec_cap) {
+        mco_da_record *r = (mco_da_record *)d->rec + d->rec_len++;
+        r->m = m;
+        r->i = (int32_t)i;
+        r->outcome = outcome;
+        r->stage = stage;
+        r->pad = 0;
+        r->dE = dE;
+        r->dEt = dEt;
+        r->a[0] = a[0];
+        r->a[1] = a[1];
+        r->a[2] = a[2];
+        r->pad2 = 0.0f;
+    }
+}
+
+/* n_sweeps delayed-acceptance cycles (same sequential order as mco_sweep). */
+int mco_da_sweep(mco_chain *c, int64_t n_sweeps)
+{
+    if (!c || !c->da || n_sweeps < 0) return MCO_ERR_INVALID;
+    for (int64_t s = 0; s < n_sweeps; ++s) {
+        for (int64_t i = 0; i < c->n; ++i) one_move_da(c, c->sweep, i);
+        c->sweep++;
+    }
+    return MCO_OK;
+}
+
+int mco_da_partial_sweep(mco_chain *c, int64_t n_moves)
+{
+    if (!c || !c->da || n_moves < 0 || n_moves > c->n) return MCO_ERR_INVALID;
+    for (int64_t i = 0; i < n_moves; ++i) one_move_da(c, c->sweep, i);
+    return MCO_OK;
+}
+
+/* DA counters: [stage-1 rejects, stage-1 overlaps, stage-2 overlaps, stage-2 rejects] */
+int mco_da_stats(const mco_chain *c, uint64_t out[4])
+{
+    if (!c || !c->da || !out) return MCO_ERR_INVALID;
+    out[0] = c->da->n_rej1;
+    out[1] = c->da->n_ovl1;
+    out[2] = c->da->n_ovl2;
+    out[3] = c->da->n_rej2;
+    return MCO_OK;
+}
+
+int mco_da_set_record(mco_chain *c, mco_da_record *buf, int64_t cap)
+{
+    if (!c || !c->da) return MCO_ERR_INVALID;
+    c->da->rec = buf;
+    c->da->rec_cap = buf ? cap : 0;
+    c->da->rec_len = 0;
+    return MCO_OK;
+}
+
+int64_t mco_da_record_len(const mco_chain *c)
+{
+    return (c && c->da) ? c->da->rec_len : 0;
+}
+
+/* Stage-1 quantities of a hypothetical move of ion i to a (no state change): features at the old and trial
+ * positions, near-field potentials, trial overlap with a counted ion, and the surrogate dEt (NaN on overlap). */
+int mco_da_probe(mco_chain *c, int64_t i, const float a[3], double v0[MCO_DA_NIN], double v1[MCO_DA_NIN], double phi[2],
+                 int *ovl, double *dEt)
+{
+    if (!c || !c->da || i < 0 || i >= c->n) return MCO_ERR_INVALID;
+    float b[3] = {c->x[3 * i], c->x[3 * i + 1], c->x[3 * i + 2]};
+    da_point(c, i, b, 0, v0, &phi[0], NULL);
+    da_point(c, i, a, 1, v1, &phi[1], ovl);
+    struct mco_da *d = c->da;
+    *dEt = *ovl ? NAN
+                : (c->lB * c->q[i]) * ((phi[1] + mco_mlp_forward(d->w, v1)) - (phi[0] + mco_mlp_forward(d->w, v0)));
+    return MCO_OK;
 }

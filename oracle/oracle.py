@@ -12,6 +12,13 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = None
 
 ACCEPT, REJECT_METROPOLIS, REJECT_OVERLAP, REJECT_WALL = 0, 1, 2, 3
+DA_REJECT1 = 4  # delayed acceptance: rejected by the surrogate stage
+MLP_NIN, MLP_H = 33, 64
+MLP_NP = MLP_H * MLP_NIN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1  # 6401, layout W1, b1, W2, b2, W3, b3
+
+DA_RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("stage", np.int32),
+                            ("pad", np.int32), ("dE", np.float64), ("dEt", np.float64), ("a", np.float32, (3,)),
+                            ("pad2", np.float32)])
 
 RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("dE", np.float64),
                          ("a", np.float32, (3,)), ("pad", np.float32), ("scale", np.float64)])
@@ -73,6 +80,27 @@ def lib():
     L.mco_record_len.restype = i64
     L.mco_delta_e.argtypes = [vp, i64, vp, ctypes.POINTER(ci)]
     L.mco_delta_e.restype = dbl
+    L.mco_exp.argtypes = [dbl]
+    L.mco_exp.restype = dbl
+    L.mco_mlp_nparams.restype = ci
+    L.mco_mlp_forward.argtypes = [vp, vp]
+    L.mco_mlp_forward.restype = dbl
+    L.mco_mlp_loss_grad.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.mco_mlp_loss_grad.restype = dbl
+    L.mco_set_surrogate.argtypes = [vp, vp, i64, dbl, ci]
+    L.mco_set_surrogate.restype = ci
+    L.mco_da_sweep.argtypes = [vp, i64]
+    L.mco_da_sweep.restype = ci
+    L.mco_da_partial_sweep.argtypes = [vp, i64]
+    L.mco_da_partial_sweep.restype = ci
+    L.mco_da_stats.argtypes = [vp, vp]
+    L.mco_da_stats.restype = ci
+    L.mco_da_set_record.argtypes = [vp, vp, i64]
+    L.mco_da_set_record.restype = ci
+    L.mco_da_record_len.argtypes = [vp]
+    L.mco_da_record_len.restype = i64
+    L.mco_da_probe.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.POINTER(ci), ctypes.POINTER(dbl)]
+    L.mco_da_probe.restype = ci
     _LIB = L
     return L
 
@@ -93,6 +121,43 @@ def move_draws(seed: int, chain: int, m: int, purpose: int = 0) -> np.ndarray:
 
 def log_L(u: float) -> float:
     return lib().mco_log(float(u))
+
+
+def exp_D(x: float) -> float:
+    """The oracle's FP64 exponential (used by the surrogate's SiLU)."""
+    return lib().mco_exp(float(x))
+
+
+def bf16_to_f64(bits) -> np.ndarray:
+    """BF16 bit patterns (uint16) to their exact values."""
+    b = np.ascontiguousarray(bits, dtype=np.uint16).astype(np.uint32) << 16
+    return b.view(np.float32).astype(np.float64)
+
+
+def f64_to_bf16(x) -> np.ndarray:
+    """Round to the nearest BF16 (ties to even) and return the bit patterns."""
+    f = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (f + 0x7FFF + ((f >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def mlp_forward(w, v) -> float:
+    """g(v) of the surrogate MLP in FP64 (w: 6401 FP64 parameters, v: 33 inputs)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return lib().mco_mlp_forward(w.ctypes.data, v.ctypes.data)
+
+
+def mlp_loss_grad(w, v0, v1, y, grad: bool = True):
+    """Mean of (g(v1) - g(v0) - y)^2 over the samples and its FP64 gradient."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    v0 = np.ascontiguousarray(v0, dtype=np.float64)
+    v1 = np.ascontiguousarray(v1, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    g = np.zeros(MLP_NP, dtype=np.float64) if grad else None
+    loss = lib().mco_mlp_loss_grad(w.ctypes.data, int(y.shape[0]), v0.ctypes.data, v1.ctypes.data, y.ctypes.data,
+                                   g.ctypes.data if grad else None)
+    return (loss, g) if grad else loss
 
 
 def total_energy(pos: np.ndarray, q: np.ndarray, l_B: float) -> float:
@@ -199,3 +264,55 @@ class OracleChain:
         ovl = ctypes.c_int()
         de = lib().mco_delta_e(self._h, int(i), aa.ctypes.data, ctypes.byref(ovl))
         return de, bool(ovl.value)
+
+    # ---- delayed acceptance (readings D1-D8 in mco.c) ----
+    def set_surrogate(self, w_bf16, r_c: float = 4.0, W: int = 160):
+        w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+        rc = lib().mco_set_surrogate(self._h, w.ctypes.data, int(w.shape[0]), float(r_c), int(W))
+        if rc != 0:
+            raise ValueError(f"mco_set_surrogate: {rc}")
+        self._darec = None
+
+    def da_sweep(self, n: int = 1):
+        rc = lib().mco_da_sweep(self._h, int(n))
+        if rc != 0:
+            raise RuntimeError(f"mco_da_sweep: {rc}")
+
+    def da_partial_sweep(self, n_moves: int):
+        rc = lib().mco_da_partial_sweep(self._h, int(n_moves))
+        if rc != 0:
+            raise RuntimeError(f"mco_da_partial_sweep: {rc}")
+
+    def da_stats(self) -> dict:
+        out = np.zeros(4, dtype=np.uint64)
+        lib().mco_da_stats(self._h, out.ctypes.data)
+        return dict(rej1=int(out[0]), ovl1=int(out[1]), ovl2=int(out[2]), rej2=int(out[3]))
+
+    def da_record(self, cap: int | None):
+        if cap is None:
+            lib().mco_da_set_record(self._h, None, 0)
+            self._darec = None
+            return
+        self._darec = np.zeros(int(cap), dtype=DA_RECORD_DTYPE)
+        lib().mco_da_set_record(self._h, self._darec.ctypes.data, int(cap))
+
+    def da_records(self) -> np.ndarray:
+        if getattr(self, "_darec", None) is None:
+            return np.zeros(0, dtype=DA_RECORD_DTYPE)
+        n = lib().mco_da_record_len(self._h)
+        return self._darec[:n].copy()
+
+    def da_probe(self, i: int, a):
+        """Stage-1 quantities of a hypothetical move (no state change): (v_old, v_trial, phi_old, phi_trial,
+        overlap, dEt)."""
+        aa = np.ascontiguousarray(a, dtype=np.float32)
+        v0 = np.zeros(MLP_NIN)
+        v1 = np.zeros(MLP_NIN)
+        ph = np.zeros(2)
+        ovl = ctypes.c_int()
+        det = ctypes.c_double()
+        rc = lib().mco_da_probe(self._h, int(i), aa.ctypes.data, v0.ctypes.data, v1.ctypes.data, ph.ctypes.data,
+                                ctypes.byref(ovl), ctypes.byref(det))
+        if rc != 0:
+            raise ValueError(f"mco_da_probe: {rc}")
+        return v0, v1, float(ph[0]), float(ph[1]), bool(ovl.value), float(det.value)
