@@ -86,19 +86,26 @@ typedef struct {
     uint64_t cyc_tier[3];    /* SM cycles in guard tiers 2, 3 and 4 */
     uint64_t ovl_scan;       /* exact overlap scans (FP32 minimum inside the overlap band) */
     uint64_t cyc_ovl_scan;   /* SM cycles in those scans */
+    uint64_t da_rej1;        /* delayed acceptance: moves rejected by the surrogate stage */
+    uint64_t da_ovl1;        /* ... overlaps found by the surrogate stage (counted in rej_overlap too) */
+    uint64_t da_fp64;        /* ... surrogate energy changes recomputed in the reference FP64 arithmetic */
+    uint64_t cyc_da1;        /* ... SM cycles in the surrogate stage, summed over work items */
 } mc_stats_t;
 
 /* Per-move validation record (mc_record_enable / mc_record_read). */
 typedef struct {
     uint64_t m;     /* move index = sweep * N + i */
     int32_t i;      /* ion */
-    int32_t outcome; /* 0 accept, 1 Metropolis reject, 2 overlap, 3 wall */
+    int32_t outcome; /* 0 accept, 1 Metropolis reject, 2 overlap, 3 wall, 4 rejected by the surrogate stage */
     double dE;      /* dE used for the ledger / decision (FP64 value when tier == 4); NaN if not evaluated */
     double dE32;    /* dE from the FP32 pair sums (NaN when not evaluated) */
     double bound;   /* proven bound of |dE32 - dE_FP64| apart from a relative 2^-20 |dE| (the static band of
                        the FP32 decision); +inf when a guard mode disabled the band */
+    double dEt;     /* delayed acceptance: the surrogate energy change (the reference FP64 value where it was
+                       computed, else FP32); NaN for plain moves and moves the surrogate did not evaluate */
     int32_t tier;   /* 0 decided from an interval, 1 from the exact FP32 sum, 2 accurate FP32, 3 double-single,
-                       4 the FP64 recomputation, 5 overlap found by the exact overlap scan */
+                       4 the FP64 recomputation, 5 overlap found by the exact overlap scan; delayed acceptance:
+                       6 decided by the surrogate stage in FP32, 7 ... in the reference FP64 arithmetic */
     int32_t pad;
 } mc_record;
 
@@ -197,13 +204,17 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
  *  MC_OPT_USE_GRAPH    1 = capture each distinct sweep count in a CUDA graph
  *                      and replay it (default 1), 0 = plain launches
  *  MC_OPT_POLICY       order of the work items of a batch: 0 = one group of
- *                      every chain in turn (default), 1 = sweep-synchronous */
+ *                      every chain in turn (default), 1 = sweep-synchronous
+ *  MC_OPT_DA           1 = chains with a surrogate (mc_set_surrogate) sweep with
+ *                      delayed acceptance (default), 0 = they sweep plainly (the
+ *                      surrogate stays set for mc_da_samples) */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3
 #define MC_OPT_SKIP_PUBLISH 4
 #define MC_OPT_USE_GRAPH 5
 #define MC_OPT_POLICY 6
+#define MC_OPT_DA 7
 int mc_set_option(mc_handle h, int option, int64_t value);
 int mc_get_option(mc_handle h, int option, int64_t *value);
 
@@ -214,6 +225,55 @@ int mc_get_option(mc_handle h, int option, int64_t *value);
  * CTA count and its trial time in ms.  The paper tunes block size and
  * threads per particle by hand (Sec. 4, Table Para).                        */
 int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t *best_ctas, double *best_ms);
+
+/* ---- Delayed acceptance with a learned surrogate ----------------------
+ * A two-stage Metropolis test (Christen & Fox, 2005) on the sequential chain of
+ * Sec. 2 (the paper's method is the plain chain; this is an exact variant that
+ * skips the O(N) sum of Eq. DeltaE for moves a cheap first stage rejects).
+ * Stage 1 of the move of ion i: overlap with a counted ion rejects; otherwise
+ * the surrogate energy change
+ *     dEt = l_B q_i ([phi_near + g(v)](x') - [phi_near + g(v)](x)),
+ * phi_near(p) = sum q_j / |p - x_j| over counted ions within r_c, g a
+ * 33-64-64-1 SiLU MLP (BF16 weights) of v(p) = 32 shell net charges around p
+ * (from a 16^3 charge grid over [-R, R]^3, shells from r_c to 2R) divided by
+ * 16 and |p| / R, passes iff u1 == 0 or dEt < -ln u1 (u1 the plain chain's
+ * acceptance draw).  Stage 2: the exact sum; accept iff u2 == 0 or
+ * dE - dEt < -ln u2, u2 the fourth word of Philox purpose 1.  Counted ions:
+ * all but ion i, the earlier ions of its group of 128 and the ions of the W
+ * groups before that group (cyclic over the sweep).  Decisions are those of
+ * the FP64 reference arithmetic, bit for bit (FP32 with proven bands, the
+ * reference recomputation inside them).
+ *
+ * mc_set_surrogate installs the 6401 BF16 weights (layout W1[64][33], b1[64],
+ * W2[64][64], b2[64], W3[64], b3; copied), the cutoff r_c (0 < r_c <= 5 sigma)
+ * and W >= 2; the launch then uses at most W - 1 persistent CTAs.  w_bf16 =
+ * NULL removes the surrogate.  Sweeps with a surrogate run one sweep per
+ * launch after a preparation pass (near-field cell list, charge grid).       */
+int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W);
+
+/* Training samples from the chain as it stands: for each ion i, the trial move
+ * the chain would make next (sweep counter unchanged, nothing moves), the
+ * features at the old and the trial position (v_pairs: N x 66, old then
+ * trial), y = the exact pair sum sum_j q_j (1/r'_j - 1/r_j) minus the
+ * near-field part phi_near(x') - phi_near(x) (the part g must learn), and
+ * valid[i] = 1 unless the trial leaves the wall or overlaps.  Host buffers,
+ * caller-owned.  Needs a surrogate set on the chain (its weights unused).  */
+int mc_da_samples(mc_handle h, int chain, float *v_pairs, float *y, uint8_t *valid);
+
+/* The surrogate MLP on the device (the project's own kernels; host buffers).
+ * mc_mlp_forward: g at n points (v: n x 33).
+ * mc_mlp_loss_grad: mean over n pairs of (g(v_trial) - g(v_old) - y)^2 and
+ *   its gradient with respect to the 6401 parameters (FP32 arithmetic with the
+ *   BF16 weights).
+ * mc_mlp_train: Adam (beta 0.9/0.999, eps 1e-8) on FP32 master weights from
+ *   w_init over `epochs` passes of mini-batches of `batch` pairs in the given
+ *   order; the forward passes use the BF16-rounded weights; w_out gets the
+ *   final BF16 weights and loss_per_epoch (nullable) each epoch's mean loss.  */
+int mc_mlp_forward(const uint16_t *w_bf16, const float *v, int64_t n, float *g);
+int mc_mlp_loss_grad(const uint16_t *w_bf16, const float *v_pairs, const float *y, int64_t n, double *loss,
+                     float *grad);
+int mc_mlp_train(const float *v_pairs, const float *y, int64_t n, const uint16_t *w_init, int epochs, int batch,
+                 float lr, uint16_t *w_out, double *loss_per_epoch);
 
 /* Total energy l_B sum_{i<j} q_i q_j / r_ij of n ions WITHOUT allocating
  * anything (no counterpart in the paper; an interface for callers that

@@ -9,10 +9,12 @@ import numpy as np
 from . import build as _build
 
 ERR_INVALID, ERR_OVERLAP_INIT, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_POISONED = -1, -2, -3, -4, -5, -6
-OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH, OPT_POLICY = 1, 2, 3, 4, 5, 6
+OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH, OPT_POLICY, OPT_DA = 1, 2, 3, 4, 5, 6, 7
+MLP_NIN, MLP_H = 33, 64
+MLP_NP = MLP_H * MLP_NIN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1  # layout W1, b1, W2, b2, W3, b3
 
 RECORD_DTYPE = np.dtype([("m", np.uint64), ("i", np.int32), ("outcome", np.int32), ("dE", np.float64),
-                         ("dE32", np.float64), ("bound", np.float64), ("tier", np.int32), ("pad", np.int32)])
+                         ("dE32", np.float64), ("bound", np.float64), ("dEt", np.float64), ("tier", np.int32), ("pad", np.int32)])
 
 TRACE_DTYPE = np.dtype([("item", np.uint64), ("t_start", np.uint64), ("t_ready", np.uint64),
                         ("t_window", np.uint64), ("t_resolved", np.uint64), ("t_published", np.uint64),
@@ -21,7 +23,7 @@ TRACE_DTYPE = np.dtype([("item", np.uint64), ("t_start", np.uint64), ("t_ready",
 _STATS_FIELDS = ["sweeps", "accepts", "rej_metropolis", "rej_overlap", "rej_wall", "guard_fp64",
                  "decided_interval", "tier2", "tier3", "tier4", "rounds", "cyc_wait_window", "cyc_tiles",
                  "cyc_resolve", "cyc_guard", "cyc_total", "cyc_tier2", "cyc_tier3", "cyc_tier4",
-                 "ovl_scan", "cyc_ovl_scan"]
+                 "ovl_scan", "cyc_ovl_scan", "da_rej1", "da_ovl1", "da_fp64", "cyc_da1"]
 
 
 class MCError(RuntimeError):
@@ -87,6 +89,11 @@ def lib():
         "mc_test_philox": ([vp, vp, i64, vp, vp], ci),
         "mc_test_log": ([vp, i64, vp], ci),
         "mc_total_energy_noalloc": ([vp, i64, dbl, vp, vp], ci),
+        "mc_set_surrogate": ([vp, ci, vp, i64, dbl, ci], ci),
+        "mc_da_samples": ([vp, ci, vp, vp, vp], ci),
+        "mc_mlp_forward": ([vp, vp, i64, vp], ci),
+        "mc_mlp_loss_grad": ([vp, vp, vp, i64, vp, vp], ci),
+        "mc_mlp_train": ([vp, vp, i64, vp, ci, ci, ctypes.c_float, vp, vp], ci),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -266,3 +273,54 @@ class System:
         out = np.zeros(cap, RECORD_DTYPE)
         n = _check(lib().mc_record_read(self._h, chain, out.ctypes.data, cap))
         return out[:n]
+
+    # ---- delayed acceptance with the learned surrogate ----
+    def set_surrogate(self, w_bf16, r_c: float = 4.0, W: int = 160, chain: int = 0):
+        """Install the surrogate's 6401 BF16 weights (uint16 bit patterns); None removes it."""
+        if w_bf16 is None:
+            _check(lib().mc_set_surrogate(self._h, chain, None, 0, float(r_c), int(W)))
+            return
+        w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+        _check(lib().mc_set_surrogate(self._h, chain, w.ctypes.data, int(w.shape[0]), float(r_c), int(W)))
+
+    def da_samples(self, chain: int = 0):
+        """Training samples of the chain's next trial moves: (v_pairs N x 66, y N, valid N)."""
+        n = int(lib().mc_num_ions(self._h, chain))
+        v = np.zeros((n, 2 * MLP_NIN), np.float32)
+        y = np.zeros(n, np.float32)
+        ok = np.zeros(n, np.uint8)
+        _check(lib().mc_da_samples(self._h, chain, v.ctypes.data, y.ctypes.data, ok.ctypes.data))
+        return v, y, ok.astype(bool)
+
+
+def mlp_forward(w_bf16, v) -> np.ndarray:
+    """The surrogate MLP at n points on the GPU (v: n x 33)."""
+    w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+    v = np.ascontiguousarray(v, dtype=np.float32).reshape(-1, MLP_NIN)
+    g = np.zeros(v.shape[0], np.float32)
+    _check(lib().mc_mlp_forward(w.ctypes.data, v.ctypes.data, v.shape[0], g.ctypes.data))
+    return g
+
+
+def mlp_loss_grad(w_bf16, v_pairs, y):
+    """Mean pair loss (g(v_trial) - g(v_old) - y)^2 and its FP32 gradient, on the GPU."""
+    w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+    v = np.ascontiguousarray(v_pairs, dtype=np.float32).reshape(-1, 2 * MLP_NIN)
+    yy = np.ascontiguousarray(y, dtype=np.float32)
+    loss = ctypes.c_double()
+    grad = np.zeros(MLP_NP, np.float32)
+    _check(lib().mc_mlp_loss_grad(w.ctypes.data, v.ctypes.data, yy.ctypes.data, v.shape[0], ctypes.byref(loss),
+                                  grad.ctypes.data))
+    return loss.value, grad
+
+
+def mlp_train(v_pairs, y, w_init, epochs: int = 10, batch: int = 8192, lr: float = 1e-3):
+    """Adam training of the surrogate on the GPU; returns (BF16 weights, loss per epoch)."""
+    v = np.ascontiguousarray(v_pairs, dtype=np.float32).reshape(-1, 2 * MLP_NIN)
+    yy = np.ascontiguousarray(y, dtype=np.float32)
+    w0 = np.ascontiguousarray(w_init, dtype=np.uint16)
+    out = np.zeros(MLP_NP, np.uint16)
+    hist = np.zeros(max(epochs, 1), np.float64)
+    _check(lib().mc_mlp_train(v.ctypes.data, yy.ctypes.data, v.shape[0], w0.ctypes.data, int(epochs), int(batch),
+                              float(lr), out.ctypes.data, hist.ctypes.data))
+    return out, hist[:epochs]

@@ -11,6 +11,7 @@
 
 #include "../../include/mc.h"
 #include "mc_device.cuh"
+#include "mc_da.cuh"
 
 namespace mcg_host {
 size_t sweep_smem_bytes();
@@ -24,6 +25,18 @@ cudaError_t gr_launch(const float4 *pos, int N, int n_bins, double dr, float rma
 cudaError_t philox_test_launch(const uint4 *ctr, const uint2 *key, int n, uint4 *out_lib, uint4 *out_curand,
                                cudaStream_t st);
 cudaError_t log_test_launch(const double *u, int n, double *out, cudaStream_t st);
+cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt, int *cellid,
+                           unsigned short *fcell0, int *Q0, int *start, int *fill, int *cell_ions, float4 *cell_pos,
+                           int *slot_of, int *dcount, int B, cudaStream_t st);
+cudaError_t da_sample_launch(const mcg::ChainDev *ch, const mcg::DADev *dd, int B, int grid, float *V, float *Y,
+                             unsigned char *valid, cudaStream_t st);
+cudaError_t mlp_forward_launch(const unsigned short *w, const float *V, long long n, float *G, float *Z, cudaStream_t st);
+cudaError_t mlp_backward_launch(const unsigned short *w, const float *Z, const float *G, const float *Y, long long npairs,
+                                float inv_n, float *D, double *loss_part, cudaStream_t st);
+cudaError_t mlp_wgrad_launch(const float *V, const float *Z, const float *D, long long npts, int nblocks, float *part,
+                             float *grad, cudaStream_t st);
+cudaError_t adam_launch(float *p, float *m, float *v, const float *g, float lr, float b1, float b2, float eps, float bc1,
+                        float bc2, unsigned short *wbf, cudaStream_t st);
 }  // namespace mcg_host
 
 namespace {
@@ -73,6 +86,19 @@ struct Chain {
     uint64_t sweeps = 0;         // host mirror of *sweep
     uint64_t sweep_base = 0;     // sweep count when the positions were last set from the host
     float4 *cur() const { return pos[sweeps & 1]; }
+    // delayed acceptance (mc_set_surrogate)
+    bool da = false;
+    mcg::DADev hda{};             // host copy of the device descriptor
+    mcg::DADev *dda = nullptr;    // device descriptor
+    unsigned short *d_w = nullptr;
+    float *d_w2n = nullptr;
+    signed char *d_shell = nullptr;
+    int *d_cell_start = nullptr, *d_cell_ions = nullptr, *d_slot_of = nullptr, *d_cnt = nullptr, *d_cellid = nullptr;
+    int *d_fill = nullptr, *d_Q0 = nullptr, *d_dcount = nullptr;
+    float4 *d_cell_pos = nullptr;
+    unsigned short *d_fcell0 = nullptr;
+    unsigned *d_dlist = nullptr;
+    int ncell = 0;
 };
 
 struct GraphKey {
@@ -103,6 +129,7 @@ struct mc_system {
     int use_graph = 1;
     int policy = 0;  // ticket order: 0 group round-robin over chains, 1 sweep-synchronous
     int sm_count = 0, occ = 0;
+    int da_on = 1;  // chains with a surrogate sweep with delayed acceptance (MC_OPT_DA)
     std::map<std::pair<long long, int>, std::pair<mcg::Ticket *, int>> scheds;  // (n_sweeps, policy) -> schedule
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
@@ -205,13 +232,17 @@ mcg::ChainDev describe(const Chain &c)
     d.key0 = (unsigned)(c.seed & 0xffffffffu);
     d.key1 = c.chain_id;
     d.ctr3 = (unsigned)(c.seed >> 32);
+    d.da = nullptr;
     return d;
 }
 
 int sync_descriptors(mc_system *h)
 {
     h->h_chains.resize(h->chains.size());
-    for (size_t i = 0; i < h->chains.size(); ++i) h->h_chains[i] = describe(h->chains[i]);
+    for (size_t i = 0; i < h->chains.size(); ++i) {
+        h->h_chains[i] = describe(h->chains[i]);
+        if (h->chains[i].da && h->da_on) h->h_chains[i].da = h->chains[i].dda;
+    }
     CK(cudaMemcpy(h->d_chains, h->h_chains.data(), sizeof(mcg::ChainDev) * h->h_chains.size(), cudaMemcpyHostToDevice));
     return MC_OK;
 }
@@ -270,6 +301,21 @@ void free_chain(Chain &c)
     cudaFree(c.rows);
     cudaFree(c.rec);
     cudaFree(c.trace);
+    cudaFree(c.dda);
+    cudaFree(c.d_w);
+    cudaFree(c.d_w2n);
+    cudaFree(c.d_shell);
+    cudaFree(c.d_cell_start);
+    cudaFree(c.d_cell_ions);
+    cudaFree(c.d_slot_of);
+    cudaFree(c.d_cnt);
+    cudaFree(c.d_cellid);
+    cudaFree(c.d_fill);
+    cudaFree(c.d_Q0);
+    cudaFree(c.d_dcount);
+    cudaFree(c.d_cell_pos);
+    cudaFree(c.d_fcell0);
+    cudaFree(c.d_dlist);
     c = Chain();
 }
 
@@ -386,14 +432,56 @@ int grid_for(mc_system *h)
     long long g = (long long)h->sm_count * h->occ;
     if (h->ctas_override > 0) g = std::min<long long>(g, h->ctas_override);
     g = std::min(g, useful);
+    // delayed acceptance: fewer resident CTAs than the exclusion depth, so every counted ion's group has
+    // finished when a work item starts
+    if (h->da_on)
+        for (auto &c : h->chains)
+            if (c.da) g = std::min<long long>(g, c.hda.W - 1);
     return (int)std::max<long long>(1, g);
+}
+
+// Captured sweep graphs depend on which chains sweep with delayed acceptance.
+void drop_graphs(mc_system *h)
+{
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
+    h->graphs.clear();
+}
+
+bool any_da(const mc_system *h)
+{
+    if (!h->da_on) return false;
+    for (auto &c : h->chains)
+        if (c.da) return true;
+    return false;
+}
+
+// Delayed acceptance: one sweep per launch, each preceded by the preparation of every surrogate chain
+// (near-field cell list and feature grid of the sweep's start positions).  The control block is copied
+// once; later launches only reset its ticket counter, so an error or abort stays visible.
+cudaError_t enqueue_da(mc_system *h, long long n, int grid, const mcg::Ticket *sched, int count)
+{
+    cudaError_t e = cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream);
+    for (long long t = 0; t < n && e == cudaSuccess; ++t) {
+        if (t > 0) e = cudaMemsetAsync(&h->d_ctl->ticket, 0, sizeof(unsigned), h->stream);
+        for (size_t ci = 0; ci < h->chains.size(); ++ci) {
+            Chain &c = h->chains[ci];
+            if (!c.da || e != cudaSuccess) continue;
+            e = mcg_host::da_prep_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid, c.d_fcell0, c.d_Q0,
+                                         c.d_cell_start, c.d_fill, c.d_cell_ions, c.d_cell_pos, c.d_slot_of,
+                                         c.d_dcount, c.B, h->stream);
+        }
+        if (e == cudaSuccess)
+            e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), 1, h->stream);
+    }
+    return e;
 }
 
 int enqueue_sweeps(mc_system *h, long long n)
 {
     mcg::Ticket *sched = nullptr;
     int count = 0;
-    int rc = schedule_for(h, n, &sched, &count);
+    const bool da = any_da(h);
+    int rc = schedule_for(h, da ? 1 : n, &sched, &count);
     if (rc) return rc;
     const int grid = grid_for(h);
     const int nch = (int)h->chains.size();
@@ -403,8 +491,13 @@ int enqueue_sweeps(mc_system *h, long long n)
         if (it == h->graphs.end()) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e1 = cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream);
-            cudaError_t e2 = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream);
+            cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
+            if (da) {
+                e2 = enqueue_da(h, n, grid, sched, count);
+            } else {
+                e1 = cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream);
+                e2 = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream);
+            }
             cudaError_t e3 = cudaStreamEndCapture(h->stream, &g);
             if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -418,6 +511,8 @@ int enqueue_sweeps(mc_system *h, long long n)
             it = h->graphs.emplace(key, ge).first;
         }
         CK(cudaGraphLaunch(it->second, h->stream));
+    } else if (da) {
+        CK(enqueue_da(h, n, grid, sched, count));
     } else {
         CK(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream));
         CK(mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream));
@@ -619,6 +714,10 @@ int mc_stats(mc_handle h, int chain, mc_stats_t *out)
     out->cyc_tier[2] = v[mcg::CNT_CYC_T4];
     out->ovl_scan = v[mcg::CNT_OVL_SCAN];
     out->cyc_ovl_scan = v[mcg::CNT_CYC_OVL];
+    out->da_rej1 = v[mcg::CNT_DA_REJ1];
+    out->da_ovl1 = v[mcg::CNT_DA_OVL1];
+    out->da_fp64 = v[mcg::CNT_DA_FP64];
+    out->cyc_da1 = v[mcg::CNT_CYC_DA1];
     return MC_OK;
 }
 
@@ -777,6 +876,10 @@ static int set_option(mc_handle h, int option, int64_t value)
         if (value < 0 || value > 1) return fail(MC_ERR_INVALID, "policy %lld", (long long)value);
         h->policy = (int)value;
         return MC_OK;
+    case MC_OPT_DA:
+        h->da_on = value ? 1 : 0;
+        drop_graphs(h);
+        return sync_descriptors(h);
     default:
         return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
@@ -804,6 +907,7 @@ int mc_get_option(mc_handle h, int option, int64_t *value)
     case MC_OPT_SKIP_PUBLISH: *value = h->skip_ticket; return MC_OK;
     case MC_OPT_USE_GRAPH: *value = h->use_graph; return MC_OK;
     case MC_OPT_POLICY: *value = h->policy; return MC_OK;
+    case MC_OPT_DA: *value = h->da_on; return MC_OK;
     default: return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
 }
@@ -869,6 +973,285 @@ int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t
     if (best_policy) *best_policy = bp;
     if (best_ctas) *best_ctas = bc == 0 ? full : bc;
     if (best_ms) *best_ms = best;
+    return MC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Delayed acceptance with the learned surrogate (see include/mc.h).
+
+int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W)
+{
+    int rc = check_chain(h, chain);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    Chain &c = h->chains[chain];
+    if (!w_bf16) {
+        c.da = false;
+        drop_graphs(h);
+        return sync_descriptors(h);
+    }
+    if (n_w != mcg::DA_NP) return fail(MC_ERR_INVALID, "the surrogate has %d weights, got %lld", mcg::DA_NP, (long long)n_w);
+    if (!(r_c > 0.0) || !(r_c <= 5.0 * c.sigma)) return fail(MC_ERR_INVALID, "r_c = %g outside (0, 5 sigma]", r_c);
+    if (W < 2) return fail(MC_ERR_INVALID, "exclusion depth W = %d below 2", W);
+    std::vector<float> wf(mcg::DA_NP);
+    for (int k = 0; k < mcg::DA_NP; ++k) {
+        const uint32_t u = (uint32_t)w_bf16[k] << 16;
+        std::memcpy(&wf[k], &u, 4);
+        if (!std::isfinite(wf[k])) return fail(MC_ERR_INVALID, "weight %d is not finite", k);
+    }
+    // near-field cells: edge >= r_c + twice the largest displacement, so the 27 cells around an ion's start
+    // position hold every ion within r_c of its old or trial position at any time of the sweep
+    const double D = (double)(float)(2.0 * c.h);
+    const double emin = (r_c + 2.0 * std::sqrt(3.0) * 0.5 * D) * (1.0 + 0x1p-8) + 1e-6;
+    const int G = std::max(1, std::min(64, (int)std::floor(2.0 * c.R / emin)));
+    // (re)allocate
+    cudaFree(c.dda); cudaFree(c.d_w); cudaFree(c.d_w2n); cudaFree(c.d_shell); cudaFree(c.d_cell_start);
+    cudaFree(c.d_cell_ions); cudaFree(c.d_slot_of); cudaFree(c.d_cnt); cudaFree(c.d_cellid); cudaFree(c.d_fill);
+    cudaFree(c.d_Q0); cudaFree(c.d_dcount); cudaFree(c.d_cell_pos); cudaFree(c.d_fcell0); cudaFree(c.d_dlist);
+    c.dda = nullptr; c.d_w = nullptr; c.d_w2n = nullptr; c.d_shell = nullptr; c.d_cell_start = nullptr;
+    c.d_cell_ions = nullptr; c.d_slot_of = nullptr; c.d_cnt = nullptr; c.d_cellid = nullptr; c.d_fill = nullptr;
+    c.d_Q0 = nullptr; c.d_dcount = nullptr; c.d_cell_pos = nullptr; c.d_fcell0 = nullptr; c.d_dlist = nullptr;
+    c.da = false;
+    c.ncell = G * G * G;
+    const size_t N = (size_t)c.N, B = (size_t)c.B;
+    CK(cudaMalloc(&c.dda, sizeof(mcg::DADev)));
+    CK(cudaMalloc(&c.d_w, sizeof(uint16_t) * mcg::DA_NP));
+    CK(cudaMalloc(&c.d_w2n, sizeof(float) * mcg::DA_H));
+    CK(cudaMalloc(&c.d_shell, mcg::DA_NSHELL + 4));
+    CK(cudaMalloc(&c.d_cell_start, sizeof(int) * ((size_t)c.ncell + 1)));
+    CK(cudaMalloc(&c.d_cnt, sizeof(int) * (size_t)c.ncell));
+    CK(cudaMalloc(&c.d_fill, sizeof(int) * (size_t)c.ncell));
+    CK(cudaMalloc(&c.d_cell_ions, sizeof(int) * N));
+    CK(cudaMalloc(&c.d_slot_of, sizeof(int) * N));
+    CK(cudaMalloc(&c.d_cellid, sizeof(int) * N));
+    CK(cudaMalloc(&c.d_cell_pos, sizeof(float4) * N));
+    CK(cudaMalloc(&c.d_fcell0, sizeof(uint16_t) * N));
+    CK(cudaMalloc(&c.d_Q0, sizeof(int) * mcg::DA_NC));
+    CK(cudaMalloc(&c.d_dcount, sizeof(int) * B));
+    CK(cudaMalloc(&c.d_dlist, sizeof(unsigned) * B * mcg::S));
+    CK(cudaMemset(c.d_dcount, 0, sizeof(int) * B));
+    // shell of a feature-cell offset: floor((e sqrt(n2) - r_c) / Delta) in FP64, clamped to 31, -1 inside r_c
+    std::vector<signed char> shell(mcg::DA_NSHELL + 4, -1);
+    const double e = (2.0 * c.R) / (double)mcg::DA_G, delta = (2.0 * c.R - r_c) / 32.0;
+    for (int n2 = 0; n2 < mcg::DA_NSHELL; ++n2) {
+        const double dist = e * std::sqrt((double)n2);
+        if (dist < r_c) continue;
+        const double k = std::floor((dist - r_c) / delta);
+        shell[n2] = (signed char)(k > 31.0 ? 31 : (int)k);
+    }
+    std::vector<float> w2n(mcg::DA_H);
+    for (int o = 0; o < mcg::DA_H; ++o) {
+        double sum = 0.0;
+        for (int i = 0; i < mcg::DA_H; ++i) sum += std::fabs((double)wf[mcg::DA_OFF_W2 + o * mcg::DA_H + i]);
+        w2n[o] = std::nextafter((float)sum, 3.0e38f);
+    }
+    CK(cudaMemcpy(c.d_w, w_bf16, sizeof(uint16_t) * mcg::DA_NP, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.d_w2n, w2n.data(), sizeof(float) * mcg::DA_H, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.d_shell, shell.data(), shell.size(), cudaMemcpyHostToDevice));
+    mcg::DADev d{};
+    d.w = c.d_w;
+    d.w2n = c.d_w2n;
+    d.shell = c.d_shell;
+    d.cell_start = c.d_cell_start;
+    d.cell_ions = c.d_cell_ions;
+    d.cell_pos = c.d_cell_pos;
+    d.slot_of = c.d_slot_of;
+    d.fcell0 = c.d_fcell0;
+    d.Q0 = c.d_Q0;
+    d.dcount = c.d_dcount;
+    d.dlist = c.d_dlist;
+    d.rc2 = r_c * r_c;
+    d.R = c.R;
+    d.rc2_lo = std::nextafter((float)(d.rc2 * (1.0 - 0x1p-19)), 0.0f);
+    d.rc2_hi = std::nextafter((float)(d.rc2 * (1.0 + 0x1p-19)), 3.0e38f);
+    d.nf_scale = (float)((double)G / (2.0 * c.R));
+    d.nf_R = (float)c.R;
+    d.Rf = (float)c.R;
+    d.icf = (float)((double)mcg::DA_G / (2.0 * c.R));
+    d.Rr = (float)c.R;
+    d.nf_G = G;
+    d.W = W;
+    c.hda = d;
+    CK(cudaMemcpy(c.dda, &d, sizeof d, cudaMemcpyHostToDevice));
+    c.da = true;
+    drop_graphs(h);
+    return sync_descriptors(h);
+}
+
+int mc_da_samples(mc_handle h, int chain, float *v_pairs, float *y, uint8_t *valid)
+{
+    int rc = check_chain(h, chain);
+    if (rc) return rc;
+    if (!v_pairs || !y || !valid) return fail(MC_ERR_INVALID, "NULL output");
+    Chain &c = h->chains[chain];
+    if (!c.dda) return fail(MC_ERR_INVALID, "chain %d has no surrogate set (mc_set_surrogate)", chain);
+    CK(cudaStreamSynchronize(h->stream));
+    const size_t N = (size_t)c.N;
+    float *dV = nullptr, *dY = nullptr;
+    unsigned char *dv = nullptr;
+    CK(cudaMalloc(&dV, sizeof(float) * 66 * N));
+    CK(cudaMalloc(&dY, sizeof(float) * N));
+    CK(cudaMalloc(&dv, N));
+    cudaError_t e = mcg_host::da_prep_launch(h->d_chains + chain, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid, c.d_fcell0,
+                                             c.d_Q0, c.d_cell_start, c.d_fill, c.d_cell_ions, c.d_cell_pos,
+                                             c.d_slot_of, c.d_dcount, c.B, h->stream);
+    if (e == cudaSuccess) e = mcg_host::da_sample_launch(h->d_chains + chain, c.dda, c.B, h->sm_count, dV, dY, dv, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v_pairs, dV, sizeof(float) * 66 * N, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, dY, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(valid, dv, N, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dV);
+    cudaFree(dY);
+    cudaFree(dv);
+    if (e != cudaSuccess) return fail(MC_ERR_CUDA, "training samples: %s", cudaGetErrorString(e));
+    return MC_OK;
+}
+
+namespace {
+
+// Device buffers of one forward/backward pass over npairs sample pairs.
+struct MlpPass {
+    float *G = nullptr, *Z = nullptr, *D = nullptr, *part = nullptr, *grad = nullptr;
+    double *lp = nullptr;
+    int nblocks = 0;
+    long long cap = 0;
+    ~MlpPass()
+    {
+        cudaFree(G); cudaFree(Z); cudaFree(D); cudaFree(part); cudaFree(grad); cudaFree(lp);
+    }
+    cudaError_t alloc(long long npairs, int sms)
+    {
+        cap = npairs;
+        nblocks = std::max(1, sms);
+        cudaError_t e;
+        if ((e = cudaMalloc(&G, sizeof(float) * 2 * npairs)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&Z, sizeof(float) * 2 * npairs * 2 * mcg::DA_H)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D, sizeof(float) * 2 * npairs * (2 * mcg::DA_H + 1))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&part, sizeof(float) * (size_t)nblocks * mcg::DA_NP)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&grad, sizeof(float) * mcg::DA_NP)) != cudaSuccess) return e;
+        return cudaMalloc(&lp, sizeof(double) * (size_t)((npairs + 255) / 256));
+    }
+    // loss partials and the gradient of the mean pair loss over npairs pairs starting at V / Y
+    cudaError_t run(const unsigned short *w, const float *V, const float *Y, long long npairs, float inv_n, cudaStream_t st)
+    {
+        cudaError_t e = mcg_host::mlp_forward_launch(w, V, 2 * npairs, G, Z, st);
+        if (e == cudaSuccess) e = mcg_host::mlp_backward_launch(w, Z, G, Y, npairs, inv_n, D, lp, st);
+        if (e == cudaSuccess) e = mcg_host::mlp_wgrad_launch(V, Z, D, 2 * npairs, nblocks, part, grad, st);
+        return e;
+    }
+};
+
+int device_sms()
+{
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+}  // namespace
+
+int mc_mlp_forward(const uint16_t *w_bf16, const float *v, int64_t n, float *g)
+{
+    if (!w_bf16 || !v || !g || n < 0) return fail(MC_ERR_INVALID, "bad arguments");
+    if (n == 0) return MC_OK;
+    unsigned short *dw = nullptr;
+    float *dv = nullptr, *dg = nullptr;
+    cudaError_t e = cudaMalloc(&dw, sizeof(uint16_t) * mcg::DA_NP);
+    if (e == cudaSuccess) e = cudaMalloc(&dv, sizeof(float) * mcg::DA_NIN * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dg, sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(dw, w_bf16, sizeof(uint16_t) * mcg::DA_NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dv, v, sizeof(float) * mcg::DA_NIN * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = mcg_host::mlp_forward_launch(dw, dv, n, dg, nullptr, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(g, dg, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(dw);
+    cudaFree(dv);
+    cudaFree(dg);
+    if (e != cudaSuccess) return fail(MC_ERR_CUDA, "mc_mlp_forward: %s", cudaGetErrorString(e));
+    return MC_OK;
+}
+
+int mc_mlp_loss_grad(const uint16_t *w_bf16, const float *v_pairs, const float *y, int64_t n, double *loss, float *grad)
+{
+    if (!w_bf16 || !v_pairs || !y || n < 1) return fail(MC_ERR_INVALID, "bad arguments");
+    unsigned short *dw = nullptr;
+    float *dv = nullptr, *dy = nullptr;
+    MlpPass pass;
+    std::vector<double> lp((size_t)((n + 255) / 256));
+    cudaError_t e = cudaMalloc(&dw, sizeof(uint16_t) * mcg::DA_NP);
+    if (e == cudaSuccess) e = cudaMalloc(&dv, sizeof(float) * 66 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dy, sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = pass.alloc(n, device_sms());
+    if (e == cudaSuccess) e = cudaMemcpy(dw, w_bf16, sizeof(uint16_t) * mcg::DA_NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dv, v_pairs, sizeof(float) * 66 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dy, y, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = pass.run(dw, dv, dy, n, 1.0f / (float)n, 0);
+    if (e == cudaSuccess && grad) e = cudaMemcpy(grad, pass.grad, sizeof(float) * mcg::DA_NP, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(lp.data(), pass.lp, sizeof(double) * lp.size(), cudaMemcpyDeviceToHost);
+    cudaFree(dw);
+    cudaFree(dv);
+    cudaFree(dy);
+    if (e != cudaSuccess) return fail(MC_ERR_CUDA, "mc_mlp_loss_grad: %s", cudaGetErrorString(e));
+    if (loss) {
+        double s = 0.0;
+        for (double x : lp) s += x;
+        *loss = s / (double)n;
+    }
+    return MC_OK;
+}
+
+int mc_mlp_train(const float *v_pairs, const float *y, int64_t n, const uint16_t *w_init, int epochs, int batch,
+                 float lr, uint16_t *w_out, double *loss_per_epoch)
+{
+    if (!v_pairs || !y || !w_init || !w_out || n < 1 || epochs < 0 || batch < 1 || !(lr > 0.0f))
+        return fail(MC_ERR_INVALID, "bad arguments");
+    const long long nb = std::min<long long>(batch, n);
+    float *dv = nullptr, *dy = nullptr, *p = nullptr, *m = nullptr, *v = nullptr;
+    unsigned short *wbf = nullptr;
+    MlpPass pass;
+    std::vector<float> p0(mcg::DA_NP);
+    for (int k = 0; k < mcg::DA_NP; ++k) {
+        const uint32_t u = (uint32_t)w_init[k] << 16;
+        std::memcpy(&p0[k], &u, 4);
+    }
+    std::vector<double> lp((size_t)((nb + 255) / 256));
+    cudaError_t e = cudaMalloc(&dv, sizeof(float) * 66 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dy, sizeof(float) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&p, sizeof(float) * mcg::DA_NP);
+    if (e == cudaSuccess) e = cudaMalloc(&m, sizeof(float) * mcg::DA_NP);
+    if (e == cudaSuccess) e = cudaMalloc(&v, sizeof(float) * mcg::DA_NP);
+    if (e == cudaSuccess) e = cudaMalloc(&wbf, sizeof(uint16_t) * mcg::DA_NP);
+    if (e == cudaSuccess) e = pass.alloc(nb, device_sms());
+    if (e == cudaSuccess) e = cudaMemcpy(dv, v_pairs, sizeof(float) * 66 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dy, y, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p, p0.data(), sizeof(float) * mcg::DA_NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m, 0, sizeof(float) * mcg::DA_NP);
+    if (e == cudaSuccess) e = cudaMemset(v, 0, sizeof(float) * mcg::DA_NP);
+    if (e == cudaSuccess) e = cudaMemcpy(wbf, w_init, sizeof(uint16_t) * mcg::DA_NP, cudaMemcpyHostToDevice);
+    long long t = 0;
+    const float b1 = 0.9f, b2 = 0.999f;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+        double sum = 0.0;
+        for (long long s0 = 0; s0 < n && e == cudaSuccess; s0 += nb) {
+            const long long np = std::min(nb, n - s0);
+            e = pass.run(wbf, dv + 66 * s0, dy + s0, np, 1.0f / (float)np, 0);
+            ++t;
+            if (e == cudaSuccess)
+                e = mcg_host::adam_launch(p, m, v, pass.grad, lr, b1, b2, 1e-8f, 1.0f - std::pow(b1, (float)t),
+                                          1.0f - std::pow(b2, (float)t), wbf, 0);
+            if (e == cudaSuccess) e = cudaMemcpy(lp.data(), pass.lp, sizeof(double) * (size_t)((np + 255) / 256), cudaMemcpyDeviceToHost);
+            for (long long q = 0; q < (np + 255) / 256; ++q) sum += lp[(size_t)q];
+        }
+        if (loss_per_epoch) loss_per_epoch[ep] = sum / (double)n;
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(w_out, wbf, sizeof(uint16_t) * mcg::DA_NP, cudaMemcpyDeviceToHost);
+    cudaFree(dv);
+    cudaFree(dy);
+    cudaFree(p);
+    cudaFree(m);
+    cudaFree(v);
+    cudaFree(wbf);
+    if (e != cudaSuccess) return fail(MC_ERR_CUDA, "mc_mlp_train: %s", cudaGetErrorString(e));
     return MC_OK;
 }
 

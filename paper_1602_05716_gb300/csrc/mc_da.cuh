@@ -1,0 +1,338 @@
+// mc_da.cuh -- device-side definitions of delayed acceptance (a two-stage
+// Metropolis test in the sense of Christen & Fox, 2005) on top of the exact
+// sequential chain of Sec. 2.
+//
+// Stage 1 decides on a cheap surrogate energy change
+//     dEt = l_B q_i ([phi_near + g(v)](x') - [phi_near + g(v)](x)),
+// phi_near the exact Coulomb sum over counted ions within r_c and g a
+// 33-64-64-1 SiLU MLP with BF16 weights fed with 32 shell net charges around
+// the point and its radial coordinate.  Survivors pay the exact O(N) sum of
+// the plain chain and are accepted with min(1, exp(-(dE - dEt))).
+//
+// Counted ions for the move of ion i in group g: every ion except i, the
+// earlier ions of g and all ions of the W groups tried just before g (cyclic
+// over the sweep).  The set depends only on the move index, so dEt is a
+// function of the current state (the delayed-acceptance ratio then keeps the
+// chain's stationary distribution exactly).  W is at least the number of
+// resident CTAs plus one, so every counted ion's current position is final
+// when the work item starts: stage 1 of all S moves of a group runs before
+// the pair sums, which then cover the stage-1 survivors only.
+#pragma once
+
+#include "mc_device.cuh"
+
+namespace mcg {
+
+constexpr int DA_G = 16;                                                        // feature grid cells per axis
+constexpr int DA_NC = DA_G * DA_G * DA_G;                                       // 4096 feature cells
+constexpr int DA_NIN = 33, DA_H = 64;                                           // MLP shape
+constexpr int DA_NP = DA_H * DA_NIN + DA_H + DA_H * DA_H + DA_H + DA_H + 1;    // 6401 parameters
+constexpr int DA_NSHELL = 3 * (DA_G - 1) * (DA_G - 1) + 1;                      // squared cell offsets 0..675
+constexpr int DA_OFF_B1 = DA_H * DA_NIN, DA_OFF_W2 = DA_OFF_B1 + DA_H, DA_OFF_B2 = DA_OFF_W2 + DA_H * DA_H,
+              DA_OFF_W3 = DA_OFF_B2 + DA_H, DA_OFF_B3 = DA_OFF_W3 + DA_H;
+constexpr int OUT_DA1 = 4;  // outcome: rejected by the surrogate stage
+
+// Per-chain delayed-acceptance state (device memory, written by the host at
+// set-up and by the per-sweep preparation kernels).
+struct DADev {
+    const unsigned short *w;       // BF16 weights, layout W1[64][33], b1, W2[64][64], b2, W3, b3
+    const float *w2n;              // ||W2[o]||_1, rounded up (error bound of the second layer)
+    const signed char *shell;      // shell of a feature-cell offset by its squared length, -1 = left out
+    const int *cell_start;         // near-field cell list of the sweep's start positions (ncell + 1)
+    const int *cell_ions;          // ion indices in cell order (N)
+    float4 *cell_pos;              // their positions in cell order; accepted moves write theirs in place
+    const int *slot_of;            // slot of ion j in the cell order (N)
+    const unsigned short *fcell0;  // feature cell of every ion at the start of the sweep (N)
+    const int *Q0;                 // net valence of every feature cell at the start of the sweep (DA_NC)
+    int *dcount;                   // per group of the sweep: feature-cell changes recorded
+    unsigned *dlist;               // per group, S entries: from | to << 12 | (valence & 0xff) << 24
+    double rc2;                    // r_c^2
+    double R;                      // sphere radius (radial input)
+    float rc2_lo, rc2_hi;          // FP32 squared distances below/above certainly inside/outside r_c
+    float nf_scale, nf_R;          // near-field cell of x: floor((x + nf_R) * nf_scale)
+    float Rf, icf;                 // feature cell of x: floor((x + Rf) * icf) in FP32 (bit-identical to the oracle)
+    float Rr;                      // fl32(R) for the FP32 radial input
+    int nf_G;                      // near-field cells per axis
+    int W;                         // exclusion depth in groups
+};
+
+__device__ __forceinline__ int da_fcell_axis(float x, float Rf, float icf)
+{
+    const float t = __fmul_rn(__fadd_rn(x, Rf), icf);
+    const int c = (int)floorf(t);
+    return c < 0 ? 0 : (c > DA_G - 1 ? DA_G - 1 : c);
+}
+
+__device__ __forceinline__ int da_fcell(const DADev &d, float x, float y, float z)
+{
+    return (da_fcell_axis(x, d.Rf, d.icf) * DA_G + da_fcell_axis(y, d.Rf, d.icf)) * DA_G + da_fcell_axis(z, d.Rf, d.icf);
+}
+
+__device__ __forceinline__ int da_ncell_axis(const DADev &d, float x)
+{
+    const int c = (int)floorf((x + d.nf_R) * d.nf_scale);
+    return c < 0 ? 0 : (c > d.nf_G - 1 ? d.nf_G - 1 : c);
+}
+
+__device__ __forceinline__ float bf16f(unsigned short b)
+{
+    return __uint_as_float((unsigned)b << 16);
+}
+
+// Is ion j counted for the move of ion i (group g = i / S) in a chain of B groups, exclusion depth Wg = min(W, B-1)?
+__device__ __forceinline__ bool da_counted(int i, int g, int B, int Wg, int j)
+{
+    if (j == i) return false;
+    const int J = j / S;
+    if (J == g) return j > i;
+    int back = g - J;
+    if (back < 0) back += B;
+    return back > Wg;
+}
+
+// exp(x) in FP64 from +, -, *, / only, the steps of the reference definition:
+// x = k ln2 + r, k = round-half-even(x / ln2_head), r = (x - k ln2_head) - k ln2_tail;
+// exp(r) by twenty nested Horner steps p = 1 + (p r) / m, m = 20 .. 1; scaled by 2^k.
+// Zero below -700, +inf above 709.
+__device__ __forceinline__ double series_exp(double x)
+{
+    const double head = 0.693147180601954460144042968750, tail = -4.2009150726810847291823431924e-11;
+    if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+    if (x < -700.0) return 0.0;
+    const double kd = rint(__ddiv_rn(x, head));
+    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(kd, head)), __dmul_rn(kd, tail));
+    double p = 1.0;
+#pragma unroll 1
+    for (int m = 20; m >= 1; --m) p = __dadd_rn(1.0, __ddiv_rn(__dmul_rn(p, r), (double)m));
+    return scalbn(p, (int)kd);
+}
+
+__device__ __forceinline__ double silu64(double z)
+{
+    return __ddiv_rn(z, __dadd_rn(1.0, series_exp(-z)));
+}
+
+// ---------------------------------------------------------------------------
+// Stage-1 building blocks shared by the sweep kernel and the training-sample kernel.
+
+constexpr int DA_FRS = 33;  // row stride of the per-point shell histograms (32 shells, padded)
+
+// Net valence of every feature cell over the ions counted for this group's moves, except that the
+// group's own later ions are left for the per-move add-back: the start-of-sweep grid, minus the own group
+// and the Wg groups before it at their start-of-sweep cells, plus the recorded cell changes of the
+// counted groups already tried in this sweep (0 .. g - Wg - 1; their records precede the ledger step
+// acquired before this call).
+__device__ inline void da_build_Q(int *Qs, const DADev &d, int g, int B, int N, const float4 *Pprev, int Wg)
+{
+    const int tid = threadIdx.x;
+    for (int q = tid; q < DA_NC; q += T) Qs[q] = __ldg(&d.Q0[q]);
+    __syncthreads();
+    const int nrem = (Wg + 1) * S;
+    for (int e = tid; e < nrem; e += T) {
+        const int t = e / S, l = e - t * S;
+        int v = g - t;
+        if (v < 0) v += B;
+        const int j = v * S + l;
+        if (j < N) atomicSub(&Qs[__ldg(&d.fcell0[j])], (int)__ldg(&Pprev[j].w));
+    }
+    for (int v = tid; v < g - Wg; v += T) {
+        const int n = __ldcg(&d.dcount[v]);
+        for (int e = 0; e < n; ++e) {
+            const unsigned x = __ldcg(&d.dlist[(size_t)v * S + e]);
+            const int q = (int)(signed char)(x >> 24);
+            atomicSub(&Qs[x & 0xfffu], q);
+            atomicAdd(&Qs[(x >> 12) & 0xfffu], q);
+        }
+    }
+    __syncthreads();
+}
+
+// Shell histogram of one point over a range of feature cells (one thread), accumulated into row F.
+__device__ __forceinline__ void da_hist_range(int *F, const int *Qs, const signed char *shell, int cp, int c0, int c1)
+{
+    const int px = cp >> 8, py = (cp >> 4) & 15, pz = cp & 15;
+    for (int q = c0; q < c1; ++q) {
+        const int v = Qs[q];
+        if (v == 0) continue;
+        const int dx = (q >> 8) - px, dy = ((q >> 4) & 15) - py, dz = (q & 15) - pz;
+        const int sh = shell[dx * dx + dy * dy + dz * dz];
+        if (sh >= 0) atomicAdd(&F[sh], v);
+    }
+}
+
+// ... plus the group's own ions after k (counted, at their old positions).
+__device__ __forceinline__ void da_hist_own(int *F, const float4 *own, const DADev &d, const signed char *shell, int cp,
+                                            int k, int nk)
+{
+    const int px = cp >> 8, py = (cp >> 4) & 15, pz = cp & 15;
+    for (int j = k + 1; j < nk; ++j) {
+        const float4 y = own[j];
+        const int q = da_fcell(d, y.x, y.y, y.z);
+        const int dx = (q >> 8) - px, dy = ((q >> 4) & 15) - py, dz = (q & 15) - pz;
+        const int sh = shell[dx * dx + dy * dy + dz * dz];
+        if (sh >= 0) atomicAdd(&F[sh], (int)y.w);
+    }
+}
+
+// FP32 radial input |p| / R with its error (<= 4u relative: three rounded operations on the squared norm,
+// the square root, the division, and fl32(R)).
+__device__ __forceinline__ float da_radial32(const DADev &d, float4 p)
+{
+    return __fdiv_rn(sqrtf(fmaf(p.z, p.z, fmaf(p.y, p.y, p.x * p.x))), d.Rr);
+}
+
+__device__ __forceinline__ float silu32(float z)
+{
+    return __fdiv_rn(z, __fadd_rn(1.0f, expf(-z)));
+}
+
+// g(v) in FP32 (BF16 weights held as floats in Wf) with a bound of |g32 - g64|, g64 the reference FP64
+// arithmetic on the same weights and exact inputs; v32 carries up to 4u relative error.
+// Per layer: FMA chains of n terms err by <= (n+1) u sum |w x|; |silu'| <= 1.1; the FP32 silu adds
+// <= 4u |h| + 2u |z| (expf within 2 ulp, one add, one division).
+__device__ inline void da_mlp32(const float *Wf, const float *w2n, const float v[DA_NIN], float &g, float &eg)
+{
+    const float *W1 = Wf, *b1 = Wf + DA_OFF_B1, *W2 = Wf + DA_OFF_W2, *b2 = Wf + DA_OFF_B2, *W3 = Wf + DA_OFF_W3;
+    const float ev32 = 4.0f * U32 * fabsf(v[32]);
+    float h1[DA_H];
+    float mh = 0.f, me = 0.f;
+#pragma unroll
+    for (int o = 0; o < DA_H; ++o) {
+        float z0 = b1[o], z1 = 0.f, M = fabsf(b1[o]);
+#pragma unroll
+        for (int i = 0; i < 32; i += 2) {
+            z0 = fmaf(W1[o * DA_NIN + i], v[i], z0);
+            z1 = fmaf(W1[o * DA_NIN + i + 1], v[i + 1], z1);
+            M = fmaf(fabsf(W1[o * DA_NIN + i]), fabsf(v[i]), M);
+            M = fmaf(fabsf(W1[o * DA_NIN + i + 1]), fabsf(v[i + 1]), M);
+        }
+        z0 = fmaf(W1[o * DA_NIN + 32], v[32], z0);
+        M = fmaf(fabsf(W1[o * DA_NIN + 32]), fabsf(v[32]), M);
+        const float z = z0 + z1;
+        const float ez = 36.0f * U32 * M + fabsf(W1[o * DA_NIN + 32]) * ev32;
+        const float h = silu32(z);
+        h1[o] = h;
+        mh = fmaxf(mh, fabsf(h));
+        me = fmaxf(me, 1.1f * ez + 4.0f * U32 * fabsf(h) + 2.0f * U32 * fabsf(z));
+    }
+    float gs = Wf[DA_OFF_B3], Mg = fabsf(Wf[DA_OFF_B3]), eacc = 0.f;
+#pragma unroll 1
+    for (int o = 0; o < DA_H; ++o) {
+        float z0 = b2[o], z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+        for (int i = 0; i < DA_H; i += 4) {
+            z0 = fmaf(W2[o * DA_H + i], h1[i], z0);
+            z1 = fmaf(W2[o * DA_H + i + 1], h1[i + 1], z1);
+            z2 = fmaf(W2[o * DA_H + i + 2], h1[i + 2], z2);
+            z3 = fmaf(W2[o * DA_H + i + 3], h1[i + 3], z3);
+        }
+        const float z = (z0 + z1) + (z2 + z3);
+        const float ez = 68.0f * U32 * (fabsf(b2[o]) + w2n[o] * mh) + w2n[o] * me;
+        const float h = silu32(z);
+        const float eh = 1.1f * ez + 4.0f * U32 * fabsf(h) + 2.0f * U32 * fabsf(z);
+        gs = fmaf(W3[o], h, gs);
+        Mg = fmaf(fabsf(W3[o]), fabsf(h), Mg);
+        eacc = fmaf(fabsf(W3[o]), eh, eacc);
+    }
+    g = gs;
+    eg = (66.0f * U32 * Mg + eacc) * (1.0f + 0x1p-8f);
+}
+
+// Near field of move k (one warp): FP32 sums of q_j / r over counted ions within r_c of the old (0) and the
+// trial (1) position, their sums of |q_j| / r, the trial's overlap with a counted ion (exact: the FP64 squared
+// distance decides inside the FP32 band), and the largest number of terms one lane added.  Membership in r_c
+// is exact the same way.
+struct NearOut {
+    float ph0, ph1, A0, A1;
+    int nt, ovl;
+};
+
+__device__ inline NearOut da_near_warp(const DADev &d, int g, int B, int Wg, int i, float4 x, float4 a, float lo2, float hi2,
+                                double sig2)
+{
+    const int lane = threadIdx.x & 31;
+    const int G = d.nf_G;
+    const int cx = da_ncell_axis(d, x.x), cy = da_ncell_axis(d, x.y), cz = da_ncell_axis(d, x.z);
+    int lo = 0, cnt = 0;
+    if (lane < 27) {
+        const int ax = cx + lane / 9 - 1, ay = cy + (lane / 3) % 3 - 1, az = cz + lane % 3 - 1;
+        if (ax >= 0 && ay >= 0 && az >= 0 && ax < G && ay < G && az < G) {
+            const int q = (ax * G + ay) * G + az;
+            lo = __ldg(&d.cell_start[q]);
+            cnt = __ldg(&d.cell_start[q + 1]) - lo;
+        }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    float ph0 = 0.f, ph1 = 0.f, A0 = 0.f, A1 = 0.f;
+    int n0 = 0, n1 = 0, ovl = 0;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        // the cell holding candidate t: the first lane m whose inclusive count exceeds t
+        int m = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, m + step - 1);
+            if (v <= t) m += step;
+        }
+        const int lo_m = __shfl_sync(0xffffffffu, lo, m);
+        const int ex_m = __shfl_sync(0xffffffffu, incl - cnt, m);
+        if (t >= total) continue;
+        const int idx = lo_m + (t - ex_m);
+        const int j = __ldg(&d.cell_ions[idx]);
+        if (!da_counted(i, g, B, Wg, j)) continue;
+        const float4 y = __ldcg(&d.cell_pos[idx]);
+        const float aq = fabsf(y.w);
+        {
+            const float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            bool in = d2 < d.rc2_lo;
+            if (!in && !(d2 > d.rc2_hi)) in = d2_fp64(x.x, x.y, x.z, y.x, y.y, y.z) < d.rc2;
+            if (in) {
+                const float r = rsqrt_approx(d2);
+                ph0 = fmaf(y.w, r, ph0);
+                A0 = fmaf(aq, r, A0);
+                ++n0;
+            }
+        }
+        {
+            const float dx = a.x - y.x, dy = a.y - y.y, dz = a.z - y.z;
+            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (d2 < lo2) ovl = 1;
+            else if (!(d2 > hi2) && d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < sig2) ovl = 1;
+            bool in = d2 < d.rc2_lo;
+            if (!in && !(d2 > d.rc2_hi)) in = d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < d.rc2;
+            if (in) {
+                const float r = rsqrt_approx(d2);
+                ph1 = fmaf(y.w, r, ph1);
+                A1 = fmaf(aq, r, A1);
+                ++n1;
+            }
+        }
+    }
+    NearOut o;
+    int nt = max(n0, n1);
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        ph0 += __shfl_xor_sync(0xffffffffu, ph0, s);
+        ph1 += __shfl_xor_sync(0xffffffffu, ph1, s);
+        A0 += __shfl_xor_sync(0xffffffffu, A0, s);
+        A1 += __shfl_xor_sync(0xffffffffu, A1, s);
+        nt = max(nt, __shfl_xor_sync(0xffffffffu, nt, s));
+        ovl |= __shfl_xor_sync(0xffffffffu, ovl, s);
+    }
+    o.ph0 = ph0;
+    o.ph1 = ph1;
+    o.A0 = A0;
+    o.A1 = A1;
+    o.nt = nt;
+    o.ovl = ovl;
+    return o;
+}
+
+}  // namespace mcg

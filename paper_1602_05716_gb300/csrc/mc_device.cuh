@@ -37,6 +37,7 @@ struct MoveRec {
     double dE;
     double dE32;
     double bound;  // proven FP32 error bound of dE32 (static part), +inf when the band was disabled
+    double dEt;    // surrogate energy change of a delayed-acceptance move (NaN otherwise)
     int tier;
     int pad;
 };
@@ -50,6 +51,8 @@ struct TraceRec {
 };
 
 // Per-chain device descriptor (read-only during a launch).
+struct DADev;
+
 struct ChainDev {
     float4 *pos[2];               // 2 x N_pad entries: x, y, z, valence (Sec. 3.1's float4 layout); the
                                   // positions after sweep v live in pos[(v + 1) & 1]
@@ -76,6 +79,7 @@ struct ChainDev {
     double Rc2;                   // (R - sigma/2)^2
     unsigned key0, key1, ctr3;    // Philox key (seed_lo, chain_id), counter word 3 (seed_hi)
     unsigned pad;
+    const struct DADev *da;       // delayed-acceptance state, nullptr for the plain chain
 };
 
 struct Ticket {
@@ -99,8 +103,10 @@ struct Ctl {
 constexpr int CNT_ACCEPT = 0, CNT_METRO = 1, CNT_OVERLAP = 2, CNT_WALL = 3, CNT_FP64 = 4, CNT_INTERVAL = 5,
               CNT_T2 = 6, CNT_T3 = 7, CNT_T4 = 8, CNT_ROUNDS = 9, CNT_CYC_WIN = 10, CNT_CYC_TILES = 11,
               CNT_CYC_RESOLVE = 12, CNT_CYC_GUARD = 13, CNT_CYC_TOTAL = 14, CNT_CYC_T2 = 15, CNT_CYC_T3 = 16,
-              CNT_CYC_T4 = 17, CNT_OVL_SCAN = 18, CNT_CYC_OVL = 19;
+              CNT_CYC_T4 = 17, CNT_OVL_SCAN = 18, CNT_CYC_OVL = 19, CNT_DA_REJ1 = 20, CNT_DA_OVL1 = 21,
+              CNT_DA_FP64 = 22, CNT_CYC_DA1 = 23;
 constexpr int NCOUNTERS = 24;
+constexpr float U32 = 0x1p-24f;  // unit roundoff of FP32
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): two 32x32 multiplies per round with
@@ -237,6 +243,29 @@ __device__ __forceinline__ float rcp_ftz(float x)
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Accurate FP32 pair term of move (old b, displacement d = a - b) against an ion y whose position is
+// settled for this move (every other group's tile, and the later ions of this group).  With e = y - b,
+// q_y (1/|a-y| - 1/|b-y|) = q_y Dd (rn ro)^2 / (rn + ro) where Dd = d . (2e - d) = |b-y|^2 - |a-y|^2: no
+// difference of two nearly equal inverse distances, so the rounding error scales with |d| / r^2 instead
+// of 1/r and the FP32 band stays narrow at large N.  Accumulates the term into s, |term| into Tt,
+// |q_y| rn ro into P (the bound's second sum) and the trial's squared distance into the minimum mn.
+__device__ __forceinline__ void pair_far(const float3 b, const float3 d, const float4 y, float &s, float &Tt, float &P,
+                                         float &mn)
+{
+    const float ex = y.x - b.x, ey = y.y - b.y, ez = y.z - b.z;
+    const float Do = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+    const float wx = fmaf(2.0f, ex, -d.x), wy = fmaf(2.0f, ey, -d.y), wz = fmaf(2.0f, ez, -d.z);
+    const float Dd = fmaf(d.z, wz, fmaf(d.y, wy, d.x * wx));
+    const float Dn = Do - Dd;
+    const float ro = rsqrt_ftz(Do), rn = rsqrt_ftz(Dn);
+    const float pr = rn * ro;
+    const float t = (Dd * pr) * (pr * rcp_ftz(rn + ro));
+    s = fmaf(y.w, t, s);
+    Tt = fmaf(fabsf(y.w), fabsf(t), Tt);
+    P = fmaf(fabsf(y.w), pr, P);
+    mn = fminf(mn, Dn);
 }
 
 // Error-free transformations in FP32 (Knuth's TwoSum, FMA-based TwoProduct).

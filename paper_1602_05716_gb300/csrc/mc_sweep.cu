@@ -35,6 +35,7 @@
 //  * Every wait is bounded by %globaltimer; on expiry the kernel records the
 //    error, raises an abort flag and all CTAs return.
 #include "mc_device.cuh"
+#include "mc_da.cuh"
 
 namespace mcg {
 
@@ -62,28 +63,34 @@ struct __align__(16) Smem {
     float plo[2][S];
     float phi[2][S];
     float dE32[S];
+    float dEt32[S];  // delayed acceptance: FP32 surrogate energy change
+    float dEtB[S];   // ... its error bound (then the stage-2 part of the static band)
     double dEv[S];  // dE used for the ledger and the records
+    double dEt64[S];  // delayed acceptance: the reference surrogate energy change, where computed
     unsigned ovo[S][WORDS], ovn[S][WORDS];    // x'_k overlaps old / trial position of in-group j < k
     unsigned wovo[S][WORDS], wovn[S][WORDS];  // ... of window ion j
     unsigned accw[WORDS], decw[WORDS], seen[WORDS], winacc[WORDS], acc0[WORDS], dec0[WORDS];
+    unsigned d64w[WORDS];  // dEt64 known
     unsigned char st[S];
     signed char outcome[S];
     unsigned char tier[S];
     unsigned char pad0[S];
+    unsigned char surv[S];  // moves that need pair sums (all moves of a plain chain; stage-1 survivors)
+    int damb[S];            // delayed acceptance: moves whose stage-1 decision needs the reference arithmetic
     double chunk[CHUNK];
     double redd[32];
     float redf[32];
     int ticket, ok, guard_k, ovl_flag;
     int hzs[2];
-    int pad1[2];
+    int ns, namb, ndl, pad1;
 };
 
 constexpr unsigned ST_WALL = 1u, ST_UZERO = 2u, ST_INACTIVE = 4u, ST_OVL_CERTAIN = 8u, ST_OVL_AMBIG = 16u,
-                   ST_OVL_POSSIBLE = 32u;
+                   ST_OVL_POSSIBLE = 32u, ST_DA_DONE = 64u;
+constexpr int OUT_INACTIVE = 15;  // padding slot of a ragged group (never recorded or counted)
 constexpr unsigned FULL = 0xffffffffu;
 
 // Bound constants (units of u = 2^-24); the derivation is in DESIGN.md ("FP32 error bound").
-constexpr float U32 = 0x1p-24f;
 constexpr float C_TERM = 10.0f;           // per-term error of q_j (1/r' - 1/r) relative to |q_j| (1/r' + 1/r)
                                           // (both-position ions, direct form)
 constexpr float C_SUM = 24.0f;            // FP32 partials of <= 16 terms, TwoSum-accumulated
@@ -143,29 +150,6 @@ __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsig
             return false;
         }
     }
-}
-
-// Accurate FP32 pair term of move (old b, displacement d = a - b) against an ion y whose position is
-// settled for this move (every other group's tile, and the later ions of this group).  With e = y - b,
-// q_y (1/|a-y| - 1/|b-y|) = q_y Dd (rn ro)^2 / (rn + ro) where Dd = d . (2e - d) = |b-y|^2 - |a-y|^2: no
-// difference of two nearly equal inverse distances, so the rounding error scales with |d| / r^2 instead
-// of 1/r and the FP32 band stays narrow at large N.  Accumulates the term into s, |term| into Tt,
-// |q_y| rn ro into P (the bound's second sum) and the trial's squared distance into the minimum mn.
-__device__ __forceinline__ void pair_far(const float3 b, const float3 d, const float4 y, float &s, float &Tt, float &P,
-                                         float &mn)
-{
-    const float ex = y.x - b.x, ey = y.y - b.y, ez = y.z - b.z;
-    const float Do = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-    const float wx = fmaf(2.0f, ex, -d.x), wy = fmaf(2.0f, ey, -d.y), wz = fmaf(2.0f, ez, -d.z);
-    const float Dd = fmaf(d.z, wz, fmaf(d.y, wy, d.x * wx));
-    const float Dn = Do - Dd;
-    const float ro = rsqrt_ftz(Do), rn = rsqrt_ftz(Dn);
-    const float pr = rn * ro;
-    const float t = (Dd * pr) * (pr * rcp_ftz(rn + ro));
-    s = fmaf(y.w, t, s);
-    Tt = fmaf(fabsf(y.w), fabsf(t), Tt);
-    P = fmaf(fabsf(y.w), pr, P);
-    mn = fminf(mn, Dn);
 }
 
 // Bound coefficients of pair_far for a move of length at most dn when every settled ion is at least sp from
@@ -322,7 +306,7 @@ __device__ __forceinline__ void block_sum(Smem &sm, double v, float bb, double &
 // |delta| / r^2 instead of 1/r.  Per-term bound ("guard tiers"):
 // |q| [ |t| (rel(Dn) + 19u) + 4u M (rn ro)^2/(rn+ro) + u |delta| (2 Ro + rho)/rho^3 ]
 // with rho a lower bound of the distance from y to the segment [b, a].
-__device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
+__device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double xs, double &dE_out)
 {
     const int tid = threadIdx.x;
     const float4 a = sm.trial[k], b = sm.own[k];
@@ -369,7 +353,7 @@ __device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
     if (tid == 0) {
         const double lq = c.ch->lB * (double)a.w;
         const double dE = lq * tot;
-        const double B2 = fabs(lq) * bt * 1.25 + 0x1p-40 * (fabs(dE) + fabs(L64)) + 1e-300;
+        const double B2 = fabs(lq) * bt * 1.25 + 0x1p-40 * (fabs(dE) + fabs(L64)) + xs + 1e-300;
         sm.redd[16] = dE;
         sm.guard_k = (dE < L64 - B2) ? 0 : ((dE > L64 + B2) ? 1 : -1);
     }
@@ -415,7 +399,7 @@ __device__ __forceinline__ void df_rsqrt(float dh, float dl, float &rh, float &r
 
 // Tier 3: every pair term in double-single arithmetic (distances from exact
 // FP32 differences); bound 2^-38 l_B |q_i| sum_j |q_j| (1/r' + 1/r).
-__device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
+__device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double xs, double &dE_out)
 {
     const int tid = threadIdx.x;
     const float4 a = sm.trial[k], b = sm.own[k];
@@ -454,7 +438,7 @@ __device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double &dE_out)
     if (tid == 0) {
         const double lq = c.ch->lB * (double)a.w;
         const double dE = lq * tot;
-        const double B3 = fabs(lq) * bt * 1.01 * 0x1p-38 + 0x1p-48 * (fabs(dE) + fabs(L64)) + 1e-300;
+        const double B3 = fabs(lq) * bt * 1.01 * 0x1p-38 + 0x1p-48 * (fabs(dE) + fabs(L64)) + xs + 1e-300;
         sm.redd[16] = dE;
         sm.guard_k = (dE < L64 - B3) ? 0 : ((dE > L64 + B3) ? 1 : -1);
     }
@@ -617,6 +601,341 @@ __device__ __forceinline__ void partial_pass(Smem &sm)
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Delayed acceptance, stage 1 (whole CTA), before the pair sums.  The in-group
+// and window correction matrices are free until step 2a and hold the scratch.
+
+// The reference (FP64) surrogate energy change of move k, identical to the oracle's arithmetic: near-field
+// sums in ascending j, exact features, FP64 MLP with the series exp.  Whole CTA; uses the window matrix as
+// scratch (free whenever this runs).  Returns the value in every thread.
+__device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
+{
+    const DADev &d = *c.ch->da;
+    const int tid = threadIdx.x;
+    const int Wg = min(d.W, c.B - 1);
+    const int i = c.k0 + k;
+    char *base = reinterpret_cast<char *>(sm.cwin);
+    constexpr int LMAX = 1024;  // near-field terms per point (r_c <= 5 sigma: at most ~740 ions at contact density)
+    int *Qs = reinterpret_cast<int *>(base);                // DA_NC ints (16384 B); later 2 x LMAX sorted terms
+    int *F = reinterpret_cast<int *>(base + 16384);         // 2 x DA_FRS ints
+    int *nl = reinterpret_cast<int *>(base + 16896);        // 2 counters
+    int *lj = reinterpret_cast<int *>(base + 17024);        // 2 x LMAX indices (8192 B)
+    double *lt = reinterpret_cast<double *>(base + 25216);  // 2 x LMAX terms (16384 B)
+    double *hb = reinterpret_cast<double *>(base + 41600);  // 2 x 64 (h1) + 2 x 64 (h2)
+    double *res = hb + 4 * DA_H;                            // phi0, phi1, g0, g1
+    signed char *shell = reinterpret_cast<signed char *>(res + 8);
+    static_assert(41600 + 8 * (4 * DA_H + 8) + DA_NSHELL <= S * CS * 4, "reference-surrogate scratch fits the window matrix");
+    static_assert(2 * LMAX * 8 <= 16384 && 2 * DA_FRS * 4 <= 512, "scratch layout");
+    const float4 x = sm.own[k], a = sm.trial[k];
+    for (int q = tid; q < DA_NSHELL; q += T) shell[q] = __ldg(&d.shell[q]);
+    if (tid < 2 * DA_FRS) F[tid] = 0;
+    if (tid < 2) nl[tid] = 0;
+    da_build_Q(Qs, d, c.g, c.B, c.N, c.Pprev, Wg);
+    // features of both points: the cell histogram split over 4 threads per point, then the own later ions
+    if (tid < 8) {
+        const int pt = tid >> 2, part = tid & 3;
+        const float4 p = pt ? a : x;
+        const int cp = da_fcell(d, p.x, p.y, p.z);
+        da_hist_range(F + pt * DA_FRS, Qs, shell, cp, part * (DA_NC / 4), (part + 1) * (DA_NC / 4));
+        if (part == 0) da_hist_own(F + pt * DA_FRS, sm.own, d, shell, cp, k, c.nk);
+    }
+    // near field: counted candidates of the 27 cells, FP64 membership, collected per point
+    {
+        const int G = d.nf_G;
+        const int cx = da_ncell_axis(d, x.x), cy = da_ncell_axis(d, x.y), cz = da_ncell_axis(d, x.z);
+        for (int cc = 0; cc < 27; ++cc) {
+            const int ax = cx + cc / 9 - 1, ay = cy + (cc / 3) % 3 - 1, az = cz + cc % 3 - 1;
+            if (ax < 0 || ay < 0 || az < 0 || ax >= G || ay >= G || az >= G) continue;
+            const int q = (ax * G + ay) * G + az;
+            const int lo = __ldg(&d.cell_start[q]), hi = __ldg(&d.cell_start[q + 1]);
+            for (int idx = lo + tid; idx < hi; idx += T) {
+                const int j = __ldg(&d.cell_ions[idx]);
+                if (!da_counted(i, c.g, c.B, Wg, j)) continue;
+                const float4 y = __ldcg(&d.cell_pos[idx]);
+                const double d20 = d2_fp64(x.x, x.y, x.z, y.x, y.y, y.z);
+                const double d21 = d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z);
+                if (d20 < d.rc2) {
+                    const int s = atomicAdd(&nl[0], 1);
+                    if (s < LMAX) {
+                        lj[s] = j;
+                        lt[s] = __ddiv_rn((double)y.w, __dsqrt_rn(d20));
+                    }
+                }
+                if (d21 < d.rc2) {
+                    const int s = atomicAdd(&nl[1], 1);
+                    if (s < LMAX) {
+                        lj[LMAX + s] = j;
+                        lt[LMAX + s] = __ddiv_rn((double)y.w, __dsqrt_rn(d21));
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ascending-j order: each entry's rank among its list, then sequential sums
+    double *sorted = reinterpret_cast<double *>(Qs);  // the grid is no longer needed
+    for (int e = tid; e < 2 * LMAX; e += T) {
+        const int pt = e / LMAX, s = e - pt * LMAX;
+        const int n = min(nl[pt], LMAX);
+        if (s < n) {
+            const int jj = lj[pt * LMAX + s];
+            int rank = 0;
+            for (int u = 0; u < n; ++u) rank += lj[pt * LMAX + u] < jj;
+            sorted[pt * LMAX + rank] = lt[pt * LMAX + s];
+        }
+    }
+    __syncthreads();
+    if (tid < 2) {
+        double ph = 0.0;
+        const int n = min(nl[tid], LMAX);
+        for (int s = 0; s < n; ++s) ph = __dadd_rn(ph, sorted[tid * LMAX + s]);
+        res[tid] = ph;
+    }
+    // MLP in FP64: 64 threads per point and layer, dot products in index order after the bias
+    const unsigned short *w = d.w;
+    if (tid < 2 * DA_H) {
+        const int pt = tid / DA_H, o = tid - pt * DA_H;
+        const float4 p = pt ? a : x;
+        double z = (double)bf16f(__ldg(&w[DA_OFF_B1 + o]));
+        for (int q = 0; q < 32; ++q)
+            z = __dadd_rn(z, __dmul_rn((double)bf16f(__ldg(&w[o * DA_NIN + q])), __dmul_rn((double)F[pt * DA_FRS + q], 0.0625)));
+        const double px = p.x, py = p.y, pz = p.z;
+        const double rad = __ddiv_rn(__dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz))), d.R);
+        z = __dadd_rn(z, __dmul_rn((double)bf16f(__ldg(&w[o * DA_NIN + 32])), rad));
+        hb[pt * DA_H + o] = silu64(z);
+    }
+    __syncthreads();
+    if (tid < 2 * DA_H) {
+        const int pt = tid / DA_H, o = tid - pt * DA_H;
+        double z = (double)bf16f(__ldg(&w[DA_OFF_B2 + o]));
+        for (int q = 0; q < DA_H; ++q)
+            z = __dadd_rn(z, __dmul_rn((double)bf16f(__ldg(&w[DA_OFF_W2 + o * DA_H + q])), hb[pt * DA_H + q]));
+        hb[2 * DA_H + pt * DA_H + o] = silu64(z);
+    }
+    __syncthreads();
+    if (tid < 2) {
+        double gg = (double)bf16f(__ldg(&w[DA_OFF_B3]));
+        for (int q = 0; q < DA_H; ++q)
+            gg = __dadd_rn(gg, __dmul_rn((double)bf16f(__ldg(&w[DA_OFF_W3 + q])), hb[2 * DA_H + tid * DA_H + q]));
+        res[2 + tid] = gg;
+    }
+    __syncthreads();
+    const double lq = __dmul_rn(c.ch->lB, (double)x.w);
+    const double v = __dmul_rn(lq, __dsub_rn(__dadd_rn(res[1], res[3]), __dadd_rn(res[0], res[2])));
+    __syncthreads();
+    return v;
+}
+
+// Bounded wait until the ledger has folded every group up to `need` (stream index s * B + g).
+__device__ bool wait_ledger(const ChainDev &ch, unsigned long long need, Ctl *ctl)
+{
+    const unsigned long long t0 = globaltimer();
+    unsigned spins = 0;
+    while (ld_acquire(ch.ledger_seq) < need) {
+        if (*(volatile int *)&ctl->abort) return false;
+        if (++spins > 16) __nanosleep(64);
+        if ((spins & 63) == 0 && (long long)(globaltimer() - t0) > ctl->timeout_ns) {
+            atomicCAS(&ctl->err, 0, KERR_TIMEOUT);
+            atomicExch(&ctl->abort, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Stage 1 of delayed acceptance for the whole group (whole CTA).  Decides the moves it rejects (overlap
+// with a counted ion, or the surrogate test), lists the survivors, and gives each survivor its stage-2
+// threshold Lf = L(u2) + dEt with the surrogate's error added to dEtB.
+__device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp64)
+{
+    const ChainDev &ch = *c.ch;
+    const DADev &d = *ch.da;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nk = c.nk, Wg = min(d.W, c.B - 1);
+    const float lBf = (float)ch.lB;
+    if (tid == 0) {
+        const unsigned long long need = c.s * (unsigned long long)c.B + (unsigned long long)max(c.g - Wg, 0);
+        sm.ok = wait_ledger(ch, need, ctl) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!sm.ok) return false;
+    char *base = reinterpret_cast<char *>(sm.cin);
+    float *Wf = reinterpret_cast<float *>(base);
+    int *Qs = reinterpret_cast<int *>(base + 25616);
+    int *Fr = reinterpret_cast<int *>(base + 42000);
+    signed char *shell = reinterpret_cast<signed char *>(base + 75792);
+    float *w2n = reinterpret_cast<float *>(base + 76480);
+    float *gv = reinterpret_cast<float *>(base + 76736);
+    float *ge = gv + 2 * S;
+    float *nph0 = ge + 2 * S, *nph1 = nph0 + S, *nA0 = nph1 + S, *nA1 = nA0 + S;
+    int *nnt = reinterpret_cast<int *>(nA1 + S), *novl = nnt + S, *ndiff = novl + S;
+    static_assert(76736 + 4 * 2 * S + 4 * 4 * S + 4 * (3 * S + 1) <= 2 * S * CS * 4, "stage-1 scratch");
+    for (int q = tid; q < DA_NP; q += T) Wf[q] = bf16f(__ldg(&d.w[q]));
+    for (int q = tid; q < DA_NSHELL; q += T) shell[q] = __ldg(&d.shell[q]);
+    if (tid < DA_H) w2n[tid] = __ldg(&d.w2n[tid]);
+    for (int q = tid; q < 2 * S * DA_FRS; q += T) Fr[q] = 0;
+    if (tid < WORDS) sm.d64w[tid] = 0u;
+    if (tid == 0) {
+        sm.namb = 0;
+        ndiff[S] = 0;
+    }
+    da_build_Q(Qs, d, c.g, c.B, c.N, c.Pprev, Wg);
+    const auto active = [&](int k) { return k < nk && !(sm.st[k] & (ST_INACTIVE | ST_WALL)); };
+    // shell histograms at the old positions (two threads per point)
+    {
+        const int k = tid >> 1, half = tid & 1;
+        if (active(k)) {
+            const float4 x = sm.own[k];
+            const int cp = da_fcell(d, x.x, x.y, x.z);
+            da_hist_range(Fr + k * DA_FRS, Qs, shell, cp, half * (DA_NC / 2), (half + 1) * (DA_NC / 2));
+            if (half == 0) da_hist_own(Fr + k * DA_FRS, sm.own, d, shell, cp, k, nk);
+        }
+    }
+    __syncthreads();
+    // trial positions in the old position's feature cell share its histogram; the others get their own
+    if (tid < S && active(tid)) {
+        const float4 x = sm.own[tid], a = sm.trial[tid];
+        if (da_fcell(d, x.x, x.y, x.z) != da_fcell(d, a.x, a.y, a.z)) ndiff[atomicAdd(&ndiff[S], 1)] = tid;
+        else
+            for (int q = 0; q < DA_FRS; ++q) Fr[(S + tid) * DA_FRS + q] = Fr[tid * DA_FRS + q];
+    }
+    __syncthreads();
+    for (int e = tid; e < 2 * ndiff[S]; e += T) {
+        const int k = ndiff[e >> 1], half = e & 1;
+        const float4 a = sm.trial[k];
+        const int cp = da_fcell(d, a.x, a.y, a.z);
+        da_hist_range(Fr + (S + k) * DA_FRS, Qs, shell, cp, half * (DA_NC / 2), (half + 1) * (DA_NC / 2));
+        if (half == 0) da_hist_own(Fr + (S + k) * DA_FRS, sm.own, d, shell, cp, k, nk);
+    }
+    __syncthreads();
+    // MLP at every point (thread = point: 0..S-1 old positions, S..2S-1 trials)
+    {
+        const int k = tid & (S - 1);
+        float g = 0.f, eg = 0.f;
+        if (active(k)) {
+            const float4 p = tid < S ? sm.own[k] : sm.trial[k];
+            float v[DA_NIN];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = (float)Fr[tid * DA_FRS + q] * 0.0625f;
+            v[32] = da_radial32(d, p);
+            da_mlp32(Wf, w2n, v, g, eg);
+        }
+        gv[tid] = g;
+        ge[tid] = eg;
+    }
+    // near field (warp per move)
+    for (int k = warp; k < nk; k += T / 32) {
+        if (!active(k)) continue;
+        const NearOut o = da_near_warp(d, c.g, c.B, Wg, c.k0 + k, sm.own[k], sm.trial[k], ch.sig2_lo, ch.sig2_hi, ch.sig2);
+        if (lane == 0) {
+            nph0[k] = o.ph0;
+            nph1[k] = o.ph1;
+            nA0[k] = o.A0;
+            nA1[k] = o.A1;
+            nnt[k] = o.nt;
+            novl[k] = o.ovl;
+        }
+    }
+    __syncthreads();
+    // FP32 surrogate energy change and its bound; stage-1 decisions outside the band
+    if (tid < S) {
+        const int k = tid;
+        unsigned stv = sm.st[k];
+        sm.dEt32[k] = __int_as_float(0x7fc00000);
+        sm.dEtB[k] = 0.f;
+        sm.dEt64[k] = __longlong_as_double(0x7ff8000000000000ll);
+        if (active(k)) {
+            if (novl[k]) {
+                sm.outcome[k] = (signed char)OUT_OVERLAP;
+                sm.tier[k] = 6;
+                stv |= ST_DA_DONE;
+            } else {
+                const float lq = lBf * sm.own[k].w;
+                const float ph0 = nph0[k], ph1 = nph1[k], g0 = gv[k], g1 = gv[S + k];
+                const float cph = ((float)nnt[k] + 16.0f) * U32;
+                const float dEt = lq * ((ph1 + g1) - (ph0 + g0));
+                const float E = fabsf(lq) *
+                                    (cph * (nA0[k] + nA1[k]) + ge[k] + ge[S + k] +
+                                     3.0f * U32 * (fabsf(ph1) + fabsf(g1) + fabsf(ph0) + fabsf(g0))) *
+                                    (1.0f + 0x1p-10f) +
+                                3.0f * U32 * fabsf(dEt);
+                sm.dEt32[k] = dEt;
+                sm.dEtB[k] = E;
+                int dec = 1;
+                if (!(stv & ST_UZERO)) {
+                    const float L = sm.Lf[k];
+                    const float b = (mode == 1 || mode == 3) ? finf()
+                                                             : (mode == 2 ? 0.f : E + 0x1p-20f * (fabsf(dEt) + fabsf(L)));
+                    dec = (dEt < L - b) ? 1 : ((dEt > L + b) ? 0 : -1);
+                }
+                if (dec == 0) {
+                    sm.outcome[k] = (signed char)OUT_DA1;
+                    sm.tier[k] = 6;
+                    stv |= ST_DA_DONE;
+                } else if (dec < 0) {
+                    sm.damb[atomicAdd(&sm.namb, 1)] = k;
+                }
+            }
+            sm.st[k] = (unsigned char)stv;
+        }
+    }
+    __syncthreads();
+    // stage-1 decisions inside the band: the reference arithmetic
+    const int na = sm.namb;
+    for (int e = 0; e < na; ++e) {
+        const int k = sm.damb[e];
+        const double v = da_dEt64(sm, c, k);
+        if (tid == 0) {
+            sm.dEt64[k] = v;
+            sm.d64w[k >> 5] |= 1u << (k & 31);
+            const unsigned long long m = c.s * (unsigned long long)c.N + (unsigned long long)(c.k0 + k);
+            const unsigned u1 = move_draws(ch, m, 0u).w >> 8;
+            const bool pass = (u1 == 0u) || v < -series_log((double)u1 * 0x1p-24);
+            if (!pass) {
+                sm.outcome[k] = (signed char)OUT_DA1;
+                sm.tier[k] = 7;
+                sm.st[k] = (unsigned char)(sm.st[k] | ST_DA_DONE);
+            }
+        }
+        __syncthreads();
+    }
+    n_fp64 += na;
+    // survivors in ascending order, and their stage-2 thresholds
+    if (tid < S) {
+        const int k = tid;
+        const bool sv = active(k) && !(sm.st[k] & ST_DA_DONE);
+        const unsigned bal = __ballot_sync(FULL, sv);
+        if (lane == 0) sm.redf[warp] = __int_as_float(__popc(bal));
+        if (sv) {
+            const unsigned long long m = c.s * (unsigned long long)c.N + (unsigned long long)(c.k0 + k);
+            const unsigned u2 = move_draws(ch, m, 1u).w >> 8;
+            unsigned stv = sm.st[k] & ~ST_UZERO;
+            const bool exact = bit(sm.d64w, k);
+            const float dEt = exact ? (float)sm.dEt64[k] : sm.dEt32[k];
+            const float E = exact ? 2.0f * U32 * fabsf(dEt) : sm.dEtB[k];
+            float L2 = finf();
+            if (u2 == 0u) stv |= ST_UZERO;
+            else L2 = -logf(__uint2float_rn(u2) * 0x1p-24f);
+            const float Lf = L2 + dEt;
+            sm.Lf[k] = Lf;
+            sm.dEtB[k] = (u2 == 0u) ? 0.f : (E + 0x1p-20f * (fabsf(L2) + fabsf(dEt)) + 2.0f * U32 * fabsf(Lf)) * (1.0f + 0x1p-10f);
+            sm.st[k] = (unsigned char)stv;
+        }
+    }
+    __syncthreads();
+    if (tid < S) {
+        const int k = tid, w = k >> 5;
+        int before = 0;
+        for (int q = 0; q < w; ++q) before += __float_as_int(sm.redf[q]);
+        const bool sv = active(k) && !(sm.st[k] & ST_DA_DONE);
+        const unsigned bal = __ballot_sync(FULL, sv);
+        if (sv) sm.surv[before + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)k;
+        if (k == S - 1) sm.ns = before + __popc(bal);
+    }
+    __syncthreads();
+    return true;
+}
+
 // One work item: the S moves of group g of chain `tk.chain` at sweep s.
 __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, const Ticket tk, int ticket, Ctl *ctl)
 {
@@ -724,17 +1043,34 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         sm.seen[tid] = 0u;
         sm.winacc[tid] = 0u;
     }
+    if (tid == 0) sm.ndl = 0;
     __syncthreads();
+
+    // 1b. delayed acceptance: stage 1 decides what it can before any pair sum; only survivors continue
+    int n_dfp64 = 0;
+    const long long cyc_da0 = clock64();
+    if (ch.da) {
+        if (!da_stage1(sm, c, ctl, mode, n_dfp64)) return false;
+    } else {
+        if (tid < S) sm.surv[tid] = (unsigned char)tid;
+        if (tid == 0) sm.ns = nk;
+        __syncthreads();
+    }
+    const long long cyc_da = clock64() - cyc_da0;
+    const int ns = sm.ns;
 
     // 2. pair sums.  Thread (p, r): moves p + 32 m (m = 0..3), column slice r of 8.
     const int p = tid / SL, r = tid % SL;
     float4 a[MPT], b[MPT];
     float3 b3[MPT], d3[MPT];
     float sA[MPT], hA[MPT], lA[MPT], AA[MPT], TA[MPT], CA[MPT], PA[MPT], mA[MPT];
+    int km[MPT];  // the move in each slot (-1: empty)
 #pragma unroll
     for (int m = 0; m < MPT; ++m) {
-        a[m] = sm.trial[p + 32 * m];
-        b[m] = sm.own[p + 32 * m];
+        km[m] = (p + 32 * m < ns) ? (int)sm.surv[p + 32 * m] : -1;
+        const int kk = km[m] < 0 ? 0 : km[m];
+        a[m] = sm.trial[kk];
+        b[m] = sm.own[kk];
         b3[m] = make_float3(b[m].x, b[m].y, b[m].z);
         d3[m] = make_float3(a[m].x - b[m].x, a[m].y - b[m].y, a[m].z - b[m].z);
         sA[m] = hA[m] = lA[m] = AA[m] = TA[m] = CA[m] = PA[m] = 0.f;
@@ -756,8 +1092,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const float4 yo = sm.own[j], yn = sm.trial[j];
 #pragma unroll
         for (int m = 0; m < MPT; ++m) {
-            const int k = p + 32 * m;
-            if (k >= nk || j == k) continue;
+            const int k = km[m];
+            if (k < 0 || j == k) continue;
             if (j > k) pair_far(b3[m], d3[m], yo, sA[m], TA[m], PA[m], mA[m]);
             else both_pair(sm.cin, sm.ovo, sm.ovn, k, j, a[m], b[m], yo, yn, sA[m], AA[m], TA[m], CA[m], lo2, hi2, sig2);
         }
@@ -769,8 +1105,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             const float4 yo = sm.wold[j], yn = sm.wtri[j];
 #pragma unroll
             for (int m = 0; m < MPT; ++m) {
-                const int k = p + 32 * m;
-                if (k >= nk) continue;
+                const int k = km[m];
+                if (k < 0) continue;
                 both_pair(sm.cwin, sm.wovo, sm.wovn, k, j, a[m], b[m], yo, yn, sA[m], AA[m], TA[m], CA[m], lo2, hi2,
                           sig2);
             }
@@ -833,7 +1169,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         if (hz > from) fence_acq_rel();
         return hz;
     };
-    if (ntl > 0) {
+    if (ntl > 0 && ns > 0) {
         if (warp == 0) {
             int hz0 = advance_horizon(-1);
             bool ok = true;
@@ -853,7 +1189,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         if (tid < S) sm.tile[0][tid] = __ldcg(&tile_src(tile_J(0))[tid]);
         __syncthreads();
     }
-    for (int i = 0; i < ntl; ++i) {
+    for (int i = 0; i < (ns > 0 ? ntl : 0); ++i) {
         const int cur = i & 1;
         const int hz = sm.hzs[i & 1];
         const bool pf = (i + 1 < ntl) && (i + 1 <= hz);
@@ -864,7 +1200,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         for (int jj = 0; jj < S / SL; ++jj) {
             const float4 y = sm.tile[cur][jj * SL + r];
 #pragma unroll
-            for (int m = 0; m < MPT; ++m) pair_far(b3[m], d3[m], y, sA[m], TA[m], PA[m], mA[m]);
+            for (int m = 0; m < MPT; ++m)
+                if (km[m] >= 0) pair_far(b3[m], d3[m], y, sA[m], TA[m], PA[m], mA[m]);
         }
         promote();
         if (pf && tid < S) sm.tile[cur ^ 1][tid] = pre;
@@ -910,7 +1247,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     if (r == 0) {
 #pragma unroll
         for (int m = 0; m < MPT; ++m) {
-            const int k = p + 32 * m;
+            const int k = km[m];
+            if (k < 0) continue;
             sm.bhi[k] = hA[m];
             sm.blo[k] = lA[m];
             sm.Ab[k] = AA[m] * (1.0f + 0x1p-10f);
@@ -957,6 +1295,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                                      : lqa * (U32 * (C_TERM * sm.Ab[k] + (C_SUM + kT) * sm.Tb[k] + kP * sm.Pb[k] +
                                                      C_CORR * sm.TCb[k]) +
                                               0x1p-40f * ch.a_max + 0x1p-36f * sm.Tb[k]));
+        if (ch.da && mode == 0) sm.bnd[k] += sm.dEtB[k];  // stage 2 compares dE with L(u2) + dEt
         sm.run[k] = 0.f;
         sm.wex[k] = 0.f;
     }
@@ -967,8 +1306,9 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const int k = tid;
         const unsigned stv = sm.st[k];
         int out = -1;
-        if (stv & ST_INACTIVE) out = 4;
+        if (stv & ST_INACTIVE) out = OUT_INACTIVE;
         else if (stv & ST_WALL) out = OUT_WALL;
+        else if (stv & ST_DA_DONE) out = sm.outcome[k];
         else if (stv & ST_OVL_CERTAIN) out = OUT_OVERLAP;
         else if (!(stv & (ST_OVL_POSSIBLE | ST_OVL_AMBIG))) {
             if (stv & ST_UZERO) out = OUT_ACCEPT;
@@ -978,7 +1318,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 out = decide_interval(sm, k, lq, base + (sm.lo_w[k] + sm.lo_i[k]), base + (sm.hi_w[k] + sm.hi_i[k]));
             }
         }
-        if (out >= 0 && out <= 3) sm.outcome[k] = (signed char)out;
+        if (out >= 0 && out <= OUT_DA1) sm.outcome[k] = (signed char)out;
         const unsigned dec = __ballot_sync(FULL, out >= 0);
         const unsigned acc = __ballot_sync(FULL, out == OUT_ACCEPT);
         if (lane == 0) {
@@ -1093,7 +1433,10 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             const long long cyc_g0 = clock64();
             const int k = first;
             const unsigned stv = sm.st[k];
-            const unsigned ua = move_draws(ch, s * (unsigned long long)N + (unsigned long long)(k0 + k), 0u).w >> 8;
+            // the acceptance draw of this decision: purpose 0, or purpose 1 for delayed acceptance's stage 2
+            const bool isda = ch.da != nullptr;
+            const unsigned ua =
+                move_draws(ch, s * (unsigned long long)N + (unsigned long long)(k0 + k), isda ? 1u : 0u).w >> 8;
             const double L64 = (ua == 0u) ? 0.0 : -series_log((double)ua * 0x1p-24);
             if ((stv & ST_OVL_AMBIG) && mode != 1) {
                 // settle the overlap question first; without an overlap the move is decided by the next round
@@ -1113,14 +1456,30 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             } else {
                 double dE = 0.0;
                 int res = -1, tier = 2;
+                // delayed acceptance compares fl(dE - dEt) with L(u2): the reference dEt, and the threshold for dE
+                double dEt64 = 0.0, thr = L64, xs = 0.0;
+                if (isda) {
+                    if (!bit(sm.d64w, k)) {
+                        const double v = da_dEt64(sm, c, k);
+                        ++n_dfp64;
+                        if (tid == 0) {
+                            sm.dEt64[k] = v;
+                            sm.d64w[k >> 5] |= 1u << (k & 31);
+                        }
+                        __syncthreads();
+                    }
+                    dEt64 = sm.dEt64[k];
+                    thr = __dadd_rn(L64, dEt64);
+                    xs = 0x1p-50 * (fabs(L64) + fabs(dEt64));
+                }
                 if (!(stv & ST_OVL_AMBIG) && mode != 1) {
                     long long q0 = clock64();
-                    res = tier2(sm, c, k, L64, dE);
+                    res = tier2(sm, c, k, thr, xs, dE);
                     cyc_t[0] += clock64() - q0;
                     if (res < 0) {
                         tier = 3;
                         q0 = clock64();
-                        res = tier3(sm, c, k, L64, dE);
+                        res = tier3(sm, c, k, thr, xs, dE);
                         cyc_t[1] += clock64() - q0;
                     }
                 }
@@ -1132,7 +1491,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                     cyc_t[2] += clock64() - q0;
                     if (ovl) res = 2;
                     else if (ua == 0u) res = 0;
-                    else res = (dE < L64) ? 0 : 1;
+                    else res = ((isda ? __dsub_rn(dE, dEt64) : dE) < L64) ? 0 : 1;
                 }
                 if (tid == 0) {
                     const int out = res == 0 ? OUT_ACCEPT : (res == 1 ? OUT_METROPOLIS : OUT_OVERLAP);
@@ -1165,8 +1524,20 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     if (tid < nk) {
         const bool acc = bit(sm.accw, tid);
         __stcg(&ch.pos[(s + 1) & 1][k0 + tid], acc ? sm.trial[tid] : sm.own[tid]);
+        if (ch.da && acc && publish) {
+            // delayed acceptance: the near-field cell list holds current positions; record feature-cell changes
+            const DADev &dd = *ch.da;
+            const int j = k0 + tid;
+            const float4 a = sm.trial[tid];
+            __stcg(&dd.cell_pos[__ldg(&dd.slot_of[j])], a);
+            const int f0 = __ldg(&dd.fcell0[j]), f1 = da_fcell(dd, a.x, a.y, a.z);
+            if (f0 != f1)
+                __stcg(&dd.dlist[(size_t)g * S + atomicAdd(&sm.ndl, 1)],
+                       (unsigned)f0 | ((unsigned)f1 << 12) | (((unsigned)(int)a.w & 0xffu) << 24));
+        }
     }
     __syncthreads();
+    if (ch.da && tid == 0 && publish) __stcg(&ch.da->dcount[g], sm.ndl);
     if (warp == 0 && publish && lane < (nk + 31) / 32)  // release after the barrier: orders every thread's stores
         st_release(&ch.flags[g * WORDS + lane], ((unsigned long long)tag_cur << 32) | sm.accw[lane]);
     const unsigned long long gt_posp = globaltimer();
@@ -1242,16 +1613,18 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         sm.ok = ok ? 1 : 0;
     }
     if (warp == 0) {
-        unsigned cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        unsigned cnt[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int k = lane; k < nk; k += 32) {
-            const int out = sm.outcome[k];
+            const int out = sm.outcome[k], tr = sm.tier[k];
             if (out >= 0 && out <= 3) cnt[out]++;
-            if (sm.tier[k] >= 2) cnt[4]++;
-            if (sm.tier[k] == 0 && (out == OUT_ACCEPT || out == OUT_METROPOLIS)) cnt[5]++;
-            if (sm.tier[k] >= 2 && sm.tier[k] <= 4) cnt[4 + sm.tier[k]]++;
+            if (tr >= 2 && tr <= 5) cnt[4]++;
+            if (tr == 0 && (out == OUT_ACCEPT || out == OUT_METROPOLIS)) cnt[5]++;
+            if (tr >= 2 && tr <= 4) cnt[4 + tr]++;
+            if (out == OUT_DA1) cnt[9]++;
+            if (out == OUT_OVERLAP && tr >= 6) cnt[10]++;
         }
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
+        for (int q = 0; q < 11; ++q) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cnt[q] += __shfl_xor_sync(FULL, cnt[q], o);
         }
@@ -1278,6 +1651,12 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 atomicAdd(&ch.stats[CNT_OVL_SCAN], (unsigned long long)n_scan);
                 atomicAdd(&ch.stats[CNT_CYC_OVL], (unsigned long long)cyc_ovl);
             }
+            if (ch.da) {
+                atomicAdd(&ch.stats[CNT_DA_REJ1], (unsigned long long)cnt[9]);
+                atomicAdd(&ch.stats[CNT_DA_OVL1], (unsigned long long)cnt[10]);
+                atomicAdd(&ch.stats[CNT_DA_FP64], (unsigned long long)n_dfp64);
+                atomicAdd(&ch.stats[CNT_CYC_DA1], (unsigned long long)cyc_da);
+            }
         }
     }
     if (ch.rec && s >= ch.rec_sweep0 && tid < nk) {
@@ -1291,6 +1670,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             rc.tier = sm.tier[k];
             rc.pad = 0;
             rc.bound = (double)sm.bnd[k];
+            rc.dEt = !ch.da ? __longlong_as_double(0x7ff8000000000000ll)
+                            : (bit(sm.d64w, k) ? sm.dEt64[k] : (double)sm.dEt32[k]);
             const int out = sm.outcome[k];
             const bool ev = out == OUT_ACCEPT || out == OUT_METROPOLIS;
             rc.dE = ev ? sm.dEv[k] : __longlong_as_double(0x7ff8000000000000ll);
