@@ -89,7 +89,8 @@ typedef struct {
     uint64_t da_rej1;        /* delayed acceptance: moves rejected by the surrogate stage */
     uint64_t da_ovl1;        /* ... overlaps found by the surrogate stage (counted in rej_overlap too) */
     uint64_t da_fp64;        /* ... surrogate energy changes recomputed in the reference FP64 arithmetic */
-    uint64_t cyc_da1;        /* ... SM cycles in the surrogate stage, summed over work items */
+    uint64_t cyc_da1;        /* ... SM cycles in the surrogate stage, summed over work items, */
+    uint64_t cyc_da_part[4]; /* ... of which: charge grid, shell histograms, MLP, near field */
 } mc_stats_t;
 
 /* Per-move validation record (mc_record_enable / mc_record_read). */

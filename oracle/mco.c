@@ -175,7 +175,6 @@ typedef struct {
 } mco_chain;
 
 static void da_free(struct mco_da *d);
-static void da_regrid(mco_chain *c);
 
 static int nthreads_cfg = 1;
 
@@ -552,7 +551,6 @@ int mco_set_positions(mco_chain *c, const float *pos_xyz)
     if (!c || !pos_xyz) return MCO_ERR_INVALID;
     if (config_valid(pos_xyz, c->n, c->sig2, c->sigma, c->Rc2, c->Rc) != 1) return MCO_ERR_OVERLAP_INIT;
     memcpy(c->x, pos_xyz, sizeof(float) * 3 * (size_t)c->n);
-    da_regrid(c);
     return MCO_OK;
 }
 
@@ -620,21 +618,22 @@ void mco_move_draws(uint64_t seed, uint32_t chain, uint64_t m, uint32_t purpose,
  *
  *  D1 Surrogate energy of ion i at point p, given the others:
  *       Et(p) = l_B q_i [phi_near(p) + g(v(p))],
- *     phi_near(p) = sum q_j / |p - x_j| over counted ions j with
- *     |p - x_j|^2 < r_c^2 (FP64 from FP32 coordinates, ascending j), and
- *     g the MLP below.  dEt = Et(x') - Et(x) is exactly antisymmetric.
+ *     phi_near(p) = sum q_j s(d) / d, d = |p - x_j|, over counted ions j with
+ *     d^2 < r_c^2 (FP64 from FP32 coordinates, ascending j), s = 1 up to
+ *     r_s = r_c / 2 and 1 - t^2 (3 - 2t), t = (d - r_s) / (r_c - r_s), beyond
+ *     (a C1 taper: an ion crossing r_c changes phi_near continuously), and g
+ *     the MLP below.  dEt = Et(x') - Et(x) is exactly antisymmetric.
  *  D2 Counted ions: all j != i except those tried in the W groups of 128
  *     ions preceding i's group in sweep order (cyclic over the sweep) and
  *     the earlier ions of i's own group.  The set depends only on the move
  *     index, so Et is a function of the current state for every move.
- *  D3 Features v(p): 32 shell net charges and the radial coordinate.  Feature
- *     grid: 16^3 cubic cells covering [-R, R]^3; the cell of a point is
- *     floor((p + R) * 16 / (2R)) per axis in FP32 arithmetic, clamped to
- *     [0, 15].  Q[c] = summed valence of counted ions in cell c.  The shell of
- *     a cell at integer offset (dx, dy, dz) from the cell of p is
- *     floor((e sqrt(n2) - r_c) / Delta), n2 = dx^2 + dy^2 + dz^2, e = 2R/16,
- *     Delta = (2R - r_c)/32, FP64, clamped to 31; cells closer than r_c are
- *     left out.  v[k] = F[k] / 16, k < 32; v[32] = |p| / R (FP64).
+ *  D3 Features v(p): 32 shell net charges and the radial coordinate.  Shell k
+ *     of p holds the counted ions j with r_s^2 <= d^2 < r_c^2 and
+ *     floor(32 (d^2 - r_s^2) / (r_c^2 - r_s^2)) = k (FP64, clamped to 31):
+ *     the taper region, where phi_near departs from the Coulomb sum.  A move
+ *     changes these counts as ions cross shells, so g can learn the part of
+ *     the energy change the taper leaves out.  v[k] = F[k] / 4, k < 32;
+ *     v[32] = |p| / R (FP64).
  *  D4 g: 33-64-64-1 MLP, SiLU after both hidden layers, BF16 weights; the
  *     reference arithmetic is FP64 with sequential dot products (bias first),
  *     silu(z) = z / (1 + exp(-z)) with the exp below.
@@ -651,7 +650,6 @@ void mco_move_draws(uint64_t seed, uint32_t chain, uint64_t m, uint32_t purpose,
  *     b2[64], W3[64], b3.
  */
 #define MCO_DA_S 128
-#define MCO_DA_G 16
 #define MCO_DA_NIN 33
 #define MCO_DA_H 64
 #define MCO_DA_NP (MCO_DA_H * MCO_DA_NIN + MCO_DA_H + MCO_DA_H * MCO_DA_H + MCO_DA_H + MCO_DA_H + 1)
@@ -659,12 +657,8 @@ void mco_move_draws(uint64_t seed, uint32_t chain, uint64_t m, uint32_t purpose,
 
 struct mco_da {
     double w[MCO_DA_NP]; /* the BF16 weights, exactly, in FP64 */
-    double rc, rc2;
+    double rc, rc2, rs, tw, rs2; /* cutoff, its square, taper start and width, taper start squared */
     int W;
-    int shell[3 * (MCO_DA_G - 1) * (MCO_DA_G - 1) + 1]; /* shell of a cell offset by its n2, -1 = left out */
-    float Rf, icf;                                    /* feature-cell arithmetic in FP32 */
-    int *cell;                                        /* feature cell of every ion (current position) */
-    int Q[MCO_DA_G * MCO_DA_G * MCO_DA_G];
     uint64_t n_rej1, n_ovl1, n_ovl2, n_rej2;
     void *rec;
     int64_t rec_cap, rec_len;
@@ -684,8 +678,6 @@ typedef struct {
 
 static void da_free(struct mco_da *d)
 {
-    if (!d) return;
-    free(d->cell);
     free(d);
 }
 
@@ -810,18 +802,6 @@ static double bf16_to_double(uint16_t b)
     return (double)f;
 }
 
-static int da_cell_axis(const struct mco_da *d, float p)
-{
-    float t = (p + d->Rf) * d->icf;
-    int c = (int)floorf(t);
-    return c < 0 ? 0 : (c > MCO_DA_G - 1 ? MCO_DA_G - 1 : c);
-}
-
-static int da_cell(const struct mco_da *d, const float p[3])
-{
-    return (da_cell_axis(d, p[0]) * MCO_DA_G + da_cell_axis(d, p[1])) * MCO_DA_G + da_cell_axis(d, p[2]);
-}
-
 /* Reading D2: is ion j counted for the move of ion i? */
 static int da_counted(const mco_chain *c, int64_t i, int64_t j)
 {
@@ -842,48 +822,35 @@ static void da_point(const mco_chain *c, int64_t i, const float p[3], int is_tri
     struct mco_da *d = c->da;
     double ph = 0.0;
     int o = 0;
-    int Q[MCO_DA_G * MCO_DA_G * MCO_DA_G];
-    memcpy(Q, d->Q, sizeof Q);
+    int F[32];
+    for (int k = 0; k < 32; ++k) F[k] = 0;
     for (int64_t j = 0; j < c->n; ++j) {
-        if (!da_counted(c, i, j)) { /* the grid holds every ion (ion i too): remove the uncounted ones */
-            Q[d->cell[j]] -= (int)c->q[j];
-            continue;
-        }
+        if (!da_counted(c, i, j)) continue;
         const float *y = c->x + 3 * j;
         double dx = (double)p[0] - (double)y[0];
         double dy = (double)p[1] - (double)y[1];
         double dz = (double)p[2] - (double)y[2];
         double d2 = (dx * dx + dy * dy) + dz * dz;
         if (is_trial && d2 < c->sig2) o = 1;
-        if (d2 < d->rc2) ph = ph + c->q[j] / sqrt(d2);
-    }
-    double F[32];
-    for (int k = 0; k < 32; ++k) F[k] = 0.0;
-    int cp = da_cell(d, p);
-    int px = cp / (MCO_DA_G * MCO_DA_G), py = (cp / MCO_DA_G) % MCO_DA_G, pz = cp % MCO_DA_G;
-    for (int cx = 0; cx < MCO_DA_G; ++cx)
-        for (int cy = 0; cy < MCO_DA_G; ++cy)
-            for (int cz = 0; cz < MCO_DA_G; ++cz) {
-                int n2 = (cx - px) * (cx - px) + (cy - py) * (cy - py) + (cz - pz) * (cz - pz);
-                int k = d->shell[n2];
-                if (k >= 0) F[k] += (double)Q[(cx * MCO_DA_G + cy) * MCO_DA_G + cz];
+        if (d2 < d->rc2) {
+            double dd = sqrt(d2);
+            if (dd <= d->rs) {
+                ph = ph + c->q[j] / dd;
+            } else {
+                double t = (dd - d->rs) / d->tw;
+                double sw = 1.0 - (t * t) * (3.0 - 2.0 * t);
+                ph = ph + c->q[j] * sw / dd;
             }
-    for (int k = 0; k < 32; ++k) v[k] = F[k] * 0.0625;
+            if (d2 >= d->rs2) {
+                int k = (int)floor(((d2 - d->rs2) / (d->rc2 - d->rs2)) * 32.0);
+                F[k > 31 ? 31 : k] += (int)c->q[j];
+            }
+        }
+    }
+    for (int k = 0; k < 32; ++k) v[k] = (double)F[k] * 0.25;
     v[32] = sqrt(((double)p[0] * (double)p[0] + (double)p[1] * (double)p[1]) + (double)p[2] * (double)p[2]) / c->R;
     *phi = ph;
     if (ovl) *ovl = o;
-}
-
-/* Feature cell of every ion and the net-charge grid of all ions (reading D3). */
-static void da_regrid(mco_chain *c)
-{
-    struct mco_da *d = c->da;
-    if (!d) return;
-    for (int k = 0; k < MCO_DA_G * MCO_DA_G * MCO_DA_G; ++k) d->Q[k] = 0;
-    for (int64_t j = 0; j < c->n; ++j) {
-        d->cell[j] = da_cell(d, c->x + 3 * j);
-        d->Q[d->cell[j]] += (int)c->q[j];
-    }
 }
 
 /* Install the surrogate: n_w = 6401 BF16 weights (layout D8), near-field cutoff r_c, exclusion depth W. */
@@ -894,30 +861,15 @@ int mco_set_surrogate(mco_chain *c, const uint16_t *w_bf16, int64_t n_w, double 
     if (!d) {
         d = (struct mco_da *)calloc(1, sizeof(struct mco_da));
         if (!d) return MCO_ERR_OOM;
-        d->cell = (int *)malloc(sizeof(int) * (size_t)c->n);
-        if (!d->cell) {
-            free(d);
-            return MCO_ERR_OOM;
-        }
         c->da = d;
     }
     for (int k = 0; k < MCO_DA_NP; ++k) d->w[k] = bf16_to_double(w_bf16[k]);
     d->rc = r_c;
     d->rc2 = r_c * r_c;
+    d->tw = 0.5 * r_c;
+    d->rs = r_c - d->tw;
+    d->rs2 = d->rs * d->rs;
     d->W = W;
-    double e = (2.0 * c->R) / (double)MCO_DA_G, delta = (2.0 * c->R - r_c) / 32.0;
-    for (int n2 = 0; n2 <= 3 * (MCO_DA_G - 1) * (MCO_DA_G - 1); ++n2) {
-        double dist = e * sqrt((double)n2);
-        if (dist < r_c) {
-            d->shell[n2] = -1;
-        } else {
-            double k = floor((dist - r_c) / delta);
-            d->shell[n2] = k > 31.0 ? 31 : (int)k;
-        }
-    }
-    d->Rf = (float)c->R;
-    d->icf = (float)((double)MCO_DA_G / (2.0 * c->R));
-    da_regrid(c);
     return MCO_OK;
 }
 
@@ -965,10 +917,6 @@ static void one_move_da(mco_chain *c, uint64_t s, int64_t i)
         }
     }
     if (outcome == MCO_ACCEPT) {
-        int cn = da_cell(d, a);
-        d->Q[d->cell[i]] -= (int)c->q[i];
-        d->Q[cn] += (int)c->q[i];
-        d->cell[i] = cn;
         c->x[3 * i] = a[0];
         c->x[3 * i + 1] = a[1];
         c->x[3 * i + 2] = a[2];

@@ -23,7 +23,8 @@ TRACE_DTYPE = np.dtype([("item", np.uint64), ("t_start", np.uint64), ("t_ready",
 _STATS_FIELDS = ["sweeps", "accepts", "rej_metropolis", "rej_overlap", "rej_wall", "guard_fp64",
                  "decided_interval", "tier2", "tier3", "tier4", "rounds", "cyc_wait_window", "cyc_tiles",
                  "cyc_resolve", "cyc_guard", "cyc_total", "cyc_tier2", "cyc_tier3", "cyc_tier4",
-                 "ovl_scan", "cyc_ovl_scan", "da_rej1", "da_ovl1", "da_fp64", "cyc_da1"]
+                 "ovl_scan", "cyc_ovl_scan", "da_rej1", "da_ovl1", "da_fp64", "cyc_da1",
+                 "cyc_da_grid", "cyc_da_hist", "cyc_da_mlp", "cyc_da_near"]
 
 
 class MCError(RuntimeError):

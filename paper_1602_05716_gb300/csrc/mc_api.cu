@@ -26,8 +26,7 @@ cudaError_t philox_test_launch(const uint4 *ctr, const uint2 *key, int n, uint4 
                                cudaStream_t st);
 cudaError_t log_test_launch(const double *u, int n, double *out, cudaStream_t st);
 cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt, int *cellid,
-                           unsigned short *fcell0, int *Q0, int *start, int *fill, int *cell_ions, float4 *cell_pos,
-                           int *slot_of, int *dcount, int B, cudaStream_t st);
+                           int *start, int *fill, int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st);
 cudaError_t da_sample_launch(const mcg::ChainDev *ch, const mcg::DADev *dd, int B, int grid, float *V, float *Y,
                              unsigned char *valid, cudaStream_t st);
 cudaError_t mlp_forward_launch(const unsigned short *w, const float *V, long long n, float *G, float *Z, cudaStream_t st);
@@ -92,12 +91,9 @@ struct Chain {
     mcg::DADev *dda = nullptr;    // device descriptor
     unsigned short *d_w = nullptr;
     float *d_w2n = nullptr;
-    signed char *d_shell = nullptr;
     int *d_cell_start = nullptr, *d_cell_ions = nullptr, *d_slot_of = nullptr, *d_cnt = nullptr, *d_cellid = nullptr;
-    int *d_fill = nullptr, *d_Q0 = nullptr, *d_dcount = nullptr;
+    int *d_fill = nullptr;
     float4 *d_cell_pos = nullptr;
-    unsigned short *d_fcell0 = nullptr;
-    unsigned *d_dlist = nullptr;
     int ncell = 0;
 };
 
@@ -304,18 +300,13 @@ void free_chain(Chain &c)
     cudaFree(c.dda);
     cudaFree(c.d_w);
     cudaFree(c.d_w2n);
-    cudaFree(c.d_shell);
     cudaFree(c.d_cell_start);
     cudaFree(c.d_cell_ions);
     cudaFree(c.d_slot_of);
     cudaFree(c.d_cnt);
     cudaFree(c.d_cellid);
     cudaFree(c.d_fill);
-    cudaFree(c.d_Q0);
-    cudaFree(c.d_dcount);
     cudaFree(c.d_cell_pos);
-    cudaFree(c.d_fcell0);
-    cudaFree(c.d_dlist);
     c = Chain();
 }
 
@@ -466,9 +457,8 @@ cudaError_t enqueue_da(mc_system *h, long long n, int grid, const mcg::Ticket *s
         for (size_t ci = 0; ci < h->chains.size(); ++ci) {
             Chain &c = h->chains[ci];
             if (!c.da || e != cudaSuccess) continue;
-            e = mcg_host::da_prep_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid, c.d_fcell0, c.d_Q0,
-                                         c.d_cell_start, c.d_fill, c.d_cell_ions, c.d_cell_pos, c.d_slot_of,
-                                         c.d_dcount, c.B, h->stream);
+            e = mcg_host::da_prep_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid, c.d_cell_start,
+                                         c.d_fill, c.d_cell_ions, c.d_cell_pos, c.d_slot_of, h->stream);
         }
         if (e == cudaSuccess)
             e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), 1, h->stream);
@@ -718,6 +708,7 @@ int mc_stats(mc_handle h, int chain, mc_stats_t *out)
     out->da_ovl1 = v[mcg::CNT_DA_OVL1];
     out->da_fp64 = v[mcg::CNT_DA_FP64];
     out->cyc_da1 = v[mcg::CNT_CYC_DA1];
+    for (int q = 0; q < 4; ++q) out->cyc_da_part[q] = v[mcg::CNT_CYC_DA_PART + q];
     return MC_OK;
 }
 
@@ -1006,19 +997,16 @@ int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w
     const double emin = (r_c + 2.0 * std::sqrt(3.0) * 0.5 * D) * (1.0 + 0x1p-8) + 1e-6;
     const int G = std::max(1, std::min(64, (int)std::floor(2.0 * c.R / emin)));
     // (re)allocate
-    cudaFree(c.dda); cudaFree(c.d_w); cudaFree(c.d_w2n); cudaFree(c.d_shell); cudaFree(c.d_cell_start);
-    cudaFree(c.d_cell_ions); cudaFree(c.d_slot_of); cudaFree(c.d_cnt); cudaFree(c.d_cellid); cudaFree(c.d_fill);
-    cudaFree(c.d_Q0); cudaFree(c.d_dcount); cudaFree(c.d_cell_pos); cudaFree(c.d_fcell0); cudaFree(c.d_dlist);
-    c.dda = nullptr; c.d_w = nullptr; c.d_w2n = nullptr; c.d_shell = nullptr; c.d_cell_start = nullptr;
-    c.d_cell_ions = nullptr; c.d_slot_of = nullptr; c.d_cnt = nullptr; c.d_cellid = nullptr; c.d_fill = nullptr;
-    c.d_Q0 = nullptr; c.d_dcount = nullptr; c.d_cell_pos = nullptr; c.d_fcell0 = nullptr; c.d_dlist = nullptr;
+    cudaFree(c.dda); cudaFree(c.d_w); cudaFree(c.d_w2n); cudaFree(c.d_cell_start); cudaFree(c.d_cell_ions);
+    cudaFree(c.d_slot_of); cudaFree(c.d_cnt); cudaFree(c.d_cellid); cudaFree(c.d_fill); cudaFree(c.d_cell_pos);
+    c.dda = nullptr; c.d_w = nullptr; c.d_w2n = nullptr; c.d_cell_start = nullptr; c.d_cell_ions = nullptr;
+    c.d_slot_of = nullptr; c.d_cnt = nullptr; c.d_cellid = nullptr; c.d_fill = nullptr; c.d_cell_pos = nullptr;
     c.da = false;
     c.ncell = G * G * G;
-    const size_t N = (size_t)c.N, B = (size_t)c.B;
+    const size_t N = (size_t)c.N;
     CK(cudaMalloc(&c.dda, sizeof(mcg::DADev)));
     CK(cudaMalloc(&c.d_w, sizeof(uint16_t) * mcg::DA_NP));
     CK(cudaMalloc(&c.d_w2n, sizeof(float) * mcg::DA_H));
-    CK(cudaMalloc(&c.d_shell, mcg::DA_NSHELL + 4));
     CK(cudaMalloc(&c.d_cell_start, sizeof(int) * ((size_t)c.ncell + 1)));
     CK(cudaMalloc(&c.d_cnt, sizeof(int) * (size_t)c.ncell));
     CK(cudaMalloc(&c.d_fill, sizeof(int) * (size_t)c.ncell));
@@ -1026,20 +1014,6 @@ int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w
     CK(cudaMalloc(&c.d_slot_of, sizeof(int) * N));
     CK(cudaMalloc(&c.d_cellid, sizeof(int) * N));
     CK(cudaMalloc(&c.d_cell_pos, sizeof(float4) * N));
-    CK(cudaMalloc(&c.d_fcell0, sizeof(uint16_t) * N));
-    CK(cudaMalloc(&c.d_Q0, sizeof(int) * mcg::DA_NC));
-    CK(cudaMalloc(&c.d_dcount, sizeof(int) * B));
-    CK(cudaMalloc(&c.d_dlist, sizeof(unsigned) * B * mcg::S));
-    CK(cudaMemset(c.d_dcount, 0, sizeof(int) * B));
-    // shell of a feature-cell offset: floor((e sqrt(n2) - r_c) / Delta) in FP64, clamped to 31, -1 inside r_c
-    std::vector<signed char> shell(mcg::DA_NSHELL + 4, -1);
-    const double e = (2.0 * c.R) / (double)mcg::DA_G, delta = (2.0 * c.R - r_c) / 32.0;
-    for (int n2 = 0; n2 < mcg::DA_NSHELL; ++n2) {
-        const double dist = e * std::sqrt((double)n2);
-        if (dist < r_c) continue;
-        const double k = std::floor((dist - r_c) / delta);
-        shell[n2] = (signed char)(k > 31.0 ? 31 : (int)k);
-    }
     std::vector<float> w2n(mcg::DA_H);
     for (int o = 0; o < mcg::DA_H; ++o) {
         double sum = 0.0;
@@ -1048,27 +1022,28 @@ int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w
     }
     CK(cudaMemcpy(c.d_w, w_bf16, sizeof(uint16_t) * mcg::DA_NP, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c.d_w2n, w2n.data(), sizeof(float) * mcg::DA_H, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c.d_shell, shell.data(), shell.size(), cudaMemcpyHostToDevice));
     mcg::DADev d{};
     d.w = c.d_w;
     d.w2n = c.d_w2n;
-    d.shell = c.d_shell;
     d.cell_start = c.d_cell_start;
     d.cell_ions = c.d_cell_ions;
     d.cell_pos = c.d_cell_pos;
     d.slot_of = c.d_slot_of;
-    d.fcell0 = c.d_fcell0;
-    d.Q0 = c.d_Q0;
-    d.dcount = c.d_dcount;
-    d.dlist = c.d_dlist;
     d.rc2 = r_c * r_c;
+    d.tw = 0.5 * r_c;
+    d.rs = r_c - d.tw;
+    d.rs2 = d.rs * d.rs;
+    d.rs2_lo = std::nextafter((float)(d.rs2 * (1.0 - 0x1p-19)), 0.0f);
+    d.rs2_hi = std::nextafter((float)(d.rs2 * (1.0 + 0x1p-19)), 3.0e38f);
+    d.rs2_f = (float)d.rs2;
+    d.c32_f = (float)(32.0 / (d.rc2 - d.rs2));
+    d.rs_f = (float)d.rs;
+    d.itw_f = (float)(1.0 / d.tw);
     d.R = c.R;
     d.rc2_lo = std::nextafter((float)(d.rc2 * (1.0 - 0x1p-19)), 0.0f);
     d.rc2_hi = std::nextafter((float)(d.rc2 * (1.0 + 0x1p-19)), 3.0e38f);
     d.nf_scale = (float)((double)G / (2.0 * c.R));
     d.nf_R = (float)c.R;
-    d.Rf = (float)c.R;
-    d.icf = (float)((double)mcg::DA_G / (2.0 * c.R));
     d.Rr = (float)c.R;
     d.nf_G = G;
     d.W = W;
@@ -1093,9 +1068,9 @@ int mc_da_samples(mc_handle h, int chain, float *v_pairs, float *y, uint8_t *val
     CK(cudaMalloc(&dV, sizeof(float) * 66 * N));
     CK(cudaMalloc(&dY, sizeof(float) * N));
     CK(cudaMalloc(&dv, N));
-    cudaError_t e = mcg_host::da_prep_launch(h->d_chains + chain, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid, c.d_fcell0,
-                                             c.d_Q0, c.d_cell_start, c.d_fill, c.d_cell_ions, c.d_cell_pos,
-                                             c.d_slot_of, c.d_dcount, c.B, h->stream);
+    cudaError_t e = mcg_host::da_prep_launch(h->d_chains + chain, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid,
+                                             c.d_cell_start, c.d_fill, c.d_cell_ions, c.d_cell_pos, c.d_slot_of,
+                                             h->stream);
     if (e == cudaSuccess) e = mcg_host::da_sample_launch(h->d_chains + chain, c.dda, c.B, h->sm_count, dV, dY, dv, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(v_pairs, dV, sizeof(float) * 66 * N, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(y, dY, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream);

@@ -1,6 +1,6 @@
 // mc_da.cu -- delayed acceptance outside the sweep kernel: the per-sweep
-// preparation (near-field cell list and feature grid of the sweep's start
-// positions), the surrogate MLP's inference and training kernels (forward,
+// preparation (near-field cell list of the sweep's start positions), the
+// surrogate MLP's inference and training kernels (forward,
 // backward, weight gradients reduced in a fixed order, Adam with BF16
 // rounding of the weights), and the kernel that turns a configuration and
 // the chain's own trial moves into training samples (features at the old and
@@ -23,7 +23,7 @@ __device__ __forceinline__ const float4 *start_positions(const ChainDev &ch)
 }
 
 __global__ void da_prep_count(const ChainDev *__restrict__ chp, int N, const DADev *__restrict__ dp, int *cnt,
-                              int *cellid, unsigned short *fcell0, int *Q0)
+                              int *cellid)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -33,9 +33,6 @@ __global__ void da_prep_count(const ChainDev *__restrict__ chp, int N, const DAD
     const int c = (da_ncell_axis(d, x.x) * G + da_ncell_axis(d, x.y)) * G + da_ncell_axis(d, x.z);
     cellid[j] = c;
     atomicAdd(&cnt[c], 1);
-    const int f = da_fcell(d, x.x, x.y, x.z);
-    fcell0[j] = (unsigned short)f;
-    atomicAdd(&Q0[f], (int)x.w);
 }
 
 // Exclusive scan of the cell counts (one block): cell_start[c] and the scatter cursors.
@@ -278,9 +275,7 @@ __global__ void adam_kernel(float *p, float *m, float *v, const float *__restric
 // MLP learns.  One block per group at a time.
 struct SampleSmem {
     float4 own[S], trial[S], tile[S];
-    int Qs[DA_NC];
     int Fr[2 * S * DA_FRS];
-    signed char shell[DA_NSHELL + 4];
     float ph0[S], ph1[S], ex[S], mn[S];
     int ovl[S];
 };
@@ -297,7 +292,6 @@ __global__ void __launch_bounds__(T, 1) da_sample_kernel(const ChainDev *__restr
     const int N = ch.N, B = ch.B, Wg = min(d.W, B - 1);
     const unsigned long long s = *ch.sweep;
     const float4 *P = ch.pos[s & 1];
-    for (int q = tid; q < DA_NSHELL; q += T) sm.shell[q] = __ldg(&d.shell[q]);
     for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
         const int k0 = g * S, nk = min(S, N - k0);
         __syncthreads();
@@ -317,19 +311,11 @@ __global__ void __launch_bounds__(T, 1) da_sample_kernel(const ChainDev *__restr
             sm.mn[k] = 3.0e38f;
         }
         for (int q = tid; q < 2 * S * DA_FRS; q += T) sm.Fr[q] = 0;
-        da_build_Q(sm.Qs, d, g, B, N, P, Wg);
-        // features (2 threads per point, old then trial positions)
-        for (int e = tid; e < 4 * S; e += T) {
-            const int pt = e >> 1, half = e & 1, k = pt & (S - 1);
-            if (k >= nk) continue;
-            const float4 p = pt < S ? sm.own[k] : sm.trial[k];
-            const int cp = da_fcell(d, p.x, p.y, p.z);
-            da_hist_range(sm.Fr + pt * DA_FRS, sm.Qs, sm.shell, cp, half * (DA_NC / 2), (half + 1) * (DA_NC / 2));
-            if (half == 0) da_hist_own(sm.Fr + pt * DA_FRS, sm.own, d, sm.shell, cp, k, nk);
-        }
-        // near field (warp per move)
+        __syncthreads();
+        // near field and shell histograms (warp per move)
         for (int k = warp; k < nk; k += T / 32) {
-            const NearOut o = da_near_warp(d, g, B, Wg, k0 + k, sm.own[k], sm.trial[k], ch.sig2_lo, ch.sig2_hi, ch.sig2);
+            const NearOut o = da_near_warp(d, g, B, Wg, k0 + k, sm.own[k], sm.trial[k], ch.sig2_lo, ch.sig2_hi, ch.sig2,
+                                           sm.Fr + k * DA_FRS, sm.Fr + (S + k) * DA_FRS);
             if (lane == 0) {
                 sm.ph0[k] = o.ph0;
                 sm.ph1[k] = o.ph1;
@@ -359,8 +345,8 @@ __global__ void __launch_bounds__(T, 1) da_sample_kernel(const ChainDev *__restr
             const int k = tid;
             const long long m = (long long)(k0 + k);
             for (int i = 0; i < 32; ++i) {
-                V[m * 66 + i] = (float)sm.Fr[k * DA_FRS + i] * 0.0625f;
-                V[m * 66 + 33 + i] = (float)sm.Fr[(S + k) * DA_FRS + i] * 0.0625f;
+                V[m * 66 + i] = (float)sm.Fr[k * DA_FRS + i] * 0.25f;
+                V[m * 66 + 33 + i] = (float)sm.Fr[(S + k) * DA_FRS + i] * 0.25f;
             }
             V[m * 66 + 32] = da_radial32(d, sm.own[k]);
             V[m * 66 + 33 + 32] = da_radial32(d, sm.trial[k]);
@@ -378,14 +364,11 @@ __global__ void __launch_bounds__(T, 1) da_sample_kernel(const ChainDev *__restr
 namespace mcg_host {
 
 cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt, int *cellid,
-                           unsigned short *fcell0, int *Q0, int *start, int *fill, int *cell_ions, float4 *cell_pos,
-                           int *slot_of, int *dcount, int B, cudaStream_t st)
+                           int *start, int *fill, int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ncell, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(Q0, 0, sizeof(int) * mcg::DA_NC, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(dcount, 0, sizeof(int) * (size_t)B, st)) != cudaSuccess) return e;
-    mcg::da_prep_count<<<(N + 255) / 256, 256, 0, st>>>(chd, N, dd, cnt, cellid, fcell0, Q0);
+    mcg::da_prep_count<<<(N + 255) / 256, 256, 0, st>>>(chd, N, dd, cnt, cellid);
     mcg::da_prep_scan<<<1, 1024, 0, st>>>(cnt, ncell, start, fill);
     mcg::da_prep_scatter<<<(N + 255) / 256, 256, 0, st>>>(chd, N, cellid, fill, cell_ions, cell_pos, slot_of);
     return cudaGetLastError();

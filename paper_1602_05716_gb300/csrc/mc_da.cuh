@@ -4,9 +4,11 @@
 //
 // Stage 1 decides on a cheap surrogate energy change
 //     dEt = l_B q_i ([phi_near + g(v)](x') - [phi_near + g(v)](x)),
-// phi_near the exact Coulomb sum over counted ions within r_c and g a
-// 33-64-64-1 SiLU MLP with BF16 weights fed with 32 shell net charges around
-// the point and its radial coordinate.  Survivors pay the exact O(N) sum of
+// phi_near the Coulomb sum over counted ions within r_c (exact up to
+// r_s = r_c / 2, then a C1 taper 1 - t^2 (3 - 2t) so that an ion crossing r_c
+// changes it continuously) and g a 33-64-64-1 SiLU MLP with BF16 weights fed
+// with the net valence of counted ions in 32 shells (equal width in d^2) of
+// the taper region around the point, and its radial coordinate.  Survivors pay the exact O(N) sum of
 // the plain chain and are accepted with min(1, exp(-(dE - dEt))).
 //
 // Counted ions for the move of ion i in group g: every ion except i, the
@@ -23,11 +25,8 @@
 
 namespace mcg {
 
-constexpr int DA_G = 16;                                                        // feature grid cells per axis
-constexpr int DA_NC = DA_G * DA_G * DA_G;                                       // 4096 feature cells
 constexpr int DA_NIN = 33, DA_H = 64;                                           // MLP shape
 constexpr int DA_NP = DA_H * DA_NIN + DA_H + DA_H * DA_H + DA_H + DA_H + 1;    // 6401 parameters
-constexpr int DA_NSHELL = 3 * (DA_G - 1) * (DA_G - 1) + 1;                      // squared cell offsets 0..675
 constexpr int DA_OFF_B1 = DA_H * DA_NIN, DA_OFF_W2 = DA_OFF_B1 + DA_H, DA_OFF_B2 = DA_OFF_W2 + DA_H * DA_H,
               DA_OFF_W3 = DA_OFF_B2 + DA_H, DA_OFF_B3 = DA_OFF_W3 + DA_H;
 constexpr int OUT_DA1 = 4;  // outcome: rejected by the surrogate stage
@@ -37,36 +36,22 @@ constexpr int OUT_DA1 = 4;  // outcome: rejected by the surrogate stage
 struct DADev {
     const unsigned short *w;       // BF16 weights, layout W1[64][33], b1, W2[64][64], b2, W3, b3
     const float *w2n;              // ||W2[o]||_1, rounded up (error bound of the second layer)
-    const signed char *shell;      // shell of a feature-cell offset by its squared length, -1 = left out
     const int *cell_start;         // near-field cell list of the sweep's start positions (ncell + 1)
     const int *cell_ions;          // ion indices in cell order (N)
     float4 *cell_pos;              // their positions in cell order; accepted moves write theirs in place
     const int *slot_of;            // slot of ion j in the cell order (N)
-    const unsigned short *fcell0;  // feature cell of every ion at the start of the sweep (N)
-    const int *Q0;                 // net valence of every feature cell at the start of the sweep (DA_NC)
-    int *dcount;                   // per group of the sweep: feature-cell changes recorded
-    unsigned *dlist;               // per group, S entries: from | to << 12 | (valence & 0xff) << 24
-    double rc2;                    // r_c^2
+    double rc2, rs2;               // r_c^2, r_s^2
+    double rs, tw;                 // taper start r_c / 2 and width r_c - r_s
     double R;                      // sphere radius (radial input)
+    float rs_f, itw_f;             // fl32(r_s), fl32(1 / width) for the FP32 taper
     float rc2_lo, rc2_hi;          // FP32 squared distances below/above certainly inside/outside r_c
+    float rs2_lo, rs2_hi;          // ... below/above certainly inside/outside r_s
+    float rs2_f, c32_f;            // fl32(r_s^2), fl32(32 / (r_c^2 - r_s^2)) for the FP32 shell index
     float nf_scale, nf_R;          // near-field cell of x: floor((x + nf_R) * nf_scale)
-    float Rf, icf;                 // feature cell of x: floor((x + Rf) * icf) in FP32 (bit-identical to the oracle)
     float Rr;                      // fl32(R) for the FP32 radial input
     int nf_G;                      // near-field cells per axis
     int W;                         // exclusion depth in groups
 };
-
-__device__ __forceinline__ int da_fcell_axis(float x, float Rf, float icf)
-{
-    const float t = __fmul_rn(__fadd_rn(x, Rf), icf);
-    const int c = (int)floorf(t);
-    return c < 0 ? 0 : (c > DA_G - 1 ? DA_G - 1 : c);
-}
-
-__device__ __forceinline__ int da_fcell(const DADev &d, float x, float y, float z)
-{
-    return (da_fcell_axis(x, d.Rf, d.icf) * DA_G + da_fcell_axis(y, d.Rf, d.icf)) * DA_G + da_fcell_axis(z, d.Rf, d.icf);
-}
 
 __device__ __forceinline__ int da_ncell_axis(const DADev &d, float x)
 {
@@ -107,6 +92,46 @@ __device__ __forceinline__ double series_exp(double x)
     return scalbn(p, (int)kd);
 }
 
+// The near-field taper s(d) in FP32: 1 up to r_s, 1 - t^2 (3 - 2t) beyond.  Its error is below 22u (|s'| <= 1.5
+// times the error of t, itself below 12u for d <= 2 r_s, plus four roundings).
+__device__ __forceinline__ float da_taper32(const DADev &d, float dist)
+{
+    if (!(dist > d.rs_f)) return 1.0f;
+    const float t = (dist - d.rs_f) * d.itw_f;
+    return 1.0f - (t * t) * (3.0f - 2.0f * t);
+}
+
+// ... and the reference FP64 term q s(d) / d (the oracle's operations in its order).
+__device__ __forceinline__ double da_term64(const DADev &d, double q, double d2)
+{
+    const double dd = __dsqrt_rn(d2);
+    if (dd <= d.rs) return __ddiv_rn(q, dd);
+    const double t = __ddiv_rn(__dsub_rn(dd, d.rs), d.tw);
+    const double sw = __dsub_rn(1.0, __dmul_rn(__dmul_rn(t, t), __dsub_rn(3.0, __dmul_rn(2.0, t))));
+    return __ddiv_rn(__dmul_rn(q, sw), dd);
+}
+
+// Shell of a counted ion in the taper region (r_s^2 <= d^2 < r_c^2, decided beforehand) from its FP32 squared
+// distance d2f; inside the FP32 error of a shell boundary (2^-13 of a shell, far above the 5u of d2f times the
+// scale) the reference FP64 formula floor(32 (d^2 - r_s^2) / (r_c^2 - r_s^2)) decides.
+__device__ __forceinline__ int da_shell(const DADev &d, float d2f, float4 p, float4 y)
+{
+    const float kf = (d2f - d.rs2_f) * d.c32_f;
+    const float fl = floorf(kf), fr = kf - fl;
+    if (fr > 0x1p-13f && fr < 1.0f - 0x1p-13f) return min(31, max(0, (int)fl));
+    const double d2 = d2_fp64(p.x, p.y, p.z, y.x, y.y, y.z);
+    const int k = (int)floor(__dmul_rn(__ddiv_rn(__dsub_rn(d2, d.rs2), __dsub_rn(d.rc2, d.rs2)), 32.0));
+    return min(31, k);
+}
+
+// ... is it in the taper region at all (exact)?
+__device__ __forceinline__ bool da_in_taper(const DADev &d, float d2f, float4 p, float4 y)
+{
+    if (d2f > d.rs2_hi) return true;
+    if (d2f < d.rs2_lo) return false;
+    return d2_fp64(p.x, p.y, p.z, y.x, y.y, y.z) >= d.rs2;
+}
+
 __device__ __forceinline__ double silu64(double z)
 {
     return __ddiv_rn(z, __dadd_rn(1.0, series_exp(-z)));
@@ -116,63 +141,6 @@ __device__ __forceinline__ double silu64(double z)
 // Stage-1 building blocks shared by the sweep kernel and the training-sample kernel.
 
 constexpr int DA_FRS = 33;  // row stride of the per-point shell histograms (32 shells, padded)
-
-// Net valence of every feature cell over the ions counted for this group's moves, except that the
-// group's own later ions are left for the per-move add-back: the start-of-sweep grid, minus the own group
-// and the Wg groups before it at their start-of-sweep cells, plus the recorded cell changes of the
-// counted groups already tried in this sweep (0 .. g - Wg - 1; their records precede the ledger step
-// acquired before this call).
-__device__ inline void da_build_Q(int *Qs, const DADev &d, int g, int B, int N, const float4 *Pprev, int Wg)
-{
-    const int tid = threadIdx.x;
-    for (int q = tid; q < DA_NC; q += T) Qs[q] = __ldg(&d.Q0[q]);
-    __syncthreads();
-    const int nrem = (Wg + 1) * S;
-    for (int e = tid; e < nrem; e += T) {
-        const int t = e / S, l = e - t * S;
-        int v = g - t;
-        if (v < 0) v += B;
-        const int j = v * S + l;
-        if (j < N) atomicSub(&Qs[__ldg(&d.fcell0[j])], (int)__ldg(&Pprev[j].w));
-    }
-    for (int v = tid; v < g - Wg; v += T) {
-        const int n = __ldcg(&d.dcount[v]);
-        for (int e = 0; e < n; ++e) {
-            const unsigned x = __ldcg(&d.dlist[(size_t)v * S + e]);
-            const int q = (int)(signed char)(x >> 24);
-            atomicSub(&Qs[x & 0xfffu], q);
-            atomicAdd(&Qs[(x >> 12) & 0xfffu], q);
-        }
-    }
-    __syncthreads();
-}
-
-// Shell histogram of one point over a range of feature cells (one thread), accumulated into row F.
-__device__ __forceinline__ void da_hist_range(int *F, const int *Qs, const signed char *shell, int cp, int c0, int c1)
-{
-    const int px = cp >> 8, py = (cp >> 4) & 15, pz = cp & 15;
-    for (int q = c0; q < c1; ++q) {
-        const int v = Qs[q];
-        if (v == 0) continue;
-        const int dx = (q >> 8) - px, dy = ((q >> 4) & 15) - py, dz = (q & 15) - pz;
-        const int sh = shell[dx * dx + dy * dy + dz * dz];
-        if (sh >= 0) atomicAdd(&F[sh], v);
-    }
-}
-
-// ... plus the group's own ions after k (counted, at their old positions).
-__device__ __forceinline__ void da_hist_own(int *F, const float4 *own, const DADev &d, const signed char *shell, int cp,
-                                            int k, int nk)
-{
-    const int px = cp >> 8, py = (cp >> 4) & 15, pz = cp & 15;
-    for (int j = k + 1; j < nk; ++j) {
-        const float4 y = own[j];
-        const int q = da_fcell(d, y.x, y.y, y.z);
-        const int dx = (q >> 8) - px, dy = ((q >> 4) & 15) - py, dz = (q & 15) - pz;
-        const int sh = shell[dx * dx + dy * dy + dz * dz];
-        if (sh >= 0) atomicAdd(&F[sh], (int)y.w);
-    }
-}
 
 // FP32 radial input |p| / R with its error (<= 4u relative: three rounded operations on the squared norm,
 // the square root, the division, and fl32(R)).
@@ -248,7 +216,7 @@ struct NearOut {
 };
 
 __device__ inline NearOut da_near_warp(const DADev &d, int g, int B, int Wg, int i, float4 x, float4 a, float lo2, float hi2,
-                                double sig2)
+                                       double sig2, int *F0, int *F1)
 {
     const int lane = threadIdx.x & 31;
     const int G = d.nf_G;
@@ -271,47 +239,63 @@ __device__ inline NearOut da_near_warp(const DADev &d, int g, int B, int Wg, int
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     float ph0 = 0.f, ph1 = 0.f, A0 = 0.f, A1 = 0.f;
     int n0 = 0, n1 = 0, ovl = 0;
-    for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + lane;
-        // the cell holding candidate t: the first lane m whose inclusive count exceeds t
-        int m = 0;
+    constexpr int U = 4;  // candidates in flight per lane: their loads are issued before any is used
+    for (int t0 = 0; t0 < total; t0 += 32 * U) {
+        int idx[U];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int v = __shfl_sync(0xffffffffu, incl, m + step - 1);
-            if (v <= t) m += step;
-        }
-        const int lo_m = __shfl_sync(0xffffffffu, lo, m);
-        const int ex_m = __shfl_sync(0xffffffffu, incl - cnt, m);
-        if (t >= total) continue;
-        const int idx = lo_m + (t - ex_m);
-        const int j = __ldg(&d.cell_ions[idx]);
-        if (!da_counted(i, g, B, Wg, j)) continue;
-        const float4 y = __ldcg(&d.cell_pos[idx]);
-        const float aq = fabsf(y.w);
-        {
-            const float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
-            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            bool in = d2 < d.rc2_lo;
-            if (!in && !(d2 > d.rc2_hi)) in = d2_fp64(x.x, x.y, x.z, y.x, y.y, y.z) < d.rc2;
-            if (in) {
-                const float r = rsqrt_approx(d2);
-                ph0 = fmaf(y.w, r, ph0);
-                A0 = fmaf(aq, r, A0);
-                ++n0;
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + 32 * u + lane;
+            // the cell holding candidate t: the first lane m whose inclusive count exceeds t
+            int m = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, m + step - 1);
+                if (v <= t) m += step;
             }
+            const int lo_m = __shfl_sync(0xffffffffu, lo, m);
+            const int ex_m = __shfl_sync(0xffffffffu, incl - cnt, m);
+            idx[u] = t < total ? lo_m + (t - ex_m) : -1;
         }
-        {
-            const float dx = a.x - y.x, dy = a.y - y.y, dz = a.z - y.z;
-            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (d2 < lo2) ovl = 1;
-            else if (!(d2 > hi2) && d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < sig2) ovl = 1;
-            bool in = d2 < d.rc2_lo;
-            if (!in && !(d2 > d.rc2_hi)) in = d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < d.rc2;
-            if (in) {
-                const float r = rsqrt_approx(d2);
-                ph1 = fmaf(y.w, r, ph1);
-                A1 = fmaf(aq, r, A1);
-                ++n1;
+        int jj[U];
+        float4 yy[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            jj[u] = idx[u] >= 0 ? __ldg(&d.cell_ions[idx[u]]) : -1;
+            yy[u] = idx[u] >= 0 ? __ldcg(&d.cell_pos[idx[u]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = jj[u];
+            if (j < 0 || !da_counted(i, g, B, Wg, j)) continue;
+            const float4 y = yy[u];
+            const float aq = fabsf(y.w);
+            {
+                const float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                bool in = d2 < d.rc2_lo;
+                if (!in && !(d2 > d.rc2_hi)) in = d2_fp64(x.x, x.y, x.z, y.x, y.y, y.z) < d.rc2;
+                if (in) {
+                    const float r = rsqrt_approx(d2);
+                    ph0 = fmaf(y.w * da_taper32(d, d2 * r), r, ph0);
+                    A0 = fmaf(aq, r, A0);
+                    ++n0;
+                    if (da_in_taper(d, d2, x, y)) atomicAdd(&F0[da_shell(d, d2, x, y)], (int)y.w);
+                }
+            }
+            {
+                const float dx = a.x - y.x, dy = a.y - y.y, dz = a.z - y.z;
+                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                if (d2 < lo2) ovl = 1;
+                else if (!(d2 > hi2) && d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < sig2) ovl = 1;
+                bool in = d2 < d.rc2_lo;
+                if (!in && !(d2 > d.rc2_hi)) in = d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < d.rc2;
+                if (in) {
+                    const float r = rsqrt_approx(d2);
+                    ph1 = fmaf(y.w * da_taper32(d, d2 * r), r, ph1);
+                    A1 = fmaf(aq, r, A1);
+                    ++n1;
+                    if (da_in_taper(d, d2, a, y)) atomicAdd(&F1[da_shell(d, d2, a, y)], (int)y.w);
+                }
             }
         }
     }

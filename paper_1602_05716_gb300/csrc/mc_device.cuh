@@ -104,8 +104,8 @@ constexpr int CNT_ACCEPT = 0, CNT_METRO = 1, CNT_OVERLAP = 2, CNT_WALL = 3, CNT_
               CNT_T2 = 6, CNT_T3 = 7, CNT_T4 = 8, CNT_ROUNDS = 9, CNT_CYC_WIN = 10, CNT_CYC_TILES = 11,
               CNT_CYC_RESOLVE = 12, CNT_CYC_GUARD = 13, CNT_CYC_TOTAL = 14, CNT_CYC_T2 = 15, CNT_CYC_T3 = 16,
               CNT_CYC_T4 = 17, CNT_OVL_SCAN = 18, CNT_CYC_OVL = 19, CNT_DA_REJ1 = 20, CNT_DA_OVL1 = 21,
-              CNT_DA_FP64 = 22, CNT_CYC_DA1 = 23;
-constexpr int NCOUNTERS = 24;
+              CNT_DA_FP64 = 22, CNT_CYC_DA1 = 23, CNT_CYC_DA_PART = 24;  // 24..27: grid, features, MLP, near field
+constexpr int NCOUNTERS = 32;
 constexpr float U32 = 0x1p-24f;  // unit roundoff of FP32
 
 // ---------------------------------------------------------------------------

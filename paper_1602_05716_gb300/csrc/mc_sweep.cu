@@ -82,7 +82,7 @@ struct __align__(16) Smem {
     float redf[32];
     int ticket, ok, guard_k, ovl_flag;
     int hzs[2];
-    int ns, namb, ndl, pad1;
+    int ns, namb, pad1[2];
 };
 
 constexpr unsigned ST_WALL = 1u, ST_UZERO = 2u, ST_INACTIVE = 4u, ST_OVL_CERTAIN = 8u, ST_OVL_AMBIG = 16u,
@@ -616,30 +616,20 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
     const int i = c.k0 + k;
     char *base = reinterpret_cast<char *>(sm.cwin);
     constexpr int LMAX = 1024;  // near-field terms per point (r_c <= 5 sigma: at most ~740 ions at contact density)
-    int *Qs = reinterpret_cast<int *>(base);                // DA_NC ints (16384 B); later 2 x LMAX sorted terms
+    double *sorted = reinterpret_cast<double *>(base);      // 2 x LMAX terms in ascending j (16384 B)
     int *F = reinterpret_cast<int *>(base + 16384);         // 2 x DA_FRS ints
     int *nl = reinterpret_cast<int *>(base + 16896);        // 2 counters
     int *lj = reinterpret_cast<int *>(base + 17024);        // 2 x LMAX indices (8192 B)
     double *lt = reinterpret_cast<double *>(base + 25216);  // 2 x LMAX terms (16384 B)
     double *hb = reinterpret_cast<double *>(base + 41600);  // 2 x 64 (h1) + 2 x 64 (h2)
     double *res = hb + 4 * DA_H;                            // phi0, phi1, g0, g1
-    signed char *shell = reinterpret_cast<signed char *>(res + 8);
-    static_assert(41600 + 8 * (4 * DA_H + 8) + DA_NSHELL <= S * CS * 4, "reference-surrogate scratch fits the window matrix");
+    static_assert(41600 + 8 * (4 * DA_H + 8) <= S * CS * 4, "reference-surrogate scratch fits the window matrix");
     static_assert(2 * LMAX * 8 <= 16384 && 2 * DA_FRS * 4 <= 512, "scratch layout");
     const float4 x = sm.own[k], a = sm.trial[k];
-    for (int q = tid; q < DA_NSHELL; q += T) shell[q] = __ldg(&d.shell[q]);
     if (tid < 2 * DA_FRS) F[tid] = 0;
     if (tid < 2) nl[tid] = 0;
-    da_build_Q(Qs, d, c.g, c.B, c.N, c.Pprev, Wg);
-    // features of both points: the cell histogram split over 4 threads per point, then the own later ions
-    if (tid < 8) {
-        const int pt = tid >> 2, part = tid & 3;
-        const float4 p = pt ? a : x;
-        const int cp = da_fcell(d, p.x, p.y, p.z);
-        da_hist_range(F + pt * DA_FRS, Qs, shell, cp, part * (DA_NC / 4), (part + 1) * (DA_NC / 4));
-        if (part == 0) da_hist_own(F + pt * DA_FRS, sm.own, d, shell, cp, k, c.nk);
-    }
-    // near field: counted candidates of the 27 cells, FP64 membership, collected per point
+    __syncthreads();
+    // near field and taper-region shells: counted candidates of the 27 cells, FP64 distances
     {
         const int G = d.nf_G;
         const int cx = da_ncell_axis(d, x.x), cy = da_ncell_axis(d, x.y), cz = da_ncell_axis(d, x.z);
@@ -652,20 +642,19 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
                 const int j = __ldg(&d.cell_ions[idx]);
                 if (!da_counted(i, c.g, c.B, Wg, j)) continue;
                 const float4 y = __ldcg(&d.cell_pos[idx]);
-                const double d20 = d2_fp64(x.x, x.y, x.z, y.x, y.y, y.z);
-                const double d21 = d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z);
-                if (d20 < d.rc2) {
-                    const int s = atomicAdd(&nl[0], 1);
+#pragma unroll
+                for (int pt = 0; pt < 2; ++pt) {
+                    const float4 p = pt ? a : x;
+                    const double dd2 = d2_fp64(p.x, p.y, p.z, y.x, y.y, y.z);
+                    if (!(dd2 < d.rc2)) continue;
+                    const int s = atomicAdd(&nl[pt], 1);
                     if (s < LMAX) {
-                        lj[s] = j;
-                        lt[s] = __ddiv_rn((double)y.w, __dsqrt_rn(d20));
+                        lj[pt * LMAX + s] = j;
+                        lt[pt * LMAX + s] = da_term64(d, (double)y.w, dd2);
                     }
-                }
-                if (d21 < d.rc2) {
-                    const int s = atomicAdd(&nl[1], 1);
-                    if (s < LMAX) {
-                        lj[LMAX + s] = j;
-                        lt[LMAX + s] = __ddiv_rn((double)y.w, __dsqrt_rn(d21));
+                    if (dd2 >= d.rs2) {
+                        const int kk = (int)floor(__dmul_rn(__ddiv_rn(__dsub_rn(dd2, d.rs2), __dsub_rn(d.rc2, d.rs2)), 32.0));
+                        atomicAdd(&F[pt * DA_FRS + min(kk, 31)], (int)y.w);
                     }
                 }
             }
@@ -673,7 +662,6 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
     }
     __syncthreads();
     // ascending-j order: each entry's rank among its list, then sequential sums
-    double *sorted = reinterpret_cast<double *>(Qs);  // the grid is no longer needed
     for (int e = tid; e < 2 * LMAX; e += T) {
         const int pt = e / LMAX, s = e - pt * LMAX;
         const int n = min(nl[pt], LMAX);
@@ -698,7 +686,7 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
         const float4 p = pt ? a : x;
         double z = (double)bf16f(__ldg(&w[DA_OFF_B1 + o]));
         for (int q = 0; q < 32; ++q)
-            z = __dadd_rn(z, __dmul_rn((double)bf16f(__ldg(&w[o * DA_NIN + q])), __dmul_rn((double)F[pt * DA_FRS + q], 0.0625)));
+            z = __dadd_rn(z, __dmul_rn((double)bf16f(__ldg(&w[o * DA_NIN + q])), __dmul_rn((double)F[pt * DA_FRS + q], 0.25)));
         const double px = p.x, py = p.y, pz = p.z;
         const double rad = __ddiv_rn(__dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz))), d.R);
         z = __dadd_rn(z, __dmul_rn((double)bf16f(__ldg(&w[o * DA_NIN + 32])), rad));
@@ -746,7 +734,7 @@ __device__ bool wait_ledger(const ChainDev &ch, unsigned long long need, Ctl *ct
 // Stage 1 of delayed acceptance for the whole group (whole CTA).  Decides the moves it rejects (overlap
 // with a counted ion, or the surrogate test), lists the survivors, and gives each survivor its stage-2
 // threshold Lf = L(u2) + dEt with the surrogate's error added to dEtB.
-__device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp64)
+__device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp64, long long *part)
 {
     const ChainDev &ch = *c.ch;
     const DADev &d = *ch.da;
@@ -760,73 +748,27 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
     __syncthreads();
     if (!sm.ok) return false;
     char *base = reinterpret_cast<char *>(sm.cin);
-    float *Wf = reinterpret_cast<float *>(base);
-    int *Qs = reinterpret_cast<int *>(base + 25616);
-    int *Fr = reinterpret_cast<int *>(base + 42000);
-    signed char *shell = reinterpret_cast<signed char *>(base + 75792);
-    float *w2n = reinterpret_cast<float *>(base + 76480);
-    float *gv = reinterpret_cast<float *>(base + 76736);
+    float *Wf = reinterpret_cast<float *>(base);                // DA_NP floats
+    int *Fr = reinterpret_cast<int *>(base + 25616);            // 2S shell histograms (old positions, then trials)
+    float *w2n = reinterpret_cast<float *>(base + 59408);
+    float *gv = reinterpret_cast<float *>(base + 59664);
     float *ge = gv + 2 * S;
     float *nph0 = ge + 2 * S, *nph1 = nph0 + S, *nA0 = nph1 + S, *nA1 = nA0 + S;
-    int *nnt = reinterpret_cast<int *>(nA1 + S), *novl = nnt + S, *ndiff = novl + S;
-    static_assert(76736 + 4 * 2 * S + 4 * 4 * S + 4 * (3 * S + 1) <= 2 * S * CS * 4, "stage-1 scratch");
+    int *nnt = reinterpret_cast<int *>(nA1 + S), *novl = nnt + S;
+    static_assert(59664 + 4 * 2 * S * 2 + 4 * 4 * S + 4 * 2 * S <= 2 * S * CS * 4, "stage-1 scratch");
     for (int q = tid; q < DA_NP; q += T) Wf[q] = bf16f(__ldg(&d.w[q]));
-    for (int q = tid; q < DA_NSHELL; q += T) shell[q] = __ldg(&d.shell[q]);
     if (tid < DA_H) w2n[tid] = __ldg(&d.w2n[tid]);
     for (int q = tid; q < 2 * S * DA_FRS; q += T) Fr[q] = 0;
     if (tid < WORDS) sm.d64w[tid] = 0u;
-    if (tid == 0) {
-        sm.namb = 0;
-        ndiff[S] = 0;
-    }
-    da_build_Q(Qs, d, c.g, c.B, c.N, c.Pprev, Wg);
+    if (tid == 0) sm.namb = 0;
+    __syncthreads();
     const auto active = [&](int k) { return k < nk && !(sm.st[k] & (ST_INACTIVE | ST_WALL)); };
-    // shell histograms at the old positions (two threads per point)
-    {
-        const int k = tid >> 1, half = tid & 1;
-        if (active(k)) {
-            const float4 x = sm.own[k];
-            const int cp = da_fcell(d, x.x, x.y, x.z);
-            da_hist_range(Fr + k * DA_FRS, Qs, shell, cp, half * (DA_NC / 2), (half + 1) * (DA_NC / 2));
-            if (half == 0) da_hist_own(Fr + k * DA_FRS, sm.own, d, shell, cp, k, nk);
-        }
-    }
-    __syncthreads();
-    // trial positions in the old position's feature cell share its histogram; the others get their own
-    if (tid < S && active(tid)) {
-        const float4 x = sm.own[tid], a = sm.trial[tid];
-        if (da_fcell(d, x.x, x.y, x.z) != da_fcell(d, a.x, a.y, a.z)) ndiff[atomicAdd(&ndiff[S], 1)] = tid;
-        else
-            for (int q = 0; q < DA_FRS; ++q) Fr[(S + tid) * DA_FRS + q] = Fr[tid * DA_FRS + q];
-    }
-    __syncthreads();
-    for (int e = tid; e < 2 * ndiff[S]; e += T) {
-        const int k = ndiff[e >> 1], half = e & 1;
-        const float4 a = sm.trial[k];
-        const int cp = da_fcell(d, a.x, a.y, a.z);
-        da_hist_range(Fr + (S + k) * DA_FRS, Qs, shell, cp, half * (DA_NC / 2), (half + 1) * (DA_NC / 2));
-        if (half == 0) da_hist_own(Fr + (S + k) * DA_FRS, sm.own, d, shell, cp, k, nk);
-    }
-    __syncthreads();
-    // MLP at every point (thread = point: 0..S-1 old positions, S..2S-1 trials)
-    {
-        const int k = tid & (S - 1);
-        float g = 0.f, eg = 0.f;
-        if (active(k)) {
-            const float4 p = tid < S ? sm.own[k] : sm.trial[k];
-            float v[DA_NIN];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) v[q] = (float)Fr[tid * DA_FRS + q] * 0.0625f;
-            v[32] = da_radial32(d, p);
-            da_mlp32(Wf, w2n, v, g, eg);
-        }
-        gv[tid] = g;
-        ge[tid] = eg;
-    }
-    // near field (warp per move)
+    // near field and taper-region shell histograms (warp per move)
+    long long tq = clock64();
     for (int k = warp; k < nk; k += T / 32) {
         if (!active(k)) continue;
-        const NearOut o = da_near_warp(d, c.g, c.B, Wg, c.k0 + k, sm.own[k], sm.trial[k], ch.sig2_lo, ch.sig2_hi, ch.sig2);
+        const NearOut o = da_near_warp(d, c.g, c.B, Wg, c.k0 + k, sm.own[k], sm.trial[k], ch.sig2_lo, ch.sig2_hi, ch.sig2,
+                                       Fr + k * DA_FRS, Fr + (S + k) * DA_FRS);
         if (lane == 0) {
             nph0[k] = o.ph0;
             nph1[k] = o.ph1;
@@ -837,6 +779,25 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
         }
     }
     __syncthreads();
+    part[3] += clock64() - tq;
+    tq = clock64();
+    // MLP at every point (thread = point: 0..S-1 old positions, S..2S-1 trials)
+    {
+        const int k = tid & (S - 1);
+        float g = 0.f, eg = 0.f;
+        if (active(k) && !novl[k]) {
+            const float4 p = tid < S ? sm.own[k] : sm.trial[k];
+            float v[DA_NIN];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = (float)Fr[tid * DA_FRS + q] * 0.25f;
+            v[32] = da_radial32(d, p);
+            da_mlp32(Wf, w2n, v, g, eg);
+        }
+        gv[tid] = g;
+        ge[tid] = eg;
+    }
+    __syncthreads();
+    part[2] += clock64() - tq;
     // FP32 surrogate energy change and its bound; stage-1 decisions outside the band
     if (tid < S) {
         const int k = tid;
@@ -852,7 +813,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
             } else {
                 const float lq = lBf * sm.own[k].w;
                 const float ph0 = nph0[k], ph1 = nph1[k], g0 = gv[k], g1 = gv[S + k];
-                const float cph = ((float)nnt[k] + 16.0f) * U32;
+                const float cph = ((float)nnt[k] + 40.0f) * U32;  // per term <= 34u of |q|/d (taper included)
                 const float dEt = lq * ((ph1 + g1) - (ph0 + g0));
                 const float E = fabsf(lq) *
                                     (cph * (nA0[k] + nA1[k]) + ge[k] + ge[S + k] +
@@ -1043,14 +1004,14 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         sm.seen[tid] = 0u;
         sm.winacc[tid] = 0u;
     }
-    if (tid == 0) sm.ndl = 0;
     __syncthreads();
 
     // 1b. delayed acceptance: stage 1 decides what it can before any pair sum; only survivors continue
     int n_dfp64 = 0;
+    long long da_part[4] = {0, 0, 0, 0};
     const long long cyc_da0 = clock64();
     if (ch.da) {
-        if (!da_stage1(sm, c, ctl, mode, n_dfp64)) return false;
+        if (!da_stage1(sm, c, ctl, mode, n_dfp64, da_part)) return false;
     } else {
         if (tid < S) sm.surv[tid] = (unsigned char)tid;
         if (tid == 0) sm.ns = nk;
@@ -1525,19 +1486,12 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const bool acc = bit(sm.accw, tid);
         __stcg(&ch.pos[(s + 1) & 1][k0 + tid], acc ? sm.trial[tid] : sm.own[tid]);
         if (ch.da && acc && publish) {
-            // delayed acceptance: the near-field cell list holds current positions; record feature-cell changes
+            // delayed acceptance: the near-field cell list holds current positions
             const DADev &dd = *ch.da;
-            const int j = k0 + tid;
-            const float4 a = sm.trial[tid];
-            __stcg(&dd.cell_pos[__ldg(&dd.slot_of[j])], a);
-            const int f0 = __ldg(&dd.fcell0[j]), f1 = da_fcell(dd, a.x, a.y, a.z);
-            if (f0 != f1)
-                __stcg(&dd.dlist[(size_t)g * S + atomicAdd(&sm.ndl, 1)],
-                       (unsigned)f0 | ((unsigned)f1 << 12) | (((unsigned)(int)a.w & 0xffu) << 24));
+            __stcg(&dd.cell_pos[__ldg(&dd.slot_of[k0 + tid])], sm.trial[tid]);
         }
     }
     __syncthreads();
-    if (ch.da && tid == 0 && publish) __stcg(&ch.da->dcount[g], sm.ndl);
     if (warp == 0 && publish && lane < (nk + 31) / 32)  // release after the barrier: orders every thread's stores
         st_release(&ch.flags[g * WORDS + lane], ((unsigned long long)tag_cur << 32) | sm.accw[lane]);
     const unsigned long long gt_posp = globaltimer();
@@ -1656,6 +1610,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 atomicAdd(&ch.stats[CNT_DA_OVL1], (unsigned long long)cnt[10]);
                 atomicAdd(&ch.stats[CNT_DA_FP64], (unsigned long long)n_dfp64);
                 atomicAdd(&ch.stats[CNT_CYC_DA1], (unsigned long long)cyc_da);
+                for (int q = 0; q < 4; ++q) atomicAdd(&ch.stats[CNT_CYC_DA_PART + q], (unsigned long long)da_part[q]);
             }
         }
     }

@@ -2,7 +2,7 @@
 
 What fixes each expected value: libm's exp; an independent numpy forward pass and central finite differences
 for the surrogate MLP; brute-force recomputation of the stage-1 features and near-field sums plus a charge
-conservation identity; exact antisymmetry of the surrogate energy change; the exact Boltzmann distance
+conservation identity; continuity of the tapered near field across r_c; exact antisymmetry of the surrogate energy change; the exact Boltzmann distance
 distribution of a confined ion pair (the delayed-acceptance chain must sample it whatever the surrogate); the
 plain chain's equilibrium averages; brute-force total energy against the ledger.
 """
@@ -116,27 +116,18 @@ def _brute_stage1(ch, pos, i, p, W, r_c, is_trial):
     d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
     ovl = bool(is_trial and (d2[counted] < 1.0).any())
     near = counted & (d2 < r_c * r_c)
-    phi = float(np.sum(q[near] / np.sqrt(d2[near])))
-    G = 16
-    Rf = np.float32(ch.R)
-    icf = np.float32(G / (2.0 * ch.R))
-
-    def cell(x):
-        c = np.floor((np.asarray(x, np.float32) + Rf) * icf).astype(np.int64)
-        return np.clip(c, 0, G - 1)
-
-    e, delta = 2.0 * ch.R / G, (2.0 * ch.R - r_c) / 32.0
-    cj = cell(pos)
-    cp = cell(p)
-    n2 = ((cj - cp[None, :]) ** 2).sum(1)
-    dist = e * np.sqrt(n2.astype(np.float64))
-    shell = np.where(dist < r_c, -1, np.minimum(np.floor((dist - r_c) / delta), 31)).astype(np.int64)
-    F = np.zeros(32)
-    for k in range(32):
-        F[k] = q[counted & (shell == k)].sum()
-    left_out = q[counted & (shell < 0)].sum()
-    v = np.concatenate([F / 16.0, [np.sqrt((float(p[0]) ** 2 + float(p[1]) ** 2) + float(p[2]) ** 2) / ch.R]])
-    return v, phi, ovl, float(q[counted].sum()), float(left_out)
+    dd = np.sqrt(d2[near])
+    r_s, tw = r_c / 2.0, r_c / 2.0
+    t = np.clip((dd - r_s) / tw, 0.0, None)
+    sw = np.where(dd <= r_s, 1.0, 1.0 - t * t * (3.0 - 2.0 * t))  # C1 taper from r_c/2 to r_c
+    phi = float(np.sum(q[near] * sw / dd))
+    # features: net valence of counted ions in 32 shells of equal width in d^2 over the taper region
+    rs2, rc2 = (r_c / 2.0) ** 2, r_c * r_c
+    band = counted & (d2 >= rs2) & (d2 < rc2)
+    k = np.minimum(np.floor(((d2 - rs2) / (rc2 - rs2)) * 32.0), 31).astype(np.int64)
+    F = np.array([q[band & (k == s)].sum() for s in range(32)])
+    v = np.concatenate([F / 4.0, [np.sqrt((float(p[0]) ** 2 + float(p[1]) ** 2) + float(p[2]) ** 2) / ch.R]])
+    return v, phi, ovl, float(q[band].sum())
 
 
 @pytest.mark.parametrize("W", [0, 1, 3])
@@ -149,15 +140,32 @@ def test_stage1_features_and_near_field_brute_force(W):
         i = int(rng.integers(0, ch.n))
         a = (pos[i] + rng.uniform(-0.4, 0.4, 3)).astype(np.float32)
         v0, v1, ph0, ph1, ovl, dEt = oc.da_probe(i, a)
-        bv0, bph0, _, tot, lo0 = _brute_stage1(ch, pos, i, pos[i], W, 4.0, False)
-        bv1, bph1, bovl, _, lo1 = _brute_stage1(ch, pos, i, a, W, 4.0, True)
+        bv0, bph0, _, q0 = _brute_stage1(ch, pos, i, pos[i], W, 4.0, False)
+        bv1, bph1, bovl, q1 = _brute_stage1(ch, pos, i, a, W, 4.0, True)
         assert (v0 == bv0).all() and (v1 == bv1).all()
         assert ovl == bovl
         assert abs(ph0 - bph0) <= 1e-12 * (1 + abs(bph0)) and abs(ph1 - bph1) <= 1e-12 * (1 + abs(bph1))
-        # conservation: shells plus the cells left out hold every counted ion's charge
-        assert abs(16.0 * v0[:32].sum() + lo0 - tot) < 1e-9 and abs(16.0 * v1[:32].sum() + lo1 - tot) < 1e-9
+        # conservation: the shells together hold the net valence of the counted ions in the taper region
+        assert 4.0 * v0[:32].sum() == q0 and 4.0 * v1[:32].sum() == q1
         checked += not ovl
     assert checked > 10
+
+
+def test_near_field_taper_is_continuous_at_the_cutoff():
+    """An ion moved across r_c changes phi_near by less than the step q / r_c a hard cutoff would give; the
+    taper makes phi_near continuous (D1)."""
+    pos = np.array([[0.0, 0.0, 0.0], [3.9999, 0.0, 0.0], [-2.0, 1.5, 0.0], [0.0, -2.2, 1.0]], np.float32)
+    q = np.array([1.0, 1.0, -1.0, 1.0], np.float32)
+    oc = oracle.OracleChain(pos, q, 1.0, 0.7, 8.0, 0.3, seed=1)
+    oc.set_surrogate(np.zeros(oracle.MLP_NP, np.uint16), r_c=4.0, W=0)
+    # phi_near at ion 0's old position, with ion 1 just inside r_c and then just outside
+    a0 = np.array([0.0, 0.0, 0.0002], np.float32)
+    ph_in = oc.da_probe(0, a0)[2]
+    moved = pos.copy()
+    moved[1, 0] = 4.0002
+    oc.set_positions(moved)
+    ph_out = oc.da_probe(0, a0)[2]
+    assert abs(ph_in - ph_out) < 1e-6, (ph_in, ph_out)  # a hard cutoff would jump by 1/4
 
 
 def test_surrogate_energy_change_is_antisymmetric():
