@@ -28,9 +28,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MC trial moves/s and G pair-evals/s per GB300 vs plain exact FP64-guarded path"
-SWEEP_SOURCES = ["paper_1602_05716_gb300/csrc/mc_sweep.cu", "paper_1602_05716_gb300/csrc/mc_device.cuh"]
+SWEEP_SOURCES = ["paper_1602_05716_gb300/csrc/mc_sweep.cu", "paper_1602_05716_gb300/csrc/mc_device.cuh",
+                 "paper_1602_05716_gb300/csrc/mc_da.cuh"]
 
-# ALU roofline of the pair term ("Roofline"): per pair-eval two MUFU reciprocal square roots and
+# ALU roofline of the pair term: per pair-eval two MUFU reciprocal square roots and
 # 14 FP32-pipe operations (6 differences, 6 multiply/fma for the two squared distances, 1 difference of the
 # inverse distances, 1 fma into the sum).  Unit rates per SM per clock on sm_103: FP32 lanes 128; MUFU rsqrt
 # MUFU_RSQ_PER_CLK (measured by the throughput probe recorded in profiles/alu_throughput_probe.md).
@@ -228,6 +229,49 @@ def run_reference(args):
     return 0
 
 
+def train_surrogate(pkg, ch, r_c: float, W: int, n_samples: int, epochs: int, max_sweeps: int = 200):
+    """The learned part of delayed acceptance (untimed): training samples from the plain chain's own trial moves
+    (GPU sample kernel) over successive plain sweeps, then Adam on the GPU (the project's MLP kernels).  Returns the
+    BF16 weights and a summary with the held-out gain over g = 0 on one later configuration."""
+    import numpy as np
+    t0 = time.perf_counter()
+    g = pkg.System([ch])
+    g.set_surrogate(np.zeros(pkg.MLP_NP, np.uint16), r_c=r_c, W=W)
+    g.set_option(pkg.OPT_DA, 0)
+    g.sweep(3)
+    vs, ys, got, sweeps = [], [], 0, 0
+    while got < n_samples and sweeps < max_sweeps:
+        g.sweep(1)
+        sweeps += 1
+        v, y, ok = g.da_samples()
+        vs.append(v[ok])
+        ys.append(y[ok])
+        got += int(ok.sum())
+    g.sweep(2)
+    vt, yt, okt = g.da_samples()
+    vt, yt = vt[okt], yt[okt]
+    V, Y = np.concatenate(vs)[:n_samples], np.concatenate(ys)[:n_samples]
+    perm = np.random.default_rng(0).permutation(len(Y))
+    V, Y = V[perm], Y[perm]
+    del vs, ys
+    rng = np.random.default_rng(1)
+    H, NIN = pkg.MLP_H, pkg.MLP_NIN
+    w0 = np.concatenate([rng.normal(0, 0.5 / NIN ** 0.5, H * NIN), np.zeros(H), rng.normal(0, 0.5 / H ** 0.5, H * H),
+                         np.zeros(H), np.zeros(H + 1)]).astype(np.float32)
+    u = w0.view(np.uint32).astype(np.uint64)
+    w0 = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+    t1 = time.perf_counter()
+    w, hist = pkg.mlp_train(V, Y, w0, epochs=epochs, batch=8192, lr=2e-3)
+    t2 = time.perf_counter()
+    held, _ = pkg.mlp_loss_grad(w, vt, yt)
+    zero = float(np.mean(yt.astype(np.float64) ** 2))
+    g.close()
+    return w, {"samples": int(len(Y)), "plain_sweeps_sampled": sweeps, "epochs": epochs,
+               "loss_first_last_epoch": [float(hist[0]), float(hist[-1])] if len(hist) else None,
+               "held_out_far_part_mse": {"g_zero": zero, "trained": float(held), "moves": int(len(yt))},
+               "sample_s": t1 - t0, "train_s": t2 - t1}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -248,11 +292,43 @@ def run_ours(args):
     moves_per_step = n * sps
     pairs_per_step = sum(c.n * (c.n - 1) for c in chains) * sps
 
+    mode = args.mode or {"da_n65536": "da", "large_n1048576": "both"}.get(args.workload, "plain")
+    da_info = None
+    w_da = None
+    if mode in ("da", "both"):
+        ch0 = chains[0]
+        w_da, da_info = train_surrogate(pkg, ch0, args.r_c, args.da_W, args.da_samples, args.da_epochs)
+
     stream = torch.cuda.Stream()
     flush = torch.empty(max(1, args.flush_mb) * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    plain_cmp = None
+    if mode in ("da", "both"):
+        # the plain exact path on the same workload, same stream and timing rules, for the ratio
+        with torch.cuda.stream(stream):
+            psys = pkg.System(chains)
+            psys.set_stream(stream.cuda_stream)
+            psteps = max(1, min(args.steps, 3))
+            for _ in range(min(args.warmup, 2)):
+                flush.zero_()
+                psys.sweep_async(sps)
+            stream.synchronize()
+            pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(psteps)]
+            for k in range(psteps):
+                flush.zero_()
+                pev[k][0].record(stream)
+                psys.sweep_async(sps)
+                pev[k][1].record(stream)
+            stream.synchronize()
+            pms = [a.elapsed_time(b) for a, b in pev]
+            psys.close()
+        plain_cmp = {"moves_per_s": moves_per_step * psteps / (sum(pms) / 1000.0), "steps": psteps,
+                     "ms_per_step": statistics.mean(pms)}
     with torch.cuda.stream(stream):
         sysm = pkg.System(chains)
         sysm.set_stream(stream.cuda_stream)
+        if w_da is not None:
+            for i in range(len(chains)):
+                sysm.set_surrogate(w_da, r_c=args.r_c, W=args.da_W, chain=i)
         tuned = sysm.autotune(2) if len(chains) > 1 else None
         for _ in range(args.warmup):
             flush.zero_()
@@ -358,6 +434,30 @@ def run_ours(args):
                        "path": "mc_set_positions(pinned host) + mc_sweep + mc_get_positions + mc_energy per step"}
         line["gpu_launches"] += 2 * args.steps
 
+    if w_da is not None:
+        moves_sw = n * stats["sweeps"]
+        surv = moves_sw - stats["da_rej1"] - stats["da_ovl1"] - stats["rej_wall"]
+        # surrogate error on one recorded sweep of the current state (moves evaluated by both stages)
+        sysm.record_enable(n)
+        sysm.sweep(1)
+        rec = sysm.records()
+        both = np.isfinite(rec["dE"]) & np.isfinite(rec["dEt"])
+        err = (rec["dE"] - rec["dEt"])[both]
+        line["metric_variant"] = "delayed acceptance with the trained surrogate (exact: decisions of the FP64 reference)"
+        line["delayed_acceptance"] = {
+            "r_c": args.r_c, "W_groups": args.da_W, "training": da_info,
+            "stage1_reject_per_move": stats["da_rej1"] / moves_sw, "stage1_overlap_per_move": stats["da_ovl1"] / moves_sw,
+            "survivors_per_move": surv / moves_sw, "accept_rate": stats["accepts"] / moves_sw,
+            "stage2_reject_per_survivor": (stats["rej_metropolis"]) / max(1, surv),
+            "surrogate_dE_error_rms_kT": float(np.sqrt(np.mean(err ** 2))) if err.size else None,
+            "surrogate_dE_error_mean_abs_kT": float(np.mean(np.abs(err))) if err.size else None,
+            "gpair_evals_executed_per_s": pair_rate * surv / moves_sw / 1e9,
+            "plain_equivalent_gpair_evals_per_s": pair_rate / 1e9,
+            "plain_path_same_gpu": plain_cmp,
+            "speedup_vs_plain": value / plain_cmp["moves_per_s"] if plain_cmp else None}
+        line["gpu_launches"] = 6 * sps * args.steps + (line["gpu_launches"] - 2 * args.steps)
+    elif plain_cmp is not None:
+        line["plain_path_same_gpu"] = plain_cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl.chains, min_seconds=args.cpu_seconds)
     if rank == 0:
@@ -380,6 +480,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--ref-moves-per-step", type=int, default=2048)
     ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--mode", choices=["plain", "da", "both"], default=None,
+                    help="plain exact path or delayed acceptance with a trained surrogate (default by workload)")
+    ap.add_argument("--r-c", dest="r_c", type=float, default=4.0)
+    ap.add_argument("--da-W", dest="da_W", type=int, default=160)
+    ap.add_argument("--da-samples", dest="da_samples", type=int, default=2_000_000)
+    ap.add_argument("--da-epochs", dest="da_epochs", type=int, default=4)
     args = ap.parse_args()
     if args.steps is None:
         args.steps = {"plain_n256": 200, "plain_n16383": 50, "batch64": 20, "da_n65536": 10,

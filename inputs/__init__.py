@@ -6,8 +6,9 @@ states follow the paper's recipe: ions placed uniformly in the confining
 sphere with hard-core rejection (Sec. 5.2), valences of the primitive-model
 electrolyte, shuffled over the ion index.
 
-Workloads (sizes of the five benchmark configurations; readings where the
-configuration text is ambiguous are recorded in the design doc):
+Workloads (sizes of the five benchmark configurations; where the stated
+counts are not neutral, one anion fewer makes N = 16383 neutral, and the batch
+draws its species mix and half-width as documented below):
   plain_n256     N=256 1:1 (128 x +1, 128 x -1), phi=0.10, l_B=0.7, h=0.5, 2000 sweeps
   plain_n16383   N=16383 2:1 (5461 x +2, 10922 x -1), phi=0.20, l_B=0.7, h=0.3, 500 sweeps
   batch64        64 chains, N log-uniform in [512, 32768], phi U[0.01,0.30],

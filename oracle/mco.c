@@ -25,7 +25,7 @@
  *     Eq. trial-outcome), l_B the Bjerrum length, energies in k_B T;
  *   - the hard spherical wall of Sec. 5.2.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   R1 random numbers: Philox4x32-10 keyed by (seed, chain), counter = move
  *      index m = sweep*N + i, replacing the paper's host-side ran4 (Sec. 3.1);
  *   R2 u_k = (w_k >> 8) * 2^-24 (exact float in [0,1)); trial coordinate
@@ -614,7 +614,7 @@ void mco_move_draws(uint64_t seed, uint32_t chain, uint64_t m, uint32_t purpose,
  * in the sense of Christen & Fox, 2005).  The paper's method is the exact
  * sequential chain of Sec. 2; this variant keeps its stationary distribution
  * and skips the O(N) sum for moves that a cheap first stage already rejects.
- * Readings D1-D8 (also listed in the design doc):
+ * Readings D1-D8:
  *
  *  D1 Surrogate energy of ion i at point p, given the others:
  *       Et(p) = l_B q_i [phi_near(p) + g(v(p))],

@@ -991,11 +991,12 @@ int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w
         std::memcpy(&wf[k], &u, 4);
         if (!std::isfinite(wf[k])) return fail(MC_ERR_INVALID, "weight %d is not finite", k);
     }
-    // near-field cells: edge >= r_c + twice the largest displacement, so the 27 cells around an ion's start
-    // position hold every ion within r_c of its old or trial position at any time of the sweep
+    // near-field reach: r_c plus the largest trial displacement plus the largest move of a candidate since the
+    // sweep's start (one per sweep); cells of edge >= reach / 2, so the cells within two of an ion's start cell
+    // hold every ion within r_c of its old or trial position at any time of the sweep
     const double D = (double)(float)(2.0 * c.h);
-    const double emin = (r_c + 2.0 * std::sqrt(3.0) * 0.5 * D) * (1.0 + 0x1p-8) + 1e-6;
-    const int G = std::max(1, std::min(64, (int)std::floor(2.0 * c.R / emin)));
+    const double reach = (r_c + 2.0 * std::sqrt(3.0) * 0.5 * D) * (1.0 + 0x1p-8) + 1e-6;
+    const int G = std::max(1, std::min(64, (int)std::floor(2.0 * c.R / (0.5 * reach))));
     // (re)allocate
     cudaFree(c.dda); cudaFree(c.d_w); cudaFree(c.d_w2n); cudaFree(c.d_cell_start); cudaFree(c.d_cell_ions);
     cudaFree(c.d_slot_of); cudaFree(c.d_cnt); cudaFree(c.d_cellid); cudaFree(c.d_fill); cudaFree(c.d_cell_pos);
@@ -1044,6 +1045,8 @@ int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w
     d.rc2_hi = std::nextafter((float)(d.rc2 * (1.0 + 0x1p-19)), 3.0e38f);
     d.nf_scale = (float)((double)G / (2.0 * c.R));
     d.nf_R = (float)c.R;
+    d.nf_edge = (float)(2.0 * c.R / (double)G);
+    d.reach2 = (float)(reach * reach * (1.0 + 0x1p-10));
     d.Rr = (float)c.R;
     d.nf_G = G;
     d.W = W;

@@ -278,6 +278,7 @@ struct SampleSmem {
     int Fr[2 * S * DA_FRS];
     float ph0[S], ph1[S], ex[S], mn[S];
     int ovl[S];
+    int wsc[T / 32][256];
 };
 
 __global__ void __launch_bounds__(T, 1) da_sample_kernel(const ChainDev *__restrict__ chp, const DADev *__restrict__ dp,
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(T, 1) da_sample_kernel(const ChainDev *__restr
         // near field and shell histograms (warp per move)
         for (int k = warp; k < nk; k += T / 32) {
             const NearOut o = da_near_warp(d, g, B, Wg, k0 + k, sm.own[k], sm.trial[k], ch.sig2_lo, ch.sig2_hi, ch.sig2,
-                                           sm.Fr + k * DA_FRS, sm.Fr + (S + k) * DA_FRS);
+                                           sm.Fr + k * DA_FRS, sm.Fr + (S + k) * DA_FRS, sm.wsc[warp]);
             if (lane == 0) {
                 sm.ph0[k] = o.ph0;
                 sm.ph1[k] = o.ph1;

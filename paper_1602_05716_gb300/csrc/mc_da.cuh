@@ -48,6 +48,8 @@ struct DADev {
     float rs2_lo, rs2_hi;          // ... below/above certainly inside/outside r_s
     float rs2_f, c32_f;            // fl32(r_s^2), fl32(32 / (r_c^2 - r_s^2)) for the FP32 shell index
     float nf_scale, nf_R;          // near-field cell of x: floor((x + nf_R) * nf_scale)
+    float nf_edge;                 // its edge (>= reach / 2, so the cells within two of x's cover the reach)
+    float reach2;                  // (r_c + largest trial + largest move of the candidate)^2, with slack
     float Rr;                      // fl32(R) for the FP32 radial input
     int nf_G;                      // near-field cells per axis
     int W;                         // exclusion depth in groups
@@ -215,28 +217,61 @@ struct NearOut {
     int nt, ovl;
 };
 
+constexpr int NF_ST = 125;  // near-field stencil: the 5^3 cells within two of the ion's cell
+
+// Near field of a move (one warp); wsc is this warp's scratch of 2 x 128 ints.  The candidates are the ions
+// of the stencil cells whose box lies within the reach of the old position x.  Lane l holds cells
+// c = l + 32 u (u < 4) at positions p = 4 l + u; the running count over positions and each position's first
+// slot go to wsc, and each candidate finds its cell by a binary search over the running counts.
 __device__ inline NearOut da_near_warp(const DADev &d, int g, int B, int Wg, int i, float4 x, float4 a, float lo2, float hi2,
-                                       double sig2, int *F0, int *F1)
+                                       double sig2, int *F0, int *F1, int *wsc)
 {
     const int lane = threadIdx.x & 31;
     const int G = d.nf_G;
     const int cx = da_ncell_axis(d, x.x), cy = da_ncell_axis(d, x.y), cz = da_ncell_axis(d, x.z);
-    int lo = 0, cnt = 0;
-    if (lane < 27) {
-        const int ax = cx + lane / 9 - 1, ay = cy + (lane / 3) % 3 - 1, az = cz + lane % 3 - 1;
-        if (ax >= 0 && ay >= 0 && az >= 0 && ax < G && ay < G && az < G) {
-            const int q = (ax * G + ay) * G + az;
-            lo = __ldg(&d.cell_start[q]);
-            cnt = __ldg(&d.cell_start[q + 1]) - lo;
+    int *pre = wsc, *cst = wsc + 128;  // by position p = 4 lane + u
+    __syncwarp();                      // the previous move's readers are done with the scratch
+    // lane-local counts of its stencil cells (c = lane + 32 u), then the warp's running sum over all cells
+    int cnt4[4], lsum = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = lane + 32 * u;
+        int n = 0, lo = 0;
+        if (c < NF_ST) {
+            const int ax = cx + c / 25 - 2, ay = cy + (c / 5) % 5 - 2, az = cz + c % 5 - 2;
+            if (ax >= 0 && ay >= 0 && az >= 0 && ax < G && ay < G && az < G) {
+                const float bx = -d.nf_R + (float)ax * d.nf_edge, by = -d.nf_R + (float)ay * d.nf_edge,
+                            bz = -d.nf_R + (float)az * d.nf_edge;
+                const float ex = fmaxf(fmaxf(bx - x.x, x.x - (bx + d.nf_edge)), 0.f);
+                const float ey = fmaxf(fmaxf(by - x.y, x.y - (by + d.nf_edge)), 0.f);
+                const float ez = fmaxf(fmaxf(bz - x.z, x.z - (bz + d.nf_edge)), 0.f);
+                if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= d.reach2) {
+                    const int q = (ax * G + ay) * G + az;
+                    lo = __ldg(&d.cell_start[q]);
+                    n = __ldg(&d.cell_start[q + 1]) - lo;
+                }
+            }
         }
+        cst[4 * lane + u] = lo;
+        cnt4[u] = n;
+        lsum += n;
     }
-    int incl = cnt;
+    int incl = lsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
+    {
+        int run = incl - lsum;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            run += cnt4[u];
+            pre[4 * lane + u] = run;  // candidates in positions 0 .. 4 lane + u
+        }
+    }
+    __syncwarp();
     float ph0 = 0.f, ph1 = 0.f, A0 = 0.f, A1 = 0.f;
     int n0 = 0, n1 = 0, ovl = 0;
     constexpr int U = 4;  // candidates in flight per lane: their loads are issued before any is used
@@ -245,16 +280,16 @@ __device__ inline NearOut da_near_warp(const DADev &d, int g, int B, int Wg, int
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int t = t0 + 32 * u + lane;
-            // the cell holding candidate t: the first lane m whose inclusive count exceeds t
-            int m = 0;
+            // the first position whose running count exceeds t (pre(-1) = 0 <= t < pre(127) = total)
+            int lo_p = -1, hi_p = 127;
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int v = __shfl_sync(0xffffffffu, incl, m + step - 1);
-                if (v <= t) m += step;
+            for (int step = 0; step < 7; ++step) {
+                const int mid = (lo_p + hi_p) >> 1;
+                if (pre[mid] <= t) lo_p = mid;
+                else hi_p = mid;
             }
-            const int lo_m = __shfl_sync(0xffffffffu, lo, m);
-            const int ex_m = __shfl_sync(0xffffffffu, incl - cnt, m);
-            idx[u] = t < total ? lo_m + (t - ex_m) : -1;
+            const int before = lo_p < 0 ? 0 : pre[lo_p];
+            idx[u] = t < total ? cst[hi_p] + (t - before) : -1;
         }
         int jj[U];
         float4 yy[U];

@@ -90,7 +90,8 @@ constexpr unsigned ST_WALL = 1u, ST_UZERO = 2u, ST_INACTIVE = 4u, ST_OVL_CERTAIN
 constexpr int OUT_INACTIVE = 15;  // padding slot of a ragged group (never recorded or counted)
 constexpr unsigned FULL = 0xffffffffu;
 
-// Bound constants (units of u = 2^-24); the derivation is in DESIGN.md ("FP32 error bound").
+// Bound constants (units of u = 2^-24) of the FP32 band: per pair term of the direct form, FP32 partial sums of
+// <= 16 terms promoted exactly by TwoSum, and the FP32 sums and interval sums of <= S corrections.
 constexpr float C_TERM = 10.0f;           // per-term error of q_j (1/r' - 1/r) relative to |q_j| (1/r' + 1/r)
                                           // (both-position ions, direct form)
 constexpr float C_SUM = 24.0f;            // FP32 partials of <= 16 terms, TwoSum-accumulated
@@ -303,7 +304,7 @@ __device__ __forceinline__ void block_sum(Smem &sm, double v, float bb, double &
 // Tier 2: accurate FP32.  With e = y - b and delta = a - b the pair's energy
 // change is q (delta . (2e - delta)) (rn ro)^2 / (rn + ro): no difference of
 // two large inverse distances, so the rounding error scales with
-// |delta| / r^2 instead of 1/r.  Per-term bound ("guard tiers"):
+// |delta| / r^2 instead of 1/r.  Per-term bound:
 // |q| [ |t| (rel(Dn) + 19u) + 4u M (rn ro)^2/(rn+ro) + u |delta| (2 Ro + rho)/rho^3 ]
 // with rho a lower bound of the distance from y to the segment [b, a].
 __device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double xs, double &dE_out)
@@ -629,12 +630,12 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
     if (tid < 2 * DA_FRS) F[tid] = 0;
     if (tid < 2) nl[tid] = 0;
     __syncthreads();
-    // near field and taper-region shells: counted candidates of the 27 cells, FP64 distances
+    // near field and taper-region shells: counted candidates of the stencil cells, FP64 distances
     {
         const int G = d.nf_G;
         const int cx = da_ncell_axis(d, x.x), cy = da_ncell_axis(d, x.y), cz = da_ncell_axis(d, x.z);
-        for (int cc = 0; cc < 27; ++cc) {
-            const int ax = cx + cc / 9 - 1, ay = cy + (cc / 3) % 3 - 1, az = cz + cc % 3 - 1;
+        for (int cc = 0; cc < NF_ST; ++cc) {
+            const int ax = cx + cc / 25 - 2, ay = cy + (cc / 5) % 5 - 2, az = cz + cc % 5 - 2;
             if (ax < 0 || ay < 0 || az < 0 || ax >= G || ay >= G || az >= G) continue;
             const int q = (ax * G + ay) * G + az;
             const int lo = __ldg(&d.cell_start[q]), hi = __ldg(&d.cell_start[q + 1]);
@@ -755,7 +756,8 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
     float *ge = gv + 2 * S;
     float *nph0 = ge + 2 * S, *nph1 = nph0 + S, *nA0 = nph1 + S, *nA1 = nA0 + S;
     int *nnt = reinterpret_cast<int *>(nA1 + S), *novl = nnt + S;
-    static_assert(59664 + 4 * 2 * S * 2 + 4 * 4 * S + 4 * 2 * S <= 2 * S * CS * 4, "stage-1 scratch");
+    int *wsc = novl + S;  // per warp: 256 ints of near-field stencil scratch
+    static_assert(59664 + 4 * 2 * S * 2 + 4 * 4 * S + 4 * 2 * S + 4 * 256 * (T / 32) <= 2 * S * CS * 4, "stage-1 scratch");
     for (int q = tid; q < DA_NP; q += T) Wf[q] = bf16f(__ldg(&d.w[q]));
     if (tid < DA_H) w2n[tid] = __ldg(&d.w2n[tid]);
     for (int q = tid; q < 2 * S * DA_FRS; q += T) Fr[q] = 0;
@@ -768,7 +770,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
     for (int k = warp; k < nk; k += T / 32) {
         if (!active(k)) continue;
         const NearOut o = da_near_warp(d, c.g, c.B, Wg, c.k0 + k, sm.own[k], sm.trial[k], ch.sig2_lo, ch.sig2_hi, ch.sig2,
-                                       Fr + k * DA_FRS, Fr + (S + k) * DA_FRS);
+                                       Fr + k * DA_FRS, Fr + (S + k) * DA_FRS, wsc + 256 * warp);
         if (lane == 0) {
             nph0[k] = o.ph0;
             nph1[k] = o.ph1;
@@ -1019,6 +1021,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     }
     const long long cyc_da = clock64() - cyc_da0;
     const int ns = sm.ns;
+    const int nm = (ns + 31) / 32;  // occupied layers of 32 move slots
 
     // 2. pair sums.  Thread (p, r): moves p + 32 m (m = 0..3), column slice r of 8.
     const int p = tid / SL, r = tid % SL;
@@ -1157,13 +1160,22 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const int Jn = (i + 1 < ntl) ? tile_J(i + 1) : -1;
         float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
         if (pf && tid < S) pre = __ldcg(&tile_src(Jn)[tid]);
-#pragma unroll 4
-        for (int jj = 0; jj < S / SL; ++jj) {
-            const float4 y = sm.tile[cur][jj * SL + r];
-#pragma unroll
-            for (int m = 0; m < MPT; ++m)
-                if (km[m] >= 0) pair_far(b3[m], d3[m], y, sA[m], TA[m], PA[m], mA[m]);
+        // occupied 32-move layers only (all of them for a plain chain); an empty slot in the last layer repeats
+        // a real move and is never written back
+#define MC_TILE_PASS(NMV)                                                              \
+    _Pragma("unroll 4") for (int jj = 0; jj < S / SL; ++jj)                            \
+    {                                                                                  \
+        const float4 y = sm.tile[cur][jj * SL + r];                                    \
+        _Pragma("unroll") for (int m = 0; m < (NMV); ++m)                              \
+            pair_far(b3[m], d3[m], y, sA[m], TA[m], PA[m], mA[m]);                     \
+    }
+        switch (nm) {
+        case 1: MC_TILE_PASS(1) break;
+        case 2: MC_TILE_PASS(2) break;
+        case 3: MC_TILE_PASS(3) break;
+        default: MC_TILE_PASS(MPT) break;
         }
+#undef MC_TILE_PASS
         promote();
         if (pf && tid < S) sm.tile[cur ^ 1][tid] = pre;
         if (warp == 0) {
