@@ -188,6 +188,10 @@ typedef struct {
     uint64_t t_start, t_ready, t_window, t_resolved, t_published;
     uint64_t n_guard; /* 1 if a guard tier ran */
     uint64_t t_positions; /* ... and published its new positions */
+    uint64_t t_tile;      /* observed the last other group's positions (0: already published at the start) */
+    uint64_t t_tiles;     /* finished the pair sums over the other groups */
+    uint64_t t_w2;        /* observed the outcome of the group two before (0: none) */
+    uint64_t t_ph[4];     /* pair sums combined, bands ready, round 0 done, oldest deep window's outcome observed */
 } mc_trace_rec;
 int mc_trace_enable(mc_handle h, int chain, int64_t cap);
 int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);

@@ -48,6 +48,8 @@ struct TraceRec {
     unsigned long long t_start, t_ready, t_window, t_resolved, t_published;
     unsigned long long n_guard;
     unsigned long long t_positions;
+    unsigned long long t_tile, t_tiles, t_w2;  // last tile observed, tiles done, second window observed
+    unsigned long long t_ph[4];                // slices combined, band ready, round 0 done, oldest deep window observed
 };
 
 // Per-chain device descriptor (read-only during a launch).

@@ -42,17 +42,23 @@ namespace mcg {
 constexpr int MPT = 4;             // moves per thread in the pair loops
 constexpr int SL = T / (S / MPT);  // column slices (8)
 constexpr int HALF = S / 2;
+constexpr int DW = 3;              // deep windows: the groups g-2 .. g-1-DW, both positions, matrices in TMEM
+constexpr unsigned TMEM_COLS = 512;  // power of two >= S * DW
+static_assert(S == 128 && T == 256 && S * DW <= (int)TMEM_COLS && TMEM_COLS <= 512, "TMEM layout");
 
 struct __align__(16) Smem {
     float4 own[S];    // this group: old positions (w = valence)
     float4 trial[S];  // this group: trial positions
     float4 wold[S];   // window group: old positions
     float4 wtri[S];   // window group: trial positions
+    float4 dold[DW][S];  // deep windows (d = 0: the group before the window): old positions
+    float4 dtri[DW][S];  // ... trial positions
     float4 tile[2][S];
     float cin[S * CS];   // c[j][k], j < k, this group
     float cwin[S * CS];  // c[j][k], window ion j
     float bhi[S], blo[S];  // sum of terms with known positions (float-float)
-    float Ab[S], Tb[S], TCb[S], Pb[S], mind2[S];  // Ab: both-position ions only; Pb: settled ions
+    float kTs[S], kPs[S];      // far-field bound coefficients of each move (kTs < 0: not bounded, FP64 tier)
+    float lo2ks[S], hi2ks[S];  // ... and its band of the overlap test on pair_far's squared distances
     float lo_w[S], hi_w[S], lo_i[S], hi_i[S];
     float Lf[S];   // -ln(u_acc) in FP32 (+inf if u_acc == 0)
     float bnd[S];  // static part of the FP32 band
@@ -69,13 +75,24 @@ struct __align__(16) Smem {
     double dEt64[S];  // delayed acceptance: the reference surrogate energy change, where computed
     unsigned ovo[S][WORDS], ovn[S][WORDS];    // x'_k overlaps old / trial position of in-group j < k
     unsigned wovo[S][WORDS], wovn[S][WORDS];  // ... of window ion j
+    unsigned dovo[DW][S][WORDS], dovn[DW][S][WORDS];  // ... of deep-window ion j
+    float wexd[S];  // deep windows: exact correction sums (their bits arrive before round 0)
+    // deep-window pass, per (ion half, move slot): float-float sum of old-position terms, bound sums; after
+    // the tiles: exact correction sums and overlap bits
+    float dsh[2][S], dsl[2][S], dsA[2][S], dsT[2][S], dsC[2][S];
+    float dpart[2][S];
+    unsigned dwo[2][S];
+    float Qs[S], mind2[S];  // combined bound sum, minimum squared distance to a settled ion
     unsigned accw[WORDS], decw[WORDS], seen[WORDS], winacc[WORDS], acc0[WORDS], dec0[WORDS];
     unsigned d64w[WORDS];  // dEt64 known
+    unsigned dacc[DW][WORDS];  // deep windows' accept bits
+    unsigned tmem;             // TMEM base address (deep-window correction matrices)
     unsigned char st[S];
     signed char outcome[S];
     unsigned char tier[S];
     unsigned char pad0[S];
     unsigned char surv[S];  // moves that need pair sums (all moves of a plain chain; stage-1 survivors)
+    unsigned char slot[S];  // inverse: move k's slot in surv (255: no pair sums)
     int damb[S];            // delayed acceptance: moves whose stage-1 decision needs the reference arithmetic
     double chunk[CHUNK];
     double redd[32];
@@ -84,6 +101,86 @@ struct __align__(16) Smem {
     int hzs[2];
     int ns, namb, pad1[2];
 };
+
+// More than half of an SM's 228 KB of shared memory: one CTA per SM, so each CTA's TMEM allocation (at most
+// 512 columns) is granted at once and never waits for another CTA.
+static_assert(sizeof(Smem) > 116 * 1024, "one CTA per SM");
+
+// Tensor memory (TMEM) holds the deep-window correction matrices: lane = move slot, column = S d + j for ion j of
+// deep window d.  tcgen05 loads and stores of shape 32x32b move one lane per thread; warp w reaches lanes
+// [32 (w mod 4), 32 (w mod 4) + 32), so each warp only touches its own lane quarter and column half.
+__device__ __forceinline__ void tmem_alloc(unsigned *dst)  // one whole warp
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr)  // one whole warp
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+// 16 consecutive columns of this thread's lane (whole warp, converged).
+__device__ __forceinline__ void tmem_st16(unsigned taddr, const float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};\n" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
+// Load and wait in one statement, so that no use of the registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16])
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive columns of this thread's lane, load and wait in one statement.
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32])
+{
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 constexpr unsigned ST_WALL = 1u, ST_UZERO = 2u, ST_INACTIVE = 4u, ST_OVL_CERTAIN = 8u, ST_OVL_AMBIG = 16u,
                    ST_OVL_POSSIBLE = 32u, ST_DA_DONE = 64u;
@@ -212,11 +309,29 @@ __device__ __forceinline__ void both_pair(float *cm, unsigned (*ovo)[WORDS], uns
     if (overlaps(d2n_n, a, yn, lo, hi, sig2)) atomicOr(&ovn[k][j >> 5], 1u << (j & 31));
 }
 
+// Both-position pair for the second window: as both_pair, returning the correction instead of storing it.
+__device__ __forceinline__ float both_pair_c(unsigned (*ovo)[WORDS], unsigned (*ovn)[WORDS], int k, int j, const float4 a,
+                                             const float4 b, const float4 yo, const float4 yn, float &s, float &A,
+                                             float &Tt, float &TC, float lo, float hi, double sig2)
+{
+    float Ao, An, d2o_n, d2n_n;
+    const float to = pair_term(a, b, yo, Ao, d2o_n);
+    const float tn = pair_term(a, b, yn, An, d2n_n);
+    s += to;
+    Tt += fabsf(to);
+    A += Ao + An;
+    const float c = tn - to;
+    TC += fabsf(c);
+    if (overlaps(d2o_n, a, yo, lo, hi, sig2)) atomicOr(&ovo[k][j >> 5], 1u << (j & 31));
+    if (overlaps(d2n_n, a, yn, lo, hi, sig2)) atomicOr(&ovn[k][j >> 5], 1u << (j & 31));
+    return c;
+}
+
 struct Ctx {
     const ChainDev *ch;
     const float4 *Pprev;  // positions after sweep s-1
     const float4 *Pcur;   // positions after sweep s (groups < g published)
-    int N, B, g, k0, nk, Jw, nwk;
+    int N, B, g, k0, nk, Jw, nwk, nd;  // nd deep windows: groups g-2 .. g-1-nd
     bool win;
     unsigned long long s;
 };
@@ -228,6 +343,8 @@ __device__ __forceinline__ float4 position_of(const Smem &sm, const Ctx &c, int 
     const int J = j / S, l = j - J * S;
     if (J == c.g) return (l < k && bit(sm.accw, l)) ? sm.trial[l] : sm.own[l];
     if (c.win && J == c.Jw) return bit(sm.winacc, l) ? sm.wtri[l] : sm.wold[l];
+    const int d = c.g - 2 - J;
+    if (J < c.g && d >= 0 && d < c.nd) return bit(sm.dacc[d], l) ? sm.dtri[d][l] : sm.dold[d][l];
     return J > c.g ? __ldcg(&c.Pprev[j]) : __ldcg(&c.Pcur[j]);
 }
 
@@ -270,6 +387,10 @@ __device__ void stage_positions(Smem &sm, const Ctx &c, int k, int j0)
         if (c.win && l < c.nwk) {
             t = c.Jw * S + l - j0;
             if (t >= 0 && t < GSTAGE) buf[t] = bit(sm.winacc, l) ? sm.wtri[l] : sm.wold[l];
+        }
+        for (int d = 0; d < c.nd; ++d) {
+            t = (c.g - 2 - d) * S + l - j0;
+            if (t >= 0 && t < GSTAGE) buf[t] = bit(sm.dacc[d], l) ? sm.dtri[d][l] : sm.dold[d][l];
         }
     }
     __syncthreads();
@@ -892,7 +1013,9 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
         for (int q = 0; q < w; ++q) before += __float_as_int(sm.redf[q]);
         const bool sv = active(k) && !(sm.st[k] & ST_DA_DONE);
         const unsigned bal = __ballot_sync(FULL, sv);
-        if (sv) sm.surv[before + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)k;
+        const int n = before + __popc(bal & ((1u << lane) - 1u));
+        if (sv) sm.surv[n] = (unsigned char)k;
+        sm.slot[k] = sv ? (unsigned char)n : (unsigned char)255;
         if (k == S - 1) sm.ns = before + __popc(bal);
     }
     __syncthreads();
@@ -929,6 +1052,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         c.win = (g == 0) ? (s > ch.sweep_base) : true;
         c.nwk = min(S, N - c.Jw * S);
     }
+    // deep windows: the groups g-2, g-3, ... before the window that belong to this sweep (always full groups)
+    c.nd = c.win ? max(0, min(DW, g - 1)) : 0;
     const float lo2 = ch.sig2_lo, hi2 = ch.sig2_hi;
     const double sig2 = ch.sig2;
     const float s2f = (float)sig2;
@@ -940,7 +1065,9 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     int n_scan = 0;
     long long cyc_t[3] = {0, 0, 0};
     const unsigned long long gt_start = globaltimer();
-    unsigned long long gt_ready = 0, gt_window = 0, gt_resolved = 0, gt_pub = 0;
+    unsigned long long gt_ready = 0, gt_window = 0, gt_resolved = 0, gt_pub = 0, gt_tile = 0, gt_tiles = 0, gt_w2 = 0;
+    unsigned long long gt_ph[4] = {0, 0, 0, 0};
+    const unsigned tbase = sm.tmem + ((unsigned)(32 * (warp & 3)) << 16);  // this warp's TMEM lane quarter
     int n_rounds = 0;
 
     // 1. own positions (version s-1) and, if active, the window's old positions (version sw-1)
@@ -948,6 +1075,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         unsigned bits;
         bool ok = wait_words(ch, g, (nk + 31) / 32, tag_prev, tag_prev, ctl, bits);
         if (ok && c.win) ok = wait_words(ch, c.Jw, (c.nwk + 31) / 32, (unsigned)sw, (unsigned)(sw + 1), ctl, bits);
+        for (int d = 0; ok && d < c.nd; ++d)  // deep windows: version s-1 (their version s may be out already)
+            ok = wait_words(ch, g - 2 - d, WORDS, tag_prev, tag_cur, ctl, bits);
         if (lane == 0) sm.ok = ok;
     }
     __syncthreads();
@@ -988,6 +1117,15 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             sm.wtri[k] = make_float4(trial_coord(x.x, w.x, ch.D), trial_coord(x.y, w.y, ch.D),
                                      trial_coord(x.z, w.z, ch.D), x.w);
         }
+        for (int d = 0; d < c.nd; ++d) {
+            const int jg = (g - 2 - d) * S + k;
+            const float4 x = __ldcg(&c.Pprev[jg]);
+            const uint4 w = move_draws(ch, s * (unsigned long long)N + (unsigned long long)jg, 0u);
+            sm.dold[d][k] = x;
+            sm.dtri[d][k] = make_float4(trial_coord(x.x, w.x, ch.D), trial_coord(x.y, w.y, ch.D),
+                                        trial_coord(x.z, w.z, ch.D), x.w);
+        }
+        sm.wexd[k] = 0.f;
         sm.st[k] = (unsigned char)stv;
         sm.outcome[k] = -1;
         sm.tier[k] = 0;
@@ -998,6 +1136,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             sm.ovn[k][w] = 0u;
             sm.wovo[k][w] = 0u;
             sm.wovn[k][w] = 0u;
+#pragma unroll
+            for (int d = 0; d < DW; ++d) {
+                sm.dovo[d][k][w] = 0u;
+                sm.dovn[d][k][w] = 0u;
+            }
         }
     }
     if (tid < WORDS) {
@@ -1005,6 +1148,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         sm.decw[tid] = 0u;
         sm.seen[tid] = 0u;
         sm.winacc[tid] = 0u;
+#pragma unroll
+        for (int d = 0; d < DW; ++d) sm.dacc[d][tid] = 0u;
     }
     __syncthreads();
 
@@ -1015,7 +1160,10 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     if (ch.da) {
         if (!da_stage1(sm, c, ctl, mode, n_dfp64, da_part)) return false;
     } else {
-        if (tid < S) sm.surv[tid] = (unsigned char)tid;
+        if (tid < S) {
+            sm.surv[tid] = (unsigned char)tid;
+            sm.slot[tid] = tid < nk ? (unsigned char)tid : (unsigned char)255;
+        }
         if (tid == 0) sm.ns = nk;
         __syncthreads();
     }
@@ -1078,6 +1226,72 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         promote();
     }
 
+    // 2b2. deep windows, both positions.  Warp (q, h): move slots 32 q + lane, ions [64 h, 64 h + 64) of each
+    // deep window.  The corrections go to TMEM (lane = slot, column = S d + j) and are summed over the accepted
+    // ions after the tiles, when the deep windows' bits are out (group-times before the window's); old-position
+    // terms (float-float, 16 terms per FP32 partial) and bound sums per (half, slot) in shared memory, merged
+    // in 2d.
+    if (c.nd > 0) {
+        const int q = warp & 3, h = warp >> 2, n = 32 * q + lane;
+        const bool act = n < ns;
+        const int k = act ? (int)sm.surv[n] : 0;
+        float sh = 0.f, sl = 0.f, A = 0.f, Tt = 0.f, TC = 0.f;
+        if (32 * q < ns) {  // warp-uniform: TMEM stores are whole-warp instructions
+            const float4 ak = sm.trial[k], bk = sm.own[k];
+            for (int d = 0; d < c.nd; ++d) {
+                unsigned ow0 = 0u, ow1 = 0u, nw0 = 0u, nw1 = 0u;
+#pragma unroll 1
+                for (int q16 = 0; q16 < HALF / 16; ++q16) {
+                    float v[16];
+                    float p16 = 0.f;
+                    unsigned o16 = 0u, n16 = 0u;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int j = h * HALF + 16 * q16 + i;
+                        const float4 yo = sm.dold[d][j], yn = sm.dtri[d][j];
+                        float Ao, An, d2o, d2n;
+                        const float to = pair_term(ak, bk, yo, Ao, d2o);
+                        const float tn = pair_term(ak, bk, yn, An, d2n);
+                        const float cv = tn - to;
+                        p16 += to;
+                        Tt += fabsf(to);
+                        A += Ao + An;
+                        TC += fabsf(cv);
+                        v[i] = cv;
+                        if (overlaps(d2o, ak, yo, lo2, hi2, sig2)) o16 |= 1u << i;
+                        if (overlaps(d2n, ak, yn, lo2, hi2, sig2)) n16 |= 1u << i;
+                    }
+                    float s2, e;
+                    two_sum(sh, p16, s2, e);
+                    sh = s2;
+                    sl += e;
+                    const int sh16 = 16 * (q16 & 1);
+                    if (q16 < 2) {
+                        ow0 |= o16 << sh16;
+                        nw0 |= n16 << sh16;
+                    } else {
+                        ow1 |= o16 << sh16;
+                        nw1 |= n16 << sh16;
+                    }
+                    __syncwarp();
+                    tmem_st16(tbase + (unsigned)(S * d + h * HALF + 16 * q16), v);
+                }
+                if (act) {
+                    sm.dovo[d][k][2 * h] = ow0;
+                    sm.dovo[d][k][2 * h + 1] = ow1;
+                    sm.dovn[d][k][2 * h] = nw0;
+                    sm.dovn[d][k][2 * h + 1] = nw1;
+                }
+            }
+            tmem_wait_st();
+        }
+        sm.dsh[h][n] = act ? sh : 0.f;
+        sm.dsl[h][n] = act ? sl : 0.f;
+        sm.dsA[h][n] = act ? A : 0.f;
+        sm.dsT[h][n] = act ? Tt : 0.f;
+        sm.dsC[h][n] = act ? TC : 0.f;
+    }
+
     // 2b'. interval sums of the corrections (threads < S: this group, threads >= S: the window);
     // needs only the two passes above, so it runs before the tiles
     __syncthreads();
@@ -1101,6 +1315,56 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 }
             sm.lo_w[k] = lo;
             sm.hi_w[k] = hi;
+            // 3a. the move's own part of step 3, which needs no tile: far-field bound coefficients, the band of
+            // the overlap test, and the overlap status from this group's and the window's ions (the deep
+            // windows' becomes exact after the tiles)
+            unsigned stv = sm.st[k];
+            const float4 ak = sm.trial[k], bk = sm.own[k];
+            const float dx = ak.x - bk.x, dy = ak.y - bk.y, dz = ak.z - bk.z;
+            const float dn = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) * (1.0f + 0x1p-18f);
+            float kT = 0.f, kP = 0.f, kO = 0.f;
+            const bool bounded = far_coeffs(dn, sp, kT, kP, kO);
+            sm.kTs[k] = bounded ? kT : -1.f;
+            sm.kPs[k] = kP;
+            // the settled ions' squared distances come from pair_far: widen the overlap band to its error
+            const float rel = kO * U32;
+            sm.lo2ks[k] = fminf(lo2, s2f * (1.0f - rel) * (1.0f - 0x1p-22f));
+            sm.hi2ks[k] = fmaxf(hi2, s2f * (1.0f + rel) * (1.0f + 0x1p-22f));
+            if (!(stv & (ST_INACTIVE | ST_WALL))) {
+                if (!bounded) stv |= ST_OVL_AMBIG;
+                unsigned any = 0, both = 0;
+#pragma unroll
+                for (int w = 0; w < WORDS; ++w) {
+                    any |= sm.ovo[k][w] | sm.ovn[k][w] | sm.wovo[k][w] | sm.wovn[k][w];
+                    both |= (sm.ovo[k][w] & sm.ovn[k][w]) | (sm.wovo[k][w] & sm.wovn[k][w]);
+#pragma unroll
+                    for (int d = 0; d < DW; ++d) both |= sm.dovo[d][k][w] & sm.dovn[d][k][w];
+                }
+                if (both) stv |= ST_OVL_CERTAIN;
+                else if (any) stv |= ST_OVL_POSSIBLE;
+                sm.st[k] = (unsigned char)stv;
+            }
+            sm.bnd[k] = finf();  // moves without pair sums keep it
+            sm.run[k] = 0.f;
+            sm.wex[k] = 0.f;
+        }
+    }
+    // the deep-window pass's partials join slice 0's accumulators of each slot (its barrier is 2b''s)
+    if (c.nd > 0 && r == 0) {
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            if (km[m] < 0) continue;
+            const int n = p + 32 * m;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                float s2, e;
+                two_sum(hA[m], sm.dsh[hh][n], s2, e);
+                hA[m] = s2;
+                lA[m] = lA[m] + sm.dsl[hh][n] + e;
+                AA[m] += sm.dsA[hh][n];
+                TA[m] += sm.dsT[hh][n];
+                CA[m] += sm.dsC[hh][n];
+            }
         }
     }
     // 2c. every other group, oldest published version first (Algorithm 2 per guest group):
@@ -1110,7 +1374,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         if (c.win && J == c.Jw) return -1;  // never reached: the window is the last in this order
         return J;
     };
-    const int ntl = (B - 1) - (c.win ? 1 : 0);
+    const int ntl = (B - 1) - (c.win ? 1 : 0) - c.nd;  // the windows are the last groups in this order
     auto tile_tag = [&](int J) -> unsigned { return J > g ? tag_prev : tag_cur; };
     auto tile_src = [&](int J) -> const float4 * { return (J > g ? c.Pprev : c.Pcur) + (size_t)J * S; };
     auto tile_words = [&](int J) -> int { return (min(S, N - J * S) + 31) / 32; };
@@ -1194,13 +1458,28 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             }
             __syncthreads();
             if (!sm.ok) return false;
+            gt_tile = globaltimer();
             if (tid < S) sm.tile[cur ^ 1][tid] = __ldcg(&tile_src(Jn)[tid]);
             __syncthreads();
         }
     }
     cyc_tiles = clock64() - cyc_t0;
+    gt_tiles = globaltimer();
 
-    // 2d. combine the 8 column slices
+    // 2d. combine the 8 column slices (warp-local) into the float-float sum, one bound sum (the bound's linear
+    // combination of the four magnitude sums, all coefficients positive) and the minimum squared distance, while
+    // warp 0 reads the deep windows' outcome words (one contiguous run of groups); then the deep windows' exact
+    // correction sums and overlap bits from TMEM.  The bound sums carry FP32 rounding of at most n u relative
+    // for n terms per thread: infl covers it.
+    const float infl = 1.0f + (float)(N / SL + 64 * DW + 64) * 0x1p-23f;
+    __syncthreads();  // 3a's per-move coefficients (no tile loop may have run since)
+    float QA[MPT];
+#pragma unroll
+    for (int m = 0; m < MPT; ++m) {
+        const float kT = sm.kTs[km[m] < 0 ? 0 : km[m]], kP = sm.kPs[km[m] < 0 ? 0 : km[m]];
+        QA[m] = (kT < 0.f) ? finf()
+                           : C_TERM * AA[m] + (C_SUM + kT + 0x1p-12f) * TA[m] + kP * PA[m] + C_CORR * CA[m];
+    }
 #pragma unroll
     for (int o = 1; o < SL; o <<= 1) {
 #pragma unroll
@@ -1210,74 +1489,92 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             two_sum(hA[m], h2, s2, e);
             hA[m] = s2;
             lA[m] = lA[m] + l2 + e;
-            AA[m] += __shfl_xor_sync(FULL, AA[m], o);
-            TA[m] += __shfl_xor_sync(FULL, TA[m], o);
-            CA[m] += __shfl_xor_sync(FULL, CA[m], o);
-            PA[m] += __shfl_xor_sync(FULL, PA[m], o);
+            QA[m] += __shfl_xor_sync(FULL, QA[m], o);
             mA[m] = fminf(mA[m], __shfl_xor_sync(FULL, mA[m], o));
         }
     }
-    if (r == 0) {
+    if (r < MPT) {  // lane r of each slice group stores move slot m = r (every lane holds the combined values)
+        float hv = hA[0], lv = lA[0], qv = QA[0], mv = mA[0];
+        int kv = km[0];
 #pragma unroll
-        for (int m = 0; m < MPT; ++m) {
-            const int k = km[m];
-            if (k < 0) continue;
-            sm.bhi[k] = hA[m];
-            sm.blo[k] = lA[m];
-            sm.Ab[k] = AA[m] * (1.0f + 0x1p-10f);
-            sm.Tb[k] = TA[m] * (1.0f + 0x1p-10f);
-            sm.TCb[k] = CA[m] * (1.0f + 0x1p-10f);
-            sm.Pb[k] = PA[m] * (1.0f + 0x1p-10f);
-            sm.mind2[k] = mA[m];
+        for (int m = 1; m < MPT; ++m)
+            if (r == m) {
+                hv = hA[m];
+                lv = lA[m];
+                qv = QA[m];
+                mv = mA[m];
+                kv = km[m];
+            }
+        if (kv >= 0) {
+            sm.bhi[kv] = hv;
+            sm.blo[kv] = lv;
+            sm.Qs[kv] = qv;
+            sm.mind2[kv] = mv;
         }
     }
+    if (c.nd > 0) {
+        if (warp == 0) {
+            unsigned bits;
+            const int nw = c.nd * WORDS;
+            const bool ok = wait_words(ch, g - 1 - c.nd, nw, tag_cur, tag_cur, ctl, bits, false, true);
+            if (lane < nw) sm.dacc[c.nd - 1 - lane / WORDS][lane % WORDS] = bits;
+            if (lane == 0) sm.ok = ok;
+        }
+        __syncthreads();
+        if (!sm.ok) return false;
+        gt_w2 = globaltimer();
+        const int q = warp & 3, h = warp >> 2, n = 32 * q + lane;
+        float sx = 0.f;
+        unsigned wo = 0u;
+        if (32 * q < ns) {  // warp-uniform
+            const int k = sm.surv[n < ns ? n : 0];
+            for (int d = 0; d < c.nd; ++d) {
+#pragma unroll
+                for (int q32 = 0; q32 < HALF / 32; ++q32) {
+                    float v[32];
+                    __syncwarp();
+                    tmem_ld32(tbase + (unsigned)(S * d + h * HALF + 32 * q32), v);
+                    const int w = 2 * h + q32;
+                    const unsigned wb = sm.dacc[d][w];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) sx += ((wb >> i) & 1u) ? v[i] : 0.f;
+                    wo |= (sm.dovn[d][k][w] & wb) | (sm.dovo[d][k][w] & ~wb);
+                }
+            }
+        }
+        sm.dpart[h][n] = sx;
+        sm.dwo[h][n] = wo;
+    }
     __syncthreads();
+    gt_ph[0] = globaltimer();
 
-    // 3. per-move preparation: overlap status and static band.
+    // 3b + 4. per move: the deep windows' exact sums and overlap, the settled ions' overlap from the minimum
+    // squared distance, the static FP32 band; then round 0: moves decided whatever the window and this group's
+    // earlier moves do
     if (tid < S) {
         const int k = tid;
         unsigned stv = sm.st[k];
-        const float4 ak = sm.trial[k], bk = sm.own[k];
-        const float dx = ak.x - bk.x, dy = ak.y - bk.y, dz = ak.z - bk.z;
-        const float dn = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) * (1.0f + 0x1p-18f);
-        float kT = 0.f, kP = 0.f, kO = 0.f;
-        const bool bounded = far_coeffs(dn, sp, kT, kP, kO);
-        if (!(stv & (ST_INACTIVE | ST_WALL))) {
-            // the settled ions' squared distances come from pair_far: widen the overlap band to its error
-            const float rel = kO * U32;
-            const float lo2k = fminf(lo2, s2f * (1.0f - rel) * (1.0f - 0x1p-22f));
-            const float hi2k = fmaxf(hi2, s2f * (1.0f + rel) * (1.0f + 0x1p-22f));
-            const float m2 = sm.mind2[k];
-            if (!bounded) stv |= ST_OVL_AMBIG;
-            else if (m2 < lo2k) stv |= ST_OVL_CERTAIN;
-            else if (!(m2 > hi2k)) stv |= ST_OVL_AMBIG;
-            unsigned any = 0, both = 0;
-#pragma unroll
-            for (int w = 0; w < WORDS; ++w) {
-                any |= sm.ovo[k][w] | sm.ovn[k][w] | sm.wovo[k][w] | sm.wovn[k][w];
-                both |= (sm.ovo[k][w] & sm.ovn[k][w]) | (sm.wovo[k][w] & sm.wovn[k][w]);
+        const int n = sm.slot[k];
+        if (n != 255) {
+            const float kT = sm.kTs[k];
+            if (c.nd > 0) {
+                sm.wexd[k] = sm.dpart[0][n] + sm.dpart[1][n];
+                if (sm.dwo[0][n] | sm.dwo[1][n]) stv |= ST_OVL_CERTAIN;
             }
-            if (both) stv |= ST_OVL_CERTAIN;
-            else if (any) stv |= ST_OVL_POSSIBLE;
+            if (!(stv & (ST_INACTIVE | ST_WALL)) && kT >= 0.f) {
+                const float m2 = sm.mind2[k];
+                if (m2 < sm.lo2ks[k]) stv |= ST_OVL_CERTAIN;
+                else if (!(m2 > sm.hi2ks[k])) stv |= ST_OVL_AMBIG;
+            }
             sm.st[k] = (unsigned char)stv;
+            const float lqa = fabsf(lBf * sm.own[k].w);
+            float bnd = (mode == 1 || mode == 3 || kT < 0.f)
+                            ? finf()
+                            : (mode == 2 ? 0.f : lqa * (U32 * (sm.Qs[k] * infl) + 0x1p-40f * ch.a_max));
+            if (ch.da && mode == 0) bnd += sm.dEtB[k];  // stage 2 compares dE with L(u2) + dEt
+            sm.bnd[k] = bnd;
         }
-        const float lqa = fabsf(lBf * sm.own[k].w);
-        sm.bnd[k] = (mode == 1 || mode == 3 || !bounded)
-                        ? finf()
-                        : (mode == 2 ? 0.f
-                                     : lqa * (U32 * (C_TERM * sm.Ab[k] + (C_SUM + kT) * sm.Tb[k] + kP * sm.Pb[k] +
-                                                     C_CORR * sm.TCb[k]) +
-                                              0x1p-40f * ch.a_max + 0x1p-36f * sm.Tb[k]));
-        if (ch.da && mode == 0) sm.bnd[k] += sm.dEtB[k];  // stage 2 compares dE with L(u2) + dEt
-        sm.run[k] = 0.f;
-        sm.wex[k] = 0.f;
-    }
-    __syncthreads();
-
-    // 4. round 0: moves decided whatever the window and this group's earlier moves do
-    if (tid < S) {
-        const int k = tid;
-        const unsigned stv = sm.st[k];
+        gt_ph[1] = globaltimer();
         int out = -1;
         if (stv & ST_INACTIVE) out = OUT_INACTIVE;
         else if (stv & ST_WALL) out = OUT_WALL;
@@ -1288,7 +1585,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             else {
                 const float lq = lBf * sm.own[k].w;
                 const float base = sm.bhi[k] + sm.blo[k];
-                out = decide_interval(sm, k, lq, base + (sm.lo_w[k] + sm.lo_i[k]), base + (sm.hi_w[k] + sm.hi_i[k]));
+                out = decide_interval(sm, k, lq, base + ((sm.lo_w[k] + sm.wexd[k]) + sm.lo_i[k]),
+                                      base + ((sm.hi_w[k] + sm.wexd[k]) + sm.hi_i[k]));
             }
         }
         if (out >= 0 && out <= OUT_DA1) sm.outcome[k] = (signed char)out;
@@ -1303,6 +1601,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     // 5. first in-group partial pass (needs only round 0's decisions), then the window's outcome (the
     // critical wait) and its exact correction sums.
     __syncthreads();
+    gt_ph[2] = globaltimer();
     if (tid < WORDS) {
         sm.acc0[tid] = sm.accw[tid];
         sm.dec0[tid] = sm.decw[tid];
@@ -1339,7 +1638,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         __syncthreads();
         if (tid < S) {
             const int k = tid;
-            sm.wex[k] = sm.wpart[0][k] + sm.wpart[1][k];
+            sm.wex[k] = (sm.wpart[0][k] + sm.wpart[1][k]) + sm.wexd[k];
             unsigned wo = 0;  // the window's overlap is now exact
 #pragma unroll
             for (int w = 0; w < WORDS; ++w) wo |= (sm.wovn[k][w] & sm.winacc[w]) | (sm.wovo[k][w] & ~sm.winacc[w]);
@@ -1520,6 +1819,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             tr.t_published = gt_pub;
             tr.n_guard = (unsigned long long)(cyc_guard > 0);
             tr.t_positions = gt_posp;
+            tr.t_tile = gt_tile;
+            tr.t_tiles = gt_tiles;
+            tr.t_w2 = gt_w2;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tr.t_ph[q] = gt_ph[q];
             ch.trace[idx] = tr;
         }
     }
@@ -1655,6 +1959,10 @@ sweep_kernel(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sch
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned t = atomicAdd(&ctl->ticket, 1u);
@@ -1664,9 +1972,14 @@ sweep_kernel(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sch
         __syncthreads();
         const int t = sm.ticket;
         __syncthreads();
-        if (t < 0) return;
-        if (!process_group(sm, chains, sched[t], t, ctl)) return;
+        if (t < 0) break;
+        if (!process_group(sm, chains, sched[t], t, ctl)) break;  // uniform: every failure exit follows a barrier
     }
+    // every exit path releases the TMEM columns before the CTA ends
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(sm.tmem);
 }
 
 // After a launch of n sweeps: advance every chain's sweep counter.
