@@ -270,6 +270,78 @@ __device__ __forceinline__ void pair_far(const float3 b, const float3 d, const f
     mn = fminf(mn, Dn);
 }
 
+// Packed FP32 pairs (sm_100 family): each lane of add/sub/mul/fma .f32x2 is the IEEE round-to-nearest result of
+// the scalar operation, so packed code gives bit-identical values at half the issue slots.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void upk2(f32x2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Two moves (packed old positions b, displacements d, negated displacements nd) against one settled ion y: the
+// arithmetic of pair_far per lane, without the |t| sum (|t| <= dn rn ro exactly, so the bound takes dn P).
+struct Mv2 {
+    f32x2 bx, by, bz, dx, dy, dz, nx, ny, nz;
+};
+
+__device__ __forceinline__ void pair_far2(const Mv2 &m, const float4 y, f32x2 &s, f32x2 &P, float &mn0, float &mn1)
+{
+    const f32x2 two = pk2(2.0f, 2.0f);
+    const f32x2 ex = sub2(pk2(y.x, y.x), m.bx), ey = sub2(pk2(y.y, y.y), m.by), ez = sub2(pk2(y.z, y.z), m.bz);
+    const f32x2 Do = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+    const f32x2 wx = fma2(two, ex, m.nx), wy = fma2(two, ey, m.ny), wz = fma2(two, ez, m.nz);
+    const f32x2 Dd = fma2(m.dz, wz, fma2(m.dy, wy, mul2(m.dx, wx)));
+    const f32x2 Dn = sub2(Do, Dd);
+    float Do0, Do1, Dn0, Dn1;
+    upk2(Do, Do0, Do1);
+    upk2(Dn, Dn0, Dn1);
+    const f32x2 ro = pk2(rsqrt_ftz(Do0), rsqrt_ftz(Do1)), rn = pk2(rsqrt_ftz(Dn0), rsqrt_ftz(Dn1));
+    const f32x2 pr = mul2(rn, ro);
+    float h0, h1;
+    upk2(add2(rn, ro), h0, h1);
+    const f32x2 t = mul2(mul2(Dd, pr), mul2(pr, pk2(rcp_ftz(h0), rcp_ftz(h1))));
+    s = fma2(pk2(y.w, y.w), t, s);
+    P = fma2(pk2(fabsf(y.w), fabsf(y.w)), pr, P);
+    mn0 = fminf(mn0, Dn0);
+    mn1 = fminf(mn1, Dn1);
+}
+
 // Error-free transformations in FP32 (Knuth's TwoSum, FMA-based TwoProduct).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {

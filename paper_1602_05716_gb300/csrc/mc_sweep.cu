@@ -1325,7 +1325,9 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             float kT = 0.f, kP = 0.f, kO = 0.f;
             const bool bounded = far_coeffs(dn, sp, kT, kP, kO);
             sm.kTs[k] = bounded ? kT : -1.f;
-            sm.kPs[k] = kP;
+            // P's coefficient also carries the tiles' |t| terms: |t| <= dn rn ro (triangle inequality), with
+            // slack for the rounding of the computed rn ro
+            sm.kPs[k] = kP + (C_SUM + kT + 0x1p-12f) * dn * (1.0f + 0x1p-16f);
             // the settled ions' squared distances come from pair_far: widen the overlap band to its error
             const float rel = kO * U32;
             sm.lo2ks[k] = fminf(lo2, s2f * (1.0f - rel) * (1.0f - 0x1p-22f));
@@ -1417,6 +1419,40 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         if (tid < S) sm.tile[0][tid] = __ldcg(&tile_src(tile_J(0))[tid]);
         __syncthreads();
     }
+    // the tiles run two moves per packed FP32x2 instruction (slots (0,1) and (2,3)); their |t| sum is bounded
+    // by dn P instead of accumulated
+    Mv2 mv[MPT / 2];
+    f32x2 s2[MPT / 2], P2[MPT / 2];
+#pragma unroll
+    for (int pp = 0; pp < MPT / 2; ++pp) {
+        const int m0 = 2 * pp, m1 = 2 * pp + 1;
+        mv[pp].bx = pk2(b3[m0].x, b3[m1].x);
+        mv[pp].by = pk2(b3[m0].y, b3[m1].y);
+        mv[pp].bz = pk2(b3[m0].z, b3[m1].z);
+        mv[pp].dx = pk2(d3[m0].x, d3[m1].x);
+        mv[pp].dy = pk2(d3[m0].y, d3[m1].y);
+        mv[pp].dz = pk2(d3[m0].z, d3[m1].z);
+        mv[pp].nx = pk2(-d3[m0].x, -d3[m1].x);
+        mv[pp].ny = pk2(-d3[m0].y, -d3[m1].y);
+        mv[pp].nz = pk2(-d3[m0].z, -d3[m1].z);
+        s2[pp] = pk2(sA[m0], sA[m1]);
+        P2[pp] = pk2(PA[m0], PA[m1]);
+    }
+    auto promote2 = [&]() {
+#pragma unroll
+        for (int pp = 0; pp < MPT / 2; ++pp) {
+            float v[2];
+            upk2(s2[pp], v[0], v[1]);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                float t2, e;
+                two_sum(hA[2 * pp + u], v[u], t2, e);
+                hA[2 * pp + u] = t2;
+                lA[2 * pp + u] += e;
+            }
+            s2[pp] = pk2(0.f, 0.f);
+        }
+    };
     for (int i = 0; i < (ns > 0 ? ntl : 0); ++i) {
         const int cur = i & 1;
         const int hz = sm.hzs[i & 1];
@@ -1426,21 +1462,20 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         if (pf && tid < S) pre = __ldcg(&tile_src(Jn)[tid]);
         // occupied 32-move layers only (all of them for a plain chain); an empty slot in the last layer repeats
         // a real move and is never written back
-#define MC_TILE_PASS(NMV)                                                              \
+#define MC_TILE_PASS(NPK)                                                              \
     _Pragma("unroll 4") for (int jj = 0; jj < S / SL; ++jj)                            \
     {                                                                                  \
         const float4 y = sm.tile[cur][jj * SL + r];                                    \
-        _Pragma("unroll") for (int m = 0; m < (NMV); ++m)                              \
-            pair_far(b3[m], d3[m], y, sA[m], TA[m], PA[m], mA[m]);                     \
+        _Pragma("unroll") for (int pp = 0; pp < (NPK); ++pp)                           \
+            pair_far2(mv[pp], y, s2[pp], P2[pp], mA[2 * pp], mA[2 * pp + 1]);          \
     }
-        switch (nm) {
-        case 1: MC_TILE_PASS(1) break;
-        case 2: MC_TILE_PASS(2) break;
-        case 3: MC_TILE_PASS(3) break;
-        default: MC_TILE_PASS(MPT) break;
+        if (nm <= 2) {
+            MC_TILE_PASS(1)
+        } else {
+            MC_TILE_PASS(MPT / 2)
         }
 #undef MC_TILE_PASS
-        promote();
+        promote2();
         if (pf && tid < S) sm.tile[cur ^ 1][tid] = pre;
         if (warp == 0) {
             const int nh = (hz < i + 8 && hz < ntl - 1) ? advance_horizon(hz) : hz;
@@ -1465,9 +1500,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     }
     cyc_tiles = clock64() - cyc_t0;
     gt_tiles = globaltimer();
+#pragma unroll
+    for (int pp = 0; pp < MPT / 2; ++pp) upk2(P2[pp], PA[2 * pp], PA[2 * pp + 1]);
 
     // 2d. combine the 8 column slices (warp-local) into the float-float sum, one bound sum (the bound's linear
-    // combination of the four magnitude sums, all coefficients positive) and the minimum squared distance, while
+    // combination of the magnitude sums, all coefficients positive) and the minimum squared distance, while
     // warp 0 reads the deep windows' outcome words (one contiguous run of groups); then the deep windows' exact
     // correction sums and overlap bits from TMEM.  The bound sums carry FP32 rounding of at most n u relative
     // for n terms per thread: infl covers it.
