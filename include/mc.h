@@ -192,6 +192,8 @@ typedef struct {
     uint64_t t_tiles;     /* finished the pair sums over the other groups */
     uint64_t t_w2;        /* observed the outcome of the group two before (0: none) */
     uint64_t t_ph[4];     /* pair sums combined, bands ready, round 0 done, oldest deep window's outcome observed */
+    uint32_t c_res[8];    /* SM cycles from the window's outcome to: window sums, exact window terms, first round,
+                             last round, resolved, outcome published, positions published, rounds run */
 } mc_trace_rec;
 int mc_trace_enable(mc_handle h, int chain, int64_t cap);
 int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);

@@ -20,7 +20,7 @@ TRACE_DTYPE = np.dtype([("item", np.uint64), ("t_start", np.uint64), ("t_ready",
                         ("t_window", np.uint64), ("t_resolved", np.uint64), ("t_published", np.uint64),
                         ("n_guard", np.uint64), ("t_positions", np.uint64),
                         ("t_tile", np.uint64), ("t_tiles", np.uint64), ("t_w2", np.uint64),
-                        ("t_ph", np.uint64, (4,))])
+                        ("t_ph", np.uint64, (4,)), ("c_res", np.uint32, (8,))])
 
 _STATS_FIELDS = ["sweeps", "accepts", "rej_metropolis", "rej_overlap", "rej_wall", "guard_fp64",
                  "decided_interval", "tier2", "tier3", "tier4", "rounds", "cyc_wait_window", "cyc_tiles",

@@ -50,6 +50,7 @@ struct TraceRec {
     unsigned long long t_positions;
     unsigned long long t_tile, t_tiles, t_w2;  // last tile observed, tiles done, second window observed
     unsigned long long t_ph[4];                // slices combined, band ready, round 0 done, oldest deep window observed
+    unsigned int c_res[8];                     // SM cycles from the window's outcome to the resolve checkpoints
 };
 
 // Per-chain device descriptor (read-only during a launch).

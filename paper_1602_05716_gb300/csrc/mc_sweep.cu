@@ -218,7 +218,7 @@ __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsig
 {
     const unsigned long long *words = outcome_words ? ch.bits : ch.flags;
     const int lane = threadIdx.x & 31;
-    const unsigned long long t0 = globaltimer();
+    unsigned long long t0 = 0;  // the clock starts at the first check, so a wait that succeeds at once reads none
     unsigned spins = 0;
     bool done = lane >= nw;
     bits = 0u;
@@ -239,13 +239,17 @@ __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsig
         ++spins;
         if (spins > 16 && sleep) __nanosleep(32);
         if ((spins & 31) == 0 && *(volatile int *)&ctl->abort) return false;
-        if ((spins & 63) == 0 && (long long)(globaltimer() - t0) > ctl->timeout_ns) {
-            if (lane == 0) {
-                if (atomicCAS(&ctl->err, 0, KERR_TIMEOUT) == 0) ctl->err_info = ((unsigned long long)J << 32) | lo;
-                atomicExch(&ctl->abort, 1);
+        if ((spins & 63) == 0) {
+            const unsigned long long now = __shfl_sync(FULL, globaltimer(), 0);
+            if (t0 == 0) t0 = now;
+            else if ((long long)(now - t0) > ctl->timeout_ns) {
+                if (lane == 0) {
+                    if (atomicCAS(&ctl->err, 0, KERR_TIMEOUT) == 0) ctl->err_info = ((unsigned long long)J << 32) | lo;
+                    atomicExch(&ctl->abort, 1);
+                }
+                __syncwarp();
+                return false;
             }
-            __syncwarp();
-            return false;
         }
     }
 }
@@ -839,15 +843,19 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
 // Bounded wait until the ledger has folded every group up to `need` (stream index s * B + g).
 __device__ bool wait_ledger(const ChainDev &ch, unsigned long long need, Ctl *ctl)
 {
-    const unsigned long long t0 = globaltimer();
+    unsigned long long t0 = 0;  // started at the first check
     unsigned spins = 0;
     while (ld_acquire(ch.ledger_seq) < need) {
         if (*(volatile int *)&ctl->abort) return false;
         if (++spins > 16) __nanosleep(64);
-        if ((spins & 63) == 0 && (long long)(globaltimer() - t0) > ctl->timeout_ns) {
-            atomicCAS(&ctl->err, 0, KERR_TIMEOUT);
-            atomicExch(&ctl->abort, 1);
-            return false;
+        if ((spins & 63) == 0) {
+            const unsigned long long now = globaltimer();
+            if (t0 == 0) t0 = now;
+            else if ((long long)(now - t0) > ctl->timeout_ns) {
+                atomicCAS(&ctl->err, 0, KERR_TIMEOUT);
+                atomicExch(&ctl->abort, 1);
+                return false;
+            }
         }
     }
     return true;
@@ -1064,9 +1072,12 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     long long cyc_start = clock64(), cyc_tiles = 0, cyc_win = 0, cyc_guard = 0, cyc_res0 = 0, cyc_ovl = 0;
     int n_scan = 0;
     long long cyc_t[3] = {0, 0, 0};
-    const unsigned long long gt_start = globaltimer();
+    const bool trc = ch.trace != nullptr;  // timeline stamps only while a trace is recorded
+    const unsigned long long gt_start = trc ? globaltimer() : 0ull;
     unsigned long long gt_ready = 0, gt_window = 0, gt_resolved = 0, gt_pub = 0, gt_tile = 0, gt_tiles = 0, gt_w2 = 0;
     unsigned long long gt_ph[4] = {0, 0, 0, 0};
+    long long cw0 = 0;
+    unsigned cres[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const unsigned tbase = sm.tmem + ((unsigned)(32 * (warp & 3)) << 16);  // this warp's TMEM lane quarter
     int n_rounds = 0;
 
@@ -1493,13 +1504,13 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             }
             __syncthreads();
             if (!sm.ok) return false;
-            gt_tile = globaltimer();
+            if (trc) gt_tile = globaltimer();
             if (tid < S) sm.tile[cur ^ 1][tid] = __ldcg(&tile_src(Jn)[tid]);
             __syncthreads();
         }
     }
     cyc_tiles = clock64() - cyc_t0;
-    gt_tiles = globaltimer();
+    if (trc) gt_tiles = globaltimer();
 #pragma unroll
     for (int pp = 0; pp < MPT / 2; ++pp) upk2(P2[pp], PA[2 * pp], PA[2 * pp + 1]);
 
@@ -1559,9 +1570,9 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         }
         __syncthreads();
         if (!sm.ok) return false;
-        gt_w2 = globaltimer();
+        if (trc) gt_w2 = globaltimer();
         const int q = warp & 3, h = warp >> 2, n = 32 * q + lane;
-        float sx = 0.f;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};  // independent partial sums
         unsigned wo = 0u;
         if (32 * q < ns) {  // warp-uniform
             const int k = sm.surv[n < ns ? n : 0];
@@ -1574,16 +1585,16 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                     const int w = 2 * h + q32;
                     const unsigned wb = sm.dacc[d][w];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) sx += ((wb >> i) & 1u) ? v[i] : 0.f;
+                    for (int i = 0; i < 32; ++i) acc[i & 3] += ((wb >> i) & 1u) ? v[i] : 0.f;
                     wo |= (sm.dovn[d][k][w] & wb) | (sm.dovo[d][k][w] & ~wb);
                 }
             }
         }
-        sm.dpart[h][n] = sx;
+        sm.dpart[h][n] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         sm.dwo[h][n] = wo;
     }
     __syncthreads();
-    gt_ph[0] = globaltimer();
+    if (trc) gt_ph[0] = globaltimer();
 
     // 3b + 4. per move: the deep windows' exact sums and overlap, the settled ions' overlap from the minimum
     // squared distance, the static FP32 band; then round 0: moves decided whatever the window and this group's
@@ -1611,7 +1622,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (ch.da && mode == 0) bnd += sm.dEtB[k];  // stage 2 compares dE with L(u2) + dEt
             sm.bnd[k] = bnd;
         }
-        gt_ph[1] = globaltimer();
+        if (trc) gt_ph[1] = globaltimer();
         int out = -1;
         if (stv & ST_INACTIVE) out = OUT_INACTIVE;
         else if (stv & ST_WALL) out = OUT_WALL;
@@ -1638,14 +1649,14 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     // 5. first in-group partial pass (needs only round 0's decisions), then the window's outcome (the
     // critical wait) and its exact correction sums.
     __syncthreads();
-    gt_ph[2] = globaltimer();
+    if (trc) gt_ph[2] = globaltimer();
     if (tid < WORDS) {
         sm.acc0[tid] = sm.accw[tid];
         sm.dec0[tid] = sm.decw[tid];
     }
     __syncthreads();
     partial_pass(sm);
-    gt_ready = globaltimer();
+    if (trc) gt_ready = globaltimer();
     const long long cyc_w0 = clock64();
     if (c.win) {
         if (warp == 0) {
@@ -1658,21 +1669,29 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         __syncthreads();
         if (!sm.ok) return false;
         cyc_win = clock64() - cyc_w0;
-        gt_window = globaltimer();
+        if (trc) gt_window = globaltimer();
+        cw0 = clock64();
         {
             const int k = tid & (S - 1), h = tid >> 7;
             float sx = 0.f;
             const unsigned wa0 = sm.winacc[2 * h], wa1 = sm.winacc[2 * h + 1];
             const float *col = &sm.cwin[(h * HALF) * CS + k];
-#pragma unroll 16
-            for (int jj = 0; jj < HALF; ++jj) {
-                const unsigned wb = jj < 32 ? wa0 : wa1;
-                const float cv = col[jj * CS];
-                sx += ((wb >> (jj & 31)) & 1u) ? cv : 0.f;
+            // four independent partial sums over batches of 16 loads issued together
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int jb = 0; jb < HALF; jb += 16) {
+                const unsigned wb = (jb < 32 ? wa0 : wa1) >> (jb & 31);
+                float cv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) cv[u] = col[(jb + u) * CS];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) acc[u & 3] += ((wb >> u) & 1u) ? cv[u] : 0.f;
             }
+            sx = (acc[0] + acc[1]) + (acc[2] + acc[3]);
             sm.wpart[h][k] = sx;
         }
         __syncthreads();
+        cres[0] = (unsigned)(clock64() - cw0);
         if (tid < S) {
             const int k = tid;
             sm.wex[k] = (sm.wpart[0][k] + sm.wpart[1][k]) + sm.wexd[k];
@@ -1683,6 +1702,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         }
     }
     __syncthreads();
+    cres[1] = (unsigned)(clock64() - cw0);
 
     // 6. rounds over this group's earlier moves: exact sums over decided ones,
     // intervals over undecided ones.  The first undecided move has only decided
@@ -1727,6 +1747,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             }
         }
         __syncthreads();
+        if (n_rounds == 1) cres[2] = (unsigned)(clock64() - cw0);
+        cres[3] = (unsigned)(clock64() - cw0);
         int first = -1;
 #pragma unroll
         for (int w = 0; w < WORDS; ++w) {
@@ -1822,14 +1844,17 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         partial_pass(sm);
     }
     const long long cyc_resolve = clock64() - cyc_res0 - cyc_guard;
-    gt_resolved = globaltimer();
+    if (trc) gt_resolved = globaltimer();
+    cres[4] = (unsigned)(clock64() - cw0);
+    cres[7] = (unsigned)n_rounds;
 
     // 7. publish: the outcome words first (the next group holds both candidate positions and needs only
     // these bits), then the final positions (version s) and their release-stored words.
     const bool publish = (long long)ticket != ctl->skip_ticket;
     if (warp == 0 && publish && lane < (nk + 31) / 32)
         st_relaxed(&ch.bits[g * WORDS + lane], ((unsigned long long)tag_cur << 32) | sm.accw[lane]);
-    gt_pub = globaltimer();
+    if (trc) gt_pub = globaltimer();
+    cres[5] = (unsigned)(clock64() - cw0);
     if (tid < nk) {
         const bool acc = bit(sm.accw, tid);
         __stcg(&ch.pos[(s + 1) & 1][k0 + tid], acc ? sm.trial[tid] : sm.own[tid]);
@@ -1842,7 +1867,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     __syncthreads();
     if (warp == 0 && publish && lane < (nk + 31) / 32)  // release after the barrier: orders every thread's stores
         st_release(&ch.flags[g * WORDS + lane], ((unsigned long long)tag_cur << 32) | sm.accw[lane]);
-    const unsigned long long gt_posp = globaltimer();
+    const unsigned long long gt_posp = trc ? globaltimer() : 0ull;
+    cres[6] = (unsigned)(clock64() - cw0);
     if (tid == 0 && ch.trace) {
         const unsigned long long item = s * (unsigned long long)B + (unsigned long long)g;
         const unsigned long long idx = item - ch.rec_sweep0 * (unsigned long long)B;
@@ -1861,6 +1887,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             tr.t_w2 = gt_w2;
 #pragma unroll
             for (int q = 0; q < 4; ++q) tr.t_ph[q] = gt_ph[q];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tr.c_res[q] = cres[q];
             ch.trace[idx] = tr;
         }
     }
@@ -1896,7 +1924,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         double gsum = 0.0;
         for (int w = 0; w < T / 32; ++w) gsum += sm.redd[w];
         const unsigned long long me = s * (unsigned long long)B + (unsigned long long)g;
-        const unsigned long long t0 = globaltimer();
+        unsigned long long t0 = 0;  // started at the first check
         unsigned spins = 0;
         bool ok = true;
         while (ld_acquire(ch.ledger_seq) != me) {
@@ -1905,11 +1933,15 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 break;
             }
             if (++spins > 16) __nanosleep(32);
-            if ((spins & 63) == 0 && (long long)(globaltimer() - t0) > ctl->timeout_ns) {
-                atomicCAS(&ctl->err, 0, KERR_TIMEOUT);
-                atomicExch(&ctl->abort, 1);
-                ok = false;
-                break;
+            if ((spins & 63) == 0) {
+                const unsigned long long now = globaltimer();
+                if (t0 == 0) t0 = now;
+                else if ((long long)(now - t0) > ctl->timeout_ns) {
+                    atomicCAS(&ctl->err, 0, KERR_TIMEOUT);
+                    atomicExch(&ctl->abort, 1);
+                    ok = false;
+                    break;
+                }
             }
         }
         if (ok) {
