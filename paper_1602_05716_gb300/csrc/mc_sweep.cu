@@ -53,7 +53,7 @@ struct __align__(16) Smem {
     float4 wtri[S];   // window group: trial positions
     float4 dold[DW][S];  // deep windows (d = 0: the group before the window): old positions
     float4 dtri[DW][S];  // ... trial positions
-    float4 tile[2][S];
+    float4 tile[2][2 * S];  // tile ring: each buffer holds one or two consecutive groups
     float cin[S * CS];   // c[j][k], j < k, this group
     float cwin[S * CS];  // c[j][k], window ion j
     float bhi[S], blo[S];  // sum of terms with known positions (float-float)
@@ -98,7 +98,7 @@ struct __align__(16) Smem {
     double redd[32];
     float redf[32];
     int ticket, ok, guard_k, ovl_flag;
-    int hzs[2];
+    int hzs[2], tcnt[2];  // per buffer: publication horizon, groups staged
     int ns, namb, pad1[2];
 };
 
@@ -1410,6 +1410,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         if (hz > from) fence_acq_rel();
         return hz;
     };
+    // Tiles are staged in pairs where both groups lie inside the publication horizon, so most barriers cover
+    // 256 ions; otherwise one group.  Buffer b (iteration parity) holds tcnt[b] groups and horizon hzs[b].
     if (ntl > 0 && ns > 0) {
         if (warp == 0) {
             int hz0 = advance_horizon(-1);
@@ -1423,11 +1425,12 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (lane == 0) {
                 sm.ok = ok;
                 sm.hzs[0] = hz0;
+                sm.tcnt[0] = (hz0 >= 1 && ntl > 1) ? 2 : 1;
             }
         }
         __syncthreads();
         if (!sm.ok) return false;
-        if (tid < S) sm.tile[0][tid] = __ldcg(&tile_src(tile_J(0))[tid]);
+        if (tid < sm.tcnt[0] * S) sm.tile[0][tid] = __ldcg(&tile_src(tile_J(tid >> 7))[tid & (S - 1)]);
         __syncthreads();
     }
     // the tiles run two moves per packed FP32x2 instruction (slots (0,1) and (2,3)); their |t| sum is bounded
@@ -1464,17 +1467,20 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             s2[pp] = pk2(0.f, 0.f);
         }
     };
-    for (int i = 0; i < (ns > 0 ? ntl : 0); ++i) {
-        const int cur = i & 1;
-        const int hz = sm.hzs[i & 1];
-        const bool pf = (i + 1 < ntl) && (i + 1 <= hz);
-        const int Jn = (i + 1 < ntl) ? tile_J(i + 1) : -1;
+    int it = 0;
+    for (int i = 0; ns > 0 && i < ntl; ++it) {
+        const int cur = it & 1;
+        const int cnt = sm.tcnt[cur];
+        const int hz = sm.hzs[cur];
+        const int in = i + cnt;  // first group of the next buffer
+        const int pn = (in < ntl && in <= hz) ? ((in + 1 < ntl && in + 1 <= hz) ? 2 : 1) : 0;  // groups prefetched
         float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pf && tid < S) pre = __ldcg(&tile_src(Jn)[tid]);
+        if (tid < pn * S) pre = __ldcg(&tile_src(tile_J(in + (tid >> 7)))[tid & (S - 1)]);
         // occupied 32-move layers only (all of them for a plain chain); an empty slot in the last layer repeats
         // a real move and is never written back
+        const int nj = cnt * (S / SL);
 #define MC_TILE_PASS(NPK)                                                              \
-    _Pragma("unroll 4") for (int jj = 0; jj < S / SL; ++jj)                            \
+    _Pragma("unroll 8") for (int jj = 0; jj < nj; ++jj)                                \
     {                                                                                  \
         const float4 y = sm.tile[cur][jj * SL + r];                                    \
         _Pragma("unroll") for (int pp = 0; pp < (NPK); ++pp)                           \
@@ -1487,19 +1493,24 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         }
 #undef MC_TILE_PASS
         promote2();
-        if (pf && tid < S) sm.tile[cur ^ 1][tid] = pre;
+        if (tid < pn * S) sm.tile[cur ^ 1][tid] = pre;
         if (warp == 0) {
-            const int nh = (hz < i + 8 && hz < ntl - 1) ? advance_horizon(hz) : hz;
-            if (lane == 0) sm.hzs[(i + 1) & 1] = nh;
+            const int nh = (hz < in + 8 && hz < ntl - 1) ? advance_horizon(hz) : hz;
+            if (lane == 0) {
+                sm.hzs[cur ^ 1] = nh;
+                sm.tcnt[cur ^ 1] = pn;
+            }
         }
         __syncthreads();
-        if (i + 1 < ntl && !pf) {  // the next tile was not published in time: wait for it now (uniform branch)
+        if (in < ntl && pn == 0) {  // the next tile was not published in time: wait for it now (uniform branch)
+            const int Jn = tile_J(in);
             if (warp == 0) {
                 unsigned bits;
                 const bool ok = wait_words(ch, Jn, tile_words(Jn), tile_tag(Jn), tile_tag(Jn), ctl, bits);
                 if (lane == 0) {
                     sm.ok = ok;
-                    sm.hzs[(i + 1) & 1] = max(sm.hzs[(i + 1) & 1], i + 1);
+                    sm.hzs[cur ^ 1] = max(sm.hzs[cur ^ 1], in);
+                    sm.tcnt[cur ^ 1] = 1;
                 }
             }
             __syncthreads();
@@ -1508,6 +1519,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (tid < S) sm.tile[cur ^ 1][tid] = __ldcg(&tile_src(Jn)[tid]);
             __syncthreads();
         }
+        i = in;
     }
     cyc_tiles = clock64() - cyc_t0;
     if (trc) gt_tiles = globaltimer();
