@@ -416,13 +416,17 @@ int schedule_for(mc_system *h, long long n, mcg::Ticket **d, int *count)
     return MC_OK;
 }
 
-int grid_for(mc_system *h)
+// Work items of a launch of n sweeps: the groups of every chain, n times.  Items of the next sweep may be in
+// flight with the current sweep's: each waits for its group's previous version, and a group's new version
+// overwrites the buffer of the version before its previous one only after every item of the previous sweep
+// has published (chain order), so no reader of that buffer remains.
+int grid_for(mc_system *h, long long n_sweeps = 1)
 {
     long long useful = 0;
     for (auto &c : h->chains) useful += c.B;
     long long g = (long long)h->sm_count * h->occ;
     if (h->ctas_override > 0) g = std::min<long long>(g, h->ctas_override);
-    g = std::min(g, useful);
+    g = std::min(g, useful * std::max(1LL, n_sweeps));
     // delayed acceptance: fewer resident CTAs than the exclusion depth, so every counted ion's group has
     // finished when a work item starts
     if (h->da_on)
@@ -473,7 +477,7 @@ int enqueue_sweeps(mc_system *h, long long n)
     const bool da = any_da(h);
     int rc = schedule_for(h, da ? 1 : n, &sched, &count);
     if (rc) return rc;
-    const int grid = grid_for(h);
+    const int grid = grid_for(h, da ? 1 : n);
     const int nch = (int)h->chains.size();
     if (h->use_graph) {
         GraphKey key{n, grid, h->policy};
