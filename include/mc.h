@@ -214,7 +214,13 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
  *                      every chain in turn (default), 1 = sweep-synchronous
  *  MC_OPT_DA           1 = chains with a surrogate (mc_set_surrogate) sweep with
  *                      delayed acceptance (default), 0 = they sweep plainly (the
- *                      surrogate stays set for mc_da_samples) */
+ *                      surrogate stays set for mc_da_samples)
+ *  MC_OPT_PAIRS        -1 = automatic (default: on for a single chain without a
+ *                      surrogate of at most 4 x SMs groups), 0 = off, 1 = on:
+ *                      thread-block clusters of two CTAs share each work item,
+ *                      the second summing every other tile for the first.  The
+ *                      trajectory is identical either way; reading it returns
+ *                      whether the mode is in effect. */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3
@@ -222,6 +228,7 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
 #define MC_OPT_USE_GRAPH 5
 #define MC_OPT_POLICY 6
 #define MC_OPT_DA 7
+#define MC_OPT_PAIRS 8
 int mc_set_option(mc_handle h, int option, int64_t value);
 int mc_get_option(mc_handle h, int option, int64_t *value);
 

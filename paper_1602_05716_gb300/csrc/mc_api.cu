@@ -18,7 +18,8 @@ size_t sweep_smem_bytes();
 cudaError_t sweep_configure();
 cudaError_t sweep_occupancy(int *blocks_per_sm);
 cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticket *sched, int n_tickets, mcg::Ctl *ctl,
-                         int n_chains, long long n_sweeps, cudaStream_t st);
+                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs);
+cudaError_t sweep_max_clusters(int *n);
 cudaError_t energy_launch(const float4 *pos, int N, double lB, double *rows, double *out, cudaStream_t st);
 cudaError_t gr_launch(const float4 *pos, int N, int n_bins, double dr, float rmax2_hi, int use_lim, double lim2,
                       unsigned long long *counts, cudaStream_t st);
@@ -101,9 +102,12 @@ struct GraphKey {
     long long n;
     int grid;
     int policy;
+    int pairs;
     bool operator<(const GraphKey &o) const
     {
-        return n != o.n ? n < o.n : (grid != o.grid ? grid < o.grid : policy < o.policy);
+        if (n != o.n) return n < o.n;
+        if (grid != o.grid) return grid < o.grid;
+        return policy != o.policy ? policy < o.policy : pairs < o.pairs;
     }
 };
 
@@ -125,6 +129,9 @@ struct mc_system {
     int use_graph = 1;
     int policy = 0;  // ticket order: 0 group round-robin over chains, 1 sweep-synchronous
     int sm_count = 0, occ = 0;
+    int pairs_opt = -1;                 // MC_OPT_PAIRS: -1 automatic, 0 off, 1 on
+    int max_clusters = 0;               // resident clusters of two CTAs (0: pairs mode unavailable)
+    mcg::PairBox *d_box = nullptr;      // one hand-over box per cluster
     int da_on = 1;  // chains with a surrogate sweep with delayed acceptance (MC_OPT_DA)
     std::map<std::pair<long long, int>, std::pair<mcg::Ticket *, int>> scheds;  // (n_sweeps, policy) -> schedule
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -338,6 +345,7 @@ int create_common(const mc_chain_desc *descs, int n_chains, mc_handle *out)
         for (auto &c : h->chains) free_chain(c);
         cudaFree(h->d_chains);
         cudaFree(h->d_ctl);
+        cudaFree(h->d_box);
         if (h->h_ctl) cudaFreeHost(h->h_ctl);
         if (h->own_stream) cudaStreamDestroy(h->own_stream);
         delete h;
@@ -349,6 +357,10 @@ int create_common(const mc_chain_desc *descs, int n_chains, mc_handle *out)
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         mcg_host::sweep_configure() != cudaSuccess || mcg_host::sweep_occupancy(&h->occ) != cudaSuccess)
         return bail(fail(MC_ERR_CUDA, "kernel configuration failed: %s", cudaGetErrorString(cudaGetLastError())));
+    if (mcg_host::sweep_max_clusters(&h->max_clusters) != cudaSuccess) {
+        h->max_clusters = 0;  // clusters unavailable: pairs mode stays off
+        cudaGetLastError();
+    }
     if (h->occ < 1) return bail(fail(MC_ERR_CUDA, "sweep kernel does not fit on an SM"));
     h->chains.resize(n_chains);
     for (int i = 0; i < n_chains; ++i) {
@@ -362,7 +374,8 @@ int create_common(const mc_chain_desc *descs, int n_chains, mc_handle *out)
     }
     if (cudaMalloc(&h->d_chains, sizeof(mcg::ChainDev) * n_chains) != cudaSuccess ||
         cudaMalloc(&h->d_ctl, sizeof(mcg::Ctl)) != cudaSuccess ||
-        cudaMallocHost(&h->h_ctl, sizeof(mcg::Ctl)) != cudaSuccess)
+        cudaMallocHost(&h->h_ctl, sizeof(mcg::Ctl)) != cudaSuccess ||
+        cudaMalloc(&h->d_box, sizeof(mcg::PairBox) * (size_t)std::max(1, h->sm_count)) != cudaSuccess)
         return bail(fail(MC_ERR_OOM, "allocation of launch state failed"));
     int rc = sync_descriptors(h);
     if (rc) return bail(rc);
@@ -465,7 +478,8 @@ cudaError_t enqueue_da(mc_system *h, long long n, int grid, const mcg::Ticket *s
                                          c.d_fill, c.d_cell_ions, c.d_cell_pos, c.d_slot_of, h->stream);
         }
         if (e == cudaSuccess)
-            e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), 1, h->stream);
+            e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), 1, h->stream,
+                                       false);
     }
     return e;
 }
@@ -477,10 +491,12 @@ int enqueue_sweeps(mc_system *h, long long n)
     const bool da = any_da(h);
     int rc = schedule_for(h, da ? 1 : n, &sched, &count);
     if (rc) return rc;
-    const int grid = grid_for(h, da ? 1 : n);
+    const bool pr = !da && h->h_ctl->pairs != 0;
+    int grid = grid_for(h, da ? 1 : n);
+    if (pr) grid = std::max(2, std::min(grid & ~1, 2 * h->max_clusters));  // whole clusters of two
     const int nch = (int)h->chains.size();
     if (h->use_graph) {
-        GraphKey key{n, grid, h->policy};
+        GraphKey key{n, grid, h->policy, pr ? 1 : 0};
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             cudaGraph_t g = nullptr;
@@ -490,7 +506,7 @@ int enqueue_sweeps(mc_system *h, long long n)
                 e2 = enqueue_da(h, n, grid, sched, count);
             } else {
                 e1 = cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream);
-                e2 = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream);
+                e2 = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream, pr);
             }
             cudaError_t e3 = cudaStreamEndCapture(h->stream, &g);
             if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -509,7 +525,7 @@ int enqueue_sweeps(mc_system *h, long long n)
         CK(enqueue_da(h, n, grid, sched, count));
     } else {
         CK(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream));
-        CK(mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream));
+        CK(mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream, pr));
     }
     for (auto &ch : h->chains) ch.sweeps += (uint64_t)n;
     return MC_OK;
@@ -518,6 +534,16 @@ int enqueue_sweeps(mc_system *h, long long n)
 // The pinned control block is copied to the device at the start of every
 // launch (also inside captured graphs), so it is rewritten only while the
 // stream is idle.
+// Pairs mode (two CTAs per work item, tiles split) for a single plain chain whose groups fit a few waves of
+// SMs: there every in-flight work item must fold each newly published tile as it appears, and splitting the
+// tiles halves that latency.  Chains with delayed acceptance and batches run one CTA per work item.
+bool pairs_on(const mc_system *h)
+{
+    if (h->max_clusters < 1 || any_da(h) || h->pairs_opt == 0) return false;
+    if (h->pairs_opt == 1) return true;
+    return h->chains.size() == 1 && h->chains[0].B <= 4LL * h->sm_count;
+}
+
 void write_ctl(mc_system *h)
 {
     mcg::Ctl *c = h->h_ctl;
@@ -525,6 +551,8 @@ void write_ctl(mc_system *h)
     c->guard_mode = h->guard_mode;
     c->timeout_ns = h->timeout_ms * 1000000ll;
     c->skip_ticket = h->skip_ticket;
+    c->pairs = pairs_on(h) ? 1 : 0;
+    c->box = h->d_box;
 }
 
 int finish(mc_system *h)
@@ -875,6 +903,11 @@ static int set_option(mc_handle h, int option, int64_t value)
         h->da_on = value ? 1 : 0;
         drop_graphs(h);
         return sync_descriptors(h);
+    case MC_OPT_PAIRS:
+        if (value < -1 || value > 1) return fail(MC_ERR_INVALID, "pairs mode %lld", (long long)value);
+        h->pairs_opt = (int)value;
+        drop_graphs(h);
+        return MC_OK;
     default:
         return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
@@ -903,6 +936,7 @@ int mc_get_option(mc_handle h, int option, int64_t *value)
     case MC_OPT_USE_GRAPH: *value = h->use_graph; return MC_OK;
     case MC_OPT_POLICY: *value = h->policy; return MC_OK;
     case MC_OPT_DA: *value = h->da_on; return MC_OK;
+    case MC_OPT_PAIRS: *value = pairs_on(h) ? 1 : 0; return MC_OK;
     default: return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
 }
@@ -975,7 +1009,16 @@ int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t
 // ---------------------------------------------------------------------------
 // Delayed acceptance with the learned surrogate (see include/mc.h).
 
+static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W);
+
 int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W)
+{
+    const int rc = set_surrogate_impl(h, chain, w_bf16, n_w, r_c, W);
+    if (check(h) == MC_OK) write_ctl(h);  // the stream is idle here; pairs mode follows the surrogate state
+    return rc;
+}
+
+static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W)
 {
     int rc = check_chain(h, chain);
     if (rc) return rc;
@@ -1246,6 +1289,7 @@ void mc_destroy(mc_handle h)
     for (auto &c : h->chains) free_chain(c);
     cudaFree(h->d_chains);
     cudaFree(h->d_ctl);
+    cudaFree(h->d_box);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;

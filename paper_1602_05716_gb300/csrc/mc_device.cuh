@@ -100,6 +100,16 @@ struct Ctl {
     long long timeout_ns;
     long long skip_ticket;        // fault injection (-1 off)
     unsigned long long err_info;  // where a wait gave up
+    int pairs;                    // 1: clusters of two CTAs share each work item's tiles (leader even, helper odd)
+    int pad_pairs;
+    struct PairBox *box;          // per cluster: the work item and the helper's per-move tile sums
+};
+
+// Hand-over from a cluster's helper CTA to its leader (global memory, ordered by the cluster barriers).
+struct PairBox {
+    int ticket;
+    int pad[3];
+    float h[128], l[128], p[128], m[128];  // per move: float-float tile sum, P sum, minimum squared distance
 };
 
 // Counter slots of ChainDev::stats.

@@ -80,6 +80,7 @@ struct __align__(16) Smem {
     // deep-window pass, per (ion half, move slot): float-float sum of old-position terms, bound sums; after
     // the tiles: exact correction sums and overlap bits
     float dsh[2][S], dsl[2][S], dsA[2][S], dsT[2][S], dsC[2][S];
+    float dlo[2][S], dhi[2][S];  // interval sums of deep window 0 (the group before the window: exact only at step 5)
     float dpart[2][S];
     unsigned dwo[2][S];
     float Qs[S], mind2[S];  // combined bound sum, minimum squared distance to a settled ion
@@ -166,6 +167,20 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16])
         : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Thread-block cluster of two (pairs mode): rank and a full barrier of both CTAs with release/acquire order
+// (the hand-over goes through global memory, so nothing reads a partner's shared memory).
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
 // 32 consecutive columns of this thread's lane, load and wait in one statement.
@@ -1031,10 +1046,14 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
 }
 
 // One work item: the S moves of group g of chain `tk.chain` at sweep s.
-__device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, const Ticket tk, int ticket, Ctl *ctl)
+// role 0: the whole work item (the cluster's leader in pairs mode: even tiles); role 1: the pairs-mode helper,
+// which sums the odd tiles for the leader and decides nothing.
+__device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, const Ticket tk, int ticket, Ctl *ctl,
+                              int role)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const bool pairs = ctl->pairs != 0, helper = role == 1;
     const ChainDev &ch = chains[tk.chain];
     Ctx c;
     c.ch = &ch;
@@ -1210,6 +1229,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         }
     };
 
+    if (!helper) {  // the helper sums tiles only
     // 2a. this group: upper triangle final (Algorithm 3), lower triangle both ways (Algorithm 4)
     for (int j = r; j < nk; j += SL) {
         const float4 yo = sm.own[j], yn = sm.trial[j];
@@ -1246,7 +1266,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const int q = warp & 3, h = warp >> 2, n = 32 * q + lane;
         const bool act = n < ns;
         const int k = act ? (int)sm.surv[n] : 0;
-        float sh = 0.f, sl = 0.f, A = 0.f, Tt = 0.f, TC = 0.f;
+        float sh = 0.f, sl = 0.f, A = 0.f, Tt = 0.f, TC = 0.f, lo0 = 0.f, hi0 = 0.f;
         if (32 * q < ns) {  // warp-uniform: TMEM stores are whole-warp instructions
             const float4 ak = sm.trial[k], bk = sm.own[k];
             for (int d = 0; d < c.nd; ++d) {
@@ -1268,6 +1288,10 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                         Tt += fabsf(to);
                         A += Ao + An;
                         TC += fabsf(cv);
+                        if (d == 0) {
+                            lo0 += fminf(cv, 0.f);
+                            hi0 += fmaxf(cv, 0.f);
+                        }
                         v[i] = cv;
                         if (overlaps(d2o, ak, yo, lo2, hi2, sig2)) o16 |= 1u << i;
                         if (overlaps(d2n, ak, yn, lo2, hi2, sig2)) n16 |= 1u << i;
@@ -1301,6 +1325,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         sm.dsA[h][n] = act ? A : 0.f;
         sm.dsT[h][n] = act ? Tt : 0.f;
         sm.dsC[h][n] = act ? TC : 0.f;
+        sm.dlo[h][n] = act ? lo0 : 0.f;
+        sm.dhi[h][n] = act ? hi0 : 0.f;
     }
 
     // 2b'. interval sums of the corrections (threads < S: this group, threads >= S: the window);
@@ -1352,6 +1378,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                     both |= (sm.ovo[k][w] & sm.ovn[k][w]) | (sm.wovo[k][w] & sm.wovn[k][w]);
 #pragma unroll
                     for (int d = 0; d < DW; ++d) both |= sm.dovo[d][k][w] & sm.dovn[d][k][w];
+                    any |= sm.dovo[0][k][w] | sm.dovn[0][k][w];  // deep window 0 is exact only at step 5
                 }
                 if (both) stv |= ST_OVL_CERTAIN;
                 else if (any) stv |= ST_OVL_POSSIBLE;
@@ -1380,14 +1407,14 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             }
         }
     }
+    }  // !helper
     // 2c. every other group, oldest published version first (Algorithm 2 per guest group):
     // J = g+1 .. B-1 (version s-1), then J = 0 .. g-1 (version s), the window excluded.
-    auto tile_J = [&](int i) -> int {
-        int J = (g + 1 + i) % B;
-        if (c.win && J == c.Jw) return -1;  // never reached: the window is the last in this order
-        return J;
-    };
-    const int ntl = (B - 1) - (c.win ? 1 : 0) - c.nd;  // the windows are the last groups in this order
+    // In pairs mode each CTA of the cluster takes every other group of this order (leader even, helper odd).
+    const int tstep = pairs ? 2 : 1, toff = helper ? 1 : 0;
+    const int ntl_all = (B - 1) - (c.win ? 1 : 0) - c.nd;  // the windows are the last groups in this order
+    const int ntl = ntl_all > toff ? (ntl_all - toff + tstep - 1) / tstep : 0;
+    auto tile_J = [&](int i) -> int { return (g + 1 + tstep * i + toff) % B; };
     auto tile_tag = [&](int J) -> unsigned { return J > g ? tag_prev : tag_cur; };
     auto tile_src = [&](int J) -> const float4 * { return (J > g ? c.Pprev : c.Pcur) + (size_t)J * S; };
     auto tile_words = [&](int J) -> int { return (min(S, N - J * S) + 31) / 32; };
@@ -1525,6 +1552,42 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     if (trc) gt_tiles = globaltimer();
 #pragma unroll
     for (int pp = 0; pp < MPT / 2; ++pp) upk2(P2[pp], PA[2 * pp], PA[2 * pp + 1]);
+    PairBox *const box = pairs ? &ctl->box[blockIdx.x >> 1] : nullptr;
+    if (helper) {
+        // combine the slices and hand the per-move tile sums to the leader
+#pragma unroll
+        for (int o = 1; o < SL; o <<= 1) {
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                const float h2 = __shfl_xor_sync(FULL, hA[m], o), l2 = __shfl_xor_sync(FULL, lA[m], o);
+                float s2, e;
+                two_sum(hA[m], h2, s2, e);
+                hA[m] = s2;
+                lA[m] = lA[m] + l2 + e;
+                PA[m] += __shfl_xor_sync(FULL, PA[m], o);
+                mA[m] = fminf(mA[m], __shfl_xor_sync(FULL, mA[m], o));
+            }
+        }
+        if (r == 0) {
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                const int k = km[m];
+                if (k < 0) continue;
+                __stcg(&box->h[k], hA[m]);
+                __stcg(&box->l[k], lA[m]);
+                __stcg(&box->p[k], PA[m]);
+                __stcg(&box->m[k], mA[m]);
+            }
+        }
+        cluster_sync_all();  // hand-over to the leader
+        return true;
+    }
+    if (pairs) {
+        cluster_sync_all();  // the helper's tile sums are in the box
+        if (tid == 0) sm.ok = *(volatile int *)&ctl->abort ? 0 : 1;
+        __syncthreads();
+        if (!sm.ok) return false;
+    }
 
     // 2d. combine the 8 column slices (warp-local) into the float-float sum, one bound sum (the bound's linear
     // combination of the magnitude sums, all coefficients positive) and the minimum squared distance, while
@@ -1566,29 +1629,36 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 kv = km[m];
             }
         if (kv >= 0) {
+            if (pairs) {  // the helper's tiles
+                float s2, e;
+                two_sum(hv, __ldcg(&box->h[kv]), s2, e);
+                hv = s2;
+                lv = lv + __ldcg(&box->l[kv]) + e;
+                qv += sm.kPs[kv] * __ldcg(&box->p[kv]);
+                mv = fminf(mv, __ldcg(&box->m[kv]));
+            }
             sm.bhi[kv] = hv;
             sm.blo[kv] = lv;
             sm.Qs[kv] = qv;
             sm.mind2[kv] = mv;
         }
     }
-    if (c.nd > 0) {
+    if (c.nd > 1) {  // deep windows 1.. (published at least two group-times before the window)
         if (warp == 0) {
             unsigned bits;
-            const int nw = c.nd * WORDS;
+            const int nw = (c.nd - 1) * WORDS;
             const bool ok = wait_words(ch, g - 1 - c.nd, nw, tag_cur, tag_cur, ctl, bits, false, true);
             if (lane < nw) sm.dacc[c.nd - 1 - lane / WORDS][lane % WORDS] = bits;
             if (lane == 0) sm.ok = ok;
         }
         __syncthreads();
         if (!sm.ok) return false;
-        if (trc) gt_w2 = globaltimer();
         const int q = warp & 3, h = warp >> 2, n = 32 * q + lane;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};  // independent partial sums
         unsigned wo = 0u;
         if (32 * q < ns) {  // warp-uniform
             const int k = sm.surv[n < ns ? n : 0];
-            for (int d = 0; d < c.nd; ++d) {
+            for (int d = 1; d < c.nd; ++d) {
 #pragma unroll
                 for (int q32 = 0; q32 < HALF / 32; ++q32) {
                     float v[32];
@@ -1617,7 +1687,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const int n = sm.slot[k];
         if (n != 255) {
             const float kT = sm.kTs[k];
-            if (c.nd > 0) {
+            if (c.nd > 1) {
                 sm.wexd[k] = sm.dpart[0][n] + sm.dpart[1][n];
                 if (sm.dwo[0][n] | sm.dwo[1][n]) stv |= ST_OVL_CERTAIN;
             }
@@ -1645,8 +1715,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             else {
                 const float lq = lBf * sm.own[k].w;
                 const float base = sm.bhi[k] + sm.blo[k];
-                out = decide_interval(sm, k, lq, base + ((sm.lo_w[k] + sm.wexd[k]) + sm.lo_i[k]),
-                                      base + ((sm.hi_w[k] + sm.wexd[k]) + sm.hi_i[k]));
+                const int n0 = sm.slot[k];
+                const float l0 = (c.nd > 0 && n0 != 255) ? sm.dlo[0][n0] + sm.dlo[1][n0] : 0.f;
+                const float h0 = (c.nd > 0 && n0 != 255) ? sm.dhi[0][n0] + sm.dhi[1][n0] : 0.f;
+                out = decide_interval(sm, k, lq, base + ((sm.lo_w[k] + (sm.wexd[k] + l0)) + sm.lo_i[k]),
+                                      base + ((sm.hi_w[k] + (sm.wexd[k] + h0)) + sm.hi_i[k]));
             }
         }
         if (out >= 0 && out <= OUT_DA1) sm.outcome[k] = (signed char)out;
@@ -1670,6 +1743,46 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     partial_pass(sm);
     if (trc) gt_ready = globaltimer();
     const long long cyc_w0 = clock64();
+    if (c.nd > 0) {
+        // deep window 0 (the group before the window, published a group-time before it): its exact correction
+        // sums from TMEM and its exact overlap
+        if (warp == 0) {
+            unsigned bits;
+            const bool ok = wait_words(ch, g - 2, WORDS, tag_cur, tag_cur, ctl, bits, false, true);
+            if (lane < WORDS) sm.dacc[0][lane] = bits;
+            if (lane == 0) sm.ok = ok;
+        }
+        __syncthreads();
+        if (!sm.ok) return false;
+        if (trc) gt_w2 = globaltimer();
+        {
+            const int q = warp & 3, h = warp >> 2, n = 32 * q + lane;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            unsigned wo = 0u;
+            if (32 * q < ns) {  // warp-uniform
+                const int k = sm.surv[n < ns ? n : 0];
+#pragma unroll
+                for (int q32 = 0; q32 < HALF / 32; ++q32) {
+                    float v[32];
+                    __syncwarp();
+                    tmem_ld32(tbase + (unsigned)(h * HALF + 32 * q32), v);
+                    const int w = 2 * h + q32;
+                    const unsigned wb = sm.dacc[0][w];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) acc[i & 3] += ((wb >> i) & 1u) ? v[i] : 0.f;
+                    wo |= (sm.dovn[0][k][w] & wb) | (sm.dovo[0][k][w] & ~wb);
+                }
+            }
+            sm.dpart[h][n] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+            sm.dwo[h][n] = wo;
+        }
+        __syncthreads();
+        if (tid < ns) {
+            const int n = tid, k = sm.surv[n];
+            sm.wexd[k] += sm.dpart[0][n] + sm.dpart[1][n];
+            if (sm.dwo[0][n] | sm.dwo[1][n]) sm.st[k] = (unsigned char)(sm.st[k] | ST_OVL_CERTAIN);
+        }
+    }
     if (c.win) {
         if (warp == 0) {
             unsigned bits;
@@ -2044,17 +2157,27 @@ sweep_kernel(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sch
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
+    const bool pairs = ctl->pairs != 0;
+    const int role = pairs ? (int)cluster_rank() : 0;
+    PairBox *const box = pairs ? &ctl->box[blockIdx.x >> 1] : nullptr;
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && role == 0) {
             const unsigned t = atomicAdd(&ctl->ticket, 1u);
             const int ab = *(volatile int *)&ctl->abort;
             sm.ticket = (ab || t >= (unsigned)n_tickets) ? -1 : (int)t;
+            if (pairs) __stcg(&box->ticket, sm.ticket);
+        }
+        if (pairs) {
+            cluster_sync_all();  // the leader's ticket is in the box
+            // the helper takes the leader's ticket; after an abort (the leader may have left) it leaves too
+            if (threadIdx.x == 0 && role == 1)
+                sm.ticket = *(volatile int *)&ctl->abort ? -1 : __ldcg(&box->ticket);
         }
         __syncthreads();
         const int t = sm.ticket;
         __syncthreads();
         if (t < 0) break;
-        if (!process_group(sm, chains, sched[t], t, ctl)) break;  // uniform: every failure exit follows a barrier
+        if (!process_group(sm, chains, sched[t], t, ctl, role)) break;  // uniform: every failure exit follows a barrier
     }
     // every exit path releases the TMEM columns before the CTA ends
     tmem_fence_before();
@@ -2090,10 +2213,44 @@ cudaError_t sweep_occupancy(int *blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mcg::sweep_kernel, mcg::T, sizeof(mcg::Smem));
 }
 
-cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticket *sched, int n_tickets, mcg::Ctl *ctl,
-                         int n_chains, long long n_sweeps, cudaStream_t st)
+// Clusters of two CTAs that can be resident at once (pairs mode); 0 if the device cannot run them.
+cudaError_t sweep_max_clusters(int *n)
 {
-    mcg::sweep_kernel<<<grid, mcg::T, sizeof(mcg::Smem), st>>>(chains, sched, n_tickets, ctl);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(mcg::T);
+    cfg.dynamicSmemBytes = sizeof(mcg::Smem);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(n, mcg::sweep_kernel, &cfg);
+}
+
+cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticket *sched, int n_tickets, mcg::Ctl *ctl,
+                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs)
+{
+    if (pairs) {  // clusters of two CTAs; grid even
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(mcg::T);
+        cfg.dynamicSmemBytes = sizeof(mcg::Smem);
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, mcg::sweep_kernel, chains, sched, n_tickets, ctl);
+        if (e != cudaSuccess) return e;
+    } else {
+        mcg::sweep_kernel<<<grid, mcg::T, sizeof(mcg::Smem), st>>>(chains, sched, n_tickets, ctl);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     mcg::advance_sweeps<<<(n_chains + 127) / 128, 128, 0, st>>>(chains, n_chains, n_sweeps, ctl);

@@ -205,12 +205,40 @@ def test_batch_equals_single(pkg):
         assert (batch.positions(k) == single.positions()).all()
 
 
-def test_bounded_wait_fault_injection(pkg):
+@pytest.mark.parametrize("n,two_one,seed", [(700, True, 301), (3000, False, 302), (129, True, 303)])
+def test_pairs_mode_identical(pkg, n, two_one, seed):
+    """Clusters of two CTAs per work item (the second summing every other tile) against one CTA per item and
+    against the oracle: positions and decisions identical, every FP32 value within its band."""
+    import paper_1602_05716_gb300 as p
+    ch = inputs.small_chain(n, phi=0.2, seed=seed, two_one=two_one, half_width=0.4)
+    runs = {}
+    for mode in (0, 1):
+        s = p.System([ch])
+        s.set_option(p.OPT_PAIRS, mode)
+        assert s.get_option(p.OPT_PAIRS) == mode
+        s.record_enable(4 * n)
+        s.sweep(4)
+        runs[mode] = (s.positions(), s.records(), s.stats())
+        s.close()
+    assert (runs[0][0] == runs[1][0]).all()
+    assert (runs[0][1]["outcome"] == runs[1][1]["outcome"]).all()
+    assert runs[0][2]["accepts"] == runs[1][2]["accepts"]
+    o = oracle.OracleChain.from_chain(ch, threads=THREADS)
+    o.record(4 * n)
+    o.sweep(4)
+    assert (runs[1][0] == o.positions()).all()
+    _compare_records(runs[1][1], o.records(), n)
+
+
+@pytest.mark.parametrize("pairs", [0, 1])
+def test_bounded_wait_fault_injection(pkg, pairs):
     """A work item that never publishes: every waiter gives up after the timeout, the call returns
-    MC_ERR_TIMEOUT, the handle is poisoned and the device stays usable."""
+    MC_ERR_TIMEOUT, the handle is poisoned and the device stays usable (one CTA per work item, and clusters of
+    two whose helper must leave with its leader)."""
     import paper_1602_05716_gb300 as p
     ch = inputs.small_chain(600, phi=0.15, seed=5)
     s = p.System([ch])
+    s.set_option(p.OPT_PAIRS, pairs)
     s.set_option(p.OPT_TIMEOUT_MS, 300)
     s.set_option(p.OPT_SKIP_PUBLISH, 3)
     with pytest.raises(p.MCError) as ei:
