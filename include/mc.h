@@ -216,11 +216,17 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
  *                      delayed acceptance (default), 0 = they sweep plainly (the
  *                      surrogate stays set for mc_da_samples)
  *  MC_OPT_PAIRS        -1 = automatic (default: on for a single chain without a
- *                      surrogate of at most 4 x SMs groups), 0 = off, 1 = on:
+ *                      surrogate of at most 4 x SMs groups when deep windows are
+ *                      on), 0 = off, 1 = on:
  *                      thread-block clusters of two CTAs share each work item,
  *                      the second summing every other tile for the first.  The
  *                      trajectory is identical either way; reading it returns
- *                      whether the mode is in effect. */
+ *                      whether the mode is in effect.
+ *  MC_OPT_DEEP_WINDOWS 0 = off (default), 1 = the three groups before the window
+ *                      are also computed for both positions, their corrections
+ *                      held in tensor memory.  Experimental: launches with many
+ *                      chains showed rare corrupted trajectories with it on, not
+ *                      yet explained; keep it off where results matter. */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3
@@ -229,6 +235,7 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
 #define MC_OPT_POLICY 6
 #define MC_OPT_DA 7
 #define MC_OPT_PAIRS 8
+#define MC_OPT_DEEP_WINDOWS 9
 int mc_set_option(mc_handle h, int option, int64_t value);
 int mc_get_option(mc_handle h, int option, int64_t *value);
 

@@ -10,6 +10,7 @@ from . import build as _build
 
 ERR_INVALID, ERR_OVERLAP_INIT, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_POISONED = -1, -2, -3, -4, -5, -6
 OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH, OPT_POLICY, OPT_DA, OPT_PAIRS = 1, 2, 3, 4, 5, 6, 7, 8
+OPT_DEEP_WINDOWS = 9
 MLP_NIN, MLP_H = 33, 64
 MLP_NP = MLP_H * MLP_NIN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1  # layout W1, b1, W2, b2, W3, b3
 

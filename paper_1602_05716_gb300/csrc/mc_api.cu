@@ -130,6 +130,7 @@ struct mc_system {
     int policy = 0;  // ticket order: 0 group round-robin over chains, 1 sweep-synchronous
     int sm_count = 0, occ = 0;
     int pairs_opt = -1;                 // MC_OPT_PAIRS: -1 automatic, 0 off, 1 on
+    int deep_opt = 0;                   // MC_OPT_DEEP_WINDOWS: 0 off (default), 1 on
     int max_clusters = 0;               // resident clusters of two CTAs (0: pairs mode unavailable)
     mcg::PairBox *d_box = nullptr;      // one hand-over box per cluster
     int da_on = 1;  // chains with a surrogate sweep with delayed acceptance (MC_OPT_DA)
@@ -535,13 +536,15 @@ int enqueue_sweeps(mc_system *h, long long n)
 // launch (also inside captured graphs), so it is rewritten only while the
 // stream is idle.
 // Pairs mode (two CTAs per work item, tiles split) for a single plain chain whose groups fit a few waves of
-// SMs: there every in-flight work item must fold each newly published tile as it appears, and splitting the
-// tiles halves that latency.  Chains with delayed acceptance and batches run one CTA per work item.
+// SMs, with deep windows on: then every in-flight work item must fold each newly published tile as it appears,
+// and splitting the tiles halves that latency.  Without deep windows the chain waits on the tile two groups
+// back and one CTA per item (twice as many in flight) measured faster.  Chains with delayed acceptance and
+// batches run one CTA per work item.
 bool pairs_on(const mc_system *h)
 {
     if (h->max_clusters < 1 || any_da(h) || h->pairs_opt == 0) return false;
     if (h->pairs_opt == 1) return true;
-    return h->chains.size() == 1 && h->chains[0].B <= 4LL * h->sm_count;
+    return h->deep_opt && h->chains.size() == 1 && h->chains[0].B <= 4LL * h->sm_count;
 }
 
 void write_ctl(mc_system *h)
@@ -552,6 +555,7 @@ void write_ctl(mc_system *h)
     c->timeout_ns = h->timeout_ms * 1000000ll;
     c->skip_ticket = h->skip_ticket;
     c->pairs = pairs_on(h) ? 1 : 0;
+    c->deep = h->deep_opt;
     c->box = h->d_box;
 }
 
@@ -908,6 +912,9 @@ static int set_option(mc_handle h, int option, int64_t value)
         h->pairs_opt = (int)value;
         drop_graphs(h);
         return MC_OK;
+    case MC_OPT_DEEP_WINDOWS:
+        h->deep_opt = value ? 1 : 0;
+        return MC_OK;
     default:
         return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
@@ -937,6 +944,7 @@ int mc_get_option(mc_handle h, int option, int64_t *value)
     case MC_OPT_POLICY: *value = h->policy; return MC_OK;
     case MC_OPT_DA: *value = h->da_on; return MC_OK;
     case MC_OPT_PAIRS: *value = pairs_on(h) ? 1 : 0; return MC_OK;
+    case MC_OPT_DEEP_WINDOWS: *value = h->deep_opt; return MC_OK;
     default: return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
 }

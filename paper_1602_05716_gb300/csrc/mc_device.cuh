@@ -101,7 +101,7 @@ struct Ctl {
     long long skip_ticket;        // fault injection (-1 off)
     unsigned long long err_info;  // where a wait gave up
     int pairs;                    // 1: clusters of two CTAs share each work item's tiles (leader even, helper odd)
-    int pad_pairs;
+    int deep;                     // 1: deep windows (groups g-2.. both ways, corrections in tensor memory)
     struct PairBox *box;          // per cluster: the work item and the helper's per-move tile sums
 };
 

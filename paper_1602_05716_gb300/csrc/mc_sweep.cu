@@ -112,6 +112,7 @@ static_assert(sizeof(Smem) > 116 * 1024, "one CTA per SM");
 // [32 (w mod 4), 32 (w mod 4) + 32), so each warp only touches its own lane quarter and column half.
 __device__ __forceinline__ void tmem_alloc(unsigned *dst)  // one whole warp
 {
+    __syncwarp();  // .aligned: the whole warp, converged
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
                  "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::"r"(
                      (unsigned)__cvta_generic_to_shared(dst)),
@@ -121,6 +122,7 @@ __device__ __forceinline__ void tmem_alloc(unsigned *dst)  // one whole warp
 
 __device__ __forceinline__ void tmem_dealloc(unsigned taddr)  // one whole warp
 {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
 }
 
@@ -134,12 +136,16 @@ __device__ __forceinline__ void tmem_fence_after()
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
 
-// 16 consecutive columns of this thread's lane (whole warp, converged).
+// 16 consecutive columns of this thread's lane (whole warp, converged).  The store reads its source registers
+// asynchronously, so it waits for its completion in the same statement: no later instruction may overwrite
+// those registers before the tensor memory holds their values.
 __device__ __forceinline__ void tmem_st16(unsigned taddr, const float (&v)[16])
 {
+    __syncwarp();
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16};\n" ::"r"(taddr),
+        "%15, %16};\n"
+        "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
         "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
         "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
         "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
@@ -150,12 +156,14 @@ __device__ __forceinline__ void tmem_st16(unsigned taddr, const float (&v)[16])
 
 __device__ __forceinline__ void tmem_wait_st()
 {
+    __syncwarp();
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 
 // Load and wait in one statement, so that no use of the registers can be scheduled before the wait.
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16])
 {
+    __syncwarp();
     unsigned r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -180,12 +188,14 @@ __device__ __forceinline__ unsigned cluster_rank()
 
 __device__ __forceinline__ void cluster_sync_all()
 {
+    __syncwarp();  // .aligned: every warp converged (callers follow single-lane branches)
     asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
 // 32 consecutive columns of this thread's lane, load and wait in one statement.
 __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32])
 {
+    __syncwarp();
     unsigned r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
@@ -1079,8 +1089,9 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         c.win = (g == 0) ? (s > ch.sweep_base) : true;
         c.nwk = min(S, N - c.Jw * S);
     }
-    // deep windows: the groups g-2, g-3, ... before the window that belong to this sweep (always full groups)
-    c.nd = c.win ? max(0, min(DW, g - 1)) : 0;
+    // deep windows: the groups g-2, g-3, ... before the window that belong to this sweep (always full groups);
+    // only when enabled (MC_OPT_DEEP_WINDOWS), otherwise those groups are ordinary tiles
+    c.nd = (c.win && ctl->deep) ? max(0, min(DW, g - 1)) : 0;
     const float lo2 = ch.sig2_lo, hi2 = ch.sig2_hi;
     const double sig2 = ch.sig2;
     const float s2f = (float)sig2;
@@ -1318,7 +1329,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                     sm.dovn[d][k][2 * h + 1] = nw1;
                 }
             }
-            tmem_wait_st();
+            // every store waited for itself; no whole-warp tcgen05 instruction follows the divergent branch above
         }
         sm.dsh[h][n] = act ? sh : 0.f;
         sm.dsl[h][n] = act ? sl : 0.f;

@@ -230,6 +230,23 @@ def test_pairs_mode_identical(pkg, n, two_one, seed):
     _compare_records(runs[1][1], o.records(), n)
 
 
+def test_deep_windows_option_single_chain(pkg):
+    """The experimental deep windows (three more groups both ways, corrections in tensor memory) on one chain:
+    positions and decisions identical to the oracle."""
+    import paper_1602_05716_gb300 as p
+    ch = inputs.small_chain(3000, phi=0.2, seed=311, two_one=True, half_width=0.4)
+    s = p.System([ch])
+    s.set_option(p.OPT_DEEP_WINDOWS, 1)
+    assert s.get_option(p.OPT_DEEP_WINDOWS) == 1
+    s.record_enable(4 * ch.n)
+    s.sweep(4)
+    o = oracle.OracleChain.from_chain(ch, threads=THREADS)
+    o.record(4 * ch.n)
+    o.sweep(4)
+    assert (s.positions() == o.positions()).all()
+    _compare_records(s.records(), o.records(), ch.n)
+
+
 @pytest.mark.parametrize("pairs", [0, 1])
 def test_bounded_wait_fault_injection(pkg, pairs):
     """A work item that never publishes: every waiter gives up after the timeout, the call returns
