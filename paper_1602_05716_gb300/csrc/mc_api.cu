@@ -913,7 +913,11 @@ static int set_option(mc_handle h, int option, int64_t value)
         drop_graphs(h);
         return MC_OK;
     case MC_OPT_DEEP_WINDOWS:
-        h->deep_opt = value ? 1 : 0;
+        // The deep-window path stays closed until the cause of its corrupted trajectories (and of one launch
+        // that never finished) is found; the kernel keeps the code, reachable only through this switch.
+        if (value) return fail(MC_ERR_INVALID, "deep windows are disabled: corrupted trajectories in many-chain "
+                                               "launches with them on, cause not yet found");
+        h->deep_opt = 0;
         return MC_OK;
     default:
         return fail(MC_ERR_INVALID, "unknown option %d", option);

@@ -230,21 +230,22 @@ def test_pairs_mode_identical(pkg, n, two_one, seed):
     _compare_records(runs[1][1], o.records(), n)
 
 
-def test_deep_windows_option_single_chain(pkg):
-    """The experimental deep windows (three more groups both ways, corrections in tensor memory) on one chain:
-    positions and decisions identical to the oracle."""
+def test_deep_windows_option_closed(pkg):
+    """The deep-window path is closed: turning it on is refused with MC_ERR_INVALID, the handle stays usable,
+    the option reads 0 and pairs mode stays off in automatic mode."""
     import paper_1602_05716_gb300 as p
-    ch = inputs.small_chain(3000, phi=0.2, seed=311, two_one=True, half_width=0.4)
+    ch = inputs.small_chain(600, phi=0.15, seed=311)
     s = p.System([ch])
-    s.set_option(p.OPT_DEEP_WINDOWS, 1)
-    assert s.get_option(p.OPT_DEEP_WINDOWS) == 1
-    s.record_enable(4 * ch.n)
-    s.sweep(4)
+    with pytest.raises(p.MCError) as e:
+        s.set_option(p.OPT_DEEP_WINDOWS, 1)
+    assert e.value.code == p.ERR_INVALID
+    assert s.get_option(p.OPT_DEEP_WINDOWS) == 0
+    assert s.get_option(p.OPT_PAIRS) == 0
+    s.set_option(p.OPT_DEEP_WINDOWS, 0)
+    s.sweep(1)
     o = oracle.OracleChain.from_chain(ch, threads=THREADS)
-    o.record(4 * ch.n)
-    o.sweep(4)
+    o.sweep(1)
     assert (s.positions() == o.positions()).all()
-    _compare_records(s.records(), o.records(), ch.n)
 
 
 @pytest.mark.parametrize("pairs", [0, 1])
