@@ -222,12 +222,11 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
  *                      the second summing every other tile for the first.  The
  *                      trajectory is identical either way; reading it returns
  *                      whether the mode is in effect.
- *  MC_OPT_DEEP_WINDOWS 0 = off (the only accepted value; setting 1 returns
- *                      MC_ERR_INVALID).  With it on, the three groups before the
- *                      window would also be computed for both positions, their
- *                      corrections held in tensor memory; launches with many
- *                      chains showed corrupted trajectories that way, cause not
- *                      yet found, so the path is closed. */
+ *  MC_OPT_DEEP_WINDOWS 1 = on (default), 0 = off: the three groups before the
+ *                      window are also computed for both positions, their
+ *                      corrections held in tensor memory, so a group waits for
+ *                      no tile later than five groups back.  The trajectory is
+ *                      identical either way. */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3

@@ -144,6 +144,7 @@ class System:
         seed, chain_id (e.g. inputs.Chain)."""
         L = lib()
         chains = list(chains)
+        self._rec_caps, self._trace_caps = {}, {}  # per chain: the capacity last enabled
         self._keep = []
         descs = (_Desc * len(chains))()
         for k, c in enumerate(chains):
@@ -260,20 +261,20 @@ class System:
 
     def record_enable(self, cap: int, chain: int = 0):
         _check(lib().mc_record_enable(self._h, chain, int(cap)))
-        self._rec_cap = int(cap)
+        self._rec_caps[chain] = int(cap)
 
     def trace_enable(self, cap: int, chain: int = 0):
         _check(lib().mc_trace_enable(self._h, chain, int(cap)))
-        self._trace_cap = int(cap)
+        self._trace_caps[chain] = int(cap)
 
     def trace(self, chain: int = 0) -> np.ndarray:
-        cap = getattr(self, "_trace_cap", 0)
+        cap = self._trace_caps.get(chain, 0)
         out = np.zeros(cap, TRACE_DTYPE)
         n = _check(lib().mc_trace_read(self._h, chain, out.ctypes.data, cap))
         return out[:n]
 
     def records(self, chain: int = 0) -> np.ndarray:
-        cap = getattr(self, "_rec_cap", 0)
+        cap = self._rec_caps.get(chain, 0)
         out = np.zeros(cap, RECORD_DTYPE)
         n = _check(lib().mc_record_read(self._h, chain, out.ctypes.data, cap))
         return out[:n]

@@ -130,7 +130,7 @@ struct mc_system {
     int policy = 0;  // ticket order: 0 group round-robin over chains, 1 sweep-synchronous
     int sm_count = 0, occ = 0;
     int pairs_opt = -1;                 // MC_OPT_PAIRS: -1 automatic, 0 off, 1 on
-    int deep_opt = 0;                   // MC_OPT_DEEP_WINDOWS: 0 off (default), 1 on
+    int deep_opt = 1;                   // MC_OPT_DEEP_WINDOWS: 1 on (default), 0 off
     int max_clusters = 0;               // resident clusters of two CTAs (0: pairs mode unavailable)
     mcg::PairBox *d_box = nullptr;      // one hand-over box per cluster
     int da_on = 1;  // chains with a surrogate sweep with delayed acceptance (MC_OPT_DA)
@@ -913,11 +913,9 @@ static int set_option(mc_handle h, int option, int64_t value)
         drop_graphs(h);
         return MC_OK;
     case MC_OPT_DEEP_WINDOWS:
-        // The deep-window path stays closed until the cause of its corrupted trajectories (and of one launch
-        // that never finished) is found; the kernel keeps the code, reachable only through this switch.
-        if (value) return fail(MC_ERR_INVALID, "deep windows are disabled: corrupted trajectories in many-chain "
-                                               "launches with them on, cause not yet found");
-        h->deep_opt = 0;
+        if (value < 0 || value > 1) return fail(MC_ERR_INVALID, "deep windows %lld", (long long)value);
+        h->deep_opt = (int)value;
+        drop_graphs(h);
         return MC_OK;
     default:
         return fail(MC_ERR_INVALID, "unknown option %d", option);

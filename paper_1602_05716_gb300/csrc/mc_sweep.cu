@@ -1090,7 +1090,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         c.nwk = min(S, N - c.Jw * S);
     }
     // deep windows: the groups g-2, g-3, ... before the window that belong to this sweep (always full groups);
-    // only when enabled (MC_OPT_DEEP_WINDOWS), otherwise those groups are ordinary tiles
+    // unless disabled (MC_OPT_DEEP_WINDOWS), otherwise those groups are ordinary tiles
     c.nd = (c.win && ctl->deep) ? max(0, min(DW, g - 1)) : 0;
     const float lo2 = ch.sig2_lo, hi2 = ch.sig2_hi;
     const double sig2 = ch.sig2;
@@ -1971,6 +1971,10 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             }
             __syncthreads();
             cyc_guard += clock64() - cyc_g0;
+        } else {
+            // every thread must have read dec0 for `exact` before it is overwritten below: a warp that read the
+            // new value would find `first` ready, take the guard tiers' barriers alone and fall out of step
+            __syncthreads();
         }
         if (tid < WORDS) {
             sm.acc0[tid] = sm.accw[tid];

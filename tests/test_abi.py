@@ -37,3 +37,34 @@ def test_binding_loads_without_gpu():
     pkg.build()
     L = pkg.lib()
     assert L.mc_last_error() is not None
+
+
+def test_record_capacity_is_kept_per_chain(monkeypatch):
+    """The binding reads each chain's records and timeline with the capacity enabled for that chain (a fake
+    library stands in for the C calls: nothing runs on a device)."""
+    from paper_1602_05716_gb300 import api
+
+    class _Fake:
+        def __init__(self):
+            self.read = []
+
+        def mc_record_enable(self, h, chain, cap):
+            return 0
+
+        mc_trace_enable = mc_record_enable
+
+        def mc_record_read(self, h, chain, out, cap):
+            self.read.append((chain, cap))
+            return 0
+
+        mc_trace_read = mc_record_read
+
+    fake = _Fake()
+    monkeypatch.setattr(api, "lib", lambda: fake)
+    s = api.System.__new__(api.System)
+    s._h, s._rec_caps, s._trace_caps = None, {}, {}
+    s.record_enable(4500, chain=0)
+    s.record_enable(1920, chain=3)
+    s.trace_enable(70, chain=1)
+    s.records(0), s.records(3), s.records(2), s.trace(1)
+    assert fake.read == [(0, 4500), (3, 1920), (2, 0), (1, 70)]

@@ -230,22 +230,28 @@ def test_pairs_mode_identical(pkg, n, two_one, seed):
     _compare_records(runs[1][1], o.records(), n)
 
 
-def test_deep_windows_option_closed(pkg):
-    """The deep-window path is closed: turning it on is refused with MC_ERR_INVALID, the handle stays usable,
-    the option reads 0 and pairs mode stays off in automatic mode."""
+@pytest.mark.parametrize("nchains", [1, 4])
+def test_deep_windows_option(pkg, nchains):
+    """Deep windows (three more groups both ways, corrections in tensor memory), on one chain and on a batch
+    of chains of mixed sizes: positions and decisions identical to the oracle; an out-of-range value is
+    refused."""
     import paper_1602_05716_gb300 as p
-    ch = inputs.small_chain(600, phi=0.15, seed=311)
-    s = p.System([ch])
-    with pytest.raises(p.MCError) as e:
-        s.set_option(p.OPT_DEEP_WINDOWS, 1)
-    assert e.value.code == p.ERR_INVALID
-    assert s.get_option(p.OPT_DEEP_WINDOWS) == 0
-    assert s.get_option(p.OPT_PAIRS) == 0
-    s.set_option(p.OPT_DEEP_WINDOWS, 0)
-    s.sweep(1)
-    o = oracle.OracleChain.from_chain(ch, threads=THREADS)
-    o.sweep(1)
-    assert (s.positions() == o.positions()).all()
+    sizes = [3000] if nchains == 1 else [1500, 900, 2100, 640]
+    chs = [inputs.small_chain(n, phi=0.2, seed=311 + q, two_one=True, half_width=0.4) for q, n in enumerate(sizes)]
+    s = p.System(chs)
+    with pytest.raises(p.MCError):
+        s.set_option(p.OPT_DEEP_WINDOWS, 2)
+    s.set_option(p.OPT_DEEP_WINDOWS, 1)
+    assert s.get_option(p.OPT_DEEP_WINDOWS) == 1
+    for q, ch in enumerate(chs):
+        s.record_enable(3 * ch.n, chain=q)
+    s.sweep(3)
+    for q, ch in enumerate(chs):
+        o = oracle.OracleChain.from_chain(ch, threads=THREADS)
+        o.record(3 * ch.n)
+        o.sweep(3)
+        assert (s.positions(q) == o.positions()).all()
+        _compare_records(s.records(q), o.records(), ch.n)
 
 
 @pytest.mark.parametrize("pairs", [0, 1])
