@@ -186,6 +186,21 @@ def cpu_baseline(chains, min_seconds: float = 8.0, max_sweeps: int = 20, threads
             "pair_evals_per_s": pairs / dt}
 
 
+def reduction_foil(pkg, ch, sweeps: int, ours: float) -> dict:
+    """Sec. 4's parallel-reduction code on the same chain from its initial positions: one kernel launch per trial
+    move, each sweep's launches replayed from one CUDA graph; CUDA-event time of the sweeps.  Its positions after
+    the sweeps are compared with the sweep kernel's (the same exact chain)."""
+    pos, _, cnt, ms = pkg.reduction_run(ch, sweeps)
+    ref = pkg.System([ch])
+    ref.sweep(sweeps)
+    same = bool((ref.positions() == pos).all())
+    ref.close()
+    v = sweeps * ch.n / (ms / 1e3)
+    return {"impl": "parallel reduction, one launch per trial move (Sec. 4)", "value": v, "unit": "moves/s",
+            "sweeps": sweeps, "launches": sweeps * (ch.n + 1), "sweep_kernel_over_foil": ours / v,
+            "positions_equal_sweep_kernel": same, "canonical_resums": cnt["canonical_resums"]}
+
+
 def replica_chains(chains, rank: int):
     """Independent replicas: every rank runs the workload's chains with chain ids shifted by rank * len(chains)
     (a new Philox key, hence an independent trajectory)."""
@@ -458,6 +473,8 @@ def run_ours(args):
         line["gpu_launches"] = 6 * sps * args.steps + (line["gpu_launches"] - 2 * args.steps)
     elif plain_cmp is not None:
         line["plain_path_same_gpu"] = plain_cmp
+    if rank == 0 and world == 1 and args.foil_sweeps > 0 and len(chains) == 1 and chains[0].n <= 65536 and w_da is None:
+        line["reduction_foil"] = reduction_foil(pkg, chains[0], args.foil_sweeps, value)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl.chains, min_seconds=args.cpu_seconds)
     if rank == 0:
@@ -480,6 +497,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--ref-moves-per-step", type=int, default=2048)
     ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--foil-sweeps", type=int, default=2,
+                    help="sweeps of Sec. 4's parallel-reduction code timed beside the headline (0: skip)")
     ap.add_argument("--mode", choices=["plain", "da", "both"], default=None,
                     help="plain exact path or delayed acceptance with a trained surrogate (default by workload)")
     ap.add_argument("--r-c", dest="r_c", type=float, default=4.0)

@@ -198,6 +198,53 @@ typedef struct {
 int mc_trace_enable(mc_handle h, int chain, int64_t cap);
 int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap);
 
+/* Energy series (Sec. 5.2: the total energy E_k monitored step by step).
+ * After enabling, the sweep kernel stores the FP64 ledger (the energy of the
+ * initial configuration plus every accepted dE) once the last group of each
+ * sweep has been folded into it: entry k is E after the (k+1)-th sweep from
+ * enabling, for the first `cap` sweeps (cap = 0 disables; the buffer is
+ * device memory owned by the library).  Read copies min(cap, enabled
+ * capacity, sweeps run since enabling) entries into the caller's host
+ * buffer and returns how many (>= 0) or an error.                           */
+int mc_energy_series_enable(mc_handle h, int chain, int64_t cap);
+int64_t mc_energy_series_read(mc_handle h, int chain, double *out, int64_t cap);
+
+/* Energy autocorrelation and integrated autocorrelation time (Sec. 5.2's
+ * definitions): with E-bar the mean over the ensemble and the steps,
+ *   C_n = <(E_k - E-bar)(E_{k+n} - E-bar)> / <(E_k - E-bar)^2>,
+ * the numerator averaged over every series and every k with k + n inside
+ * the series, the denominator over every entry; T_c = 1/2 + sum_{k=1}^{max_lag}
+ * C_k (the paper's infinite sum, cut at max_lag by the caller).  Host only,
+ * no device and no handle.  series: n_series rows of n_steps FP64 values,
+ * row r at series + r * stride (caller-owned, read only); C: max_lag + 1
+ * outputs (C[0] = 1); Tc may be NULL.  MC_ERR_INVALID for NULL pointers,
+ * n_series < 1, n_steps < 2, stride < n_steps, max_lag outside
+ * [0, n_steps), a non-finite entry, or a series without variance.         */
+int mc_energy_autocorr(const double *series, int64_t n_series, int64_t n_steps, int64_t stride, int64_t max_lag,
+                       double *C, double *Tc);
+
+/* The parallel-reduction comparison code of Sec. 4, as a foil for mc_sweep:
+ * one kernel launch per trial move, the N - 1 pair terms spread over blocks
+ * of 1,024 threads (one pair each), block subtotals left in global memory and
+ * counted by an atomic, the last block to finish deciding the move and
+ * updating the ion.  It runs the same exact chain as mc_sweep (Sec. 2's
+ * sequential updating, the same draws and decisions from sweep 0 of the
+ * description's positions), so after n sweeps its positions equal those of
+ * mc_create + mc_sweep(n).  Each sweep's N launches replay from one CUDA
+ * graph for N <= 65,536 (plain launches above).  Blocks until done.
+ *   desc      one chain, validated as by mc_create (caller-owned, read only)
+ *   pos_out   N x 3 floats, host, caller-owned: the positions after the sweeps
+ *   dE_sum    (nullable) FP64 sum of the accepted moves' dE
+ *   counts    (nullable) 5 counters: accepted, rejected by the Metropolis
+ *             test, by overlap, by the wall, and moves whose tree sum fell
+ *             within its rounding bound of the threshold and were re-summed
+ *             in the canonical order
+ *   ms        (nullable) CUDA-event time of the sweeps on the call's stream
+ * Device memory is allocated and released inside the call.  Errors as
+ * mc_create, MC_ERR_INVALID for n_sweeps < 0 or a NULL pos_out.            */
+int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, float *pos_out, double *dE_sum, uint64_t *counts,
+                     double *ms);
+
 /* Options (mc_set_option):
  *  MC_OPT_GUARD_MODE   0 = FP32 with proven error band (default),
  *                      1 = recompute every evaluated move in FP64,

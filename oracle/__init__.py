@@ -10,14 +10,15 @@ other than itself (cuRAND's host Philox stream, math.log, closed-form 2- and
 distance distribution, the ideal-gas limit and the Debye-Hueckel limiting law).  The delayed-acceptance part is
 pinned by finite differences of the MLP gradient, libm's exp, brute-force features and near-field sums, exact
 antisymmetry of the surrogate energy change, and the exact confined-pair distribution sampled by the
-delayed-acceptance chain.
+delayed-acceptance chain.  The energy autocorrelation (Sec. 5.2) is pinned by values derived by hand from its
+definition, exact alternating series, affine invariance and the AR(1) closed form.
 """
 from .oracle import (OracleChain, build, lib, philox4x32_10, move_draws, log_L, total_energy,
                      RECORD_DTYPE, ACCEPT, REJECT_METROPOLIS, REJECT_OVERLAP, REJECT_WALL,
                      DA_REJECT1, DA_RECORD_DTYPE, MLP_NIN, MLP_H, MLP_NP, exp_D, bf16_to_f64, f64_to_bf16,
-                     mlp_forward, mlp_loss_grad)
+                     mlp_forward, mlp_loss_grad, energy_autocorr)
 
 __all__ = ["OracleChain", "build", "lib", "philox4x32_10", "move_draws", "log_L", "total_energy",
            "RECORD_DTYPE", "ACCEPT", "REJECT_METROPOLIS", "REJECT_OVERLAP", "REJECT_WALL",
            "DA_REJECT1", "DA_RECORD_DTYPE", "MLP_NIN", "MLP_H", "MLP_NP", "exp_D", "bf16_to_f64", "f64_to_bf16",
-           "mlp_forward", "mlp_loss_grad"]
+           "mlp_forward", "mlp_loss_grad", "energy_autocorr"]

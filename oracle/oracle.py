@@ -166,6 +166,23 @@ def total_energy(pos: np.ndarray, q: np.ndarray, l_B: float) -> float:
     return lib().mco_total_energy_of(pos.ctypes.data, qd.ctypes.data, int(qd.shape[0]), float(l_B))
 
 
+def energy_autocorr(series, max_lag: int):
+    """Sec. 5.2's autocorrelation of the total energy, written out from its definition: E-bar is the mean over
+    the ensemble (rows) and the steps (columns); C_n is the mean of (E_k - E-bar)(E_{k+n} - E-bar) over every row
+    and every k with k + n in the row, divided by the mean of (E_k - E-bar)^2 over every entry; the integrated
+    time is T_c = 1/2 + sum_{k=1}^{max_lag} C_k (the paper's infinite sum, cut at max_lag).  FP64 numpy."""
+    E = np.asarray(series, dtype=np.float64)
+    if E.ndim == 1:
+        E = E[None, :]
+    n_steps = E.shape[1]
+    if not (0 <= max_lag < n_steps) or n_steps < 2:
+        raise ValueError("max_lag must lie in [0, n_steps) and n_steps >= 2")
+    dev = E - E.mean()
+    den = np.mean(dev * dev)
+    C = np.array([np.mean(dev[:, : n_steps - n] * dev[:, n:]) / den for n in range(max_lag + 1)])
+    return C, 0.5 + float(np.sum(C[1:]))
+
+
 class OracleChain:
     """One sequential Metropolis chain, FP64 canonical arithmetic (mco_* API)."""
 

@@ -84,6 +84,10 @@ def lib():
         "mc_record_read": ([vp, ci, vp, i64], i64),
         "mc_trace_enable": ([vp, ci, i64], ci),
         "mc_trace_read": ([vp, ci, vp, i64], i64),
+        "mc_energy_series_enable": ([vp, ci, i64], ci),
+        "mc_energy_series_read": ([vp, ci, vp, i64], i64),
+        "mc_energy_autocorr": ([vp, i64, i64, i64, i64, vp, vp], ci),
+        "mc_reduction_run": ([ctypes.POINTER(_Desc), i64, vp, vp, vp, vp], ci),
         "mc_set_option": ([vp, ci, i64], ci),
         "mc_get_option": ([vp, ci, vp], ci),
         "mc_autotune": ([vp, i64, vp, vp, vp], ci),
@@ -144,7 +148,7 @@ class System:
         seed, chain_id (e.g. inputs.Chain)."""
         L = lib()
         chains = list(chains)
-        self._rec_caps, self._trace_caps = {}, {}  # per chain: the capacity last enabled
+        self._rec_caps, self._trace_caps, self._eser_caps = {}, {}, {}  # per chain: the capacity last enabled
         self._keep = []
         descs = (_Desc * len(chains))()
         for k, c in enumerate(chains):
@@ -273,6 +277,18 @@ class System:
         n = _check(lib().mc_trace_read(self._h, chain, out.ctypes.data, cap))
         return out[:n]
 
+    def energy_series_enable(self, cap: int, chain: int = 0):
+        """Record the FP64 ledger after each of the next `cap` sweeps of the chain (0 disables)."""
+        _check(lib().mc_energy_series_enable(self._h, chain, int(cap)))
+        self._eser_caps[chain] = int(cap)
+
+    def energy_series(self, chain: int = 0) -> np.ndarray:
+        """The recorded energies E_k, one per sweep run since enabling (at most the enabled capacity)."""
+        cap = self._eser_caps.get(chain, 0)
+        out = np.zeros(cap, np.float64)
+        n = _check(lib().mc_energy_series_read(self._h, chain, out.ctypes.data, cap))
+        return out[:n]
+
     def records(self, chain: int = 0) -> np.ndarray:
         cap = self._rec_caps.get(chain, 0)
         out = np.zeros(cap, RECORD_DTYPE)
@@ -296,6 +312,37 @@ class System:
         ok = np.zeros(n, np.uint8)
         _check(lib().mc_da_samples(self._h, chain, v.ctypes.data, y.ctypes.data, ok.ctypes.data))
         return v, y, ok.astype(bool)
+
+
+def reduction_run(chain, n_sweeps: int):
+    """Sec. 4's parallel-reduction code (one launch per trial move) on one chain description, from sweep 0.
+    Returns (positions after the sweeps, sum of accepted dE, counters, CUDA-event milliseconds of the sweeps);
+    counters: accepted, rejected by the Metropolis test, by overlap, by the wall, re-summed canonically."""
+    p = np.ascontiguousarray(chain.pos, dtype=np.float32).reshape(-1, 3)
+    q = np.ascontiguousarray(chain.q, dtype=np.float32)
+    d = _Desc(p.ctypes.data, q.ctypes.data, q.shape[0], float(chain.sigma), float(chain.l_B), float(chain.R),
+              float(chain.half_width), int(chain.seed), int(chain.chain_id))
+    out = np.zeros_like(p)
+    dE = ctypes.c_double()
+    counts = np.zeros(5, np.uint64)
+    ms = ctypes.c_double()
+    _check(lib().mc_reduction_run(ctypes.byref(d), int(n_sweeps), out.ctypes.data, ctypes.byref(dE),
+                                  counts.ctypes.data, ctypes.byref(ms)))
+    keys = ("accepts", "rej_metropolis", "rej_overlap", "rej_wall", "canonical_resums")
+    return out, dE.value, {k: int(v) for k, v in zip(keys, counts)}, ms.value
+
+
+def energy_autocorr(series, max_lag: int):
+    """Sec. 5.2's energy autocorrelation C_0..C_max_lag and T_c = 1/2 + sum_{k=1}^{max_lag} C_k of one series
+    (1-D) or an ensemble of equally long series (2-D, one per row), computed by the library on the host."""
+    e = np.ascontiguousarray(series, dtype=np.float64)
+    if e.ndim == 1:
+        e = e[None, :]
+    C = np.zeros(int(max_lag) + 1, np.float64)
+    tc = ctypes.c_double()
+    _check(lib().mc_energy_autocorr(e.ctypes.data, e.shape[0], e.shape[1], e.shape[1], int(max_lag), C.ctypes.data,
+                                    ctypes.byref(tc)))
+    return C, tc.value
 
 
 def mlp_forward(w_bf16, v) -> np.ndarray:

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmcgb300.so")
-SOURCES = ["mc_sweep.cu", "mc_aux.cu", "mc_da.cu", "mc_api.cu"]
+SOURCES = ["mc_sweep.cu", "mc_aux.cu", "mc_da.cu", "mc_reduction.cu", "mc_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-warn-spills"]
 

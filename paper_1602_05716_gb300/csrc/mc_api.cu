@@ -37,6 +37,9 @@ cudaError_t mlp_wgrad_launch(const float *V, const float *Z, const float *D, lon
                              float *grad, cudaStream_t st);
 cudaError_t adam_launch(float *p, float *m, float *v, const float *g, float lr, float b1, float b2, float eps, float bc1,
                         float bc2, unsigned short *wbf, cudaStream_t st);
+cudaError_t reduction_sweep_launch(const mcg::ChainDev *chd, float4 *pos, int N, unsigned long long *sweep, void *part,
+                                   unsigned *count, double *ledger, unsigned long long *cnt, cudaStream_t st);
+size_t reduction_part_bytes(int N);
 }  // namespace mcg_host
 
 namespace {
@@ -83,6 +86,9 @@ struct Chain {
     mcg::TraceRec *trace = nullptr;
     long long trace_cap = 0;
     unsigned long long rec_sweep0 = 0;
+    double *eser = nullptr;      // energy series (mc_energy_series_enable)
+    long long eser_cap = 0;
+    unsigned long long eser_sweep0 = 0;
     uint64_t sweeps = 0;         // host mirror of *sweep
     uint64_t sweep_base = 0;     // sweep count when the positions were last set from the host
     float4 *cur() const { return pos[sweeps & 1]; }
@@ -218,6 +224,9 @@ mcg::ChainDev describe(const Chain &c)
     d.trace_cap = c.trace_cap;
     d.rec_sweep0 = c.rec_sweep0;
     d.rec_cap = c.rec_cap;
+    d.eser = c.eser;
+    d.eser_cap = c.eser_cap;
+    d.eser_sweep0 = c.eser_sweep0;
     d.N = c.N;
     d.B = c.B;
     d.D = (float)(2.0 * c.h);
@@ -251,7 +260,8 @@ int sync_descriptors(mc_system *h)
     return MC_OK;
 }
 
-int init_chain(mc_system *h, Chain &c, const mc_chain_desc &d)
+// The checks of mc_create on one chain description: parameters, finite inputs, wall and overlap.
+int check_desc(const mc_chain_desc &d)
 {
     if (!d.pos_xyz || !d.q) return fail(MC_ERR_INVALID, "NULL positions or valences");
     if (d.n < 1 || d.n > (int64_t)1 << 30) return fail(MC_ERR_INVALID, "N = %lld out of range", (long long)d.n);
@@ -263,7 +273,12 @@ int init_chain(mc_system *h, Chain &c, const mc_chain_desc &d)
         if (!std::isfinite(d.q[i]) || !std::isfinite(d.pos_xyz[3 * i]) || !std::isfinite(d.pos_xyz[3 * i + 1]) ||
             !std::isfinite(d.pos_xyz[3 * i + 2]))
             return fail(MC_ERR_INVALID, "non-finite input at ion %lld", (long long)i);
-    int rc = validate(d.pos_xyz, d.n, d.sigma, d.R);
+    return validate(d.pos_xyz, d.n, d.sigma, d.R);
+}
+
+int init_chain(mc_system *h, Chain &c, const mc_chain_desc &d)
+{
+    int rc = check_desc(d);
     if (rc) return rc;
     c.N = (int)d.n;
     c.B = (c.N + mcg::S - 1) / mcg::S;
@@ -305,6 +320,7 @@ void free_chain(Chain &c)
     cudaFree(c.rows);
     cudaFree(c.rec);
     cudaFree(c.trace);
+    cudaFree(c.eser);
     cudaFree(c.dda);
     cudaFree(c.d_w);
     cudaFree(c.d_w2n);
@@ -863,6 +879,181 @@ int64_t mc_trace_read(mc_handle h, int chain, mc_trace_rec *out, int64_t cap)
     CK(cudaStreamSynchronize(h->stream));
     if (n > 0) CK(cudaMemcpy(out, c.trace, sizeof(mc_trace_rec) * (size_t)n, cudaMemcpyDeviceToHost));
     return n;
+}
+
+int mc_energy_series_enable(mc_handle h, int chain, int64_t cap)
+{
+    int rc = check_chain(h, chain);
+    if (rc) return rc;
+    if (cap < 0) return fail(MC_ERR_INVALID, "cap < 0");
+    Chain &c = h->chains[chain];
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(c.eser);
+    c.eser = nullptr;
+    c.eser_cap = 0;
+    if (cap > 0) {
+        CK(cudaMalloc(&c.eser, sizeof(double) * (size_t)cap));
+        CK(cudaMemset(c.eser, 0xff, sizeof(double) * (size_t)cap));  // NaN until written
+        c.eser_cap = cap;
+    }
+    c.eser_sweep0 = c.sweeps;
+    return sync_descriptors(h);
+}
+
+int64_t mc_energy_series_read(mc_handle h, int chain, double *out, int64_t cap)
+{
+    int rc = check_chain(h, chain);
+    if (rc) return rc;
+    if (!out || cap < 0) return fail(MC_ERR_INVALID, "bad series buffer");
+    Chain &c = h->chains[chain];
+    CK(cudaStreamSynchronize(h->stream));
+    const int64_t done = c.sweeps > c.eser_sweep0 ? (int64_t)(c.sweeps - c.eser_sweep0) : 0;
+    const int64_t n = std::min<int64_t>(std::min<int64_t>(cap, c.eser_cap), done);
+    if (n > 0) CK(cudaMemcpy(out, c.eser, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+    return n;
+}
+
+int mc_energy_autocorr(const double *series, int64_t n_series, int64_t n_steps, int64_t stride, int64_t max_lag,
+                       double *C, double *Tc)
+{
+    if (!series || !C) return fail(MC_ERR_INVALID, "NULL series or output");
+    if (n_series < 1 || n_steps < 2 || stride < n_steps || max_lag < 0 || max_lag >= n_steps)
+        return fail(MC_ERR_INVALID, "bad shape (series %lld, steps %lld, stride %lld, max_lag %lld)",
+                    (long long)n_series, (long long)n_steps, (long long)stride, (long long)max_lag);
+    // mean over the ensemble and the steps, with a compensated sum (Neumaier) so that the deviations keep their
+    // precision when the mean is large against the fluctuations
+    double sum = 0.0, comp = 0.0;
+    for (int64_t r = 0; r < n_series; ++r)
+        for (int64_t k = 0; k < n_steps; ++k) {
+            const double v = series[r * stride + k];
+            if (!std::isfinite(v)) return fail(MC_ERR_INVALID, "non-finite energy at series %lld step %lld",
+                                               (long long)r, (long long)k);
+            const double t = sum + v;
+            comp += std::fabs(sum) >= std::fabs(v) ? (sum - t) + v : (v - t) + sum;
+            sum = t;
+        }
+    const double mean = (sum + comp) / (double)(n_series * n_steps);
+    std::vector<double> dev((size_t)(n_series * n_steps));
+    for (int64_t r = 0; r < n_series; ++r)
+        for (int64_t k = 0; k < n_steps; ++k) dev[(size_t)(r * n_steps + k)] = series[r * stride + k] - mean;
+    for (int64_t n = 0; n <= max_lag; ++n) {
+        double acc = 0.0;
+        for (int64_t r = 0; r < n_series; ++r) {
+            const double *d = &dev[(size_t)(r * n_steps)];
+            for (int64_t k = 0; k + n < n_steps; ++k) acc += d[k] * d[k + n];
+        }
+        C[n] = acc / (double)(n_series * (n_steps - n));
+    }
+    const double var = C[0];
+    if (!(var > 0.0)) return fail(MC_ERR_INVALID, "the energy series has no variance");
+    C[0] = 1.0;
+    double tc = 0.5;
+    for (int64_t n = 1; n <= max_lag; ++n) {
+        C[n] /= var;
+        tc += C[n];
+    }
+    if (Tc) *Tc = tc;
+    return MC_OK;
+}
+
+int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, float *pos_out, double *dE_sum,
+                     uint64_t *counts, double *ms)
+{
+    if (!desc) return fail(MC_ERR_INVALID, "NULL description");
+    int rc = check_desc(*desc);
+    if (rc) return rc;
+    if (n_sweeps < 0) return fail(MC_ERR_INVALID, "n_sweeps < 0");
+    if (!pos_out) return fail(MC_ERR_INVALID, "NULL output positions");
+    const mc_chain_desc &d = *desc;
+    Chain c;
+    c.N = (int)d.n;
+    c.B = (c.N + mcg::S - 1) / mcg::S;
+    c.sigma = d.sigma;
+    c.lB = d.l_B;
+    c.R = d.R;
+    c.h = d.half_width;
+    c.seed = d.seed;
+    c.chain_id = d.chain_id;
+    c.q.assign(d.q, d.q + d.n);
+    const mcg::ChainDev hd = describe(c);  // Philox key, trial width, wall, sigma^2, l_B, N
+    // device state, released on every path
+    struct Dev {
+        mcg::ChainDev *chd = nullptr;
+        float4 *pos = nullptr;
+        void *part = nullptr;
+        unsigned char *slab = nullptr;  // count (u32, padded to 8), sweep (u64), ledger (f64), 5 counters (u64)
+        cudaStream_t st = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Dev()
+        {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (st) cudaStreamDestroy(st);
+            cudaFree(chd);
+            cudaFree(pos);
+            cudaFree(part);
+            cudaFree(slab);
+        }
+    } v;
+    const int N = c.N;
+    std::vector<float4> hp((size_t)N);
+    for (int i = 0; i < N; ++i)
+        hp[(size_t)i] = make_float4(d.pos_xyz[3 * i], d.pos_xyz[3 * i + 1], d.pos_xyz[3 * i + 2], d.q[i]);
+    CK(cudaStreamCreateWithFlags(&v.st, cudaStreamNonBlocking));
+    CK(cudaMalloc(&v.chd, sizeof(mcg::ChainDev)));
+    CK(cudaMalloc(&v.pos, sizeof(float4) * (size_t)N));
+    CK(cudaMalloc(&v.part, mcg_host::reduction_part_bytes(N)));
+    constexpr size_t SLAB = 8 + 8 + 8 + 5 * 8;
+    CK(cudaMalloc(&v.slab, SLAB));
+    unsigned *count = reinterpret_cast<unsigned *>(v.slab);
+    unsigned long long *sweep = reinterpret_cast<unsigned long long *>(v.slab + 8);
+    double *ledger = reinterpret_cast<double *>(v.slab + 16);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(v.slab + 24);
+    CK(cudaMemsetAsync(v.slab, 0, SLAB, v.st));
+    CK(cudaMemcpyAsync(v.chd, &hd, sizeof hd, cudaMemcpyHostToDevice, v.st));
+    CK(cudaMemcpyAsync(v.pos, hp.data(), sizeof(float4) * (size_t)N, cudaMemcpyHostToDevice, v.st));
+    CK(cudaEventCreate(&v.e0));
+    CK(cudaEventCreate(&v.e1));
+    // one sweep = N launches: captured once into a graph for N up to 2^16, plain launches above
+    const bool graph = N <= (1 << 16);
+    if (graph && n_sweeps > 0) {
+        CK(cudaStreamBeginCapture(v.st, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = mcg_host::reduction_sweep_launch(v.chd, v.pos, N, sweep, v.part, count, ledger, cnt, v.st);
+        const cudaError_t ce = cudaStreamEndCapture(v.st, &v.graph);
+        CK(le);
+        CK(ce);
+        CK(cudaGraphInstantiate(&v.exec, v.graph, 0));
+    }
+    CK(cudaEventRecord(v.e0, v.st));
+    for (int64_t s = 0; s < n_sweeps; ++s) {
+        if (graph) CK(cudaGraphLaunch(v.exec, v.st));
+        else CK(mcg_host::reduction_sweep_launch(v.chd, v.pos, N, sweep, v.part, count, ledger, cnt, v.st));
+    }
+    CK(cudaEventRecord(v.e1, v.st));
+    CK(cudaStreamSynchronize(v.st));
+    if (ms) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, v.e0, v.e1));
+        *ms = (double)t;
+    }
+    CK(cudaMemcpy(hp.data(), v.pos, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < N; ++i) {
+        pos_out[3 * i] = hp[(size_t)i].x;
+        pos_out[3 * i + 1] = hp[(size_t)i].y;
+        pos_out[3 * i + 2] = hp[(size_t)i].z;
+    }
+    double led = 0.0;
+    unsigned long long hc[5];
+    CK(cudaMemcpy(&led, ledger, sizeof led, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost));
+    if (dE_sum) *dE_sum = led;
+    if (counts)
+        for (int q = 0; q < 5; ++q) counts[q] = hc[q];
+    return MC_OK;
 }
 
 int64_t mc_record_read(mc_handle h, int chain, mc_record *out, int64_t cap)

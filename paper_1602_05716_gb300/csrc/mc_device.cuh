@@ -71,6 +71,9 @@ struct ChainDev {
     long long trace_cap;
     unsigned long long rec_sweep0;  // sweep at which recording started
     long long rec_cap;
+    double *eser;                 // energy series: the ledger after each sweep (mc_energy_series_enable) or nullptr
+    long long eser_cap;
+    unsigned long long eser_sweep0;  // sweep stored in eser[0]
     int N;
     int B;                        // groups: ceil(N / S)
     float D;                      // fl32(2h)

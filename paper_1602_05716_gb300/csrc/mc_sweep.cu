@@ -2086,7 +2086,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         }
         if (ok) {
             volatile double *L = ch.ledger;
-            *L = *L + gsum;
+            const double e = *L + gsum;
+            *L = e;
+            // the last group of sweep s folded: e is the total energy after that sweep (Sec. 5.2's E_k)
+            if (g == B - 1 && ch.eser && s >= ch.eser_sweep0 && s - ch.eser_sweep0 < (unsigned long long)ch.eser_cap)
+                ch.eser[s - ch.eser_sweep0] = e;
             st_release(ch.ledger_seq, me + 1);
         }
         sm.ok = ok ? 1 : 0;

@@ -254,6 +254,70 @@ def test_deep_windows_option(pkg, nchains):
         _compare_records(s.records(q), o.records(), ch.n)
 
 
+@pytest.mark.parametrize("n,two_one,phi,sweeps", [(2, False, 0.05, 20), (33, True, 0.1, 6), (1500, True, 0.2, 2),
+                                                  (2100, False, 0.25, 1)])
+def test_reduction_foil_matches_oracle(pkg, n, two_one, phi, sweeps):
+    """Sec. 4's parallel-reduction code (one launch per trial move, 1,024-thread blocks, the last block decides):
+    positions and counters identical to the oracle's after the same sweeps (one block, several blocks with a
+    ragged last one); the accepted dE sum within the ledger tolerance."""
+    import paper_1602_05716_gb300 as p
+    ch = inputs.small_chain(n, phi=phi, seed=900 + n, two_one=two_one, half_width=0.4)
+    pos, dE, cnt, ms = p.reduction_run(ch, sweeps)
+    oc = oracle.OracleChain.from_chain(ch, threads=THREADS)
+    led0, rec0 = oc.energy()
+    oc.sweep(sweeps)
+    assert (pos == oc.positions()).all()
+    so = oc.stats()
+    assert (cnt["accepts"], cnt["rej_metropolis"], cnt["rej_overlap"], cnt["rej_wall"]) == \
+        (so["accept"], so["rej_metropolis"], so["rej_overlap"], so["rej_wall"])
+    led1, _ = oc.energy(recompute=False)
+    assert abs(dE - (led1 - led0)) < 1e-9 * max(1.0, abs(rec0)) * max(1, n / 100)
+    assert ms > 0.0
+
+
+def test_energy_series_matches_oracle_ledger(pkg):
+    """Sec. 5.2's E_k: the ledger stored by the sweep kernel after every sweep, across single- and multi-sweep
+    launches and CUDA-graph replays: equal to the ledger read after the same sweep, within the ledger tolerance
+    of the oracle's after each sweep, nothing stored past the capacity; C_n and T_c of the stored series against
+    the oracle's definition on the oracle's series."""
+    import paper_1602_05716_gb300 as p
+    n = 700
+    ch = inputs.small_chain(n, phi=0.2, seed=4242, two_one=True, half_width=0.4)
+    gs, oc = _pair(ch)
+    cap = 12
+    gs.energy_series_enable(cap)
+    led_o, done, after3 = [], 0, None
+    for st in [1, 1, 1, 5, 4, 2]:  # 14 sweeps: the last two past the capacity
+        gs.sweep(st)
+        for _ in range(st):
+            oc.sweep(1)
+            led_o.append(oc.energy(recompute=False)[0])
+        done += st
+        if done == 3:
+            after3 = gs.energy(recompute=False)[0]
+    assert (gs.positions() == oc.positions()).all()
+    E = gs.energy_series()
+    Eo = np.array(led_o[:cap])
+    assert E.shape == (cap,) and np.isfinite(E).all()
+    assert E[2] == after3
+    scale = max(1.0, abs(oc.energy()[1]))
+    delta = np.abs(E - Eo).max()
+    assert delta < 1e-6 * scale * max(1, n / 100)
+    C_g, t_g = p.energy_autocorr(E, 5)
+    C_o, t_o = oracle.energy_autocorr(Eo, 5)
+    # a perturbation of at most delta per entry moves each C_n by at most about 8 delta max|E - E-bar| / var
+    dev = Eo - Eo.mean()
+    tol = 8.0 * delta * np.abs(dev).max() / np.mean(dev * dev) + 1e-12
+    assert np.abs(C_g - C_o).max() <= tol and abs(t_g - t_o) <= 6 * tol
+    # a second chain of a batch records only when enabled
+    ch2 = inputs.small_chain(300, phi=0.15, seed=77)
+    s2 = p.System([ch, ch2])
+    s2.energy_series_enable(4, chain=1)
+    s2.sweep(3)
+    assert s2.energy_series(0).shape == (0,) and s2.energy_series(1).shape == (3,)
+    assert s2.energy_series(1)[-1] == s2.energy(chain=1, recompute=False)[0]
+
+
 @pytest.mark.parametrize("pairs", [0, 1])
 def test_bounded_wait_fault_injection(pkg, pairs):
     """A work item that never publishes: every waiter gives up after the timeout, the call returns
