@@ -223,6 +223,45 @@ int64_t mc_energy_series_read(mc_handle h, int chain, double *out, int64_t cap);
 int mc_energy_autocorr(const double *series, int64_t n_series, int64_t n_steps, int64_t stride, int64_t max_lag,
                        double *C, double *Tc);
 
+/* Dressed-ion analysis of pair correlations (Sec. 5.2): renormalised inverse
+ * Debye length, valences and dielectric constant from the far field of
+ * g_{++}, g_{+-}, g_{--}.  Reduced units: lengths in sigma, energies in k_BT,
+ * eps = 1 / (4 pi l_B).  Host only, no device and no handle.
+ *   counts     3 x n_bins pair counts as mc_gr_histogram returns them (++,
+ *              mixed, --), summed over any number of configurations
+ *   n_ref_p/m  the interior reference ions of each sign behind those counts
+ *              (summed over the same configurations)
+ *   dens_p/m   number densities of the positive and negative ions
+ *   q_p, q_m   bare valences (q_p > 0 > q_m)
+ *   r_lo..r_hi the far-field window: bins whose centre (k + 1/2) dr lies in it
+ * Steps: g_ab(bin) = counts / (N_ref,a n_b V_bin) (mixed: counts /
+ * ((N_ref,+ n_- + N_ref,- n_+) V_bin)); U_ab = -ln g_ab; rho^q_+ = n_+ q_+
+ * g_{++} + n_- q_- g_{+-}, rho^q_- = n_+ q_+ g_{+-} + n_- q_- g_{--};
+ * ln|r rho^q_+-| fitted by least squares with one common slope -kappa_R (and
+ * each line's own slope); q^R from -kappa_R^2 U / (4 pi l_B rho^q) averaged
+ * over the window, two ways for each sign; eps_R / eps from -kappa_R^2 q^R
+ * e^{-kappa_R r} / (4 pi r rho^q) averaged likewise; and both sides of
+ * (kappa_R / kappa)^2 = (q_+^R - q_-^R) / (q_+ - q_-).  Window bins with an
+ * empty class or rho^q of the wrong sign (not screening) are skipped.
+ *   g          (nullable) 3 x n_bins: the normalised g_ab (NaN where the
+ *              normalisation is zero)
+ *   out        the parameters; MC_ERR_INVALID for NULL counts/out, bad sizes
+ *              or parameters, or fewer than 2 usable window bins.          */
+typedef struct {
+    double kappa;         /* bare: sqrt(4 pi l_B (n_+ q_+^2 + n_- q_-^2)) */
+    double kappa_R;       /* common far-field slope of ln|r rho^q_+| and ln|r rho^q_-| */
+    double kappa_R_pm[2]; /* each line's own slope: around a positive, around a negative ion */
+    double qR_p[2];       /* q_+^R from U_{++} / rho^q_+ and from U_{-+} / rho^q_- */
+    double qR_m[2];       /* q_-^R from U_{+-} / rho^q_+ and from U_{--} / rho^q_- */
+    double epsR_pm[2];    /* eps_R / eps around a positive and a negative ion */
+    double rd_lhs;        /* (kappa_R / kappa)^2 */
+    double rd_rhs;        /* (q_+^R - q_-^R) / (q_+ - q_-), each q^R the mean of its two estimates */
+    int64_t n_fit;        /* window bins used */
+} mc_dit_result;
+int mc_dressed_ion_analysis(const uint64_t *counts, int n_bins, double r_max, double n_ref_p, double n_ref_m,
+                            double dens_p, double dens_m, double q_p, double q_m, double l_B, double r_lo,
+                            double r_hi, double *g, mc_dit_result *out);
+
 /* The parallel-reduction comparison code of Sec. 4, as a foil for mc_sweep:
  * one kernel launch per trial move, the N - 1 pair terms spread over blocks
  * of 1,024 threads (one pair each), block subtotals left in global memory and

@@ -11,14 +11,18 @@ distance distribution, the ideal-gas limit and the Debye-Hueckel limiting law). 
 pinned by finite differences of the MLP gradient, libm's exp, brute-force features and near-field sums, exact
 antisymmetry of the surrogate energy change, and the exact confined-pair distribution sampled by the
 delayed-acceptance chain.  The energy autocorrelation (Sec. 5.2) is pinned by values derived by hand from its
-definition, exact alternating series, affine invariance and the AR(1) closed form.
+definition, exact alternating series, affine invariance and the AR(1) closed form; the dressed-ion
+analysis (Sec. 5.2) by the ideal gas (g = 1), synthetic far fields of known renormalised parameters and
+the Debye-Hueckel limit.
 """
 from .oracle import (OracleChain, build, lib, philox4x32_10, move_draws, log_L, total_energy,
                      RECORD_DTYPE, ACCEPT, REJECT_METROPOLIS, REJECT_OVERLAP, REJECT_WALL,
                      DA_REJECT1, DA_RECORD_DTYPE, MLP_NIN, MLP_H, MLP_NP, exp_D, bf16_to_f64, f64_to_bf16,
-                     mlp_forward, mlp_loss_grad, energy_autocorr)
+                     mlp_forward, mlp_loss_grad, energy_autocorr, dressed_ion_analysis,
+                     pair_correlations)
 
 __all__ = ["OracleChain", "build", "lib", "philox4x32_10", "move_draws", "log_L", "total_energy",
            "RECORD_DTYPE", "ACCEPT", "REJECT_METROPOLIS", "REJECT_OVERLAP", "REJECT_WALL",
            "DA_REJECT1", "DA_RECORD_DTYPE", "MLP_NIN", "MLP_H", "MLP_NP", "exp_D", "bf16_to_f64", "f64_to_bf16",
-           "mlp_forward", "mlp_loss_grad", "energy_autocorr"]
+           "mlp_forward", "mlp_loss_grad", "energy_autocorr", "dressed_ion_analysis",
+           "pair_correlations"]

@@ -183,6 +183,64 @@ def energy_autocorr(series, max_lag: int):
     return C, 0.5 + float(np.sum(C[1:]))
 
 
+def pair_correlations(counts, r_max, n_ref_p, n_ref_m, dens_p, dens_m):
+    """g_{++}, g_{+-}, g_{--} from ordered-pair counts around reference ions: counts / (N_ref,a n_b V_shell), the
+    mixed class around both signs, V_shell = 4/3 pi (r_{k+1}^3 - r_k^3); NaN where the normalisation is 0."""
+    counts = np.asarray(counts, dtype=np.float64).reshape(3, -1)
+    n_bins = counts.shape[1]
+    edges = (r_max / n_bins) * np.arange(n_bins + 1)
+    vshell = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    norm = np.stack([n_ref_p * dens_p * vshell, (n_ref_p * dens_m + n_ref_m * dens_p) * vshell,
+                     n_ref_m * dens_m * vshell])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(norm > 0, counts / norm, np.nan)
+
+
+def dressed_ion_analysis(counts, r_max, n_ref_p, n_ref_m, dens_p, dens_m, q_p, q_m, l_B, r_lo, r_hi):
+    """Sec. 5.2's dressed-ion analysis, step by step in the paper's order (reduced units: lengths in sigma,
+    energies in k_BT, eps = 1/(4 pi l_B)).  counts: 3 x n_bins ordered-pair counts (++, mixed, --) around
+    n_ref_p / n_ref_m reference ions.  Returns a dict with g, kappa, kappa_R (common slope), kappa_R_pm, qR_p,
+    qR_m (two estimates each), epsR_pm, rd_lhs, rd_rhs, n_fit.
+      g_ab = counts / (N_ref,a n_b V_shell)        (pair correlations from the histogram)
+      U_ab = -ln g_ab                               (potential of mean force)
+      rho^q_a = n_+ q_+ g_{+a} + n_- q_- g_{-a}     (charge density around a fixed ion of sign a)
+      ln|r rho^q_a| = const - kappa_R r             (far-field line; one slope for both signs)
+      q^R = -eps kappa_R^2 U / rho^q                (two ways for each sign)
+      eps_R = -eps kappa_R^2 q^R e^{-kappa_R r} / (4 pi r rho^q)
+      (kappa_R / kappa)^2 vs (q_+^R - q_-^R) / (q_+ - q_-)."""
+    g = pair_correlations(counts, r_max, n_ref_p, n_ref_m, dens_p, dens_m)
+    n_bins = g.shape[1]
+    dr = r_max / n_bins
+    gpp, gpm, gmm = g
+    r = dr * (np.arange(n_bins) + 0.5)
+    rho_p = dens_p * q_p * gpp + dens_m * q_m * gpm
+    rho_m = dens_p * q_p * gpm + dens_m * q_m * gmm
+    use = (r >= r_lo) & (r <= r_hi) & (gpp > 0) & (gpm > 0) & (gmm > 0) & (rho_p < 0) & (rho_m > 0)
+    if use.sum() < 2:
+        raise ValueError("fewer than 2 usable bins in the window")
+    r, rho_p, rho_m = r[use], rho_p[use], rho_m[use]
+    U_pp, U_pm, U_mm = -np.log(gpp[use]), -np.log(gpm[use]), -np.log(gmm[use])
+    y_p, y_m = np.log(np.abs(r * rho_p)), np.log(np.abs(r * rho_m))
+    slope_p = np.linalg.lstsq(np.stack([np.ones_like(r), r], 1), y_p, rcond=None)[0][1]
+    slope_m = np.linalg.lstsq(np.stack([np.ones_like(r), r], 1), y_m, rcond=None)[0][1]
+    n = r.size
+    A = np.zeros((2 * n, 3))
+    A[:n, 0] = 1.0
+    A[n:, 1] = 1.0
+    A[:, 2] = np.concatenate([r, r])
+    kappa_R = -np.linalg.lstsq(A, np.concatenate([y_p, y_m]), rcond=None)[0][2]
+    eps = 1.0 / (4.0 * np.pi * l_B)
+    qR_p = (np.mean(-eps * kappa_R ** 2 * U_pp / rho_p), np.mean(-eps * kappa_R ** 2 * U_pm / rho_m))
+    qR_m = (np.mean(-eps * kappa_R ** 2 * U_pm / rho_p), np.mean(-eps * kappa_R ** 2 * U_mm / rho_m))
+    qp, qm = np.mean(qR_p), np.mean(qR_m)
+    epsR = (np.mean(-kappa_R ** 2 * qp * np.exp(-kappa_R * r) / (4 * np.pi * r * rho_p)),
+            np.mean(-kappa_R ** 2 * qm * np.exp(-kappa_R * r) / (4 * np.pi * r * rho_m)))
+    kappa = np.sqrt(4.0 * np.pi * l_B * (dens_p * q_p ** 2 + dens_m * q_m ** 2))
+    return dict(g=g, kappa=float(kappa), kappa_R=float(kappa_R), kappa_R_pm=(float(-slope_p), float(-slope_m)),
+                qR_p=tuple(map(float, qR_p)), qR_m=tuple(map(float, qR_m)), epsR_pm=tuple(map(float, epsR)),
+                rd_lhs=float((kappa_R / kappa) ** 2), rd_rhs=float((qp - qm) / (q_p - q_m)), n_fit=int(n))
+
+
 class OracleChain:
     """One sequential Metropolis chain, FP64 canonical arithmetic (mco_* API)."""
 

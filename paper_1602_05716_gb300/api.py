@@ -42,6 +42,12 @@ class _Desc(ctypes.Structure):
                 ("half_width", ctypes.c_double), ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32)]
 
 
+class _DIT(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("kappa_R", ctypes.c_double), ("kappa_R_pm", ctypes.c_double * 2),
+                ("qR_p", ctypes.c_double * 2), ("qR_m", ctypes.c_double * 2), ("epsR_pm", ctypes.c_double * 2),
+                ("rd_lhs", ctypes.c_double), ("rd_rhs", ctypes.c_double), ("n_fit", ctypes.c_int64)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in _STATS_FIELDS]
 
@@ -88,6 +94,8 @@ def lib():
         "mc_energy_series_read": ([vp, ci, vp, i64], i64),
         "mc_energy_autocorr": ([vp, i64, i64, i64, i64, vp, vp], ci),
         "mc_reduction_run": ([ctypes.POINTER(_Desc), i64, vp, vp, vp, vp], ci),
+        "mc_dressed_ion_analysis": ([vp, ci, dbl, dbl, dbl, dbl, dbl, dbl, dbl, dbl, dbl, dbl, vp,
+                                     ctypes.POINTER(_DIT)], ci),
         "mc_set_option": ([vp, ci, i64], ci),
         "mc_get_option": ([vp, ci, vp], ci),
         "mc_autotune": ([vp, i64, vp, vp, vp], ci),
@@ -330,6 +338,21 @@ def reduction_run(chain, n_sweeps: int):
                                   counts.ctypes.data, ctypes.byref(ms)))
     keys = ("accepts", "rej_metropolis", "rej_overlap", "rej_wall", "canonical_resums")
     return out, dE.value, {k: int(v) for k, v in zip(keys, counts)}, ms.value
+
+
+def dressed_ion_analysis(counts, r_max, n_ref_p, n_ref_m, dens_p, dens_m, q_p, q_m, l_B, r_lo, r_hi):
+    """Sec. 5.2's renormalised parameters from g(r) counts (3 x n_bins as mc_gr_histogram returns them), computed
+    by the library on the host.  Returns a dict: g (3 x n_bins), kappa, kappa_R, kappa_R_pm, qR_p, qR_m, epsR_pm,
+    rd_lhs, rd_rhs, n_fit."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64).reshape(3, -1)
+    n_bins = c.shape[1]
+    g = np.zeros((3, n_bins), np.float64)
+    o = _DIT()
+    _check(lib().mc_dressed_ion_analysis(c.ctypes.data, n_bins, float(r_max), float(n_ref_p), float(n_ref_m),
+                                         float(dens_p), float(dens_m), float(q_p), float(q_m), float(l_B),
+                                         float(r_lo), float(r_hi), g.ctypes.data, ctypes.byref(o)))
+    return dict(g=g, kappa=o.kappa, kappa_R=o.kappa_R, kappa_R_pm=tuple(o.kappa_R_pm), qR_p=tuple(o.qR_p),
+                qR_m=tuple(o.qR_m), epsR_pm=tuple(o.epsR_pm), rd_lhs=o.rd_lhs, rd_rhs=o.rd_rhs, n_fit=int(o.n_fit))
 
 
 def energy_autocorr(series, max_lag: int):

@@ -956,6 +956,98 @@ int mc_energy_autocorr(const double *series, int64_t n_series, int64_t n_steps, 
     return MC_OK;
 }
 
+int mc_dressed_ion_analysis(const uint64_t *counts, int n_bins, double r_max, double n_ref_p, double n_ref_m,
+                            double dens_p, double dens_m, double q_p, double q_m, double l_B, double r_lo,
+                            double r_hi, double *g, mc_dit_result *out)
+{
+    if (!counts || !out) return fail(MC_ERR_INVALID, "NULL counts or result");
+    if (n_bins < 2 || !(r_max > 0.0) || !(n_ref_p >= 0.0) || !(n_ref_m >= 0.0) || !(dens_p > 0.0) ||
+        !(dens_m > 0.0) || !(q_p > 0.0) || !(q_m < 0.0) || !(l_B > 0.0) || !(r_lo < r_hi) || !std::isfinite(r_hi))
+        return fail(MC_ERR_INVALID, "bad analysis parameters");
+    const double PI = 3.14159265358979323846;
+    const double dr = r_max / (double)n_bins;
+    std::vector<double> gg((size_t)3 * n_bins);
+    for (int k = 0; k < n_bins; ++k) {
+        const double r0 = dr * k, r1 = dr * (k + 1);
+        const double vb = 4.0 / 3.0 * PI * (r1 * r1 * r1 - r0 * r0 * r0);
+        const double norm[3] = {n_ref_p * dens_p * vb, (n_ref_p * dens_m + n_ref_m * dens_p) * vb,
+                                n_ref_m * dens_m * vb};
+        for (int c = 0; c < 3; ++c)
+            gg[(size_t)c * n_bins + k] = norm[c] > 0.0 ? (double)counts[(size_t)c * n_bins + k] / norm[c] : NAN;
+    }
+    if (g)
+        for (size_t t = 0; t < gg.size(); ++t) g[t] = gg[t];
+    // usable window bins: all three classes populated, both charge densities screening
+    std::vector<double> rr, yp, ym, Upp, Upm, Umm, rhp, rhm;
+    for (int k = 0; k < n_bins; ++k) {
+        const double r = dr * (k + 0.5);
+        if (r < r_lo || r > r_hi) continue;
+        const double gpp = gg[k], gpm = gg[(size_t)n_bins + k], gmm = gg[(size_t)2 * n_bins + k];
+        if (!(gpp > 0.0 && gpm > 0.0 && gmm > 0.0)) continue;
+        const double rho_p = dens_p * q_p * gpp + dens_m * q_m * gpm;  // around a positive ion
+        const double rho_m = dens_p * q_p * gpm + dens_m * q_m * gmm;  // around a negative ion
+        if (!(rho_p < 0.0 && rho_m > 0.0)) continue;
+        rr.push_back(r);
+        yp.push_back(std::log(std::fabs(r * rho_p)));
+        ym.push_back(std::log(std::fabs(r * rho_m)));
+        Upp.push_back(-std::log(gpp));
+        Upm.push_back(-std::log(gpm));
+        Umm.push_back(-std::log(gmm));
+        rhp.push_back(rho_p);
+        rhm.push_back(rho_m);
+    }
+    const size_t nf = rr.size();
+    if (nf < 2) return fail(MC_ERR_INVALID, "fewer than 2 usable bins in the window [%g, %g]", r_lo, r_hi);
+    // least squares: one slope each, and one common slope with an intercept per line
+    double rm = 0.0, ypm = 0.0, ymm = 0.0;
+    for (size_t t = 0; t < nf; ++t) {
+        rm += rr[t];
+        ypm += yp[t];
+        ymm += ym[t];
+    }
+    rm /= (double)nf;
+    ypm /= (double)nf;
+    ymm /= (double)nf;
+    double sxx = 0.0, sxp = 0.0, sxm = 0.0;
+    for (size_t t = 0; t < nf; ++t) {
+        const double dx = rr[t] - rm;
+        sxx += dx * dx;
+        sxp += dx * (yp[t] - ypm);
+        sxm += dx * (ym[t] - ymm);
+    }
+    mc_dit_result o{};
+    o.kappa = std::sqrt(4.0 * PI * l_B * (dens_p * q_p * q_p + dens_m * q_m * q_m));
+    o.kappa_R_pm[0] = -sxp / sxx;
+    o.kappa_R_pm[1] = -sxm / sxx;
+    o.kappa_R = -(sxp + sxm) / (2.0 * sxx);  // the same abscissae on both lines
+    const double k2 = o.kappa_R * o.kappa_R, c4 = 4.0 * PI * l_B;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t t = 0; t < nf; ++t) {
+        a[0] += -k2 * Upp[t] / (c4 * rhp[t]);  // q_+^R around a positive ion
+        a[1] += -k2 * Upm[t] / (c4 * rhm[t]);  // q_+^R around a negative ion (U_{-+} = U_{+-})
+        a[2] += -k2 * Upm[t] / (c4 * rhp[t]);  // q_-^R around a positive ion
+        a[3] += -k2 * Umm[t] / (c4 * rhm[t]);  // q_-^R around a negative ion
+    }
+    o.qR_p[0] = a[0] / (double)nf;
+    o.qR_p[1] = a[1] / (double)nf;
+    o.qR_m[0] = a[2] / (double)nf;
+    o.qR_m[1] = a[3] / (double)nf;
+    const double qp = 0.5 * (o.qR_p[0] + o.qR_p[1]), qm = 0.5 * (o.qR_m[0] + o.qR_m[1]);
+    double ep = 0.0, em = 0.0;
+    for (size_t t = 0; t < nf; ++t) {
+        const double e = std::exp(-o.kappa_R * rr[t]) / (4.0 * PI * rr[t]);
+        ep += -k2 * qp * e / rhp[t];
+        em += -k2 * qm * e / rhm[t];
+    }
+    o.epsR_pm[0] = ep / (double)nf;
+    o.epsR_pm[1] = em / (double)nf;
+    o.rd_lhs = k2 / (o.kappa * o.kappa);
+    o.rd_rhs = (qp - qm) / (q_p - q_m);
+    o.n_fit = (int64_t)nf;
+    *out = o;
+    return MC_OK;
+}
+
 int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, float *pos_out, double *dE_sum,
                      uint64_t *counts, double *ms)
 {

@@ -1,0 +1,180 @@
+"""Dressed-ion analysis of pair correlations (Sec. 5.2): renormalised inverse Debye length, valences and
+dielectric constant from the far field of g_{++}, g_{+-}, g_{--}.
+
+The oracle is pinned to the ideal gas (g = 1 from independently counted uniform points), to synthetic far fields
+built here from the dressed-ion forms with known parameters, and to the Debye-Hueckel limit; the library's host
+function is then checked against the oracle.  No device is used."""
+import numpy as np
+import pytest
+
+import oracle
+
+PI = np.pi
+
+
+def _synthetic_counts(r_max, n_bins, n_ref, dens, qR, lB, eps_ratio, kappa_R):
+    """Ordered-pair counts N_ref,a n_b V_shell g_ab(r_k) at the bin centres, with the linear-response g_ab = 1 - U_ab
+    and U_ab = l_B (eps/eps_R) q_a^R q_b^R e^{-kappa_R r} / r.  With kappa_R^2 = 4 pi l_B sum_a n_a q_a q_a^R and a
+    neutral mixture, rho^q_a = -(kappa_R^2 / 4 pi)(eps/eps_R) q_a^R e^{-kappa_R r} / r holds exactly; only
+    -ln g = U + U^2/2 + ... departs from U."""
+    dr = r_max / n_bins
+    edges = dr * np.arange(n_bins + 1)
+    vsh = 4.0 / 3.0 * PI * (edges[1:] ** 3 - edges[:-1] ** 3)
+    r = dr * (np.arange(n_bins) + 0.5)
+    f = lB / eps_ratio * np.exp(-kappa_R * r) / r
+    U = {"pp": f * qR[0] * qR[0], "pm": f * qR[0] * qR[1], "mm": f * qR[1] * qR[1]}
+    c = np.stack([n_ref[0] * dens[0] * vsh * (1 - U["pp"]),
+                  (n_ref[0] * dens[1] + n_ref[1] * dens[0]) * vsh * (1 - U["pm"]),
+                  n_ref[1] * dens[1] * vsh * (1 - U["mm"])])
+    return np.rint(c).astype(np.uint64)
+
+
+# 3:-1 at the paper's kind of state point: bare valences 3 and -1, renormalised 4 and -0.9 (Sec. 5.2 reports
+# 4.125 and -0.884), eps_R / eps = 1.3
+Q = (3.0, -1.0)
+DENS = (0.002, 0.006)
+LB = 0.95
+NREF = (1.0e15, 3.0e15)
+R_MAX, NB = 24.0, 240
+WIN = (12.0, 20.0)
+
+
+def _case(qR, eps_ratio):
+    kR = np.sqrt(4 * PI * LB * (DENS[0] * Q[0] * qR[0] + DENS[1] * Q[1] * qR[1]))
+    c = _synthetic_counts(R_MAX, NB, NREF, DENS, qR, LB, eps_ratio, kR)
+    return c, kR
+
+
+def _run_oracle(c):
+    return oracle.dressed_ion_analysis(c, R_MAX, NREF[0], NREF[1], DENS[0], DENS[1], Q[0], Q[1], LB, *WIN)
+
+
+def test_oracle_recovers_synthetic_far_field():
+    """kappa_R to rounding (the charge densities are exact), q^R and eps_R / eps within the window's largest U
+    (about 8e-4 at r = 12 for the ++ pair: -ln(1 - U) = U (1 + U/2 + ...)), both sides of the RD relation, and
+    the bare kappa = sqrt(4 pi l_B sum n q^2)."""
+    qR, er = (4.0, -0.9), 1.3
+    c, kR = _case(qR, er)
+    o = _run_oracle(c)
+    assert o["n_fit"] == 80
+    assert abs(o["kappa"] - np.sqrt(4 * PI * LB * (DENS[0] * 9 + DENS[1]))) < 1e-14
+    assert abs(o["kappa_R"] / kR - 1) < 1e-6
+    assert all(abs(k / kR - 1) < 1e-6 for k in o["kappa_R_pm"])
+    assert all(abs(v / qR[0] - 1) < 2e-3 for v in o["qR_p"])
+    assert all(abs(v / qR[1] - 1) < 2e-3 for v in o["qR_m"])
+    assert all(abs(v / er - 1) < 4e-3 for v in o["epsR_pm"])
+    assert abs(o["rd_lhs"] - (kR / o["kappa"]) ** 2) < 1e-6
+    assert abs(o["rd_rhs"] / o["rd_lhs"] - 1) < 2e-3
+    # the relation holds for the construction: (kappa_R / kappa)^2 = (q+^R - q-^R) / (q+ - q-)
+    assert abs((qR[0] - qR[1]) / (Q[0] - Q[1]) - o["rd_lhs"]) < 1e-6
+
+
+def test_oracle_debye_hueckel_limit():
+    """Unrenormalised far field (q^R = q, eps_R = eps, hence kappa_R = kappa): every ratio is 1."""
+    c, kR = _case(Q, 1.0)
+    o = _run_oracle(c)
+    assert abs(kR / o["kappa"] - 1) < 1e-14
+    assert abs(o["kappa_R"] / o["kappa"] - 1) < 1e-6
+    assert all(abs(v / Q[0] - 1) < 2e-3 for v in o["qR_p"]) and all(abs(v / Q[1] - 1) < 2e-3 for v in o["qR_m"])
+    assert all(abs(v - 1) < 4e-3 for v in o["epsR_pm"])
+    assert abs(o["rd_lhs"] - 1) < 1e-5 and abs(o["rd_rhs"] - 1) < 2e-3
+
+
+def _ideal_gas_counts(n_each, Rb, r_max, n_bins, seed):
+    """Uniform points in a ball of radius Rb, half positive, half negative; ordered pairs (i interior, i.e. at
+    least r_max from the boundary; j any other point) counted by brute force."""
+    rng = np.random.default_rng(seed)
+    n = 2 * n_each
+    x = rng.standard_normal((n, 3))
+    x *= (Rb * rng.random(n) ** (1 / 3) / np.linalg.norm(x, axis=1))[:, None]
+    s = np.where(np.arange(n) < n_each, 1, -1)
+    interior = np.linalg.norm(x, axis=1) <= Rb - r_max
+    counts = np.zeros((3, n_bins), np.uint64)
+    dr = r_max / n_bins
+    for i in np.nonzero(interior)[0]:
+        d = np.linalg.norm(x - x[i], axis=1)
+        d[i] = np.inf
+        k = np.floor(d / dr)
+        ok = k < n_bins
+        cls = np.where((s[i] > 0) & (s > 0), 0, np.where((s[i] < 0) & (s < 0), 2, 1))
+        np.add.at(counts, (cls[ok], k[ok].astype(np.int64)), 1)
+    n_ref = (int((interior & (s > 0)).sum()), int((interior & (s < 0)).sum()))
+    V = 4.0 / 3.0 * PI * Rb ** 3
+    return counts, n_ref, (n_each / V, n_each / V)
+
+
+def test_oracle_pair_correlations_ideal_gas():
+    """g = 1 for independent uniform points, counts and reference ions summed over four configurations as the
+    histogram is meant to be used.  Besides each bin's Poisson noise, the whole curve moves with the number of
+    points that happen to lie in the interior (about 1/sqrt(3400) per configuration, 0.9 % for four): each bin
+    within 5 sigma + 3 %, each class's mean within 2.5 %.  A mixed class normalised around one sign only would be
+    off by 100 %, a shell volume taken at the inner edge by 9 % on average, and the 1/N difference between like
+    and unlike partner densities is 2.5e-4."""
+    counts = np.zeros((3, 30), np.uint64)
+    n_ref = np.zeros(2)
+    for seed in range(4):
+        c, nr, dens = _ideal_gas_counts(4000, 12.0, 3.0, 30, seed=seed)
+        counts += c
+        n_ref += nr
+    g = oracle.pair_correlations(counts, 3.0, n_ref[0], n_ref[1], dens[0], dens[1])
+    sel = slice(3, None)
+    sig = 1 / np.sqrt(np.maximum(counts[:, sel].astype(np.float64), 1))
+    assert (np.abs(g[:, sel] - 1) < 5 * sig + 0.03).all()
+    assert np.abs(g[:, sel].mean(axis=1) - 1).max() < 0.025
+
+
+def test_oracle_refuses_an_empty_window():
+    c, _ = _case((4.0, -0.9), 1.3)
+    with pytest.raises(ValueError):
+        oracle.dressed_ion_analysis(c, R_MAX, NREF[0], NREF[1], DENS[0], DENS[1], Q[0], Q[1], LB, 30.0, 40.0)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1602_05716_gb300 as p
+    p.build()
+    return p
+
+
+def _noisy(c, seed):
+    rng = np.random.default_rng(seed)
+    lam = c.astype(np.float64) * 1e-12  # counts of a smaller sample: Poisson noise flips the far tail's sign
+    return rng.poisson(lam).astype(np.uint64)
+
+
+@pytest.mark.parametrize("which", ["renormalised", "debye_hueckel", "noisy"])
+def test_library_matches_oracle(pkg, which):
+    """The library's host function against the oracle on the same counts: the same usable bins, g to 1e-12
+    relative (the shell volume r_{k+1}^3 - r_k^3 cancels about log2(r / 3 dr) <= 7 bits at r = 24, dr = 0.1, and
+    the two sides cube differently), and every parameter to 1e-9 relative (FP64 sums in different orders)."""
+    if which == "debye_hueckel":
+        c, _ = _case(Q, 1.0)
+        nref = NREF
+    else:
+        c, _ = _case((4.0, -0.9), 1.3)
+        nref = NREF
+    if which == "noisy":
+        c = _noisy(c, 17)
+        nref = (NREF[0] * 1e-12, NREF[1] * 1e-12)
+    args = (R_MAX, nref[0], nref[1], DENS[0], DENS[1], Q[0], Q[1], LB, *WIN)
+    lo = pkg.dressed_ion_analysis(c, *args)
+    ora = oracle.dressed_ion_analysis(c, *args)
+    assert lo["n_fit"] == ora["n_fit"] >= 2
+    both = np.isfinite(ora["g"])
+    assert (np.isfinite(lo["g"]) == both).all()
+    assert np.allclose(lo["g"][both], ora["g"][both], rtol=1e-12, atol=0)
+    for k in ("kappa", "kappa_R", "rd_lhs", "rd_rhs"):
+        assert abs(lo[k] - ora[k]) <= 1e-9 * abs(ora[k]), k
+    for k in ("kappa_R_pm", "qR_p", "qR_m", "epsR_pm"):
+        assert np.allclose(lo[k], ora[k], rtol=1e-9, atol=0), k
+
+
+def test_library_refuses_bad_input(pkg):
+    c, _ = _case((4.0, -0.9), 1.3)
+    good = dict(r_max=R_MAX, n_ref_p=NREF[0], n_ref_m=NREF[1], dens_p=DENS[0], dens_m=DENS[1], q_p=Q[0], q_m=Q[1],
+                l_B=LB, r_lo=WIN[0], r_hi=WIN[1])
+    for bad in [dict(q_p=-3.0), dict(q_m=1.0), dict(l_B=0.0), dict(r_lo=20.0, r_hi=12.0), dict(dens_p=0.0),
+                dict(r_lo=30.0, r_hi=40.0)]:
+        with pytest.raises(pkg.MCError) as e:
+            pkg.dressed_ion_analysis(c, **{**good, **bad})
+        assert e.value.code == pkg.ERR_INVALID
