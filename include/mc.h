@@ -266,12 +266,17 @@ int mc_dressed_ion_analysis(const uint64_t *counts, int n_bins, double r_max, do
  * one kernel launch per trial move, the N - 1 pair terms spread over blocks
  * of 1,024 threads (one pair each), block subtotals left in global memory and
  * counted by an atomic, the last block to finish deciding the move and
- * updating the ion.  It runs the same exact chain as mc_sweep (Sec. 2's
- * sequential updating, the same draws and decisions from sweep 0 of the
- * description's positions), so after n sweeps its positions equal those of
- * mc_create + mc_sweep(n).  Each sweep's N launches replay from one CUDA
- * graph for N <= 65,536 (plain launches above).  Blocks until done.
+ * updating the ion.  With MC_SCHEME_SEQUENTIAL it runs the same exact chain
+ * as mc_sweep (Sec. 2's sequential updating, the same draws and decisions
+ * from sweep 0 of the description's positions), so after n sweeps its
+ * positions equal those of mc_create + mc_sweep(n).  With MC_SCHEME_RANDOM it
+ * runs Sec. 2's random updating scheme: cycle s has N steps, step t has move
+ * index m = s N + t and moves ion floor(u N / 2^64), u = w1 2^32 + w0 from
+ * the Philox draws of purpose 3 at m (trial and acceptance draws as in the
+ * sequential scheme, purpose 0 at m).  Each cycle's N launches replay from
+ * one CUDA graph for N <= 65,536 (plain launches above).  Blocks until done.
  *   desc      one chain, validated as by mc_create (caller-owned, read only)
+ *   scheme    MC_SCHEME_SEQUENTIAL or MC_SCHEME_RANDOM
  *   pos_out   N x 3 floats, host, caller-owned: the positions after the sweeps
  *   dE_sum    (nullable) FP64 sum of the accepted moves' dE
  *   counts    (nullable) 5 counters: accepted, rejected by the Metropolis
@@ -280,9 +285,12 @@ int mc_dressed_ion_analysis(const uint64_t *counts, int n_bins, double r_max, do
  *             in the canonical order
  *   ms        (nullable) CUDA-event time of the sweeps on the call's stream
  * Device memory is allocated and released inside the call.  Errors as
- * mc_create, MC_ERR_INVALID for n_sweeps < 0 or a NULL pos_out.            */
-int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, float *pos_out, double *dE_sum, uint64_t *counts,
-                     double *ms);
+ * mc_create, MC_ERR_INVALID for n_sweeps < 0, an unknown scheme or a NULL
+ * pos_out.                                                                   */
+#define MC_SCHEME_SEQUENTIAL 0
+#define MC_SCHEME_RANDOM 1
+int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, float *pos_out, double *dE_sum,
+                     uint64_t *counts, double *ms);
 
 /* Options (mc_set_option):
  *  MC_OPT_GUARD_MODE   0 = FP32 with proven error band (default),

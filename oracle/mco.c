@@ -402,10 +402,9 @@ static int metropolis_accept(double dE, uint32_t uacc)
     return dE < -mco_log(u);
 }
 
-/* One sequential trial move of ion i at sweep index s (Sec. 2 steps a-c). */
-static void one_move(mco_chain *c, uint64_t s, int64_t i)
+/* One trial move of ion i with move index m (Sec. 2 steps b-c; the selection, step a, is the caller's). */
+static void one_move_m(mco_chain *c, uint64_t m, int64_t i)
 {
-    uint64_t m = s * (uint64_t)c->n + (uint64_t)i;
     float a[3];
     uint32_t uacc = trial(c, m, i, a);
     float b[3] = {c->x[3 * i], c->x[3 * i + 1], c->x[3 * i + 2]};
@@ -449,6 +448,39 @@ static void one_move(mco_chain *c, uint64_t s, int64_t i)
         r->pad = 0.0f;
         r->scale = isnan(dE) ? NAN : move_scale(c, i, a, b);
     }
+}
+
+/* One sequential trial move of ion i at sweep index s: move index s N + i. */
+static void one_move(mco_chain *c, uint64_t s, int64_t i)
+{
+    one_move_m(c, s * (uint64_t)c->n + (uint64_t)i, i);
+}
+
+/* The ion selected by step m of the random updating scheme (Sec. 2, step a
+ * "at random"): u = w1 2^32 + w0 from the draws of purpose 3 at move index
+ * m, ion floor(u N / 2^64) (uniform up to N / 2^64).                          */
+int64_t mco_random_index(const mco_chain *c, uint64_t m)
+{
+    uint32_t w[4];
+    move_draws(c->seed, c->chain, m, 3u, w);
+    const uint64_t u = ((uint64_t)w[1] << 32) | (uint64_t)w[0];
+    return (int64_t)(((unsigned __int128)u * (unsigned __int128)(uint64_t)c->n) >> 64);
+}
+
+/* n_cycles Monte Carlo cycles of the random updating scheme (Sec. 2): N steps
+ * each, step t of cycle s moving the ion mco_random_index selects for move
+ * index s N + t; every ion moves once per cycle on average.                  */
+int mco_random_sweep(mco_chain *c, int64_t n_cycles)
+{
+    if (!c || n_cycles < 0) return MCO_ERR_INVALID;
+    for (int64_t s = 0; s < n_cycles; ++s) {
+        for (int64_t t = 0; t < c->n; ++t) {
+            const uint64_t m = c->sweep * (uint64_t)c->n + (uint64_t)t;
+            one_move_m(c, m, mco_random_index(c, m));
+        }
+        c->sweep++;
+    }
+    return MCO_OK;
 }
 
 /* n_sweeps Monte Carlo cycles: ions 0..N-1 tried once each, in ascending

@@ -60,6 +60,10 @@ def lib():
     L.mco_sweep.restype = ci
     L.mco_partial_sweep.argtypes = [vp, i64]
     L.mco_partial_sweep.restype = ci
+    L.mco_random_sweep.argtypes = [vp, i64]
+    L.mco_random_sweep.restype = ci
+    L.mco_random_index.argtypes = [vp, u64]
+    L.mco_random_index.restype = i64
     L.mco_energy.argtypes = [vp, vp, vp]
     L.mco_energy.restype = ci
     L.mco_total_energy_of.argtypes = [vp, vp, i64, dbl]
@@ -279,6 +283,16 @@ class OracleChain:
         rc = lib().mco_sweep(self._h, int(n))
         if rc != 0:
             raise RuntimeError(f"mco_sweep: {rc}")
+
+    def random_sweep(self, n: int = 1):
+        """n cycles of the random updating scheme (Sec. 2): N steps each, the ion chosen at random per step."""
+        rc = lib().mco_random_sweep(self._h, int(n))
+        if rc != 0:
+            raise RuntimeError(f"mco_random_sweep: {rc}")
+
+    def random_index(self, m: int) -> int:
+        """The ion the random updating scheme moves at move index m."""
+        return int(lib().mco_random_index(self._h, int(m)))
 
     def partial_sweep(self, n_moves: int):
         rc = lib().mco_partial_sweep(self._h, int(n_moves))

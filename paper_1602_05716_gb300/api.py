@@ -93,7 +93,7 @@ def lib():
         "mc_energy_series_enable": ([vp, ci, i64], ci),
         "mc_energy_series_read": ([vp, ci, vp, i64], i64),
         "mc_energy_autocorr": ([vp, i64, i64, i64, i64, vp, vp], ci),
-        "mc_reduction_run": ([ctypes.POINTER(_Desc), i64, vp, vp, vp, vp], ci),
+        "mc_reduction_run": ([ctypes.POINTER(_Desc), i64, ci, vp, vp, vp, vp], ci),
         "mc_dressed_ion_analysis": ([vp, ci, dbl, dbl, dbl, dbl, dbl, dbl, dbl, dbl, dbl, dbl, vp,
                                      ctypes.POINTER(_DIT)], ci),
         "mc_set_option": ([vp, ci, i64], ci),
@@ -322,10 +322,11 @@ class System:
         return v, y, ok.astype(bool)
 
 
-def reduction_run(chain, n_sweeps: int):
-    """Sec. 4's parallel-reduction code (one launch per trial move) on one chain description, from sweep 0.
-    Returns (positions after the sweeps, sum of accepted dE, counters, CUDA-event milliseconds of the sweeps);
-    counters: accepted, rejected by the Metropolis test, by overlap, by the wall, re-summed canonically."""
+def reduction_run(chain, n_sweeps: int, scheme: int = 0):
+    """Sec. 4's parallel-reduction code (one launch per trial move) on one chain description, from sweep 0, with
+    Sec. 2's sequential (scheme 0) or random (scheme 1) updating.  Returns (positions after the sweeps, sum of
+    accepted dE, counters, CUDA-event milliseconds of the sweeps); counters: accepted, rejected by the Metropolis
+    test, by overlap, by the wall, re-summed canonically."""
     p = np.ascontiguousarray(chain.pos, dtype=np.float32).reshape(-1, 3)
     q = np.ascontiguousarray(chain.q, dtype=np.float32)
     d = _Desc(p.ctypes.data, q.ctypes.data, q.shape[0], float(chain.sigma), float(chain.l_B), float(chain.R),
@@ -334,7 +335,7 @@ def reduction_run(chain, n_sweeps: int):
     dE = ctypes.c_double()
     counts = np.zeros(5, np.uint64)
     ms = ctypes.c_double()
-    _check(lib().mc_reduction_run(ctypes.byref(d), int(n_sweeps), out.ctypes.data, ctypes.byref(dE),
+    _check(lib().mc_reduction_run(ctypes.byref(d), int(n_sweeps), int(scheme), out.ctypes.data, ctypes.byref(dE),
                                   counts.ctypes.data, ctypes.byref(ms)))
     keys = ("accepts", "rej_metropolis", "rej_overlap", "rej_wall", "canonical_resums")
     return out, dE.value, {k: int(v) for k, v in zip(keys, counts)}, ms.value

@@ -37,8 +37,9 @@ cudaError_t mlp_wgrad_launch(const float *V, const float *Z, const float *D, lon
                              float *grad, cudaStream_t st);
 cudaError_t adam_launch(float *p, float *m, float *v, const float *g, float lr, float b1, float b2, float eps, float bc1,
                         float bc2, unsigned short *wbf, cudaStream_t st);
-cudaError_t reduction_sweep_launch(const mcg::ChainDev *chd, float4 *pos, int N, unsigned long long *sweep, void *part,
-                                   unsigned *count, double *ledger, unsigned long long *cnt, cudaStream_t st);
+cudaError_t reduction_sweep_launch(const mcg::ChainDev *chd, float4 *pos, int N, int random_scheme,
+                                   unsigned long long *sweep, void *part, unsigned *count, double *ledger,
+                                   unsigned long long *cnt, cudaStream_t st);
 size_t reduction_part_bytes(int N);
 }  // namespace mcg_host
 
@@ -1048,13 +1049,14 @@ int mc_dressed_ion_analysis(const uint64_t *counts, int n_bins, double r_max, do
     return MC_OK;
 }
 
-int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, float *pos_out, double *dE_sum,
+int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, float *pos_out, double *dE_sum,
                      uint64_t *counts, double *ms)
 {
     if (!desc) return fail(MC_ERR_INVALID, "NULL description");
     int rc = check_desc(*desc);
     if (rc) return rc;
     if (n_sweeps < 0) return fail(MC_ERR_INVALID, "n_sweeps < 0");
+    if (scheme != MC_SCHEME_SEQUENTIAL && scheme != MC_SCHEME_RANDOM) return fail(MC_ERR_INVALID, "scheme %d", scheme);
     if (!pos_out) return fail(MC_ERR_INVALID, "NULL output positions");
     const mc_chain_desc &d = *desc;
     Chain c;
@@ -1114,7 +1116,7 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, float *pos_out
     const bool graph = N <= (1 << 16);
     if (graph && n_sweeps > 0) {
         CK(cudaStreamBeginCapture(v.st, cudaStreamCaptureModeThreadLocal));
-        const cudaError_t le = mcg_host::reduction_sweep_launch(v.chd, v.pos, N, sweep, v.part, count, ledger, cnt, v.st);
+        const cudaError_t le = mcg_host::reduction_sweep_launch(v.chd, v.pos, N, scheme, sweep, v.part, count, ledger, cnt, v.st);
         const cudaError_t ce = cudaStreamEndCapture(v.st, &v.graph);
         CK(le);
         CK(ce);
@@ -1123,7 +1125,7 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, float *pos_out
     CK(cudaEventRecord(v.e0, v.st));
     for (int64_t s = 0; s < n_sweeps; ++s) {
         if (graph) CK(cudaGraphLaunch(v.exec, v.st));
-        else CK(mcg_host::reduction_sweep_launch(v.chd, v.pos, N, sweep, v.part, count, ledger, cnt, v.st));
+        else CK(mcg_host::reduction_sweep_launch(v.chd, v.pos, N, scheme, sweep, v.part, count, ledger, cnt, v.st));
     }
     CK(cudaEventRecord(v.e1, v.st));
     CK(cudaStreamSynchronize(v.st));

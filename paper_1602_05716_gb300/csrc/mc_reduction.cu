@@ -5,7 +5,8 @@
 // leaves its subtotal in global memory, counts itself done with an atomic, and the last block to finish decides
 // the move and updates the ion (Sec. 4's global counter of completed blocks; here the last block is the one whose
 // increment completes the count, so no thread spins).  A sweep is N such launches in index order (Sec. 2's
-// sequential updating), replayed from one CUDA graph.
+// sequential updating), or N launches each moving an ion drawn at random (Sec. 2's random updating), replayed
+// from one CUDA graph.
 //
 // Decisions are those of the exact chain: every term is the FP64 canonical term (IEEE sqrt and division) of the
 // sequential definition; the tree sums differ from the canonical sequential sum by less than a proven bound, and a
@@ -53,11 +54,22 @@ __device__ __forceinline__ void block_reduce(double &s, double &a, int &o, doubl
     }
 }
 
-// One trial move of ion i at the sweep held in *sweep.  Grid: ceil(N / RT) blocks of RT threads.
+// The ion that step m of the random updating scheme moves (Sec. 2, selection at random): u = w1 2^32 + w0 from
+// the draws of purpose 3 at move index m, ion floor(u N / 2^64).
+__device__ __forceinline__ int random_index(const ChainDev &ch, unsigned long long m)
+{
+    const uint4 w = move_draws(ch, m, 3u);
+    const unsigned long long u = ((unsigned long long)w.y << 32) | (unsigned long long)w.x;
+    return (int)__umul64hi(u, (unsigned long long)ch.N);
+}
+
+// Step t of the cycle held in *sweep: move index m = sweep N + t, the ion t (sequential updating) or the one
+// random_index selects (random updating).  Grid: ceil(N / RT) blocks of RT threads.
 // cnt: accepted, Metropolis-rejected, overlap-rejected, wall-rejected, re-summed in the canonical order.
-__global__ void __launch_bounds__(RT) reduction_move(const ChainDev *__restrict__ chp, float4 *pos, int i,
-                                                      const unsigned long long *sweep, RedPart *part,
-                                                      unsigned *count, double *ledger, unsigned long long *cnt)
+__global__ void __launch_bounds__(RT) reduction_move(const ChainDev *__restrict__ chp, float4 *pos, int t,
+                                                      int random_scheme, const unsigned long long *sweep,
+                                                      RedPart *part, unsigned *count, double *ledger,
+                                                      unsigned long long *cnt)
 {
     __shared__ double ws[32], wa[32], terms[RT];
     __shared__ int wo[32];
@@ -65,7 +77,8 @@ __global__ void __launch_bounds__(RT) reduction_move(const ChainDev *__restrict_
     const ChainDev &ch = *chp;
     const int tid = threadIdx.x;
     const int N = ch.N;
-    const unsigned long long m = *sweep * (unsigned long long)N + (unsigned long long)i;
+    const unsigned long long m = *sweep * (unsigned long long)N + (unsigned long long)t;
+    const int i = random_scheme ? random_index(ch, m) : t;
     const float4 b = pos[i];
     const uint4 w = move_draws(ch, m, 0u);
     const float4 a = make_float4(trial_coord(b.x, w.x, ch.D), trial_coord(b.y, w.y, ch.D),
@@ -170,14 +183,15 @@ __global__ void reduction_advance(unsigned long long *sweep)
 
 namespace mcg_host {
 
-// One sweep: N single-move launches in index order, then the sweep counter.  `part` holds reduction_part_bytes(N).
-cudaError_t reduction_sweep_launch(const mcg::ChainDev *chd, float4 *pos, int N, unsigned long long *sweep, void *part,
-                                   unsigned *count, double *ledger, unsigned long long *cnt, cudaStream_t st)
+// One cycle: N single-move launches (steps 0..N-1), then the cycle counter.  `part` holds reduction_part_bytes(N).
+cudaError_t reduction_sweep_launch(const mcg::ChainDev *chd, float4 *pos, int N, int random_scheme,
+                                   unsigned long long *sweep, void *part, unsigned *count, double *ledger,
+                                   unsigned long long *cnt, cudaStream_t st)
 {
     const int nb = (N + mcg::RT - 1) / mcg::RT;
     mcg::RedPart *pp = static_cast<mcg::RedPart *>(part);
-    for (int i = 0; i < N; ++i) {
-        mcg::reduction_move<<<nb, mcg::RT, 0, st>>>(chd, pos, i, sweep, pp, count, ledger, cnt);
+    for (int t = 0; t < N; ++t) {
+        mcg::reduction_move<<<nb, mcg::RT, 0, st>>>(chd, pos, t, random_scheme, sweep, pp, count, ledger, cnt);
     }
     mcg::reduction_advance<<<1, 1, 0, st>>>(sweep);
     return cudaGetLastError();

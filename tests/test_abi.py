@@ -68,3 +68,16 @@ def test_record_capacity_is_kept_per_chain(monkeypatch):
     s.trace_enable(70, chain=1)
     s.records(0), s.records(3), s.records(2), s.trace(1)
     assert fake.read == [(0, 4500), (3, 1920), (2, 0), (1, 70)]
+
+
+def test_reduction_run_refuses_an_unknown_scheme():
+    """The scheme is checked with the description, before any device call."""
+    import numpy as np
+    from paper_1602_05716_gb300 import api
+    api.build()
+    p = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0]], np.float32)
+    q = np.array([1.0, -1.0], np.float32)
+    d = api._Desc(p.ctypes.data, q.ctypes.data, 2, 1.0, 0.7, 5.0, 0.3, 1, 0)
+    out = np.zeros_like(p)
+    rc = api.lib().mc_reduction_run(ctypes.byref(d), 1, 2, out.ctypes.data, None, None, None)
+    assert rc == api.ERR_INVALID

@@ -254,18 +254,20 @@ def test_deep_windows_option(pkg, nchains):
         _compare_records(s.records(q), o.records(), ch.n)
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("n,two_one,phi,sweeps", [(2, False, 0.05, 20), (33, True, 0.1, 6), (1500, True, 0.2, 2),
                                                   (2100, False, 0.25, 1)])
-def test_reduction_foil_matches_oracle(pkg, n, two_one, phi, sweeps):
-    """Sec. 4's parallel-reduction code (one launch per trial move, 1,024-thread blocks, the last block decides):
-    positions and counters identical to the oracle's after the same sweeps (one block, several blocks with a
-    ragged last one); the accepted dE sum within the ledger tolerance."""
+def test_reduction_foil_matches_oracle(pkg, n, two_one, phi, sweeps, scheme):
+    """Sec. 4's parallel-reduction code (one launch per trial move, 1,024-thread blocks, the last block decides),
+    with Sec. 2's sequential (0) or random (1) updating: positions and counters identical to the oracle's after the
+    same cycles (one block, several blocks with a ragged last one); the accepted dE sum within the ledger
+    tolerance."""
     import paper_1602_05716_gb300 as p
     ch = inputs.small_chain(n, phi=phi, seed=900 + n, two_one=two_one, half_width=0.4)
-    pos, dE, cnt, ms = p.reduction_run(ch, sweeps)
+    pos, dE, cnt, ms = p.reduction_run(ch, sweeps, scheme)
     oc = oracle.OracleChain.from_chain(ch, threads=THREADS)
     led0, rec0 = oc.energy()
-    oc.sweep(sweeps)
+    (oc.random_sweep if scheme else oc.sweep)(sweeps)
     assert (pos == oc.positions()).all()
     so = oc.stats()
     assert (cnt["accepts"], cnt["rej_metropolis"], cnt["rej_overlap"], cnt["rej_wall"]) == \
