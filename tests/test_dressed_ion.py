@@ -178,3 +178,45 @@ def test_library_refuses_bad_input(pkg):
         with pytest.raises(pkg.MCError) as e:
             pkg.dressed_ion_analysis(c, **{**good, **bad})
         assert e.value.code == pkg.ERR_INVALID
+
+
+def _paper_values():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "dressed_ion_sec5_2.txt")
+    vals = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+def test_paper_values_satisfy_the_rd_relation_as_read():
+    """Sec. 5.2's printed 3:-1 results against Eq. RD as the analysis reads it, (kappa_R / kappa)^2 =
+    (q_+^R - q_-^R) / (q_+ - q_-): 1.245 against 1.252, within the 0.6 % the paper's own numbers allow; a reading
+    with sums instead of differences would give 1.62 and fails."""
+    v = _paper_values()
+    lhs = (v["debye_length_A"] / v["renormalised_debye_length_A"]) ** 2
+    rhs = (v["qR_plus"] - v["qR_minus"]) / (v["q_plus"] - v["q_minus"])
+    assert abs(rhs / lhs - 1) < 0.01
+    assert abs((v["qR_plus"] + v["qR_minus"]) / (v["q_plus"] + v["q_minus"]) / lhs - 1) > 0.2
+
+
+def test_analysis_recovers_the_paper_state_point(pkg):
+    """A synthetic far field at Sec. 5.2's printed state: kappa from the bare Debye length (28.53 A, lengths in
+    units of the 7.5 A diameter), q^R = 4.125 and -0.884, kappa_R fixed by the exact relation of the construction;
+    the library returns the printed valences and a kappa_R within 1 % of the printed 25.57 A."""
+    v = _paper_values()
+    sigma_A, lB = 7.5, 7.117 / 7.5
+    kappa = sigma_A / v["debye_length_A"]
+    # densities of a neutral 3:-1 mixture with that kappa: kappa^2 = 4 pi l_B (9 n_+ + n_-), n_- = 3 n_+
+    n_p = kappa ** 2 / (4 * PI * lB * 12.0)
+    dens = (n_p, 3.0 * n_p)
+    qR = (v["qR_plus"], v["qR_minus"])
+    kR = np.sqrt(4 * PI * lB * (dens[0] * 3.0 * qR[0] + dens[1] * -1.0 * qR[1]))
+    c = _synthetic_counts(80.0, 400, NREF, dens, qR, lB, 1.2, kR)
+    o = pkg.dressed_ion_analysis(c, 80.0, NREF[0], NREF[1], dens[0], dens[1], 3.0, -1.0, lB, 30.0, 60.0)
+    assert abs(o["kappa"] / kappa - 1) < 1e-12
+    assert abs(sigma_A / o["kappa_R"] / v["renormalised_debye_length_A"] - 1) < 0.01
+    assert all(abs(x / qR[0] - 1) < 2e-3 for x in o["qR_p"]) and all(abs(x / qR[1] - 1) < 2e-3 for x in o["qR_m"])
