@@ -13,6 +13,13 @@
 #include "mc_device.cuh"
 #include "mc_da.cuh"
 
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define MC_HAVE_NVTX 1
+#endif
+#endif
+
 namespace mcg_host {
 size_t sweep_smem_bytes();
 cudaError_t sweep_configure();
@@ -46,6 +53,27 @@ size_t reduction_part_bytes(int N);
 namespace {
 
 thread_local std::string g_err;
+
+// One NVTX range per entry point: named spans on the host timeline of Nsight tools when one is attached, a few
+// nanoseconds otherwise (NVTX v3 loads no tool library unless a tool asks for it).
+struct Range {
+    explicit Range(const char *name)
+    {
+#ifdef MC_HAVE_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~Range()
+    {
+#ifdef MC_HAVE_NVTX
+        nvtxRangePop();
+#endif
+    }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 int fail(int code, const char *fmt, ...)
 {
@@ -619,11 +647,13 @@ int mc_create(const float *pos_xyz, const float *q, int64_t n, double sigma, dou
 
 int mc_create_batch(const mc_chain_desc *descs, int n_chains, mc_handle *out)
 {
+    Range nv("mc_create_batch");
     return create_common(descs, n_chains, out);
 }
 
 int mc_sweep_async(mc_handle h, int64_t n_sweeps)
 {
+    Range nv("mc_sweep_async");
     int rc = check(h);
     if (rc) return rc;
     if (n_sweeps < 0) return fail(MC_ERR_INVALID, "n_sweeps < 0");
@@ -633,6 +663,7 @@ int mc_sweep_async(mc_handle h, int64_t n_sweeps)
 
 int mc_synchronize(mc_handle h)
 {
+    Range nv("mc_synchronize");
     int rc = check(h);
     if (rc) return rc;
     return finish(h);
@@ -640,6 +671,7 @@ int mc_synchronize(mc_handle h)
 
 int mc_sweep(mc_handle h, int64_t n_sweeps)
 {
+    Range nv("mc_sweep");
     int rc = mc_sweep_async(h, n_sweeps);
     if (rc) return rc;
     return finish(h);
@@ -656,6 +688,7 @@ int mc_set_stream(mc_handle h, void *cuda_stream)
 
 int mc_energy(mc_handle h, int chain, double *ledger, double *recomputed)
 {
+    Range nv("mc_energy");
     int rc = check_chain(h, chain);
     if (rc) return rc;
     Chain &c = h->chains[chain];
@@ -671,6 +704,7 @@ int mc_energy(mc_handle h, int chain, double *ledger, double *recomputed)
 
 int mc_gr_histogram(mc_handle h, int chain, int n_bins, double r_max, double wall_margin, uint64_t *counts)
 {
+    Range nv("mc_gr_histogram");
     int rc = check_chain(h, chain);
     if (rc) return rc;
     if (n_bins < 1 || n_bins > 4096 || !(r_max > 0.0) || !counts || !std::isfinite(wall_margin))
@@ -697,6 +731,7 @@ int mc_gr_histogram(mc_handle h, int chain, int n_bins, double r_max, double wal
 
 int mc_get_positions(mc_handle h, int chain, float *pos_xyz)
 {
+    Range nv("mc_get_positions");
     int rc = check_chain(h, chain);
     if (rc) return rc;
     if (!pos_xyz) return fail(MC_ERR_INVALID, "NULL buffer");
@@ -714,6 +749,7 @@ int mc_get_positions(mc_handle h, int chain, float *pos_xyz)
 
 int mc_set_positions(mc_handle h, int chain, const float *pos_xyz)
 {
+    Range nv("mc_set_positions");
     int rc = check_chain(h, chain);
     if (rc) return rc;
     if (!pos_xyz) return fail(MC_ERR_INVALID, "NULL buffer");
@@ -1052,6 +1088,7 @@ int mc_dressed_ion_analysis(const uint64_t *counts, int n_bins, double r_max, do
 int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, float *pos_out, double *dE_sum,
                      uint64_t *counts, double *ms)
 {
+    Range nv("mc_reduction_run");
     if (!desc) return fail(MC_ERR_INVALID, "NULL description");
     int rc = check_desc(*desc);
     if (rc) return rc;
@@ -1308,6 +1345,7 @@ static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, in
 
 int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W)
 {
+    Range nv("mc_set_surrogate");
     const int rc = set_surrogate_impl(h, chain, w_bf16, n_w, r_c, W);
     if (check(h) == MC_OK) write_ctl(h);  // the stream is idle here; pairs mode follows the surrogate state
     return rc;
@@ -1401,6 +1439,7 @@ static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, in
 
 int mc_da_samples(mc_handle h, int chain, float *v_pairs, float *y, uint8_t *valid)
 {
+    Range nv("mc_da_samples");
     int rc = check_chain(h, chain);
     if (rc) return rc;
     if (!v_pairs || !y || !valid) return fail(MC_ERR_INVALID, "NULL output");
@@ -1523,6 +1562,7 @@ int mc_mlp_loss_grad(const uint16_t *w_bf16, const float *v_pairs, const float *
 int mc_mlp_train(const float *v_pairs, const float *y, int64_t n, const uint16_t *w_init, int epochs, int batch,
                  float lr, uint16_t *w_out, double *loss_per_epoch)
 {
+    Range nv("mc_mlp_train");
     if (!v_pairs || !y || !w_init || !w_out || n < 1 || epochs < 0 || batch < 1 || !(lr > 0.0f))
         return fail(MC_ERR_INVALID, "bad arguments");
     const long long nb = std::min<long long>(batch, n);
