@@ -81,3 +81,13 @@ def test_reduction_run_refuses_an_unknown_scheme():
     out = np.zeros_like(p)
     rc = api.lib().mc_reduction_run(ctypes.byref(d), 1, 2, out.ctypes.data, None, None, None)
     assert rc == api.ERR_INVALID
+
+
+def test_binding_declares_every_abi_function():
+    """The Python binding gives every function of include/mc.h a ctypes signature under the same name."""
+    from paper_1602_05716_gb300 import api
+    api.build()
+    L = api.lib()
+    for name in _declared("mc.h"):
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
