@@ -32,6 +32,20 @@
 //    an accurate FP32 form (error proportional to the displacement), then in
 //    double-single arithmetic, and finally in the oracle's FP64 arithmetic and
 //    summation order, each tier with its own bound.
+//  * The three groups before the window ("deep windows") are computed for
+//    both positions too (on unless MC_OPT_DEEP_WINDOWS is 0).  Their
+//    corrections live in tensor memory, written and read back with
+//    tcgen05.st/ld, each warp in its own 32-lane quarter, so the last other
+//    group a work item waits for is five groups back.
+//  * Pairs mode (MC_OPT_PAIRS): a cluster of two CTAs shares one work item.
+//    The helper sums every other tile and hands its sums over through a
+//    global box, ordered by the cluster barriers.
+//  * Barrier discipline: every __syncthreads sits under a CTA-uniform
+//    condition.  A shared value that decides a branch containing barriers is
+//    read by every thread before any thread may rewrite it, with a barrier in
+//    between.  The resolve rounds put a barrier on both branches for this
+//    reason: a warp that read a rewritten value once took the guard tiers'
+//    barriers alone.
 //  * Every wait is bounded by %globaltimer; on expiry the kernel records the
 //    error, raises an abort flag and all CTAs return.
 #include "mc_device.cuh"
