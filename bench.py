@@ -1,16 +1,23 @@
 #!/usr/bin/env python3
 """Throughput of the exact sequential Metropolis path on GB300 (moves/s and G pair-evals/s).
 
-Workload (default): N = 16383 ions of a 2:1 primitive-model electrolyte (5461 x +2, 10922 x -1), sigma = 1,
-l_B = 0.7, hard sphere at volume fraction 0.20, displacement half-width 0.3, 500 sweeps = 50 steps of 10
-sweeps.  One step is one launch of the persistent sweep kernel (all trial moves of 10 sweeps: random draws,
-trial positions, wall test, FP32 pair sums, FP64 guard, decisions, position updates, ledger).
+Workload (default): N = 1,048,576 ions of a 2:1 primitive-model electrolyte (349525 x +2, 699051 x -1), sigma = 1,
+l_B = 0.7, hard sphere at volume fraction 0.30, displacement half-width 0.2, one sweep per step.  Three arms are
+timed with the same steps and rules on the same GPU:
+  plain   the exact path: random draws, trial positions, wall test, FP32 pair sums, FP64 guard, decisions,
+          position updates, ledger (one persistent launch per step);
+  da_g0   delayed acceptance with g = 0: the tapered near field alone as stage 1 (overlap pre-rejection plus the
+          near-field energy), the exact sum as stage 2;
+  da      delayed acceptance with the surrogate trained on the GPU by the project's own MLP kernels.
+The line's `value` is the trained arm; the other two sit beside it with their own rooflines.  Roofline work is the
+pair-evals actually executed: every move's N - 1 on the plain path, the stage-1 survivors' N - 1 with delayed
+acceptance (the plain-equivalent rate is reported separately).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME] [--mode M]
 
 Prints one JSON line (rank 0).  With --gpus N > 1 (launched by torch.distributed.run) every rank runs an
-independent replica chain (chain id = rank; no data-path collective: the path does not shard) and the value
-is the moves of all ranks divided by the slowest rank's time.
+independent replica chain (chain id shifted by rank; no data-path collective: the path does not shard) and the
+value is the moves of all ranks divided by the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -40,6 +47,10 @@ MUFU_RSQ_PER_CLK = 16.0
 ALG_FP32_PER_PAIR = 14.0
 RSQ_PER_PAIR = 2.0
 
+DEFAULT_SPS = {"plain_n256": 10, "plain_n16383": 10, "batch64": 10, "da_n65536": 1, "large_n1048576": 1}
+DEFAULT_STEPS = {"plain_n256": 200, "plain_n16383": 50, "batch64": 20, "da_n65536": 20, "large_n1048576": 10}
+DEFAULT_MODE = {"da_n65536": "both", "large_n1048576": "both"}
+
 
 def peak_pairs_per_clk_sm() -> float:
     return min(MUFU_RSQ_PER_CLK / RSQ_PER_PAIR, FP32_PER_CLK / ALG_FP32_PER_PAIR)
@@ -53,9 +64,10 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload: str):
+def measured_traffic(workload: str, arm: str = "plain"):
     """DRAM bytes per step of the sweep kernel from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", f"sweep_kernel_{workload}.md")
+    name = f"sweep_kernel_{workload}.md" if arm == "plain" else f"sweep_kernel_{workload}_{arm}.md"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             for line in f:
@@ -151,39 +163,33 @@ def reduce_max_sum(t_local: float, moves_local: float, world: int, device=None):
     return float(tt.item()), float(mm.item())
 
 
-def cpu_baseline(chains, min_seconds: float = 8.0, max_sweeps: int = 20, threads: int | None = None) -> dict:
-    """The FP64 oracle, as it stands, on the host cores: whole sweeps of the workload's chains (round-robin,
-    one sweep each in turn) from their initial configurations, until the time budget is spent."""
+def sample_moves(n: int, requested: int | None) -> int:
+    """Moves per sample of the oracle: a prefix of consecutive moves of the chain from its initial configuration
+    (2048 unless asked otherwise, at most one sweep)."""
+    return max(1, min(n, int(requested) if requested else 2048))
+
+
+def oracle_samples(ch, moves: int, steps: int, warmup: int, threads: int) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: `warmup` untimed then `steps` timed samples of `moves`
+    consecutive trial moves each, continuing the chain from its initial configuration.  The one sampling rule of
+    both the reference arm and the cpu_baseline field."""
     import oracle
-    threads = threads or os.cpu_count() or 1
-    ocs = [oracle.OracleChain.from_chain(c, threads=threads) for c in chains]
-    t0 = time.perf_counter()
-    moves = pairs = sweeps = 0
-    k = 0
-    prefix = 2048  # chains above 65536 ions are sampled by a prefix of their first sweep's moves
-    while sweeps < max_sweeps * len(chains):
-        c = chains[k % len(chains)]
-        if c.n > 65536:
-            ocs[k % len(chains)].partial_sweep(prefix)
-            moves += prefix
-            pairs += prefix * (c.n - 1)
-        else:
-            ocs[k % len(chains)].sweep(1)
-            moves += c.n
-            pairs += c.pair_evals_per_sweep
-        sweeps += 1
-        k += 1
-        if time.perf_counter() - t0 >= min_seconds:
-            break
-    dt = time.perf_counter() - t0
-    what = (f"the N={chains[0].n} chain" if len(chains) == 1 else
-            f"{min(sweeps, len(chains))} of the {len(chains)} chains in turn")
-    kind = "full sweeps" if max(c.n for c in chains) <= 65536 else f"{prefix}-move prefixes of the first sweep"
-    return {"value": moves / dt, "unit": "moves/s", "cores": threads, "kind": "oracle",
-            "sample": f"{sweeps} {kind} ({moves} moves, {pairs:.3g} pair-evals) of {what} from the initial "
-                      f"configuration, {dt:.2f} s wall, FP64 canonical oracle with chunk-parallel sums on "
-                      f"{threads} threads",
-            "pair_evals_per_s": pairs / dt}
+    oc = oracle.OracleChain.from_chain(ch, threads=threads)
+    for _ in range(warmup):
+        oc.partial_sweep(moves)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oc.partial_sweep(moves)
+        times.append(time.perf_counter() - t0)
+    oc.close()
+    dt = sum(times)
+    value = steps * moves / dt
+    return {"value": value, "unit": "moves/s", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} timed samples (after {warmup} untimed) of {moves} consecutive trial moves of the "
+                      f"N={ch.n} chain from its initial configuration (FP64 canonical oracle, chunk-parallel sums "
+                      f"on {threads} threads), {dt:.2f} s",
+            "pair_evals_per_s": value * (ch.n - 1), "ms_per_step": 1000.0 * dt / steps}
 
 
 def reduction_foil(pkg, ch, sweeps: int, ours: float) -> dict:
@@ -218,27 +224,18 @@ def run_reference(args):
     if rank != 0:
         return 0
     import inputs
-    ch = inputs.workload(args.workload).chains[0]
-    import oracle
+    wl = inputs.workload(args.workload)
+    ch = wl.chains[0]
     threads = os.cpu_count() or 1
-    oc = oracle.OracleChain.from_chain(ch, threads=threads)
-    # each step: a bounded sample of the workload (a fixed number of moves), sized so K+W steps end in minutes
-    moves_per_step = max(1, min(ch.n, int(args.ref_moves_per_step)))
-    for _ in range(args.warmup):
-        oc.partial_sweep(moves_per_step)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oc.partial_sweep(moves_per_step)
-    dt = time.perf_counter() - t0
-    value = args.steps * moves_per_step / dt
-    sample = (f"{args.steps} steps x {moves_per_step} moves (prefix of a sweep) of the N={ch.n} chain, FP64 oracle "
-              f"on {threads} threads")
+    moves = sample_moves(ch.n, args.ref_moves)
+    cb = oracle_samples(ch, moves, args.steps, args.warmup, threads)
+    value = cb["value"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "N": ch.n},
-            "gpair_evals_per_s": value * (ch.n - 1) / 1e9,
-            "cpu_baseline": {"value": value, "unit": "moves/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "config": {"workload": args.workload, "N": ch.n, "moves_per_step": moves},
+            "gpair_evals_per_s": cb["pair_evals_per_s"] / 1e9,
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -287,6 +284,115 @@ def train_surrogate(pkg, ch, r_c: float, W: int, n_samples: int, epochs: int, ma
                "sample_s": t1 - t0, "train_s": t2 - t1}
 
 
+def dE_error(pkg, ch, moves: int, threads: int) -> dict:
+    """Per-move dE error of the plain path: the first `moves` moves of sweep 0 recorded on the GPU (the FP32 value
+    the kernel decided from) against the oracle's FP64 records of the same moves, relative to the tolerance scale
+    l_B |q_i| sum_j |q_j| (1/r' + 1/r); the decisions must agree move for move."""
+    import numpy as np
+
+    import oracle
+    moves = min(moves, ch.n)
+    g = pkg.System([ch])
+    g.record_enable(moves)
+    g.sweep(1)
+    gr = g.records()[:moves]
+    g.close()
+    oc = oracle.OracleChain.from_chain(ch, threads=threads)
+    oc.record(moves)
+    oc.partial_sweep(moves)
+    orc = oc.records()
+    oc.close()
+    same = bool((gr["outcome"] == orc["outcome"]).all() and (gr["m"] == orc["m"]).all())
+    ev = ((orc["outcome"] == oracle.ACCEPT) | (orc["outcome"] == oracle.REJECT_METROPOLIS)) & np.isfinite(gr["dE32"])
+    err = np.abs(gr["dE32"][ev] - orc["dE"][ev]) / np.maximum(orc["scale"][ev], 1e-300)
+    return {"dE_rel_err_max": float(err.max()) if err.size else None,
+            "dE_rel_err_mean": float(err.mean()) if err.size else None, "moves": int(moves),
+            "evaluated": int(err.size), "decisions_equal_oracle": same,
+            "basis": "|dE_FP32 - dE_oracle_FP64| / (l_B |q_i| sum_j |q_j| (1/r' + 1/r)), first moves of sweep 0"}
+
+
+def time_arm(pkg, chains, stream, flush, steps: int, warmup: int, sps: int, world: int, local: int,
+             surrogate=None, r_c: float = 4.0, W: int = 160, sampler=None) -> dict:
+    """One arm: warm-up steps, then `steps` timed steps of `sps` sweeps each, CUDA events on the launch stream around
+    every graph replay, L2 flushed between steps outside the events.  Returns times, counters and the system."""
+    import torch
+    with torch.cuda.stream(stream):
+        sysm = pkg.System(chains)
+        sysm.set_stream(stream.cuda_stream)
+        if surrogate is not None:
+            for i in range(len(chains)):
+                sysm.set_surrogate(surrogate, r_c=r_c, W=W, chain=i)
+        tuned = sysm.autotune(2) if len(chains) > 1 else None
+        for _ in range(warmup):
+            flush.zero_()
+            sysm.sweep_async(sps)
+        stream.synchronize()
+        sysm.synchronize()
+        before = [sysm.stats(i) for i in range(len(chains))]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk = sampler(local) if sampler else None
+        if clk:
+            clk.__enter__()
+        w0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()  # L2 flush between timed steps (default 512 MiB > 129 MB L2), outside the events
+            ev[k][0].record(stream)
+            sysm.sweep_async(sps)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        if clk:
+            clk.__exit__(None, None, None)
+        sysm.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+    after = [sysm.stats(i) for i in range(len(chains))]
+    delta = {k: sum(a[k] - b[k] for a, b in zip(after, before)) for k in after[0] if k not in ("drift_last", "drift_max")}
+    return {"sys": sysm, "step_ms": step_ms, "wall": wall, "delta": delta, "tuned": tuned,
+            "clocks": clk.summary() if clk else None}
+
+
+def roofline(pairs_per_step: float, step_ms, info: dict, max_mhz: float, load_mhz, traffic, kernel: str) -> dict:
+    peak = info["sm_count"] * peak_pairs_per_clk_sm() * max_mhz * 1e6
+    achieved = pairs_per_step / (statistics.mean(step_ms) / 1000.0)
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-evals/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_basis": f"{info['sm_count']} SMs x min(MUFU rsqrt {MUFU_RSQ_PER_CLK:g}/clk / 2 per pair, FP32 "
+                          f"{FP32_PER_CLK:g}/clk / {ALG_FP32_PER_PAIR:g} per pair) x {max_mhz:g} MHz (max SM clock)",
+            "frac_at_load_clock": (achieved / (peak * load_mhz / max_mhz)) if load_mhz else None,
+            "kernel": kernel}
+
+
+def arm_summary(arm: dict, chains, sps: int, steps: int, info, max_mhz, load_mhz, traffic, da: bool) -> dict:
+    n = sum(c.n for c in chains)
+    d = arm["delta"]
+    moves = n * sps * steps
+    t = sum(arm["step_ms"]) / 1000.0
+    plain_pairs = sum(c.n * (c.n - 1) for c in chains) * sps * steps
+    if da:
+        surv = moves - d["da_rej1"] - d["da_ovl1"] - d["rej_wall"]
+        executed = surv * (chains[0].n - 1) if len(chains) == 1 else plain_pairs * surv / max(1, moves)
+        kernel = "mcg::sweep_kernel with the surrogate stage (one launch per sweep), CUDA events on its stream"
+    else:
+        surv = moves
+        executed = plain_pairs
+        kernel = "mcg::sweep_kernel (one launch per step), CUDA events on its stream"
+    out = {"moves_per_s": moves / t, "ms_per_step": statistics.mean(arm["step_ms"]), "steps": steps,
+           "gpair_evals_executed_per_s": executed / t / 1e9,
+           "roofline": roofline(executed / steps, arm["step_ms"], info, max_mhz, load_mhz, traffic, kernel),
+           "accept_rate": d["accepts"] / moves, "overlap_rejects_per_move": d["rej_overlap"] / moves,
+           "guard_per_move": d["guard_fp64"] / moves, "guard_tiers_2_3_4": [d["tier2"], d["tier3"], d["tier4"]]}
+    if da:
+        out.update({"plain_equivalent_gpair_evals_per_s": plain_pairs / t / 1e9,
+                    "survivors_per_move": surv / moves, "stage1_reject_per_move": d["da_rej1"] / moves,
+                    "stage1_overlap_per_move": d["da_ovl1"] / moves,
+                    "stage2_reject_per_survivor": d["rej_metropolis"] / max(1, surv)})
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -305,93 +411,49 @@ def run_ours(args):
     sps = args.sweeps_per_step
     n = sum(c.n for c in chains)
     moves_per_step = n * sps
-    pairs_per_step = sum(c.n * (c.n - 1) for c in chains) * sps
+    mode = args.mode or DEFAULT_MODE.get(args.workload, "plain")
+    info = pkg.device_info()
+    peaks = peaks_file()
+    max_mhz = float(peaks.get("sm_max_mhz") or info["sm_clock_khz"] / 1000.0)
 
-    mode = args.mode or {"da_n65536": "da", "large_n1048576": "both"}.get(args.workload, "plain")
-    da_info = None
-    w_da = None
+    da_info = w_da = None
     if mode in ("da", "both"):
-        ch0 = chains[0]
-        w_da, da_info = train_surrogate(pkg, ch0, args.r_c, args.da_W, args.da_samples, args.da_epochs)
+        w_da, da_info = train_surrogate(pkg, chains[0], args.r_c, args.da_W, args.da_samples, args.da_epochs)
 
     stream = torch.cuda.Stream()
     flush = torch.empty(max(1, args.flush_mb) * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
-    plain_cmp = None
+    arms = {}
+    if mode in ("plain", "both"):
+        arms["plain"] = time_arm(pkg, chains, stream, flush, args.steps, args.warmup, sps, world, local,
+                                 sampler=ClockSampler)
+        if mode == "both":
+            arms["plain"]["sys"].close()
+    if mode == "both":
+        arms["da_g0"] = time_arm(pkg, chains, stream, flush, args.steps, args.warmup, sps, world, local,
+                                 surrogate=np.zeros(pkg.MLP_NP, np.uint16), r_c=args.r_c, W=args.da_W,
+                                 sampler=ClockSampler)
+        arms["da_g0"]["sys"].close()
     if mode in ("da", "both"):
-        # the plain exact path on the same workload, same stream and timing rules, for the ratio
-        with torch.cuda.stream(stream):
-            psys = pkg.System(chains)
-            psys.set_stream(stream.cuda_stream)
-            psteps = max(1, min(args.steps, 3))
-            for _ in range(min(args.warmup, 2)):
-                flush.zero_()
-                psys.sweep_async(sps)
-            stream.synchronize()
-            pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(psteps)]
-            for k in range(psteps):
-                flush.zero_()
-                pev[k][0].record(stream)
-                psys.sweep_async(sps)
-                pev[k][1].record(stream)
-            stream.synchronize()
-            pms = [a.elapsed_time(b) for a, b in pev]
-            psys.close()
-        plain_cmp = {"moves_per_s": moves_per_step * psteps / (sum(pms) / 1000.0), "steps": psteps,
-                     "ms_per_step": statistics.mean(pms)}
-    with torch.cuda.stream(stream):
-        sysm = pkg.System(chains)
-        sysm.set_stream(stream.cuda_stream)
-        if w_da is not None:
-            for i in range(len(chains)):
-                sysm.set_surrogate(w_da, r_c=args.r_c, W=args.da_W, chain=i)
-        tuned = sysm.autotune(2) if len(chains) > 1 else None
-        for _ in range(args.warmup):
-            flush.zero_()
-            sysm.sweep_async(sps)
-        stream.synchronize()
-        sysm.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            w0 = time.perf_counter()
-            for k in range(args.steps):
-                flush.zero_()  # L2 flush between timed steps (default 512 MiB > 129 MB L2), outside the events
-                ev[k][0].record(stream)
-                sysm.sweep_async(sps)
-                ev[k][1].record(stream)
-            stream.synchronize()
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - w0
-        sysm.synchronize()
-        step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = sum(step_ms) / 1000.0
+        arms["da"] = time_arm(pkg, chains, stream, flush, args.steps, args.warmup, sps, world, local,
+                              surrogate=w_da, r_c=args.r_c, W=args.da_W, sampler=ClockSampler)
+    head_name = "da" if "da" in arms else "plain"
+    head = arms[head_name]
+    sysm = head["sys"]
+    t_local = sum(head["step_ms"]) / 1000.0
     t_max, moves_total = reduce_max_sum(t_local, float(moves_per_step * args.steps), world,
                                         device=torch.device("cuda", local))
     if world > 1:
         torch.distributed.barrier()
-    stats = {k: sum(sysm.stats(i)[k] for i in range(len(chains))) for k in sysm.stats(0)}
+    value = moves_total / t_max
+    csum = head["clocks"] or {}
+    load_mhz = csum.get("sm_mhz")
+    summaries = {k: arm_summary(a, chains, sps, args.steps, info, max_mhz, (a["clocks"] or {}).get("sm_mhz"),
+                                measured_traffic(args.workload, "da" if k.startswith("da") else "plain"),
+                                k.startswith("da"))
+                 for k, a in arms.items()}
+    hs = summaries[head_name]
     energies = [sysm.energy(i) for i in range(len(chains))]
     led, rec = energies[0]
-    value = moves_total / t_max
-    pair_rate = pairs_per_step * args.steps * (moves_total / (moves_per_step * args.steps)) / t_max
-
-    # roofline of the dominant kernel (the persistent sweep kernel: one launch per step)
-    info = pkg.device_info()
-    peaks = peaks_file()
-    max_mhz = float(peaks.get("sm_max_mhz") or info["sm_clock_khz"] / 1000.0)
-    peak = info["sm_count"] * peak_pairs_per_clk_sm() * max_mhz * 1e6
-    mean_step_s = statistics.mean(step_ms) / 1000.0
-    achieved = pairs_per_step / mean_step_s
-    csum = clk.summary()
-    load_mhz = csum.get("sm_mhz")
-    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-evals/s",
-            "frac": achieved / peak, "traffic": measured_traffic(args.workload),
-            "peak_basis": f"{info['sm_count']} SMs x min(MUFU rsqrt {MUFU_RSQ_PER_CLK:g}/clk / 2 per pair, FP32 "
-                          f"{FP32_PER_CLK:g}/clk / {ALG_FP32_PER_PAIR:g} per pair) x {max_mhz:g} MHz (max SM clock)",
-            "frac_at_load_clock": (achieved / (peak * load_mhz / max_mhz)) if load_mhz else None,
-            "kernel": "mcg::sweep_kernel (one launch per step, timed by CUDA events on its stream)"}
 
     line = {"metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps, "higher_is_better": True,
@@ -402,18 +464,34 @@ def run_ours(args):
                        "l_B": chains[0].l_B if len(chains) == 1 else "U[0.5,2.0]",
                        "half_width": chains[0].half_width,
                        "l2": f"flushed between steps ({args.flush_mb} MiB device write outside the timed events)",
-                       "parallelism": f"replicas x{world}", "autotune": tuned},
-            "gpair_evals_per_s": pair_rate / 1e9,
-            "roofline": roof,
+                       "parallelism": f"replicas x{world}", "autotune": head["tuned"],
+                       "path": {"da": "delayed acceptance, trained surrogate", "plain": "plain exact"}[head_name]},
+            "gpair_evals_per_s": hs["gpair_evals_executed_per_s"],
+            "roofline": hs["roofline"],
             "clocks": csum,
-            "gpu_launches": 2 * args.steps,
-            "accept_rate": stats["accepts"] / max(1, n * stats["sweeps"] // len(chains)),
-            "guard_per_move": stats["guard_fp64"] / max(1, n * stats["sweeps"] // len(chains)),
-            "guard_tiers_2_3_4": [stats["tier2"], stats["tier3"], stats["tier4"]],
-            "interval_decided_per_move": stats["decided_interval"] / max(1, n * stats["sweeps"] // len(chains)),
+            "accept_rate": hs["accept_rate"], "guard_per_move": hs["guard_per_move"],
+            "guard_tiers_2_3_4": hs["guard_tiers_2_3_4"],
             "energy": {"ledger": led, "recomputed": rec, "drift": led - rec,
                        "max_abs_drift_over_chains": max(abs(a - b) for a, b in energies)},
-            "wall_s": wall}
+            "wall_s": head["wall"]}
+    kernels_per_step = (5 * sps) if head_name == "da" else 2
+    line["gpu_launches"] = kernels_per_step * args.steps
+    if head_name == "da":
+        line["metric_variant"] = "delayed acceptance with the trained surrogate (decisions of the FP64 reference)"
+        line["delayed_acceptance"] = dict(summaries["da"], r_c=args.r_c, W_groups=args.da_W, training=da_info)
+        # surrogate error on one recorded sweep of the current state (moves evaluated by both stages)
+        sysm.record_enable(n)
+        sysm.sweep(1)
+        rr = sysm.records()
+        both = np.isfinite(rr["dE"]) & np.isfinite(rr["dEt"])
+        err = (rr["dE"] - rr["dEt"])[both]
+        line["delayed_acceptance"]["surrogate_dE_error_rms_kT"] = float(np.sqrt(np.mean(err ** 2))) if err.size else None
+        line["delayed_acceptance"]["surrogate_dE_error_mean_abs_kT"] = float(np.mean(np.abs(err))) if err.size else None
+        for k in ("plain", "da_g0"):
+            if k in summaries:
+                s = summaries[k]
+                line[{"plain": "plain_path_same_gpu", "da_g0": "da_g_zero_same_gpu"}[k]] = dict(
+                    s, speedup_of_trained=value / s["moves_per_s"] if world == 1 else None)
 
     # end to end through the C ABI with host buffers: upload positions, sweep, read positions + ledger back
     if not args.no_e2e:
@@ -447,36 +525,20 @@ def run_ours(args):
         line["e2e"] = {"value": mv / t_e2e, "unit": "moves/s", "h2d_bytes_per_step": 16 * npad,
                        "d2h_bytes_per_step": 16 * n + 8 * len(chains),
                        "path": "mc_set_positions(pinned host) + mc_sweep + mc_get_positions + mc_energy per step"}
-        line["gpu_launches"] += 2 * args.steps
+        line["gpu_launches"] += kernels_per_step * args.steps
+    sysm.close()
 
-    if w_da is not None:
-        moves_sw = n * stats["sweeps"]
-        surv = moves_sw - stats["da_rej1"] - stats["da_ovl1"] - stats["rej_wall"]
-        # surrogate error on one recorded sweep of the current state (moves evaluated by both stages)
-        sysm.record_enable(n)
-        sysm.sweep(1)
-        rec = sysm.records()
-        both = np.isfinite(rec["dE"]) & np.isfinite(rec["dEt"])
-        err = (rec["dE"] - rec["dEt"])[both]
-        line["metric_variant"] = "delayed acceptance with the trained surrogate (exact: decisions of the FP64 reference)"
-        line["delayed_acceptance"] = {
-            "r_c": args.r_c, "W_groups": args.da_W, "training": da_info,
-            "stage1_reject_per_move": stats["da_rej1"] / moves_sw, "stage1_overlap_per_move": stats["da_ovl1"] / moves_sw,
-            "survivors_per_move": surv / moves_sw, "accept_rate": stats["accepts"] / moves_sw,
-            "stage2_reject_per_survivor": (stats["rej_metropolis"]) / max(1, surv),
-            "surrogate_dE_error_rms_kT": float(np.sqrt(np.mean(err ** 2))) if err.size else None,
-            "surrogate_dE_error_mean_abs_kT": float(np.mean(np.abs(err))) if err.size else None,
-            "gpair_evals_executed_per_s": pair_rate * surv / moves_sw / 1e9,
-            "plain_equivalent_gpair_evals_per_s": pair_rate / 1e9,
-            "plain_path_same_gpu": plain_cmp,
-            "speedup_vs_plain": value / plain_cmp["moves_per_s"] if plain_cmp else None}
-        line["gpu_launches"] = 6 * sps * args.steps + (line["gpu_launches"] - 2 * args.steps)
-    elif plain_cmp is not None:
-        line["plain_path_same_gpu"] = plain_cmp
+    threads = os.cpu_count() or 1
+    if rank == 0 and world == 1 and args.err_moves > 0 and len(chains) == 1:
+        line["dE_error"] = dE_error(pkg, chains[0], args.err_moves, threads)
+        line["dE_rel_err_max"] = line["dE_error"]["dE_rel_err_max"]
+        line["dE_rel_err_mean"] = line["dE_error"]["dE_rel_err_mean"]
     if rank == 0 and world == 1 and args.foil_sweeps > 0 and len(chains) == 1 and chains[0].n <= 65536 and w_da is None:
         line["reduction_foil"] = reduction_foil(pkg, chains[0], args.foil_sweeps, value)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl.chains, min_seconds=args.cpu_seconds)
+        ch0 = wl.chains[0]
+        cb = oracle_samples(ch0, sample_moves(ch0.n, args.ref_moves), args.cpu_steps, 1, threads)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "pair_evals_per_s")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -487,30 +549,35 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=None, help="default: the workload's sweeps / sweeps-per-step")
+    ap.add_argument("--steps", type=int, default=None, help="default: by workload (the configuration's sweeps)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="plain_n16383")
-    ap.add_argument("--sweeps-per-step", type=int, default=10)
+    ap.add_argument("--workload", default="large_n1048576")
+    ap.add_argument("--sweeps-per-step", type=int, default=None, help="default: 1 at N >= 65536, else 10")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=8.0)
-    ap.add_argument("--ref-moves-per-step", type=int, default=2048)
+    ap.add_argument("--cpu-steps", type=int, default=5, help="timed oracle samples of the cpu_baseline field")
+    ap.add_argument("--ref-moves", type=int, default=None,
+                    help="moves per oracle sample (reference arm and cpu_baseline alike; default 2048)")
+    ap.add_argument("--err-moves", type=int, default=4096,
+                    help="moves of sweep 0 whose FP32 dE is compared with the oracle's (0: skip)")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--foil-sweeps", type=int, default=2,
                     help="sweeps of Sec. 4's parallel-reduction code timed beside the headline (0: skip)")
     ap.add_argument("--mode", choices=["plain", "da", "both"], default=None,
-                    help="plain exact path or delayed acceptance with a trained surrogate (default by workload)")
+                    help="plain exact path, delayed acceptance with a trained surrogate, or both (plain, g = 0 and "
+                         "trained arms; default by workload)")
     ap.add_argument("--r-c", dest="r_c", type=float, default=4.0)
     ap.add_argument("--da-W", dest="da_W", type=int, default=160)
     ap.add_argument("--da-samples", dest="da_samples", type=int, default=2_000_000)
     ap.add_argument("--da-epochs", dest="da_epochs", type=int, default=4)
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {"plain_n256": 200, "plain_n16383": 50, "batch64": 20, "da_n65536": 10,
-                      "large_n1048576": 1}.get(args.workload, 50)
-    if args.steps < 1 or args.warmup < 0:
-        raise SystemExit("--steps >= 1, --warmup >= 0")
+        args.steps = DEFAULT_STEPS.get(args.workload, 50)
+    if args.sweeps_per_step is None:
+        args.sweeps_per_step = DEFAULT_SPS.get(args.workload, 10)
+    if args.steps < 1 or args.warmup < 0 or args.sweeps_per_step < 1:
+        raise SystemExit("--steps >= 1, --warmup >= 0, --sweeps-per-step >= 1")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -90,7 +90,11 @@ typedef struct {
     uint64_t da_ovl1;        /* ... overlaps found by the surrogate stage (counted in rej_overlap too) */
     uint64_t da_fp64;        /* ... surrogate energy changes recomputed in the reference FP64 arithmetic */
     uint64_t cyc_da1;        /* ... SM cycles in the surrogate stage, summed over work items, */
-    uint64_t cyc_da_part[4]; /* ... of which: charge grid, shell histograms, MLP, near field */
+    uint64_t cyc_da_part[4]; /* ... of which: [2] the MLP, [3] the near field with its shell histograms
+                                ([0] and [1] stay 0) */
+    uint64_t drift_checks;   /* periodic drift checks run (MC_OPT_DRIFT_EVERY) */
+    double drift_last;       /* |ledger - E| at the last check, E the accurate recomputed energy */
+    double drift_max;        /* largest |ledger - E| over the checks */
 } mc_stats_t;
 
 /* Per-move validation record (mc_record_enable / mc_record_read). */
@@ -140,8 +144,11 @@ int mc_set_stream(mc_handle h, void *cuda_stream);
 
 /* Energy of chain `chain`: *ledger = initial energy + sum of accepted dE (FP64
  * running ledger); *recomputed (nullable) = l_B sum_{i<j} q_i q_j / r_ij of the
- * current configuration, FP32 pair terms with FP64 row sums (the drift check).
- * Sec. 5.2 monitors the total energy to judge equilibration.                */
+ * current configuration (the drift check), every term in float-float
+ * arithmetic: exact coordinate differences, a float-float squared distance,
+ * one Newton step on rsqrt (about 2e-14 relative per term), FP64 sums in a
+ * fixed order that depends on N only.  The initial ledger is the same
+ * computation.  Sec. 5.2 monitors the total energy to judge equilibration.  */
 int mc_energy(mc_handle h, int chain, double *ledger, double *recomputed);
 
 /* Pair-distance histogram behind g_{++}, g_{+-}, g_{--} (Sec. 5.2, Fig. PCF).
@@ -320,7 +327,15 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
  *                      window are also computed for both positions, their
  *                      corrections held in tensor memory, so a group waits for
  *                      no tile later than five groups back.  The trajectory is
- *                      identical either way. */
+ *                      identical either way.
+ *  MC_OPT_DRIFT_EVERY  K >= 1: inside each mc_sweep / mc_sweep_async call,
+ *                      after every K completed sweeps, recompute every
+ *                      chain's energy on the device (as mc_energy's
+ *                      recomputed value) and store |ledger - E| in the
+ *                      chain's drift_last, drift_max and drift_checks
+ *                      (mc_stats); a call of fewer than K sweeps runs no
+ *                      check.  Captured in the same CUDA graph as the sweeps.
+ *                      0 = off (default).  The trajectory is unchanged. */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3
@@ -330,6 +345,7 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
 #define MC_OPT_DA 7
 #define MC_OPT_PAIRS 8
 #define MC_OPT_DEEP_WINDOWS 9
+#define MC_OPT_DRIFT_EVERY 10
 int mc_set_option(mc_handle h, int option, int64_t value);
 int mc_get_option(mc_handle h, int option, int64_t *value);
 
@@ -345,32 +361,42 @@ int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t
  * A two-stage Metropolis test (Christen & Fox, 2005) on the sequential chain of
  * Sec. 2 (the paper's method is the plain chain; this is an exact variant that
  * skips the O(N) sum of Eq. DeltaE for moves a cheap first stage rejects).
- * Stage 1 of the move of ion i: overlap with a counted ion rejects; otherwise
- * the surrogate energy change
- *     dEt = l_B q_i ([phi_near + g(v)](x') - [phi_near + g(v)](x)),
- * phi_near(p) = sum q_j / |p - x_j| over counted ions within r_c, g a
- * 33-64-64-1 SiLU MLP (BF16 weights) of v(p) = 32 shell net charges around p
- * (from a 16^3 charge grid over [-R, R]^3, shells from r_c to 2R) divided by
- * 16 and |p| / R, passes iff u1 == 0 or dEt < -ln u1 (u1 the plain chain's
- * acceptance draw).  Stage 2: the exact sum; accept iff u2 == 0 or
- * dE - dEt < -ln u2, u2 the fourth word of Philox purpose 1.  Counted ions:
- * all but ion i, the earlier ions of its group of 128 and the ions of the W
- * groups before that group (cyclic over the sweep).  Decisions are those of
- * the FP64 reference arithmetic, bit for bit (FP32 with proven bands, the
- * reference recomputation inside them).
+ * Counted ions of the move of ion i in group g = i / 128: every ion except i,
+ * the earlier ions of g and the ions of the W groups tried just before g
+ * (cyclic over the sweep); the set depends only on the move index.
+ * Stage 1: a trial that overlaps a counted ion is rejected; otherwise the
+ * surrogate energy change
+ *     dEt = l_B q_i ([phi_near + g(v)](x') - [phi_near + g(v)](x))
+ * decides: pass iff u1 == 0 or dEt < -ln u1 (u1 the plain chain's acceptance
+ * draw, Philox purpose 0).  With d = |p - x_j| the FP64 distance of the FP32
+ * centres, r_s = r_c / 2 and t = (d - r_s) / (r_c - r_s):
+ *     phi_near(p) = sum over counted j with d^2 < r_c^2 of q_j s(d) / d,
+ *     s(d) = 1 for d <= r_s, 1 - t^2 (3 - 2t) beyond (a C1 taper to 0 at r_c),
+ * added in ascending j.  g is a 33-64-64-1 MLP, SiLU after both hidden layers,
+ * BF16 weights, fed with
+ *     v[k] = F_k / 4 (k < 32),  v[32] = |p| / R,
+ * F_k the net valence of the counted ions in the taper region
+ * r_s^2 <= d^2 < r_c^2 whose shell index floor(32 (d^2 - r_s^2) / (r_c^2 -
+ * r_s^2)) (FP64, clamped to 31) is k: 32 shells of equal width in d^2.
+ * Stage 2 (survivors only): the exact sum of the plain chain (overlap with any
+ * ion rejects); accept iff u2 == 0 or dE - dEt < -ln u2, u2 the fourth word of
+ * Philox purpose 1.  Decisions are those of the FP64 reference arithmetic, bit
+ * for bit (FP32 with proven bands, the reference recomputation inside them).
  *
  * mc_set_surrogate installs the 6401 BF16 weights (layout W1[64][33], b1[64],
  * W2[64][64], b2[64], W3[64], b3; copied), the cutoff r_c (0 < r_c <= 5 sigma)
  * and W >= 2; the launch then uses at most W - 1 persistent CTAs.  w_bf16 =
  * NULL removes the surrogate.  Sweeps with a surrogate run one sweep per
- * launch after a preparation pass (near-field cell list, charge grid).       */
+ * launch after a preparation pass that builds a near-field cell list of the
+ * sweep's start positions (no charge grid).                                  */
 int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W);
 
 /* Training samples from the chain as it stands: for each ion i, the trial move
  * the chain would make next (sweep counter unchanged, nothing moves), the
- * features at the old and the trial position (v_pairs: N x 66, old then
- * trial), y = the exact pair sum sum_j q_j (1/r'_j - 1/r_j) minus the
- * near-field part phi_near(x') - phi_near(x) (the part g must learn), and
+ * features v above at the old and the trial position (v_pairs: N x 66, old
+ * then trial), y = the exact pair sum sum_{j != i} q_j (1/r'_j - 1/r_j) minus
+ * the tapered near-field part phi_near(x') - phi_near(x) (the part g must
+ * learn: l_B q_i y is dE - dEt for g = 0), and
  * valid[i] = 1 unless the trial leaves the wall or overlaps.  Host buffers,
  * caller-owned.  Needs a surrogate set on the chain (its weights unused).  */
 int mc_da_samples(mc_handle h, int chain, float *v_pairs, float *y, uint8_t *valid);
@@ -402,8 +428,11 @@ int mc_mlp_train(const float *v_pairs, const float *y, int64_t n, const uint16_t
  * The row sums live in one fixed device array of 1,048,576 doubles (8 MiB)
  * that the library's module carries on every GPU that loads it, until the
  * process exits; n > 1,048,576 returns MC_ERR_INVALID.  The first call on a
- * device looks up the array's address with that device current: make it
- * before any stream capture.  All calls share the array, so calls that
+ * device looks up the array's address with that device current, and so does
+ * the first call after the device's context was destroyed and created anew
+ * (cudaDeviceReset), since the module may then sit at another address: make
+ * that call before any stream capture (inside one it returns MC_ERR_INVALID
+ * and enqueues nothing).  All calls share the array, so calls that
  * overlap on the GPU race; every call rewrites the rows it reads, so nothing
  * needs clearing.  The call only enqueues work on `stream`.                  */
 int mc_total_energy_noalloc(const void *pos_q_dev, int64_t n, double l_B, double *energy_dev, void *stream);

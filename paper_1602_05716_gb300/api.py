@@ -11,6 +11,7 @@ from . import build as _build
 ERR_INVALID, ERR_OVERLAP_INIT, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_POISONED = -1, -2, -3, -4, -5, -6
 OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH, OPT_POLICY, OPT_DA, OPT_PAIRS = 1, 2, 3, 4, 5, 6, 7, 8
 OPT_DEEP_WINDOWS = 9
+OPT_DRIFT_EVERY = 10
 MLP_NIN, MLP_H = 33, 64
 MLP_NP = MLP_H * MLP_NIN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1  # layout W1, b1, W2, b2, W3, b3
 
@@ -48,8 +49,12 @@ class _DIT(ctypes.Structure):
                 ("rd_lhs", ctypes.c_double), ("rd_rhs", ctypes.c_double), ("n_fit", ctypes.c_int64)]
 
 
+_STATS_FLOAT_FIELDS = ["drift_last", "drift_max"]
+
+
 class _Stats(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_uint64) for f in _STATS_FIELDS]
+    _fields_ = ([(f, ctypes.c_uint64) for f in _STATS_FIELDS] + [("drift_checks", ctypes.c_uint64)] +
+                [(f, ctypes.c_double) for f in _STATS_FLOAT_FIELDS])
 
 
 _LIB = None
@@ -244,7 +249,10 @@ class System:
     def stats(self, chain: int = 0) -> dict:
         s = _Stats()
         _check(lib().mc_stats(self._h, chain, ctypes.byref(s)))
-        return {f: int(getattr(s, f)) for f in _STATS_FIELDS}
+        out = {f: int(getattr(s, f)) for f in _STATS_FIELDS}
+        out["drift_checks"] = int(s.drift_checks)
+        out.update({f: float(getattr(s, f)) for f in _STATS_FLOAT_FIELDS})
+        return out
 
     def get_state(self, chain: int = 0) -> dict:
         pos = np.zeros((self.n[chain], 3), np.float32)

@@ -27,7 +27,9 @@ cudaError_t sweep_occupancy(int *blocks_per_sm);
 cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticket *sched, int n_tickets, mcg::Ctl *ctl,
                          int n_chains, long long n_sweeps, cudaStream_t st, bool pairs);
 cudaError_t sweep_max_clusters(int *n);
-cudaError_t energy_launch(const float4 *pos, int N, double lB, double *rows, double *out, cudaStream_t st);
+int energy_ff_parts(int N);
+cudaError_t energy_ff_launch(const float4 *pos0, const float4 *pos1, const unsigned long long *sweep, int N, double lB,
+                             double *part, double *out, const double *ledger, double *drift, cudaStream_t st);
 cudaError_t gr_launch(const float4 *pos, int N, int n_bins, double dr, float rmax2_hi, int use_lim, double lim2,
                       unsigned long long *counts, cudaStream_t st);
 cudaError_t philox_test_launch(const uint4 *ctr, const uint2 *key, int n, uint4 *out_lib, uint4 *out_curand,
@@ -109,7 +111,8 @@ struct Chain {
     unsigned long long *stats = nullptr;
     unsigned long long *sweep = nullptr;
     double *e_out = nullptr;
-    double *rows = nullptr;      // energy scratch (lazy)
+    double *eparts = nullptr;    // partial sums of the accurate energy (energy_ff_parts(N) doubles)
+    double *drift = nullptr;     // periodic drift check: last |ledger - E|, its maximum, number of checks
     mcg::MoveRec *rec = nullptr;
     long long rec_cap = 0;
     mcg::TraceRec *trace = nullptr;
@@ -138,11 +141,13 @@ struct GraphKey {
     int grid;
     int policy;
     int pairs;
+    long long drift;
     bool operator<(const GraphKey &o) const
     {
         if (n != o.n) return n < o.n;
         if (grid != o.grid) return grid < o.grid;
-        return policy != o.policy ? policy < o.policy : pairs < o.pairs;
+        if (policy != o.policy) return policy < o.policy;
+        return pairs != o.pairs ? pairs < o.pairs : drift < o.drift;
     }
 };
 
@@ -166,6 +171,7 @@ struct mc_system {
     int sm_count = 0, occ = 0;
     int pairs_opt = -1;                 // MC_OPT_PAIRS: -1 automatic, 0 off, 1 on
     int deep_opt = 1;                   // MC_OPT_DEEP_WINDOWS: 1 on (default), 0 off
+    long long drift_every = 0;          // MC_OPT_DRIFT_EVERY: accurate energy and drift check every K sweeps (0 off)
     int max_clusters = 0;               // resident clusters of two CTAs (0: pairs mode unavailable)
     mcg::PairBox *d_box = nullptr;      // one hand-over box per cluster
     int da_on = 1;  // chains with a surrogate sweep with delayed acceptance (MC_OPT_DA)
@@ -330,11 +336,12 @@ int init_chain(mc_system *h, Chain &c, const mc_chain_desc &d)
     c.ledger_seq = (unsigned long long *)(c.slab + 8);
     c.sweep = (unsigned long long *)(c.slab + 16);
     c.e_out = (double *)(c.slab + 24);
+    c.drift = (double *)(c.slab + 32);  // 3 doubles: last drift, maximum, checks
     c.stats = (unsigned long long *)(c.slab + 64);  // NCOUNTERS counters
     rc = upload_positions(h, c, d.pos_xyz, h->stream);
     if (rc) return rc;
-    CK(cudaMalloc(&c.rows, sizeof(double) * (size_t)c.N));
-    CK(mcg_host::energy_launch(c.cur(), c.N, c.lB, c.rows, c.ledger, h->stream));
+    CK(cudaMalloc(&c.eparts, sizeof(double) * (size_t)mcg_host::energy_ff_parts(c.N)));
+    CK(mcg_host::energy_ff_launch(c.cur(), nullptr, nullptr, c.N, c.lB, c.eparts, c.ledger, nullptr, nullptr, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return MC_OK;
 }
@@ -346,7 +353,7 @@ void free_chain(Chain &c)
     cudaFree(c.flags);
     cudaFree(c.bits);
     cudaFree(c.slab);
-    cudaFree(c.rows);
+    cudaFree(c.eparts);
     cudaFree(c.rec);
     cudaFree(c.trace);
     cudaFree(c.eser);
@@ -509,6 +516,20 @@ bool any_da(const mc_system *h)
     return false;
 }
 
+// The periodic drift check (MC_OPT_DRIFT_EVERY): the accurate energy of every chain's current positions (the
+// buffer is chosen on the device from the sweep counter, so captured graphs replay correctly) and the drift
+// |ledger - E| folded into the chain's last / maximum / count.
+cudaError_t enqueue_drift(mc_system *h)
+{
+    cudaError_t e = cudaSuccess;
+    for (size_t ci = 0; ci < h->chains.size() && e == cudaSuccess; ++ci) {
+        Chain &c = h->chains[ci];
+        e = mcg_host::energy_ff_launch(c.pos[0], c.pos[1], c.sweep, c.N, c.lB, c.eparts, c.e_out, c.ledger, c.drift,
+                                       h->stream);
+    }
+    return e;
+}
+
 // Delayed acceptance: one sweep per launch, each preceded by the preparation of every surrogate chain
 // (near-field cell list and feature grid of the sweep's start positions).  The control block is copied
 // once; later launches only reset its ticket counter, so an error or abort stays visible.
@@ -526,6 +547,27 @@ cudaError_t enqueue_da(mc_system *h, long long n, int grid, const mcg::Ticket *s
         if (e == cudaSuccess)
             e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), 1, h->stream,
                                        false);
+        if (e == cudaSuccess && h->drift_every > 0 && (t + 1) % h->drift_every == 0) e = enqueue_drift(h);
+    }
+    return e;
+}
+
+// Plain chains: n sweeps as persistent launches of at most K sweeps each (K = MC_OPT_DRIFT_EVERY, or all n when the
+// check is off), a drift check after every full K.
+cudaError_t enqueue_plain(mc_system *h, long long n, int grid, bool pr)
+{
+    const int nch = (int)h->chains.size();
+    const long long K = h->drift_every > 0 ? h->drift_every : n;
+    cudaError_t e = cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream);
+    for (long long done = 0; done < n && e == cudaSuccess;) {
+        const long long m = std::min(K, n - done);
+        mcg::Ticket *sched = nullptr;
+        int count = 0;
+        if (schedule_for(h, m, &sched, &count) != MC_OK) return cudaErrorInvalidValue;
+        if (done > 0) e = cudaMemsetAsync(&h->d_ctl->ticket, 0, sizeof(unsigned), h->stream);
+        if (e == cudaSuccess) e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, m, h->stream, pr);
+        done += m;
+        if (e == cudaSuccess && h->drift_every > 0 && m == K) e = enqueue_drift(h);
     }
     return e;
 }
@@ -535,14 +577,20 @@ int enqueue_sweeps(mc_system *h, long long n)
     mcg::Ticket *sched = nullptr;
     int count = 0;
     const bool da = any_da(h);
-    int rc = schedule_for(h, da ? 1 : n, &sched, &count);
+    const long long per = da ? 1 : (h->drift_every > 0 ? std::min<long long>(n, h->drift_every) : n);
+    int rc = schedule_for(h, per, &sched, &count);
     if (rc) return rc;
+    if (!da && h->drift_every > 0 && n > h->drift_every) {  // the schedule of the last, shorter launch
+        mcg::Ticket *s2 = nullptr;
+        int c2 = 0;
+        if ((rc = schedule_for(h, n % h->drift_every ? n % h->drift_every : h->drift_every, &s2, &c2))) return rc;
+    }
     const bool pr = !da && h->h_ctl->pairs != 0;
-    int grid = grid_for(h, da ? 1 : n);
+    int grid = grid_for(h, per);
     if (pr) grid = std::max(2, std::min(grid & ~1, 2 * h->max_clusters));  // whole clusters of two
     const int nch = (int)h->chains.size();
     if (h->use_graph) {
-        GraphKey key{n, grid, h->policy, pr ? 1 : 0};
+        GraphKey key{n, grid, h->policy, pr ? 1 : 0, h->drift_every};
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             cudaGraph_t g = nullptr;
@@ -551,8 +599,7 @@ int enqueue_sweeps(mc_system *h, long long n)
             if (da) {
                 e2 = enqueue_da(h, n, grid, sched, count);
             } else {
-                e1 = cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream);
-                e2 = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream, pr);
+                e2 = enqueue_plain(h, n, grid, pr);
             }
             cudaError_t e3 = cudaStreamEndCapture(h->stream, &g);
             if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -570,8 +617,7 @@ int enqueue_sweeps(mc_system *h, long long n)
     } else if (da) {
         CK(enqueue_da(h, n, grid, sched, count));
     } else {
-        CK(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream));
-        CK(mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, n, h->stream, pr));
+        CK(enqueue_plain(h, n, grid, pr));
     }
     for (auto &ch : h->chains) ch.sweeps += (uint64_t)n;
     return MC_OK;
@@ -695,7 +741,8 @@ int mc_energy(mc_handle h, int chain, double *ledger, double *recomputed)
     CK(cudaStreamSynchronize(h->stream));
     if (ledger) CK(cudaMemcpy(ledger, c.ledger, sizeof(double), cudaMemcpyDeviceToHost));
     if (recomputed) {
-        CK(mcg_host::energy_launch(c.cur(), c.N, c.lB, c.rows, c.e_out, h->stream));
+        CK(mcg_host::energy_ff_launch(c.cur(), nullptr, nullptr, c.N, c.lB, c.eparts, c.e_out, nullptr, nullptr,
+                                      h->stream));
         CK(cudaStreamSynchronize(h->stream));
         CK(cudaMemcpy(recomputed, c.e_out, sizeof(double), cudaMemcpyDeviceToHost));
     }
@@ -798,6 +845,11 @@ int mc_stats(mc_handle h, int chain, mc_stats_t *out)
     out->da_fp64 = v[mcg::CNT_DA_FP64];
     out->cyc_da1 = v[mcg::CNT_CYC_DA1];
     for (int q = 0; q < 4; ++q) out->cyc_da_part[q] = v[mcg::CNT_CYC_DA_PART + q];
+    double dr[3];
+    CK(cudaMemcpy(dr, c.drift, sizeof dr, cudaMemcpyDeviceToHost));
+    out->drift_checks = (uint64_t)dr[2];
+    out->drift_last = dr[0];
+    out->drift_max = dr[1];
     return MC_OK;
 }
 
@@ -1239,6 +1291,10 @@ static int set_option(mc_handle h, int option, int64_t value)
         h->deep_opt = (int)value;
         drop_graphs(h);
         return MC_OK;
+    case MC_OPT_DRIFT_EVERY:
+        if (value < 0) return fail(MC_ERR_INVALID, "drift check period %lld", (long long)value);
+        h->drift_every = value;
+        return MC_OK;
     default:
         return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
@@ -1269,6 +1325,7 @@ int mc_get_option(mc_handle h, int option, int64_t *value)
     case MC_OPT_DA: *value = h->da_on; return MC_OK;
     case MC_OPT_PAIRS: *value = pairs_on(h) ? 1 : 0; return MC_OK;
     case MC_OPT_DEEP_WINDOWS: *value = h->deep_opt; return MC_OK;
+    case MC_OPT_DRIFT_EVERY: *value = h->drift_every; return MC_OK;
     default: return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
 }
@@ -1430,6 +1487,9 @@ static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, in
     d.Rr = (float)c.R;
     d.nf_G = G;
     d.W = W;
+    d.mlp_zero = 1;
+    for (int k = 0; k < mcg::DA_NP; ++k)
+        if (w_bf16[k] & 0x7fffu) d.mlp_zero = 0;
     c.hda = d;
     CK(cudaMemcpy(c.dda, &d, sizeof d, cudaMemcpyHostToDevice));
     c.da = true;

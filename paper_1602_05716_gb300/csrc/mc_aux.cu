@@ -105,6 +105,163 @@ __global__ void __launch_bounds__(EB) gr_hist(const float4 *__restrict__ pos, in
         if (hist[b]) atomicAdd(&counts[b], hist[b]);
 }
 
+// ---------------------------------------------------------------------------
+// Accurate total energy (initial ledger, mc_energy's recomputation, the periodic drift check):
+// E = l_B sum_{i<j} q_i q_j / r_ij with every term in float-float arithmetic.  The coordinate differences are
+// exact (TwoSum), the squared distance is a float-float sum of exact squares (FMA TwoProduct), 1/r is one Newton
+// step r0 (1 + (1 - d2 r0^2) / 2) from rsqrt.approx with the residual formed from the exact square of r0, so a
+// term's relative error is about 1.5 (2^-22.9)^2 + a few 2^-48 (~2e-14) instead of the FP32 form's ~2^-21.
+// Sums: float-float over 64 columns, FP64 per row tile, a fixed tree per block, the blocks' partials in order.
+// The upper triangle is cut into pairs of row tiles {b, B-1-b} (equal work, B + 1 column tiles) and each pair into
+// C column classes; B and C depend on N only, so the result does not depend on the device.
+constexpr int ET = 128;             // rows per row tile
+constexpr int EFF_TARGET_BLOCKS = 1216;
+
+__host__ __device__ inline int eff_row_pairs(int N)
+{
+    const int B = (N + ET - 1) / ET;
+    return (B + 1) / 2;
+}
+
+__host__ __device__ inline int eff_classes(int N)
+{
+    const int B = (N + ET - 1) / ET, P = (B + 1) / 2;
+    int C = (EFF_TARGET_BLOCKS + P - 1) / P;
+    return C < 1 ? 1 : (C > B + 1 ? B + 1 : C);
+}
+
+__device__ __forceinline__ void ff_sum(float a, float b, float &s, float &e)  // Knuth's TwoSum
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void ff_sq(float h, float &p, float &e)  // h^2 = p + e exactly
+{
+    p = __fmul_rn(h, h);
+    e = __fmaf_rn(h, h, -p);
+}
+
+// q_j / |a - y| as th + tl.
+__device__ __forceinline__ void ff_term(const float4 a, const float4 y, float &th, float &tl)
+{
+    float hx, lx, hy, ly, hz, lz;
+    ff_sum(a.x, -y.x, hx, lx);
+    ff_sum(a.y, -y.y, hy, ly);
+    ff_sum(a.z, -y.z, hz, lz);
+    float px, ex, py, ey, pz, ez;
+    ff_sq(hx, px, ex);
+    ff_sq(hy, py, ey);
+    ff_sq(hz, pz, ez);
+    float s1, e1, s2, e2;
+    ff_sum(px, py, s1, e1);
+    ff_sum(s1, pz, s2, e2);
+    float low = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(ex, ey)), ez);
+    low = __fmaf_rn(__fmul_rn(2.0f, hx), lx, low);
+    low = __fmaf_rn(__fmul_rn(2.0f, hy), ly, low);
+    low = __fmaf_rn(__fmul_rn(2.0f, hz), lz, low);
+    const float dh = __fadd_rn(s2, low);                  // Fast2Sum: |s2| >= |low|
+    const float dl = __fsub_rn(low, __fsub_rn(dh, s2));
+    const float r0 = rsqrt_approx(dh);
+    float q0, q1;
+    ff_sq(r0, q0, q1);
+    float t = __fmaf_rn(-dh, q0, 1.0f);
+    t = __fmaf_rn(-dh, q1, t);
+    t = __fmaf_rn(-dl, q0, t);
+    const float rl = __fmul_rn(__fmul_rn(0.5f, r0), t);
+    th = __fmul_rn(y.w, r0);
+    tl = __fmaf_rn(y.w, rl, __fmaf_rn(y.w, r0, -th));
+}
+
+// Positions: pos0, or, when sweep is non-null, the buffer of the chain's current state pos[*sweep & 1] (read on the
+// device, so a captured graph replays correctly whatever the sweep count).
+__global__ void __launch_bounds__(2 * ET) energy_ff_part(const float4 *pos0, const float4 *pos1,
+                                                          const unsigned long long *sweep, int N,
+                                                          double *__restrict__ part)
+{
+    __shared__ float4 tile[ET];
+    const float4 *__restrict__ pos = (sweep && (*sweep & 1ull)) ? pos1 : pos0;
+    __shared__ double red[2 * ET];
+    const int B = (N + ET - 1) / ET, P = (B + 1) / 2, C = eff_classes(N);
+    const int b = blockIdx.x / C, c = blockIdx.x % C;
+    const int r = threadIdx.x & (ET - 1), h = threadIdx.x >> 7;
+    double tot = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        const int I = side == 0 ? b : B - 1 - b;
+        if (side == 1 && I == b) break;  // the middle row tile of an odd B
+        const int i = I * ET + r;
+        const float4 a = i < N ? __ldg(&pos[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        double row = 0.0;
+        for (int J = I + c; J < B; J += C) {
+            __syncthreads();
+            if (threadIdx.x < ET) {
+                const int j = J * ET + threadIdx.x;
+                tile[threadIdx.x] = j < N ? __ldg(&pos[j]) : make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+            }
+            __syncthreads();
+            if (i >= N) continue;
+            float ah = 0.f, al = 0.f;
+            const int l0 = h * (ET / 2);
+            if (J == I) {
+                for (int l = l0; l < l0 + ET / 2; ++l) {
+                    if (l <= r) continue;  // strictly upper: j > i
+                    float th, tl, s, e;
+                    ff_term(a, tile[l], th, tl);
+                    ff_sum(ah, th, s, e);
+                    ah = s;
+                    al = __fadd_rn(al, __fadd_rn(e, tl));
+                }
+            } else {
+#pragma unroll 4
+                for (int l = l0; l < l0 + ET / 2; ++l) {
+                    float th, tl, s, e;
+                    ff_term(a, tile[l], th, tl);
+                    ff_sum(ah, th, s, e);
+                    ah = s;
+                    al = __fadd_rn(al, __fadd_rn(e, tl));
+                }
+            }
+            row = __dadd_rn(row, __dadd_rn((double)ah, (double)al));
+        }
+        tot = __dadd_rn(tot, __dmul_rn((double)a.w, row));
+    }
+    red[threadIdx.x] = tot;
+    __syncthreads();
+    for (int w = ET; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+    (void)P;
+}
+
+// E = l_B sum of the partials in order; optionally the drift |ledger - E| folded into (last, max, count).
+__global__ void energy_ff_reduce(const double *__restrict__ part, int n_part, double lB, double *__restrict__ out,
+                                 const double *__restrict__ ledger, double *__restrict__ drift)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    const int per = (n_part + 255) / 256;
+    for (int k = threadIdx.x * per; k < min(n_part, (int)(threadIdx.x + 1) * per); ++k) s = __dadd_rn(s, part[k]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double E = __dmul_rn(lB, red[0]);
+        *out = E;
+        if (drift) {
+            const double d = fabs(__dsub_rn(*ledger, E));
+            drift[0] = d;
+            drift[1] = fmax(drift[1], d);
+            drift[2] = __dadd_rn(drift[2], 1.0);
+        }
+    }
+}
+
 __global__ void philox_test(const uint4 *__restrict__ ctr, const uint2 *__restrict__ key, int n, uint4 *out_lib,
                             uint4 *out_curand)
 {
@@ -128,6 +285,23 @@ cudaError_t energy_launch(const float4 *pos, int N, double lB, double *rows, dou
 {
     mcg::energy_rows<<<(N + mcg::EB - 1) / mcg::EB, mcg::EB, 0, st>>>(pos, N, rows);
     mcg::energy_reduce<<<1, 1024, 0, st>>>(rows, N, lB, out);
+    return cudaGetLastError();
+}
+
+// Number of FP64 partials of the accurate energy of N ions (the caller's scratch).
+int energy_ff_parts(int N)
+{
+    return mcg::eff_row_pairs(N) * mcg::eff_classes(N);
+}
+
+// out = accurate total energy of pos0 (sweep == NULL) or of pos[*sweep & 1]; with ledger/drift non-null also the
+// drift fold (see energy_ff_reduce).
+cudaError_t energy_ff_launch(const float4 *pos0, const float4 *pos1, const unsigned long long *sweep, int N, double lB,
+                             double *part, double *out, const double *ledger, double *drift, cudaStream_t st)
+{
+    const int n = energy_ff_parts(N);
+    mcg::energy_ff_part<<<n, 2 * mcg::ET, 0, st>>>(pos0, pos1, sweep, N, part);
+    mcg::energy_ff_reduce<<<1, 256, 0, st>>>(part, n, lB, out, ledger, drift);
     return cudaGetLastError();
 }
 
@@ -176,9 +350,42 @@ namespace {
 constexpr long long NOALLOC_MAX_IONS = 1ll << 20;  // 8 MiB of FP64 row sums
 static __device__ __align__(256) double g_noalloc_rows[NOALLOC_MAX_IONS];
 
+// The array's device address belongs to the context the module was loaded into.  A context that is destroyed and
+// created anew (cudaDeviceReset, or the primary context released and retained again) may load the module at
+// another address, so the cached address is keyed by the context's unique id and looked up again when it changes.
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mutex;
 double *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+unsigned long long g_noalloc_ctx[NOALLOC_MAX_DEVICES];  // id of the context the address belongs to (0: none)
+
+typedef int (*ctx_get_current_fn)(void **);
+typedef int (*ctx_get_id_fn)(void *, unsigned long long *);
+
+// Unique id of the calling thread's current context, 0 when none is current (or the driver lacks the call).
+unsigned long long current_ctx_id()
+{
+    static ctx_get_current_fn get_cur = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_cur = reinterpret_cast<ctx_get_current_fn>(f1);
+            get_id = reinterpret_cast<ctx_get_id_fn>(f2);
+        }
+        looked_up = true;
+    }
+    if (!get_cur || !get_id) return 0ull;
+    void *ctx = nullptr;
+    if (get_cur(&ctx) != 0 || !ctx) return 0ull;
+    unsigned long long id = 0ull;
+    if (get_id(ctx, &id) != 0) return 0ull;
+    return id;
+}
 
 }  // namespace
 
@@ -196,13 +403,22 @@ extern "C" int mc_total_energy_noalloc(const void *pos_q_dev, int64_t n, double 
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return mcg_host::set_error(MC_ERR_INVALID, "device ordinal too large");
     double *rows = nullptr;
     {
-        // set-up, once per device, with that device current: the array's device address
+        // set-up, once per device and context, with that device current: the array's device address
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
+        const unsigned long long ctx = current_ctx_id();
+        if (!g_noalloc_ptr[dev] || ctx == 0ull || ctx != g_noalloc_ctx[dev]) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            e = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs);
+            if (e != cudaSuccess) return mcg_host::set_error(MC_ERR_CUDA, cudaGetErrorString(e));
+            if (cs != cudaStreamCaptureStatusNone)
+                return mcg_host::set_error(MC_ERR_INVALID,
+                                           "first call on this device (or after a context reset) inside a stream "
+                                           "capture: make one call before capturing");
             void *ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_noalloc_rows);
             if (e != cudaSuccess || !ptr) return mcg_host::set_error(MC_ERR_CUDA, cudaGetErrorString(e));
             g_noalloc_ptr[dev] = static_cast<double *>(ptr);
+            g_noalloc_ctx[dev] = current_ctx_id();  // the look-up made the primary context current if none was
         }
         rows = g_noalloc_ptr[dev];
     }

@@ -53,6 +53,7 @@ struct DADev {
     float Rr;                      // fl32(R) for the FP32 radial input
     int nf_G;                      // near-field cells per axis
     int W;                         // exclusion depth in groups
+    int mlp_zero;                  // every weight is +-0, so g = 0 exactly: the FP32 MLP pass is skipped
 };
 
 __device__ __forceinline__ int da_ncell_axis(const DADev &d, float x)

@@ -328,8 +328,16 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
     return r;
 }
 
-// Two moves (packed old positions b, displacements d, negated displacements nd) against one settled ion y: the
-// arithmetic of pair_far per lane, without the |t| sum (|t| <= dn rn ro exactly, so the bound takes dn P).
+// Two moves (packed old positions b, displacements d, negated displacements nd) against one settled ion y.  Do, Dd
+// and Dn as in pair_far; then the term with two MUFU operations instead of three:
+//   s = rsqrt(Do Dn) = rn ro,   w = rsqrt(Do + Dn + 2 (Do Dn) s) = 1 / (sqrt(Do) + sqrt(Dn)) = rn ro / (rn + ro),
+//   t = (Dd s) w = Dd (rn ro)^2 / (rn + ro).
+// Relative error of t beyond Dd's own: with Do, Dn off by delta_o, delta_n (relative), s is within
+// (|delta_o| + |delta_n| + u) / 2 + 2^-22.9, sqrt(Do Dn) = (Do Dn) s within that + u, Do + Dn + 2 sqrt(Do Dn) (a sum
+// of positive terms) within max(|delta_o|, |delta_n|) + 4.7u, w within half of that + 2^-22.9, so t is within
+// |delta_o| + |delta_n| + 9.2u: below the rel(Dn) + 19u (|delta_o| <= 3u) of pair_far's per-term bound.  Without the
+// |t| sum (|t| <= dn rn ro exactly, so the bound takes dn P); P sums |q| s, which is within rel(Dn) / 2 + 5u of
+// rn ro, inside the bound's 2^-16 slack for the rounding of rn ro.
 struct Mv2 {
     f32x2 bx, by, bz, dx, dy, dz, nx, ny, nz;
 };
@@ -342,18 +350,50 @@ __device__ __forceinline__ void pair_far2(const Mv2 &m, const float4 y, f32x2 &s
     const f32x2 wx = fma2(two, ex, m.nx), wy = fma2(two, ey, m.ny), wz = fma2(two, ez, m.nz);
     const f32x2 Dd = fma2(m.dz, wz, fma2(m.dy, wy, mul2(m.dx, wx)));
     const f32x2 Dn = sub2(Do, Dd);
-    float Do0, Do1, Dn0, Dn1;
-    upk2(Do, Do0, Do1);
-    upk2(Dn, Dn0, Dn1);
-    const f32x2 ro = pk2(rsqrt_ftz(Do0), rsqrt_ftz(Do1)), rn = pk2(rsqrt_ftz(Dn0), rsqrt_ftz(Dn1));
-    const f32x2 pr = mul2(rn, ro);
-    float h0, h1;
-    upk2(add2(rn, ro), h0, h1);
-    const f32x2 t = mul2(mul2(Dd, pr), mul2(pr, pk2(rcp_ftz(h0), rcp_ftz(h1))));
+    const f32x2 pd = mul2(Do, Dn);
+    float p0, p1;
+    upk2(pd, p0, p1);
+    const f32x2 sr = pk2(rsqrt_ftz(p0), rsqrt_ftz(p1));
+    const f32x2 c2 = fma2(two, mul2(pd, sr), add2(Do, Dn));
+    float c0, c1;
+    upk2(c2, c0, c1);
+    const f32x2 w = pk2(rsqrt_ftz(c0), rsqrt_ftz(c1));
+    const f32x2 t = mul2(mul2(Dd, sr), w);
     s = fma2(pk2(y.w, y.w), t, s);
-    P = fma2(pk2(fabsf(y.w), fabsf(y.w)), pr, P);
+    P = fma2(pk2(fabsf(y.w), fabsf(y.w)), sr, P);
+    float Dn0, Dn1;
+    upk2(Dn, Dn0, Dn1);
     mn0 = fminf(mn0, Dn0);
     mn1 = fminf(mn1, Dn1);
+}
+
+// One move against one settled ion: lane 0 of pair_far2's arithmetic, operation for operation (every packed lane
+// rounds like the scalar operation), for a third occupied layer of 32 move slots.
+__device__ __forceinline__ void pair_far1(const Mv2 &m, const float4 y, float &s, float &P, float &mn)
+{
+    float bx, by, bz, dx, dy, dz, nx, ny, nz, u;
+    upk2(m.bx, bx, u);
+    upk2(m.by, by, u);
+    upk2(m.bz, bz, u);
+    upk2(m.dx, dx, u);
+    upk2(m.dy, dy, u);
+    upk2(m.dz, dz, u);
+    upk2(m.nx, nx, u);
+    upk2(m.ny, ny, u);
+    upk2(m.nz, nz, u);
+    const float ex = __fsub_rn(y.x, bx), ey = __fsub_rn(y.y, by), ez = __fsub_rn(y.z, bz);
+    const float Do = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
+    const float wx = __fmaf_rn(2.0f, ex, nx), wy = __fmaf_rn(2.0f, ey, ny), wz = __fmaf_rn(2.0f, ez, nz);
+    const float Dd = __fmaf_rn(dz, wz, __fmaf_rn(dy, wy, __fmul_rn(dx, wx)));
+    const float Dn = __fsub_rn(Do, Dd);
+    const float pd = __fmul_rn(Do, Dn);
+    const float sr = rsqrt_ftz(pd);
+    const float c2 = __fmaf_rn(2.0f, __fmul_rn(pd, sr), __fadd_rn(Do, Dn));
+    const float w = rsqrt_ftz(c2);
+    const float t = __fmul_rn(__fmul_rn(Dd, sr), w);
+    s = __fmaf_rn(y.w, t, s);
+    P = __fmaf_rn(fabsf(y.w), sr, P);
+    mn = fminf(mn, Dn);
 }
 
 // Error-free transformations in FP32 (Knuth's TwoSum, FMA-based TwoProduct).

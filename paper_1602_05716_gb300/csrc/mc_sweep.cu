@@ -951,11 +951,12 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
     __syncthreads();
     part[3] += clock64() - tq;
     tq = clock64();
-    // MLP at every point (thread = point: 0..S-1 old positions, S..2S-1 trials)
+    // MLP at every point (thread = point: 0..S-1 old positions, S..2S-1 trials); with all weights zero g = 0
+    // exactly (every layer's output is silu(0) = 0 and the last one is 0), so the pass is skipped
     {
         const int k = tid & (S - 1);
         float g = 0.f, eg = 0.f;
-        if (active(k) && !novl[k]) {
+        if (active(k) && !novl[k] && !d.mlp_zero) {
             const float4 p = tid < S ? sm.own[k] : sm.trial[k];
             float v[DA_NIN];
 #pragma unroll
@@ -1540,6 +1541,18 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     }
         if (nm <= 2) {
             MC_TILE_PASS(1)
+        } else if (nm == 3) {  // three occupied layers: one packed pair and the third layer alone
+            float s3, s3b, p3, p3b;
+            upk2(s2[1], s3, s3b);
+            upk2(P2[1], p3, p3b);
+            _Pragma("unroll 8") for (int jj = 0; jj < nj; ++jj)
+            {
+                const float4 y = sm.tile[cur][jj * SL + r];
+                pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
+                pair_far1(mv[1], y, s3, p3, mA[2]);
+            }
+            s2[1] = pk2(s3, s3b);
+            P2[1] = pk2(p3, p3b);
         } else {
             MC_TILE_PASS(MPT / 2)
         }

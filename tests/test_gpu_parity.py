@@ -422,3 +422,69 @@ def test_large_n1048576_sampled_parity(pkg):
         assert ((x[a] - x[b]) ** 2).sum() >= 1.0
     led, rec = g.energy()
     assert abs(led - rec) < 1e-5 * abs(rec), (led, rec)
+
+
+def _magnitude(pos, q, l_B, block=1024):
+    """l_B sum_{i<j} |q_i q_j| / r_ij (FP64, numpy, by row blocks): the scale of the energy's rounding error."""
+    x = pos.astype(np.float64)
+    qa = np.abs(q.astype(np.float64))
+    tot = 0.0
+    for i0 in range(0, len(x), block):
+        d = x[i0:i0 + block, None, :] - x[None, :, :]
+        r = np.sqrt((d * d).sum(-1))
+        idx = np.arange(i0, min(i0 + block, len(x)))
+        r[np.arange(len(idx)), idx] = np.inf
+        tot += float((qa[idx, None] * qa[None, :] / r).sum())
+    return 0.5 * l_B * tot
+
+
+@pytest.mark.parametrize("n,two_one,seed", [(700, True, 501), (20000, False, 502)])
+def test_accurate_energy_against_oracle(pkg, n, two_one, seed):
+    """The recomputed energy (float-float terms, FP64 sums) against the oracle's brute-force FP64 energy of the same
+    positions, within 1e-11 of the magnitude sum (the FP32 form was good to ~1e-7), at the start and after sweeps;
+    the initial ledger is the same computation."""
+    ch = inputs.small_chain(n, phi=0.2, seed=seed, two_one=two_one, half_width=0.4)
+    import paper_1602_05716_gb300 as p
+    gs = p.System([ch])
+    mag = _magnitude(ch.pos, ch.q, ch.l_B)
+    e0 = oracle.total_energy(ch.pos, ch.q, ch.l_B)
+    led, rec = gs.energy()
+    assert abs(led - e0) <= 1e-11 * mag and abs(rec - e0) <= 1e-11 * mag, (led, rec, e0, mag)
+    gs.sweep(2)
+    pos = gs.positions()
+    _, rec = gs.energy()
+    e1 = oracle.total_energy(pos, ch.q, ch.l_B)
+    assert abs(rec - e1) <= 1e-11 * mag, (rec, e1, mag)
+    gs.close()
+
+
+def test_periodic_drift_check(pkg):
+    """MC_OPT_DRIFT_EVERY = 1: a drift check after every sweep, inside the captured sweep loop.  The trajectory is
+    the oracle's; the stored drift equals |ledger - E| with E the oracle's brute-force energy of the final
+    positions (within 1e-10 of the magnitude sum); the count follows the rule (after every full K sweeps of a
+    call), also when the graph is replayed with the other buffer parity."""
+    ch = inputs.small_chain(700, phi=0.2, seed=503, two_one=True, half_width=0.4)
+    import paper_1602_05716_gb300 as p
+    gs, oc = _pair(ch)
+    gs.set_option(p.OPT_DRIFT_EVERY, 1)
+    assert gs.get_option(p.OPT_DRIFT_EVERY) == 1
+    gs.sweep(3)
+    gs.sweep(3)  # the same graph replayed, the positions now in the other buffer
+    oc.sweep(6)
+    pos = gs.positions()
+    assert (pos == oc.positions()).all()
+    st = gs.stats()
+    assert st["drift_checks"] == 6
+    led = gs.energy(recompute=False)[0]
+    mag = _magnitude(pos, ch.q, ch.l_B)
+    e_or = oracle.total_energy(pos, ch.q, ch.l_B)
+    assert abs(st["drift_last"] - abs(led - e_or)) <= 1e-10 * mag, (st["drift_last"], led, e_or)
+    assert st["drift_max"] >= st["drift_last"]
+    assert abs(led - oc.energy(recompute=False)[0]) <= 1e-6 * mag
+    # K = 3 over a call of 7 sweeps: checks after sweeps 3 and 6 of the call only
+    gs.set_option(p.OPT_DRIFT_EVERY, 3)
+    gs.sweep(7)
+    oc.sweep(7)
+    assert (gs.positions() == oc.positions()).all()
+    assert gs.stats()["drift_checks"] == 8
+    gs.close()
