@@ -38,12 +38,10 @@ METRIC = "MC trial moves/s and G pair-evals/s per GB300 vs plain exact FP64-guar
 SWEEP_SOURCES = ["paper_1602_05716_gb300/csrc/mc_sweep.cu", "paper_1602_05716_gb300/csrc/mc_device.cuh",
                  "paper_1602_05716_gb300/csrc/mc_da.cuh"]
 
-# ALU roofline of the pair term: per pair-eval two MUFU reciprocal square roots and
-# 14 FP32-pipe operations (6 differences, 6 multiply/fma for the two squared distances, 1 difference of the
-# inverse distances, 1 fma into the sum).  Unit rates per SM per clock on sm_103: FP32 lanes 128; MUFU rsqrt
-# MUFU_RSQ_PER_CLK (measured on GB300 with an in-kernel clock64 throughput probe: 15.98 rsqrt/clk/SM).
-FP32_PER_CLK = 128.0
-MUFU_RSQ_PER_CLK = 16.0
+# ALU roofline of the pair term: per pair-eval two MUFU reciprocal square roots and 14 FP32-pipe operations
+# (6 differences, 6 multiply/fma for the two squared distances, 1 difference of the inverse distances, 1 fma into
+# the sum).  The unit rates are measured on the GPU the bench runs on (mc_unit_rates: rsqrt.approx and packed FFMA
+# chains at 8..64 resident warps per SM); the peak takes the highest measured rate of each unit.
 ALG_FP32_PER_PAIR = 14.0
 RSQ_PER_PAIR = 2.0
 
@@ -52,8 +50,9 @@ DEFAULT_STEPS = {"plain_n256": 200, "plain_n16383": 50, "batch64": 20, "da_n6553
 DEFAULT_MODE = {"da_n65536": "both", "large_n1048576": "both"}
 
 
-def peak_pairs_per_clk_sm() -> float:
-    return min(MUFU_RSQ_PER_CLK / RSQ_PER_PAIR, FP32_PER_CLK / ALG_FP32_PER_PAIR)
+def peak_pairs_per_clk_sm(rsqrt_per_clk: float, fp32_per_clk: float) -> float:
+    """Pair-evals per SM clock the two units allow: min(rsqrt rate / 2, FP32 rate / 14)."""
+    return min(rsqrt_per_clk / RSQ_PER_PAIR, fp32_per_clk / ALG_FP32_PER_PAIR)
 
 
 def source_hash() -> str:
@@ -355,18 +354,21 @@ def time_arm(pkg, chains, stream, flush, steps: int, warmup: int, sps: int, worl
             "clocks": clk.summary() if clk else None}
 
 
-def roofline(pairs_per_step: float, step_ms, info: dict, max_mhz: float, load_mhz, traffic, kernel: str) -> dict:
-    peak = info["sm_count"] * peak_pairs_per_clk_sm() * max_mhz * 1e6
+def roofline(pairs_per_step: float, step_ms, info: dict, max_mhz: float, load_mhz, traffic, kernel: str,
+             rates: dict) -> dict:
+    r_rsq, r_fp32 = max(rates["rsqrt_per_clk_sm"]), max(rates["fp32_per_clk_sm"])
+    peak = info["sm_count"] * peak_pairs_per_clk_sm(r_rsq, r_fp32) * max_mhz * 1e6
     achieved = pairs_per_step / (statistics.mean(step_ms) / 1000.0)
     return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-evals/s",
             "frac": achieved / peak, "traffic": traffic,
-            "peak_basis": f"{info['sm_count']} SMs x min(MUFU rsqrt {MUFU_RSQ_PER_CLK:g}/clk / 2 per pair, FP32 "
-                          f"{FP32_PER_CLK:g}/clk / {ALG_FP32_PER_PAIR:g} per pair) x {max_mhz:g} MHz (max SM clock)",
+            "peak_basis": f"{info['sm_count']} SMs x min(MUFU rsqrt {r_rsq:.2f}/clk / 2 per pair, FP32 {r_fp32:.1f}/clk "
+                          f"/ {ALG_FP32_PER_PAIR:g} per pair) x {max_mhz:g} MHz (max SM clock); unit rates measured "
+                          f"on this GPU by mc_unit_rates (highest of 8..64 warps per SM)",
             "frac_at_load_clock": (achieved / (peak * load_mhz / max_mhz)) if load_mhz else None,
             "kernel": kernel}
 
 
-def arm_summary(arm: dict, chains, sps: int, steps: int, info, max_mhz, load_mhz, traffic, da: bool) -> dict:
+def arm_summary(arm: dict, chains, sps: int, steps: int, info, max_mhz, load_mhz, traffic, da: bool, rates) -> dict:
     n = sum(c.n for c in chains)
     d = arm["delta"]
     moves = n * sps * steps
@@ -382,7 +384,7 @@ def arm_summary(arm: dict, chains, sps: int, steps: int, info, max_mhz, load_mhz
         kernel = "mcg::sweep_kernel (one launch per step), CUDA events on its stream"
     out = {"moves_per_s": moves / t, "ms_per_step": statistics.mean(arm["step_ms"]), "steps": steps,
            "gpair_evals_executed_per_s": executed / t / 1e9,
-           "roofline": roofline(executed / steps, arm["step_ms"], info, max_mhz, load_mhz, traffic, kernel),
+           "roofline": roofline(executed / steps, arm["step_ms"], info, max_mhz, load_mhz, traffic, kernel, rates),
            "accept_rate": d["accepts"] / moves, "overlap_rejects_per_move": d["rej_overlap"] / moves,
            "guard_per_move": d["guard_fp64"] / moves, "guard_tiers_2_3_4": [d["tier2"], d["tier3"], d["tier4"]]}
     if da:
@@ -415,6 +417,7 @@ def run_ours(args):
     info = pkg.device_info()
     peaks = peaks_file()
     max_mhz = float(peaks.get("sm_max_mhz") or info["sm_clock_khz"] / 1000.0)
+    rates = pkg.unit_rates()
 
     da_info = w_da = None
     if mode in ("da", "both"):
@@ -449,7 +452,7 @@ def run_ours(args):
     load_mhz = csum.get("sm_mhz")
     summaries = {k: arm_summary(a, chains, sps, args.steps, info, max_mhz, (a["clocks"] or {}).get("sm_mhz"),
                                 measured_traffic(args.workload, "da" if k.startswith("da") else "plain"),
-                                k.startswith("da"))
+                                k.startswith("da"), rates)
                  for k, a in arms.items()}
     hs = summaries[head_name]
     energies = [sysm.energy(i) for i in range(len(chains))]
@@ -468,6 +471,7 @@ def run_ours(args):
                        "path": {"da": "delayed acceptance, trained surrogate", "plain": "plain exact"}[head_name]},
             "gpair_evals_per_s": hs["gpair_evals_executed_per_s"],
             "roofline": hs["roofline"],
+            "unit_rates": rates,
             "clocks": csum,
             "accept_rate": hs["accept_rate"], "guard_per_move": hs["guard_per_move"],
             "guard_tiers_2_3_4": hs["guard_tiers_2_3_4"],

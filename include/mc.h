@@ -335,7 +335,15 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
  *                      chain's drift_last, drift_max and drift_checks
  *                      (mc_stats); a call of fewer than K sweeps runs no
  *                      check.  Captured in the same CUDA graph as the sweeps.
- *                      0 = off (default).  The trajectory is unchanged. */
+ *                      0 = off (default).  The trajectory is unchanged.
+ *  MC_OPT_HELPERS      0 = off (default), 1 = on when pairs mode is off:
+ *                      launch the 512-thread form of the sweep kernel, whose
+ *                      second 256 threads run half of every work item's pair
+ *                      sums over the other groups with a small register
+ *                      budget, while the first 256 run the work items as
+ *                      before.  The trajectory is identical either way;
+ *                      reading it returns whether the form is in effect.
+ *                      The autotuner tries it. */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3
@@ -346,16 +354,24 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
 #define MC_OPT_PAIRS 8
 #define MC_OPT_DEEP_WINDOWS 9
 #define MC_OPT_DRIFT_EVERY 10
+#define MC_OPT_HELPERS 11
 int mc_set_option(mc_handle h, int option, int64_t value);
 int mc_get_option(mc_handle h, int option, int64_t *value);
 
-/* Autotuner for batches: times trial_sweeps sweeps for every candidate work
- * order (MC_OPT_POLICY) and persistent CTA count (all resident slots, 3/4,
- * 1/2), keeps the fastest in the handle and restores every chain's state,
- * so the trajectories are unchanged.  Outputs (nullable): the chosen policy,
- * CTA count and its trial time in ms.  The paper tunes block size and
+/* Autotuner: times trial_sweeps sweeps of every candidate and keeps the
+ * fastest in the handle, restoring every chain's state, so the trajectories
+ * are unchanged.  First the kernel shape at the current work order and CTA
+ * count: pairs mode (MC_OPT_PAIRS), deep windows (MC_OPT_DEEP_WINDOWS) and
+ * helper warps (MC_OPT_HELPERS), every combination the device and the chains
+ * allow (pairs mode and helper warps exclude each other; pairs mode needs
+ * clusters and no surrogate); then, with that shape, every work order
+ * (MC_OPT_POLICY) and persistent CTA count (all resident slots, 3/4, 1/2).
+ * Outputs (nullable): the chosen policy, CTA count, shape (bit 0 pairs
+ * mode, bit 1 deep windows, bit 2 helper warps; the options are set to it)
+ * and the winner's trial time in ms.  The paper tunes block size and
  * threads per particle by hand (Sec. 4, Table Para).                        */
-int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t *best_ctas, double *best_ms);
+int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t *best_ctas, int64_t *best_shape,
+                double *best_ms);
 
 /* ---- Delayed acceptance with a learned surrogate ----------------------
  * A two-stage Metropolis test (Christen & Fox, 2005) on the sequential chain of
@@ -450,6 +466,16 @@ int mc_device_info(int *sm_count, int *sm_clock_khz, int *cc_major, int *cc_mino
  * curand_Philox4x32_10 for n (counter, key) pairs; ctr: n*4, key: n*2,
  * out_lib / out_curand: n*4 (all host arrays).                               */
 int mc_test_philox(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t *out_lib, uint32_t *out_curand);
+
+/* Measurement hook behind the ALU roofline (no counterpart in the paper):
+ * the throughput of the two units the pair term uses, measured on the
+ * current device.  Every thread runs 8 independent chains of one operation;
+ * blocks of 256 threads, 1, 2, 4 and 8 of them per SM (8 to 64 resident
+ * warps); clock64 around the loop.  rates (8 doubles, host): row w = 0..3
+ * for 8 << w warps per SM, column 0 = rsqrt.approx.ftz per SM clock, column
+ * 1 = FP32 operations per SM clock as packed fma.rn.f32x2 (two each).  Runs
+ * synchronously on the default stream for about a millisecond.             */
+int mc_unit_rates(double *rates);
 
 /* Test hook: the library's device FP64 logarithm L(u) for n values. */
 int mc_test_log(const double *u, int64_t n, double *out);

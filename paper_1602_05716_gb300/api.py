@@ -12,6 +12,7 @@ ERR_INVALID, ERR_OVERLAP_INIT, ERR_CUDA, ERR_TIMEOUT, ERR_OOM, ERR_POISONED = -1
 OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH, OPT_POLICY, OPT_DA, OPT_PAIRS = 1, 2, 3, 4, 5, 6, 7, 8
 OPT_DEEP_WINDOWS = 9
 OPT_DRIFT_EVERY = 10
+OPT_HELPERS = 11
 MLP_NIN, MLP_H = 33, 64
 MLP_NP = MLP_H * MLP_NIN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1  # layout W1, b1, W2, b2, W3, b3
 
@@ -103,12 +104,13 @@ def lib():
                                      ctypes.POINTER(_DIT)], ci),
         "mc_set_option": ([vp, ci, i64], ci),
         "mc_get_option": ([vp, ci, vp], ci),
-        "mc_autotune": ([vp, i64, vp, vp, vp], ci),
+        "mc_autotune": ([vp, i64, vp, vp, vp, vp], ci),
         "mc_destroy": ([vp], None),
         "mc_last_error": ([], ctypes.c_char_p),
         "mc_device_info": ([vp, vp, vp, vp], ci),
         "mc_test_philox": ([vp, vp, i64, vp, vp], ci),
         "mc_test_log": ([vp, i64, vp], ci),
+        "mc_unit_rates": ([vp], ci),
         "mc_total_energy_noalloc": ([vp, i64, dbl, vp, vp], ci),
         "mc_set_surrogate": ([vp, ci, vp, i64, dbl, ci], ci),
         "mc_da_samples": ([vp, ci, vp, vp, vp], ci),
@@ -144,6 +146,13 @@ def test_philox(ctr: np.ndarray, key: np.ndarray):
     b = np.zeros((n, 4), np.uint32)
     _check(lib().mc_test_philox(ctr.ctypes.data, key.ctypes.data, n, a.ctypes.data, b.ctypes.data))
     return a, b
+
+
+def unit_rates() -> dict:
+    """rsqrt and FP32 (packed FFMA) operations per SM clock on the current GPU at 8, 16, 32 and 64 warps per SM."""
+    r = np.zeros(8, np.float64)
+    _check(lib().mc_unit_rates(r.ctypes.data))
+    return {"warps_per_sm": [8, 16, 32, 64], "rsqrt_per_clk_sm": r[0::2].tolist(), "fp32_per_clk_sm": r[1::2].tolist()}
 
 
 def test_log(u: np.ndarray) -> np.ndarray:
@@ -227,9 +236,11 @@ class System:
         return v.value
 
     def autotune(self, trial_sweeps: int = 2) -> dict:
-        pol, ctas, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
-        _check(lib().mc_autotune(self._h, int(trial_sweeps), ctypes.byref(pol), ctypes.byref(ctas), ctypes.byref(ms)))
-        return dict(policy=pol.value, ctas=ctas.value, trial_ms=ms.value)
+        """Kernel shape, then work order and CTA count (mc_autotune); the handle keeps the winner."""
+        pol, ctas, shape, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().mc_autotune(self._h, int(trial_sweeps), ctypes.byref(pol), ctypes.byref(ctas), ctypes.byref(shape),
+                                 ctypes.byref(ms)))
+        return dict(policy=pol.value, ctas=ctas.value, shape=shape.value, trial_ms=ms.value)
 
     def energy(self, chain: int = 0, recompute: bool = True):
         led = ctypes.c_double()

@@ -25,7 +25,8 @@ size_t sweep_smem_bytes();
 cudaError_t sweep_configure();
 cudaError_t sweep_occupancy(int *blocks_per_sm);
 cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticket *sched, int n_tickets, mcg::Ctl *ctl,
-                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs);
+                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs, bool help);
+cudaError_t sweep_occupancy_h(int *blocks_per_sm);
 cudaError_t sweep_max_clusters(int *n);
 int energy_ff_parts(int N);
 cudaError_t energy_ff_launch(const float4 *pos0, const float4 *pos1, const unsigned long long *sweep, int N, double lB,
@@ -35,6 +36,7 @@ cudaError_t gr_launch(const float4 *pos, int N, int n_bins, double dr, float rma
 cudaError_t philox_test_launch(const uint4 *ctr, const uint2 *key, int n, uint4 *out_lib, uint4 *out_curand,
                                cudaStream_t st);
 cudaError_t log_test_launch(const double *u, int n, double *out, cudaStream_t st);
+cudaError_t unit_rates(int sms, double *out);
 cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt, int *cellid,
                            int *start, int *fill, int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st);
 cudaError_t da_sample_launch(const mcg::ChainDev *ch, const mcg::DADev *dd, int B, int grid, float *V, float *Y,
@@ -172,6 +174,8 @@ struct mc_system {
     int pairs_opt = -1;                 // MC_OPT_PAIRS: -1 automatic, 0 off, 1 on
     int deep_opt = 1;                   // MC_OPT_DEEP_WINDOWS: 1 on (default), 0 off
     long long drift_every = 0;          // MC_OPT_DRIFT_EVERY: accurate energy and drift check every K sweeps (0 off)
+    int helpers_opt = 0;                // MC_OPT_HELPERS: 0 off (default), 1 on
+    int occ_h = 0;                      // resident CTAs per SM of the helper-warp kernel (0: unavailable)
     int max_clusters = 0;               // resident clusters of two CTAs (0: pairs mode unavailable)
     mcg::PairBox *d_box = nullptr;      // one hand-over box per cluster
     int da_on = 1;  // chains with a surrogate sweep with delayed acceptance (MC_OPT_DA)
@@ -410,6 +414,10 @@ int create_common(const mc_chain_desc *descs, int n_chains, mc_handle *out)
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         mcg_host::sweep_configure() != cudaSuccess || mcg_host::sweep_occupancy(&h->occ) != cudaSuccess)
         return bail(fail(MC_ERR_CUDA, "kernel configuration failed: %s", cudaGetErrorString(cudaGetLastError())));
+    if (mcg_host::sweep_occupancy_h(&h->occ_h) != cudaSuccess) {
+        h->occ_h = 0;  // the helper-warp kernel cannot run: one group of warps per work item
+        cudaGetLastError();
+    }
     if (mcg_host::sweep_max_clusters(&h->max_clusters) != cudaSuccess) {
         h->max_clusters = 0;  // clusters unavailable: pairs mode stays off
         cudaGetLastError();
@@ -516,6 +524,15 @@ bool any_da(const mc_system *h)
     return false;
 }
 
+// Helper warps (MC_OPT_HELPERS): the 2T-thread kernel whose second half takes half of every tile pass; used when
+// asked for (directly or by the autotuner) and pairs mode is off.  Off by default: on GB300 it measured slower.
+bool pairs_on(const mc_system *h);
+bool helpers_on(const mc_system *h)
+{
+    if (h->occ_h < 1 || h->helpers_opt != 1) return false;
+    return !pairs_on(h);
+}
+
 // The periodic drift check (MC_OPT_DRIFT_EVERY): the accurate energy of every chain's current positions (the
 // buffer is chosen on the device from the sweep counter, so captured graphs replay correctly) and the drift
 // |ledger - E| folded into the chain's last / maximum / count.
@@ -546,7 +563,7 @@ cudaError_t enqueue_da(mc_system *h, long long n, int grid, const mcg::Ticket *s
         }
         if (e == cudaSuccess)
             e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), 1, h->stream,
-                                       false);
+                                       false, helpers_on(h));
         if (e == cudaSuccess && h->drift_every > 0 && (t + 1) % h->drift_every == 0) e = enqueue_drift(h);
     }
     return e;
@@ -565,7 +582,8 @@ cudaError_t enqueue_plain(mc_system *h, long long n, int grid, bool pr)
         int count = 0;
         if (schedule_for(h, m, &sched, &count) != MC_OK) return cudaErrorInvalidValue;
         if (done > 0) e = cudaMemsetAsync(&h->d_ctl->ticket, 0, sizeof(unsigned), h->stream);
-        if (e == cudaSuccess) e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, m, h->stream, pr);
+        if (e == cudaSuccess)
+            e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, m, h->stream, pr, !pr && helpers_on(h));
         done += m;
         if (e == cudaSuccess && h->drift_every > 0 && m == K) e = enqueue_drift(h);
     }
@@ -1295,6 +1313,12 @@ static int set_option(mc_handle h, int option, int64_t value)
         if (value < 0) return fail(MC_ERR_INVALID, "drift check period %lld", (long long)value);
         h->drift_every = value;
         return MC_OK;
+    case MC_OPT_HELPERS:
+        if (value < 0 || value > 1) return fail(MC_ERR_INVALID, "helpers %lld", (long long)value);
+        if (value == 1 && h->occ_h < 1) return fail(MC_ERR_INVALID, "the helper-warp kernel does not fit an SM");
+        h->helpers_opt = (int)value;
+        drop_graphs(h);
+        return MC_OK;
     default:
         return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
@@ -1326,13 +1350,15 @@ int mc_get_option(mc_handle h, int option, int64_t *value)
     case MC_OPT_PAIRS: *value = pairs_on(h) ? 1 : 0; return MC_OK;
     case MC_OPT_DEEP_WINDOWS: *value = h->deep_opt; return MC_OK;
     case MC_OPT_DRIFT_EVERY: *value = h->drift_every; return MC_OK;
+    case MC_OPT_HELPERS: *value = helpers_on(h) ? 1 : 0; return MC_OK;
     default: return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
 }
 
 // Autotuner: time trial launches of every candidate (ticket order x CTA count)
 // on a saved copy of every chain's state, keep the fastest, restore the state.
-int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t *best_ctas, double *best_ms)
+int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t *best_ctas, int64_t *best_shape,
+                double *best_ms)
 {
     int rc = check(h);
     if (rc) return rc;
@@ -1351,28 +1377,75 @@ int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t
         rc = mc_get_state(h, (int)i, saved[i].pos.data(), &saved[i].sweeps, &saved[i].ledger, &saved[i].st);
         if (rc) return rc;
     }
-    const int full = std::max(1, grid_for(h));
-    const int old_policy = h->policy, old_ctas = h->ctas_override;
-    std::vector<int> ctas = {full, std::max(1, (3 * full) / 4), std::max(1, full / 2)};
-    double best = 1e300;
-    int bp = old_policy, bc = old_ctas;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // one candidate: warm launch (schedule and graph built outside the timing), then trial_sweeps timed
+    auto trial = [&](double &ms_out) -> int {
+        int r = enqueue_sweeps(h, 1);
+        if (!r) r = finish(h);
+        if (r) return r;
+        cudaEventRecord(e0, h->stream);
+        r = enqueue_sweeps(h, trial_sweeps);
+        cudaEventRecord(e1, h->stream);
+        if (!r) r = finish(h);
+        if (r) return r;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_out = ms;
+        return MC_OK;
+    };
+    // shape: bit 0 pairs mode, bit 1 deep windows, bit 2 helper warps (pairs mode and helpers exclude each other)
+    auto apply_shape = [&](int sh) -> int {
+        int r = set_option(h, MC_OPT_PAIRS, (sh & 1) ? 1 : 0);
+        if (!r) r = set_option(h, MC_OPT_DEEP_WINDOWS, (sh >> 1) & 1);
+        if (!r) r = set_option(h, MC_OPT_HELPERS, (sh >> 2) & 1);
+        write_ctl(h);
+        return r;
+    };
+    const int old_pairs = h->pairs_opt, old_deep = h->deep_opt, old_help = h->helpers_opt;
+    double best = 1e300;
+    int bshape = -1;
+    // 1. kernel shape at the default work order and CTA count
+    for (int sh = 0; sh < 8 && rc == 0; ++sh) {
+        if ((sh & 1) && (sh & 4)) continue;
+        if ((sh & 1) && (h->max_clusters < 1 || any_da(h))) continue;
+        if ((sh & 4) && h->occ_h < 1) continue;
+        if (apply_shape(sh)) {  // not available here: skip the candidate
+            g_err.clear();
+            continue;
+        }
+        double ms = 0.0;
+        rc = trial(ms);
+        if (!rc && ms < best) {
+            best = ms;
+            bshape = sh;
+        }
+    }
+    if (!rc && bshape >= 0) rc = apply_shape(bshape);
+    if (rc || bshape < 0) {
+        h->pairs_opt = old_pairs;
+        h->deep_opt = old_deep;
+        h->helpers_opt = old_help;
+        drop_graphs(h);
+        write_ctl(h);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc ? rc : fail(MC_ERR_INVALID, "no kernel shape could run");
+    }
+    // 2. work order x persistent CTA count with that shape
+    const int full = std::max(1, grid_for(h));
+    const int old_policy = h->policy, old_ctas = h->ctas_override;
+    std::vector<int> ctas = {full, std::max(1, (3 * full) / 4), std::max(1, full / 2)};
+    best = 1e300;
+    int bp = old_policy, bc = old_ctas;
     for (int pol = 0; pol < 2 && rc == 0; ++pol)
         for (int nc : ctas) {
             h->policy = pol;
             h->ctas_override = nc;
-            rc = enqueue_sweeps(h, 1);  // warm: schedule and graph built outside the timing
-            if (!rc) rc = finish(h);
+            double ms = 0.0;
+            rc = trial(ms);
             if (rc) break;
-            cudaEventRecord(e0, h->stream);
-            rc = enqueue_sweeps(h, trial_sweeps);
-            cudaEventRecord(e1, h->stream);
-            if (!rc) rc = finish(h);
-            if (rc) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best) {
                 best = ms;
                 bp = pol;
@@ -1390,6 +1463,7 @@ int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t
     }
     if (best_policy) *best_policy = bp;
     if (best_ctas) *best_ctas = bc == 0 ? full : bc;
+    if (best_shape) *best_shape = bshape;
     if (best_ms) *best_ms = best;
     return MC_OK;
 }
@@ -1725,6 +1799,16 @@ int mc_test_philox(const uint32_t *ctr, const uint32_t *key, int64_t n, uint32_t
     cudaFree(dr);
     cudaFree(dk);
     if (e != cudaSuccess) return fail(MC_ERR_CUDA, "philox test: %s", cudaGetErrorString(e));
+    return MC_OK;
+}
+
+int mc_unit_rates(double *rates)
+{
+    if (!rates) return fail(MC_ERR_INVALID, "NULL output");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(mcg_host::unit_rates(sms, rates));
     return MC_OK;
 }
 

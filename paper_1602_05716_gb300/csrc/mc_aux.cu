@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "../../include/mc.h"
 #include "mc_device.cuh"
@@ -262,6 +263,65 @@ __global__ void energy_ff_reduce(const double *__restrict__ part, int n_part, do
     }
 }
 
+// ---------------------------------------------------------------------------
+// Unit-rate probes behind the ALU roofline (mc_unit_rates): every thread runs UR_CHAINS independent chains of one
+// operation, 64 warps per SM (8 blocks of 256 threads at <= 32 registers), and block 0's thread 0 reads clock64
+// around the loop.  Rates are operations per SM clock.
+constexpr int UR_CHAINS = 8;
+
+__global__ void __launch_bounds__(256, 8) rate_rsqrt(int iters, float *out, long long *cyc)
+{
+    float x[UR_CHAINS];
+#pragma unroll
+    for (int q = 0; q < UR_CHAINS; ++q) x[q] = 1.5f + 1e-6f * (float)(threadIdx.x + q);
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < UR_CHAINS; ++q) {
+            float r;
+            asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[q]));
+            x[q] = r + 0.5f;
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < UR_CHAINS; ++q) s += x[q];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+}
+
+__global__ void __launch_bounds__(256, 8) rate_ffma2(int iters, float *out, long long *cyc)
+{
+    f32x2 a[UR_CHAINS];
+#pragma unroll
+    for (int q = 0; q < UR_CHAINS; ++q) a[q] = pk2(1.f + 1e-7f * (float)(threadIdx.x * q), 1.f - 1e-7f * (float)q);
+    const f32x2 b = pk2(0.9999f, 0.9998f), c = pk2(1e-6f, 2e-6f);
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < UR_CHAINS; ++q) {
+            f32x2 r;
+            asm volatile("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a[q]), "l"(b), "l"(c));
+            a[q] = r;
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < UR_CHAINS; ++q) {
+        float u, v;
+        upk2(a[q], u, v);
+        s += u + v;
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+}
+
 __global__ void philox_test(const uint4 *__restrict__ ctr, const uint2 *__restrict__ key, int n, uint4 *out_lib,
                             uint4 *out_curand)
 {
@@ -315,6 +375,38 @@ cudaError_t gr_launch(const float4 *pos, int N, int n_bins, double dr, float rma
     }
     mcg::gr_hist<<<(N + mcg::EB - 1) / mcg::EB, mcg::EB, sm, st>>>(pos, N, n_bins, dr, rmax2_hi, use_lim, lim2, counts);
     return cudaGetLastError();
+}
+
+// Unit rates per SM clock at 8, 16, 32 and 64 resident warps per SM (rows), for rsqrt.approx.ftz and packed
+// FFMA2 (columns; FFMA2 counted as two FP32 operations).  Host buffers out[8]; blocks synchronously.
+cudaError_t unit_rates(int sms, double *out)
+{
+    float *buf = nullptr;
+    long long *cyc = nullptr;
+    cudaError_t e = cudaMalloc(&buf, sizeof(float) * (size_t)sms * 8 * 256);
+    if (e == cudaSuccess) e = cudaMalloc(&cyc, sizeof(long long) * (size_t)sms * 8);
+    std::vector<long long> hc((size_t)sms * 8);
+    const int iters = 4096;
+    for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind)
+        for (int w = 0; w < 4 && e == cudaSuccess; ++w) {
+            const int bps = 1 << w, nb = sms * bps;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                if (kind == 0) mcg::rate_rsqrt<<<nb, 256>>>(iters, buf, cyc);
+                else mcg::rate_ffma2<<<nb, 256>>>(iters, buf, cyc);
+                e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            }
+            if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * nb, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) break;
+            double mc = 0.0;
+            for (int b = 0; b < nb; ++b) mc += (double)hc[b];
+            mc /= nb;
+            const double ops = 256.0 * bps * iters * mcg::UR_CHAINS * (kind == 0 ? 1.0 : 2.0);
+            out[2 * w + kind] = ops / mc;
+        }
+    cudaFree(buf);
+    cudaFree(cyc);
+    return e;
 }
 
 cudaError_t philox_test_launch(const uint4 *ctr, const uint2 *key, int n, uint4 *out_lib, uint4 *out_curand,

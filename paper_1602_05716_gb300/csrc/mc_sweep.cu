@@ -114,8 +114,16 @@ struct __align__(16) Smem {
     float redf[32];
     int ticket, ok, guard_k, ovl_flag;
     int hzs[2], tcnt[2];  // per buffer: publication horizon, groups staged
-    int ns, namb, pad1[2];
+    int ns, namb;     // stage-1 survivors, ambiguous stage-1 moves
+    int hcmd[2], hntl[2];  // helper warps: command and tile count of the hand-over, by its parity
 };
+
+// The helper warps' per-move tile sums (float-float, P, minimum squared distance), handed to the work-item warps
+// between the tile pass and the slice combine.  They alias part and wpart, which are first written after it.
+__device__ __forceinline__ float *help_h(Smem &sm) { return sm.part[0]; }
+__device__ __forceinline__ float *help_l(Smem &sm) { return sm.part[1]; }
+__device__ __forceinline__ float *help_p(Smem &sm) { return sm.wpart[0]; }
+__device__ __forceinline__ float *help_m(Smem &sm) { return sm.wpart[1]; }
 
 // More than half of an SM's 228 KB of shared memory: one CTA per SM, so each CTA's TMEM allocation (at most
 // 512 columns) is granted at once and never waits for another CTA.
@@ -248,6 +256,22 @@ __device__ __forceinline__ unsigned below(int k, int w)
 {
     return (w * 32 + 32 <= k) ? 0xffffffffu : (w * 32 >= k ? 0u : ((1u << (k - w * 32)) - 1u));
 }
+
+// Barriers.  Barrier 1 spans the T threads that run the work items: every barrier of the work-item code.  In the
+// kernel with helper warps (2T threads), barrier 2 spans those and the helpers during the tile pass, and barrier 0
+// the whole CTA at start and exit.
+__device__ __forceinline__ void bar_main()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(T) : "memory");
+}
+
+__device__ __forceinline__ void bar_all()
+{
+    asm volatile("bar.sync 2, %0;" ::"n"(2 * T) : "memory");
+}
+
+// Tile-pass hand-over to the helper warps (Smem::hcmd).
+constexpr int HC_SKIP = 0, HC_RUN = 1, HC_EXIT = 2;
 
 // Warp 0 waits until the sweep tags of the nw words of group J lie in [lo, hi]
 // (acquire).  Returns false on timeout, protocol error or abort.  bits (lane w)
@@ -413,14 +437,14 @@ __device__ void stage_positions(Smem &sm, const Ctx &c, int k, int j0)
 {
     float4 *buf = stage_buf(sm);
     const int tid = threadIdx.x;
-    __syncthreads();
+    bar_main();
 #pragma unroll
     for (int u = 0; u < GSTAGE / T; ++u) {
         const int t = u * T + tid, j = j0 + t;
         const float4 *src = ((j >> 7) > c.g) ? c.Pprev : c.Pcur;
         buf[t] = (j < c.N) ? __ldcg(&src[j]) : make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
     }
-    __syncthreads();
+    bar_main();
     if (tid < S) {
         const int l = tid;
         int t = c.k0 + l - j0;
@@ -436,7 +460,7 @@ __device__ void stage_positions(Smem &sm, const Ctx &c, int k, int j0)
             if (t >= 0 && t < GSTAGE) buf[t] = bit(sm.dacc[d], l) ? sm.dtri[d][l] : sm.dold[d][l];
         }
     }
-    __syncthreads();
+    bar_main();
 }
 
 // Sum of per-thread FP64 values and FP32 bound terms over the CTA (thread 0 gets it).
@@ -452,7 +476,7 @@ __device__ __forceinline__ void block_sum(Smem &sm, double v, float bb, double &
         sm.redd[tid >> 5] = v;
         sm.redf[tid >> 5] = bb;
     }
-    __syncthreads();
+    bar_main();
     tot = 0.0;
     btot = 0.0;
     if (tid == 0)
@@ -522,10 +546,10 @@ __device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double xs, doubl
         sm.redd[16] = dE;
         sm.guard_k = (dE < L64 - B2) ? 0 : ((dE > L64 + B2) ? 1 : -1);
     }
-    __syncthreads();
+    bar_main();
     const int out = sm.guard_k;
     dE_out = sm.redd[16];
-    __syncthreads();
+    bar_main();
     return out;
 }
 
@@ -607,10 +631,10 @@ __device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double xs, doubl
         sm.redd[16] = dE;
         sm.guard_k = (dE < L64 - B3) ? 0 : ((dE > L64 + B3) ? 1 : -1);
     }
-    __syncthreads();
+    bar_main();
     const int out = sm.guard_k;
     dE_out = sm.redd[16];
-    __syncthreads();
+    bar_main();
     return out;
 }
 
@@ -641,7 +665,7 @@ __device__ void tier4(Smem &sm, const Ctx &c, int k, double &dE_out, bool &ovl_o
             }
             terms[t] = v;
         }
-        __syncthreads();
+        bar_main();
         // each 1024-ion chunk is summed sequentially by its own thread (chunks are independent)
         if (tid < GSTAGE / CHUNK) {
             const int cb = j0 + tid * CHUNK;
@@ -653,17 +677,17 @@ __device__ void tier4(Smem &sm, const Ctx &c, int k, double &dE_out, bool &ovl_o
             }
             sm.redd[tid] = s;
         }
-        __syncthreads();
+        bar_main();
         if (tid == 0)
             for (int q = 0; q < GSTAGE / CHUNK; ++q)
                 if (j0 + q * CHUNK < N) total = __dadd_rn(total, sm.redd[q]);
     }
-    __syncthreads();
+    bar_main();
     if (tid == 0) sm.redd[16] = __dmul_rn(__dmul_rn(c.ch->lB, (double)a.w), total);
-    __syncthreads();
+    bar_main();
     dE_out = sm.redd[16];
     ovl_out = sm.ovl_flag != 0;
-    __syncthreads();
+    bar_main();
 }
 
 // Exact overlap test of move k's trial position against every other ion as move k sees it (all earlier
@@ -691,9 +715,9 @@ __device__ bool overlap_exact(Smem &sm, const Ctx &c, int k)
             if (d2 < pre && j < c.N && j != i && d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < sig2) sm.ovl_flag = 1;
         }
     }
-    __syncthreads();
+    bar_main();
     const bool o = sm.ovl_flag != 0;
-    __syncthreads();
+    bar_main();
     return o;
 }
 
@@ -763,7 +787,7 @@ __device__ __forceinline__ void partial_pass(Smem &sm)
     sm.part[h][k] = sx;
     sm.plo[h][k] = lo;
     sm.phi[h][k] = hi;
-    __syncthreads();
+    bar_main();
 }
 
 // ---------------------------------------------------------------------------
@@ -793,7 +817,7 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
     const float4 x = sm.own[k], a = sm.trial[k];
     if (tid < 2 * DA_FRS) F[tid] = 0;
     if (tid < 2) nl[tid] = 0;
-    __syncthreads();
+    bar_main();
     // near field and taper-region shells: counted candidates of the stencil cells, FP64 distances
     {
         const int G = d.nf_G;
@@ -825,7 +849,7 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
             }
         }
     }
-    __syncthreads();
+    bar_main();
     // ascending-j order: each entry's rank among its list, then sequential sums
     for (int e = tid; e < 2 * LMAX; e += T) {
         const int pt = e / LMAX, s = e - pt * LMAX;
@@ -837,7 +861,7 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
             sorted[pt * LMAX + rank] = lt[pt * LMAX + s];
         }
     }
-    __syncthreads();
+    bar_main();
     if (tid < 2) {
         double ph = 0.0;
         const int n = min(nl[tid], LMAX);
@@ -857,7 +881,7 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
         z = __dadd_rn(z, __dmul_rn((double)bf16f(__ldg(&w[o * DA_NIN + 32])), rad));
         hb[pt * DA_H + o] = silu64(z);
     }
-    __syncthreads();
+    bar_main();
     if (tid < 2 * DA_H) {
         const int pt = tid / DA_H, o = tid - pt * DA_H;
         double z = (double)bf16f(__ldg(&w[DA_OFF_B2 + o]));
@@ -865,17 +889,17 @@ __device__ double da_dEt64(Smem &sm, const Ctx &c, int k)
             z = __dadd_rn(z, __dmul_rn((double)bf16f(__ldg(&w[DA_OFF_W2 + o * DA_H + q])), hb[pt * DA_H + q]));
         hb[2 * DA_H + pt * DA_H + o] = silu64(z);
     }
-    __syncthreads();
+    bar_main();
     if (tid < 2) {
         double gg = (double)bf16f(__ldg(&w[DA_OFF_B3]));
         for (int q = 0; q < DA_H; ++q)
             gg = __dadd_rn(gg, __dmul_rn((double)bf16f(__ldg(&w[DA_OFF_W3 + q])), hb[2 * DA_H + tid * DA_H + q]));
         res[2 + tid] = gg;
     }
-    __syncthreads();
+    bar_main();
     const double lq = __dmul_rn(c.ch->lB, (double)x.w);
     const double v = __dmul_rn(lq, __dsub_rn(__dadd_rn(res[1], res[3]), __dadd_rn(res[0], res[2])));
-    __syncthreads();
+    bar_main();
     return v;
 }
 
@@ -914,7 +938,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
         const unsigned long long need = c.s * (unsigned long long)c.B + (unsigned long long)max(c.g - Wg, 0);
         sm.ok = wait_ledger(ch, need, ctl) ? 1 : 0;
     }
-    __syncthreads();
+    bar_main();
     if (!sm.ok) return false;
     char *base = reinterpret_cast<char *>(sm.cin);
     float *Wf = reinterpret_cast<float *>(base);                // DA_NP floats
@@ -931,7 +955,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
     for (int q = tid; q < 2 * S * DA_FRS; q += T) Fr[q] = 0;
     if (tid < WORDS) sm.d64w[tid] = 0u;
     if (tid == 0) sm.namb = 0;
-    __syncthreads();
+    bar_main();
     const auto active = [&](int k) { return k < nk && !(sm.st[k] & (ST_INACTIVE | ST_WALL)); };
     // near field and taper-region shell histograms (warp per move)
     long long tq = clock64();
@@ -948,7 +972,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
             novl[k] = o.ovl;
         }
     }
-    __syncthreads();
+    bar_main();
     part[3] += clock64() - tq;
     tq = clock64();
     // MLP at every point (thread = point: 0..S-1 old positions, S..2S-1 trials); with all weights zero g = 0
@@ -967,7 +991,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
         gv[tid] = g;
         ge[tid] = eg;
     }
-    __syncthreads();
+    bar_main();
     part[2] += clock64() - tq;
     // FP32 surrogate energy change and its bound; stage-1 decisions outside the band
     if (tid < S) {
@@ -1011,7 +1035,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
             sm.st[k] = (unsigned char)stv;
         }
     }
-    __syncthreads();
+    bar_main();
     // stage-1 decisions inside the band: the reference arithmetic
     const int na = sm.namb;
     for (int e = 0; e < na; ++e) {
@@ -1029,7 +1053,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
                 sm.st[k] = (unsigned char)(sm.st[k] | ST_DA_DONE);
             }
         }
-        __syncthreads();
+        bar_main();
     }
     n_fp64 += na;
     // survivors in ascending order, and their stage-2 thresholds
@@ -1054,7 +1078,7 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
             sm.st[k] = (unsigned char)stv;
         }
     }
-    __syncthreads();
+    bar_main();
     if (tid < S) {
         const int k = tid, w = k >> 5;
         int before = 0;
@@ -1066,15 +1090,175 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
         sm.slot[k] = sv ? (unsigned char)n : (unsigned char)255;
         if (k == S - 1) sm.ns = before + __popc(bal);
     }
-    __syncthreads();
+    bar_main();
     return true;
 }
 
 // One work item: the S moves of group g of chain `tk.chain` at sweep s.
 // role 0: the whole work item (the cluster's leader in pairs mode: even tiles); role 1: the pairs-mode helper,
 // which sums the odd tiles for the leader and decides nothing.
+// One buffer of the tile ring against the thread's moves: cnt staged groups of S ions, column slices of NSL (8 for
+// one group of warps, 16 when the helper warps take slices 8..15), this thread's slice r0.  Only the occupied
+// 32-move layers run (nm of them): one packed pair for <= 2, a packed pair and the third layer alone for 3, two
+// packed pairs for 4; an empty slot in the last layer repeats a real move and is never written back.
+template <int NSL>
+__device__ __forceinline__ void tile_buffer(const float4 *tile, int cnt, int r0, int nm, const Mv2 (&mv)[MPT / 2],
+                                            f32x2 (&s2)[MPT / 2], f32x2 (&P2)[MPT / 2], float (&mA)[MPT])
+{
+    const int nj = cnt * (S / NSL);
+    if (nm <= 2) {
+#pragma unroll 8
+        for (int jj = 0; jj < nj; ++jj) pair_far2(mv[0], tile[jj * NSL + r0], s2[0], P2[0], mA[0], mA[1]);
+    } else if (nm == 3) {
+        float s3, s3b, p3, p3b;
+        upk2(s2[1], s3, s3b);
+        upk2(P2[1], p3, p3b);
+#pragma unroll 8
+        for (int jj = 0; jj < nj; ++jj) {
+            const float4 y = tile[jj * NSL + r0];
+            pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
+            pair_far1(mv[1], y, s3, p3, mA[2]);
+        }
+        s2[1] = pk2(s3, s3b);
+        P2[1] = pk2(p3, p3b);
+    } else {
+#pragma unroll 8
+        for (int jj = 0; jj < nj; ++jj) {
+            const float4 y = tile[jj * NSL + r0];
+            pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
+            pair_far2(mv[1], y, s2[1], P2[1], mA[2], mA[3]);
+        }
+    }
+}
+
+// The packed move data of thread row p (move slots p + 32 m) from the staged positions.
+__device__ __forceinline__ void tile_moves(const Smem &sm, int p, int ns, int (&km)[MPT], Mv2 (&mv)[MPT / 2])
+{
+    float3 b3[MPT], d3[MPT];
+#pragma unroll
+    for (int m = 0; m < MPT; ++m) {
+        km[m] = (p + 32 * m < ns) ? (int)sm.surv[p + 32 * m] : -1;
+        const int kk = km[m] < 0 ? 0 : km[m];
+        const float4 a = sm.trial[kk], b = sm.own[kk];
+        b3[m] = make_float3(b.x, b.y, b.z);
+        d3[m] = make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+    }
+#pragma unroll
+    for (int pp = 0; pp < MPT / 2; ++pp) {
+        const int m0 = 2 * pp, m1 = 2 * pp + 1;
+        mv[pp].bx = pk2(b3[m0].x, b3[m1].x);
+        mv[pp].by = pk2(b3[m0].y, b3[m1].y);
+        mv[pp].bz = pk2(b3[m0].z, b3[m1].z);
+        mv[pp].dx = pk2(d3[m0].x, d3[m1].x);
+        mv[pp].dy = pk2(d3[m0].y, d3[m1].y);
+        mv[pp].dz = pk2(d3[m0].z, d3[m1].z);
+        mv[pp].nx = pk2(-d3[m0].x, -d3[m1].x);
+        mv[pp].ny = pk2(-d3[m0].y, -d3[m1].y);
+        mv[pp].nz = pk2(-d3[m0].z, -d3[m1].z);
+    }
+}
+
+// The helper warps (threads T..2T-1 of the 2T-thread kernel): column slices 8..15 of every work item's tile pass,
+// in step with the work-item warps at barrier 2.  Per item: the hand-over barrier (command RUN, SKIP or EXIT, and
+// the tile count, in the slot of the hand-over's parity: the work-item warps write the other slot next, so a slow
+// helper never reads a newer command), the tile loop with the same barriers and the same decisions as the
+// work-item warps (all read from shared memory written before the barrier that precedes the read), then the
+// per-move sums into shared memory and the closing barrier.  After an abort seen in the loop both sides leave the
+// item; the work-item warps then send EXIT.
+__device__ void helper_loop(Smem &sm)
+{
+    const int ht = threadIdx.x - T;
+    const int p = ht / SL, r = ht % SL;
+    int hseq = 0;
+    for (;;) {
+        bar_all();  // hand-over
+        const int cmd = sm.hcmd[hseq & 1], ntl = sm.hntl[hseq & 1];
+        ++hseq;
+        if (cmd == HC_EXIT) return;
+        if (cmd != HC_RUN) continue;
+        const int ns = sm.ns, nm = (ns + 31) / 32;
+        int km[MPT];
+        Mv2 mv[MPT / 2];
+        tile_moves(sm, p, ns, km, mv);
+        f32x2 s2[MPT / 2], P2[MPT / 2];
+        float hA[MPT], lA[MPT], mA[MPT];
+#pragma unroll
+        for (int pp = 0; pp < MPT / 2; ++pp) {
+            s2[pp] = pk2(0.f, 0.f);
+            P2[pp] = pk2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            hA[m] = lA[m] = 0.f;
+            mA[m] = finf();
+        }
+        bool ok = true;
+        int it = 0;
+        for (int i = 0; i < ntl; ++it) {
+            const int cur = it & 1;
+            const int cnt = sm.tcnt[cur];
+            const int hz = sm.hzs[cur];
+            const int in = i + cnt;
+            const int pn = (in < ntl && in <= hz) ? ((in + 1 < ntl && in + 1 <= hz) ? 2 : 1) : 0;
+            tile_buffer<2 * SL>(sm.tile[cur], cnt, SL + r, nm, mv, s2, P2, mA);
+#pragma unroll
+            for (int pp = 0; pp < MPT / 2; ++pp) {
+                float v[2];
+                upk2(s2[pp], v[0], v[1]);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    float t2, e;
+                    two_sum(hA[2 * pp + u], v[u], t2, e);
+                    hA[2 * pp + u] = t2;
+                    lA[2 * pp + u] += e;
+                }
+                s2[pp] = pk2(0.f, 0.f);
+            }
+            bar_all();  // the iteration's barrier
+            if (in < ntl && pn == 0) {
+                bar_all();  // the next tile has been waited for
+                if (!sm.ok) {
+                    ok = false;
+                    break;
+                }
+                bar_all();  // ... and staged
+            }
+            i = in;
+        }
+        if (!ok) continue;
+        float PA[MPT];
+#pragma unroll
+        for (int pp = 0; pp < MPT / 2; ++pp) upk2(P2[pp], PA[2 * pp], PA[2 * pp + 1]);
+#pragma unroll
+        for (int o = 1; o < SL; o <<= 1) {
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                const float h2 = __shfl_xor_sync(FULL, hA[m], o), l2 = __shfl_xor_sync(FULL, lA[m], o);
+                float t2, e;
+                two_sum(hA[m], h2, t2, e);
+                hA[m] = t2;
+                lA[m] = lA[m] + l2 + e;
+                PA[m] += __shfl_xor_sync(FULL, PA[m], o);
+                mA[m] = fminf(mA[m], __shfl_xor_sync(FULL, mA[m], o));
+            }
+        }
+        if (r < MPT) {  // lane r of each slice group stores move slot m = r
+#pragma unroll
+            for (int m = 0; m < MPT; ++m)
+                if (r == m && km[m] >= 0) {
+                    help_h(sm)[km[m]] = hA[m];
+                    help_l(sm)[km[m]] = lA[m];
+                    help_p(sm)[km[m]] = PA[m];
+                    help_m(sm)[km[m]] = mA[m];
+                }
+        }
+        bar_all();  // the sums are in shared memory
+    }
+}
+
+template <bool HELP>
 __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, const Ticket tk, int ticket, Ctl *ctl,
-                              int role)
+                              int role, int &hseq)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -1135,7 +1319,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             ok = wait_words(ch, g - 2 - d, WORDS, tag_prev, tag_cur, ctl, bits);
         if (lane == 0) sm.ok = ok;
     }
-    __syncthreads();
+    bar_main();
     if (!sm.ok) return false;
     if (tid < S) {
         const int k = tid;
@@ -1207,7 +1391,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
 #pragma unroll
         for (int d = 0; d < DW; ++d) sm.dacc[d][tid] = 0u;
     }
-    __syncthreads();
+    bar_main();
 
     // 1b. delayed acceptance: stage 1 decides what it can before any pair sum; only survivors continue
     int n_dfp64 = 0;
@@ -1221,7 +1405,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             sm.slot[tid] = tid < nk ? (unsigned char)tid : (unsigned char)255;
         }
         if (tid == 0) sm.ns = nk;
-        __syncthreads();
+        bar_main();
     }
     const long long cyc_da = clock64() - cyc_da0;
     const int ns = sm.ns;
@@ -1357,7 +1541,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
 
     // 2b'. interval sums of the corrections (threads < S: this group, threads >= S: the window);
     // needs only the two passes above, so it runs before the tiles
-    __syncthreads();
+    bar_main();
     {
         const int k = tid & (S - 1), h = tid >> 7;
         float lo = 0.f, hi = 0.f;
@@ -1481,10 +1665,10 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 sm.tcnt[0] = (hz0 >= 1 && ntl > 1) ? 2 : 1;
             }
         }
-        __syncthreads();
+        bar_main();
         if (!sm.ok) return false;
         if (tid < sm.tcnt[0] * S) sm.tile[0][tid] = __ldcg(&tile_src(tile_J(tid >> 7))[tid & (S - 1)]);
-        __syncthreads();
+        bar_main();
     }
     // the tiles run two moves per packed FP32x2 instruction (slots (0,1) and (2,3)); their |t| sum is bounded
     // by dn P instead of accumulated
@@ -1520,8 +1704,22 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             s2[pp] = pk2(0.f, 0.f);
         }
     };
+    // with helper warps: hand the tile pass over (they wait at barrier 2); they take column slices 8..15
+    const bool tiles_run = ntl > 0 && ns > 0;
+    if (HELP) {
+        if (tid == 0) {
+            sm.hcmd[hseq & 1] = tiles_run ? HC_RUN : HC_SKIP;
+            sm.hntl[hseq & 1] = ntl;
+        }
+        ++hseq;
+        bar_all();
+    }
+    auto tile_bar = [&]() {
+        if (HELP) bar_all();
+        else bar_main();
+    };
     int it = 0;
-    for (int i = 0; ns > 0 && i < ntl; ++it) {
+    for (int i = 0; tiles_run && i < ntl; ++it) {
         const int cur = it & 1;
         const int cnt = sm.tcnt[cur];
         const int hz = sm.hzs[cur];
@@ -1529,34 +1727,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const int pn = (in < ntl && in <= hz) ? ((in + 1 < ntl && in + 1 <= hz) ? 2 : 1) : 0;  // groups prefetched
         float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
         if (tid < pn * S) pre = __ldcg(&tile_src(tile_J(in + (tid >> 7)))[tid & (S - 1)]);
-        // occupied 32-move layers only (all of them for a plain chain); an empty slot in the last layer repeats
-        // a real move and is never written back
-        const int nj = cnt * (S / SL);
-#define MC_TILE_PASS(NPK)                                                              \
-    _Pragma("unroll 8") for (int jj = 0; jj < nj; ++jj)                                \
-    {                                                                                  \
-        const float4 y = sm.tile[cur][jj * SL + r];                                    \
-        _Pragma("unroll") for (int pp = 0; pp < (NPK); ++pp)                           \
-            pair_far2(mv[pp], y, s2[pp], P2[pp], mA[2 * pp], mA[2 * pp + 1]);          \
-    }
-        if (nm <= 2) {
-            MC_TILE_PASS(1)
-        } else if (nm == 3) {  // three occupied layers: one packed pair and the third layer alone
-            float s3, s3b, p3, p3b;
-            upk2(s2[1], s3, s3b);
-            upk2(P2[1], p3, p3b);
-            _Pragma("unroll 8") for (int jj = 0; jj < nj; ++jj)
-            {
-                const float4 y = sm.tile[cur][jj * SL + r];
-                pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
-                pair_far1(mv[1], y, s3, p3, mA[2]);
-            }
-            s2[1] = pk2(s3, s3b);
-            P2[1] = pk2(p3, p3b);
-        } else {
-            MC_TILE_PASS(MPT / 2)
-        }
-#undef MC_TILE_PASS
+        // occupied 32-move layers only (all of them for a plain chain)
+        tile_buffer<HELP ? 2 * SL : SL>(sm.tile[cur], cnt, r, nm, mv, s2, P2, mA);
         promote2();
         if (tid < pn * S) sm.tile[cur ^ 1][tid] = pre;
         if (warp == 0) {
@@ -1566,7 +1738,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 sm.tcnt[cur ^ 1] = pn;
             }
         }
-        __syncthreads();
+        tile_bar();
         if (in < ntl && pn == 0) {  // the next tile was not published in time: wait for it now (uniform branch)
             const int Jn = tile_J(in);
             if (warp == 0) {
@@ -1578,14 +1750,15 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                     sm.tcnt[cur ^ 1] = 1;
                 }
             }
-            __syncthreads();
+            tile_bar();
             if (!sm.ok) return false;
             if (trc) gt_tile = globaltimer();
             if (tid < S) sm.tile[cur ^ 1][tid] = __ldcg(&tile_src(Jn)[tid]);
-            __syncthreads();
+            tile_bar();
         }
         i = in;
     }
+    if (HELP && tiles_run) bar_all();  // the helpers' per-move sums are in shared memory
     cyc_tiles = clock64() - cyc_t0;
     if (trc) gt_tiles = globaltimer();
 #pragma unroll
@@ -1623,7 +1796,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     if (pairs) {
         cluster_sync_all();  // the helper's tile sums are in the box
         if (tid == 0) sm.ok = *(volatile int *)&ctl->abort ? 0 : 1;
-        __syncthreads();
+        bar_main();
         if (!sm.ok) return false;
     }
 
@@ -1633,7 +1806,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     // correction sums and overlap bits from TMEM.  The bound sums carry FP32 rounding of at most n u relative
     // for n terms per thread: infl covers it.
     const float infl = 1.0f + (float)(N / SL + 64 * DW + 64) * 0x1p-23f;
-    __syncthreads();  // 3a's per-move coefficients (no tile loop may have run since)
+    bar_main();  // 3a's per-move coefficients (no tile loop may have run since)
     float QA[MPT];
 #pragma unroll
     for (int m = 0; m < MPT; ++m) {
@@ -1675,6 +1848,14 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 qv += sm.kPs[kv] * __ldcg(&box->p[kv]);
                 mv = fminf(mv, __ldcg(&box->m[kv]));
             }
+            if (HELP && tiles_run) {  // the helper warps' column slices
+                float s2, e;
+                two_sum(hv, help_h(sm)[kv], s2, e);
+                hv = s2;
+                lv = lv + help_l(sm)[kv] + e;
+                qv += sm.kPs[kv] * help_p(sm)[kv];
+                mv = fminf(mv, help_m(sm)[kv]);
+            }
             sm.bhi[kv] = hv;
             sm.blo[kv] = lv;
             sm.Qs[kv] = qv;
@@ -1689,7 +1870,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (lane < nw) sm.dacc[c.nd - 1 - lane / WORDS][lane % WORDS] = bits;
             if (lane == 0) sm.ok = ok;
         }
-        __syncthreads();
+        bar_main();
         if (!sm.ok) return false;
         const int q = warp & 3, h = warp >> 2, n = 32 * q + lane;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};  // independent partial sums
@@ -1713,7 +1894,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         sm.dpart[h][n] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         sm.dwo[h][n] = wo;
     }
-    __syncthreads();
+    bar_main();
     if (trc) gt_ph[0] = globaltimer();
 
     // 3b + 4. per move: the deep windows' exact sums and overlap, the settled ions' overlap from the minimum
@@ -1771,13 +1952,13 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
 
     // 5. first in-group partial pass (needs only round 0's decisions), then the window's outcome (the
     // critical wait) and its exact correction sums.
-    __syncthreads();
+    bar_main();
     if (trc) gt_ph[2] = globaltimer();
     if (tid < WORDS) {
         sm.acc0[tid] = sm.accw[tid];
         sm.dec0[tid] = sm.decw[tid];
     }
-    __syncthreads();
+    bar_main();
     partial_pass(sm);
     if (trc) gt_ready = globaltimer();
     const long long cyc_w0 = clock64();
@@ -1790,7 +1971,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (lane < WORDS) sm.dacc[0][lane] = bits;
             if (lane == 0) sm.ok = ok;
         }
-        __syncthreads();
+        bar_main();
         if (!sm.ok) return false;
         if (trc) gt_w2 = globaltimer();
         {
@@ -1814,7 +1995,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             sm.dpart[h][n] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
             sm.dwo[h][n] = wo;
         }
-        __syncthreads();
+        bar_main();
         if (tid < ns) {
             const int n = tid, k = sm.surv[n];
             sm.wexd[k] += sm.dpart[0][n] + sm.dpart[1][n];
@@ -1829,7 +2010,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (lane < WORDS) sm.winacc[lane] = (lane < nw) ? bits : 0u;
             if (lane == 0) sm.ok = ok;
         }
-        __syncthreads();
+        bar_main();
         if (!sm.ok) return false;
         cyc_win = clock64() - cyc_w0;
         if (trc) gt_window = globaltimer();
@@ -1853,7 +2034,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             sx = (acc[0] + acc[1]) + (acc[2] + acc[3]);
             sm.wpart[h][k] = sx;
         }
-        __syncthreads();
+        bar_main();
         cres[0] = (unsigned)(clock64() - cw0);
         if (tid < S) {
             const int k = tid;
@@ -1864,7 +2045,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (wo) sm.st[k] = (unsigned char)(sm.st[k] | ST_OVL_CERTAIN);
         }
     }
-    __syncthreads();
+    bar_main();
     cres[1] = (unsigned)(clock64() - cw0);
 
     // 6. rounds over this group's earlier moves: exact sums over decided ones,
@@ -1909,7 +2090,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 sm.accw[warp] |= acc;
             }
         }
-        __syncthreads();
+        bar_main();
         if (n_rounds == 1) cres[2] = (unsigned)(clock64() - cw0);
         cres[3] = (unsigned)(clock64() - cw0);
         int first = -1;
@@ -1960,7 +2141,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                             sm.dEt64[k] = v;
                             sm.d64w[k >> 5] |= 1u << (k & 31);
                         }
-                        __syncthreads();
+                        bar_main();
                     }
                     dEt64 = sm.dEt64[k];
                     thr = __dadd_rn(L64, dEt64);
@@ -1996,18 +2177,18 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                     if (out == OUT_ACCEPT) sm.accw[k >> 5] |= 1u << (k & 31);
                 }
             }
-            __syncthreads();
+            bar_main();
             cyc_guard += clock64() - cyc_g0;
         } else {
             // every thread must have read dec0 for `exact` before it is overwritten below: a warp that read the
             // new value would find `first` ready, take the guard tiers' barriers alone and fall out of step
-            __syncthreads();
+            bar_main();
         }
         if (tid < WORDS) {
             sm.acc0[tid] = sm.accw[tid];
             sm.dec0[tid] = sm.decw[tid];
         }
-        __syncthreads();
+        bar_main();
         partial_pass(sm);
     }
     const long long cyc_resolve = clock64() - cyc_res0 - cyc_guard;
@@ -2031,7 +2212,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             __stcg(&dd.cell_pos[__ldg(&dd.slot_of[k0 + tid])], sm.trial[tid]);
         }
     }
-    __syncthreads();
+    bar_main();
     if (warp == 0 && publish && lane < (nk + 31) / 32)  // release after the barrier: orders every thread's stores
         st_release(&ch.flags[g * WORDS + lane], ((unsigned long long)tag_cur << 32) | sm.accw[lane]);
     const unsigned long long gt_posp = trc ? globaltimer() : 0ull;
@@ -2069,7 +2250,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (bit(sm.accw, j)) sx += sm.cin[j * CS + k];
         sm.part[h][k] = sx;
     }
-    __syncthreads();
+    bar_main();
     double mydE = 0.0;
     if (tid < S) {
         const int k = tid;
@@ -2086,7 +2267,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mydE += __shfl_xor_sync(FULL, mydE, o);
     if (lane == 0) sm.redd[warp] = mydE;
-    __syncthreads();
+    bar_main();
     if (tid == 0 && publish) {
         double gsum = 0.0;
         for (int w = 0; w < T / 32; ++w) gsum += sm.redd[w];
@@ -2190,7 +2371,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             ch.rec[idx] = rc;
         }
     }
-    __syncthreads();
+    bar_main();
     return sm.ok != 0;
 }
 
@@ -2219,11 +2400,60 @@ sweep_kernel(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sch
             if (threadIdx.x == 0 && role == 1)
                 sm.ticket = *(volatile int *)&ctl->abort ? -1 : __ldcg(&box->ticket);
         }
-        __syncthreads();
+        bar_main();
         const int t = sm.ticket;
-        __syncthreads();
+        bar_main();
         if (t < 0) break;
-        if (!process_group(sm, chains, sched[t], t, ctl, role)) break;  // uniform: every failure exit follows a barrier
+        int hseq = 0;
+        // uniform: every failure exit follows a barrier
+        if (!process_group<false>(sm, chains, sched[t], t, ctl, role, hseq)) break;
+    }
+    // every exit path releases the TMEM columns before the CTA ends
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(sm.tmem);
+}
+
+// The same persistent loop with helper warps: 2T threads, one CTA per SM.  Warpgroups 0-1 (threads < T) run the
+// work items exactly as sweep_kernel does, with a larger register budget; warpgroups 2-3 give registers up and only
+// take column slices 8..15 of each tile pass (helper_loop), doubling the warps that hide the pair terms' latency.
+// Register split (setmaxnreg, per warpgroup): 2 x 128 x HELP_REGS_MAIN + 2 x 128 x HELP_REGS_TILE = 2T x 128, the
+// launch's own total, so the increase never waits.  Never used with pairs mode.
+constexpr int HELP_REGS_MAIN = 168, HELP_REGS_TILE = 88;
+static_assert(HELP_REGS_MAIN + HELP_REGS_TILE == 256 && HELP_REGS_MAIN % 8 == 0 && HELP_REGS_TILE % 8 == 0,
+              "register split within the launch's 128 per thread");
+
+__global__ void __launch_bounds__(2 * T, 1)
+sweep_kernel_h(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sched, int n_tickets, Ctl *ctl)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x >= T) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(HELP_REGS_TILE));
+        helper_loop(sm);
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(HELP_REGS_MAIN));
+        int hseq = 0;
+        for (;;) {
+            if (threadIdx.x == 0) {
+                const unsigned t = atomicAdd(&ctl->ticket, 1u);
+                const int ab = *(volatile int *)&ctl->abort;
+                sm.ticket = (ab || t >= (unsigned)n_tickets) ? -1 : (int)t;
+            }
+            bar_main();
+            const int t = sm.ticket;
+            bar_main();
+            if (t < 0) break;
+            if (!process_group<true>(sm, chains, sched[t], t, ctl, 0, hseq)) break;
+        }
+        // release the helper warps (they wait at the next hand-over)
+        if (threadIdx.x == 0) sm.hcmd[hseq & 1] = HC_EXIT;
+        bar_all();
     }
     // every exit path releases the TMEM columns before the CTA ends
     tmem_fence_before();
@@ -2251,7 +2481,17 @@ size_t sweep_smem_bytes()
 
 cudaError_t sweep_configure()
 {
-    return cudaFuncSetAttribute(mcg::sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(mcg::Smem));
+    cudaError_t e = cudaFuncSetAttribute(mcg::sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(mcg::Smem));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(mcg::sweep_kernel_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(mcg::Smem));
+}
+
+// Resident CTAs of the helper-warp kernel per SM (0 if it cannot run).
+cudaError_t sweep_occupancy_h(int *blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mcg::sweep_kernel_h, 2 * mcg::T,
+                                                         sizeof(mcg::Smem));
 }
 
 cudaError_t sweep_occupancy(int *blocks_per_sm)
@@ -2277,9 +2517,11 @@ cudaError_t sweep_max_clusters(int *n)
 }
 
 cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticket *sched, int n_tickets, mcg::Ctl *ctl,
-                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs)
+                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs, bool help)
 {
-    if (pairs) {  // clusters of two CTAs; grid even
+    if (help && !pairs) {
+        mcg::sweep_kernel_h<<<grid, 2 * mcg::T, sizeof(mcg::Smem), st>>>(chains, sched, n_tickets, ctl);
+    } else if (pairs) {  // clusters of two CTAs; grid even
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -3,10 +3,12 @@ traffic is reported only while the kernel source still matches the hash recorded
 import bench
 
 
-def test_alu_peak_is_the_mufu_bound():
-    """min(16 MUFU rsqrt per clock / 2 per pair-eval, 128 FP32 lanes / 14 ops per pair-eval) = 8 pair-evals per
-    SM clock: the MUFU pipe binds."""
-    assert bench.peak_pairs_per_clk_sm() == 8.0
+def test_alu_peak_takes_the_binding_unit():
+    """min(rsqrt rate / 2 per pair-eval, FP32 rate / 14 ops per pair-eval): with 28 rsqrt and 225 FP32 operations per
+    SM clock (the rates measured at 64 warps per SM on GB300) the MUFU binds at 14 pair-evals per clock; a slower
+    FP32 pipe takes over."""
+    assert bench.peak_pairs_per_clk_sm(28.0, 225.0) == 14.0
+    assert bench.peak_pairs_per_clk_sm(32.0, 140.0) == 10.0
 
 
 def test_traffic_only_for_the_source_it_was_measured_on(monkeypatch):

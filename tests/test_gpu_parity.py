@@ -370,6 +370,10 @@ def test_autotune_keeps_trajectories(pkg):
     tuned.sweep(2)
     info = tuned.autotune(2)
     assert info["policy"] in (0, 1) and info["ctas"] >= 1
+    sh = info["shape"]  # bit 0 pairs mode, bit 1 deep windows, bit 2 helper warps; the handle keeps it
+    assert 0 <= sh < 8 and not ((sh & 1) and (sh & 4))
+    assert tuned.get_option(p.OPT_PAIRS) == (sh & 1) and tuned.get_option(p.OPT_HELPERS) == (sh >> 2) & 1
+    assert tuned.get_option(p.OPT_DEEP_WINDOWS) == (sh >> 1) & 1
     tuned.sweep(3)
     for k, ch in enumerate(chains):
         o = oracle.OracleChain.from_chain(ch)
@@ -488,3 +492,30 @@ def test_periodic_drift_check(pkg):
     assert (gs.positions() == oc.positions()).all()
     assert gs.stats()["drift_checks"] == 8
     gs.close()
+
+
+@pytest.mark.parametrize("n,two_one,seed,deep", [(3000, True, 601, 1), (2100, False, 602, 0), (700, True, 603, 1)])
+def test_helper_warps_identical(pkg, n, two_one, seed, deep):
+    """The 512-thread kernel (helper warps take half of every tile pass) against the 256-thread kernel and the
+    oracle: positions and decisions identical, every FP32 value within its band."""
+    import paper_1602_05716_gb300 as p
+    ch = inputs.small_chain(n, phi=0.2, seed=seed, two_one=two_one, half_width=0.4)
+    runs = {}
+    for helpers in (0, 1):
+        s = p.System([ch])
+        s.set_option(p.OPT_PAIRS, 0)
+        s.set_option(p.OPT_DEEP_WINDOWS, deep)
+        s.set_option(p.OPT_HELPERS, helpers)
+        assert s.get_option(p.OPT_HELPERS) == helpers
+        s.record_enable(4 * n)
+        s.sweep(2)
+        s.sweep(2)
+        runs[helpers] = (s.positions(), s.records(), s.stats())
+        s.close()
+    assert (runs[0][0] == runs[1][0]).all()
+    assert (runs[0][1]["outcome"] == runs[1][1]["outcome"]).all()
+    o = oracle.OracleChain.from_chain(ch, threads=THREADS)
+    o.record(4 * n)
+    o.sweep(4)
+    assert (runs[1][0] == o.positions()).all()
+    _compare_records(runs[1][1], o.records(), n)
