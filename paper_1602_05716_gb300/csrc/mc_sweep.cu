@@ -54,6 +54,7 @@
 namespace mcg {
 
 constexpr int MPT = 4;             // moves per thread in the pair loops
+constexpr int TG = 4;              // groups per tile-ring buffer (one barrier per buffer)
 constexpr int SL = T / (S / MPT);  // column slices (8)
 constexpr int HALF = S / 2;
 constexpr int DW = 3;              // deep windows: the groups g-2 .. g-1-DW, both positions, matrices in TMEM
@@ -67,7 +68,7 @@ struct __align__(16) Smem {
     float4 wtri[S];   // window group: trial positions
     float4 dold[DW][S];  // deep windows (d = 0: the group before the window): old positions
     float4 dtri[DW][S];  // ... trial positions
-    float4 tile[2][2 * S];  // tile ring: each buffer holds one or two consecutive groups
+    float4 tile[2][TG * S];  // tile ring: each buffer holds 1..TG consecutive groups
     float cin[S * CS];   // c[j][k], j < k, this group
     float cwin[S * CS];  // c[j][k], window ion j
     float bhi[S], blo[S];  // sum of terms with known positions (float-float)
@@ -1097,41 +1098,72 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
 // One work item: the S moves of group g of chain `tk.chain` at sweep s.
 // role 0: the whole work item (the cluster's leader in pairs mode: even tiles); role 1: the pairs-mode helper,
 // which sums the odd tiles for the leader and decides nothing.
+// Groups staged in the buffer after the one holding groups up to in - 1: the consecutive groups in, in + 1, ... that
+// exist (< ntl) and lie inside the publication horizon hz, at most TG; 0 when group in is not known to be published.
+__device__ __forceinline__ int next_groups(int in, int ntl, int hz)
+{
+    int pn = 0;
+#pragma unroll
+    for (int k = 0; k < TG; ++k)
+        if (pn == k && in + k < ntl && in + k <= hz) pn = k + 1;
+    return pn;
+}
+
 // One buffer of the tile ring against the thread's moves: cnt staged groups of S ions, column slices of NSL (8 for
 // one group of warps, 16 when the helper warps take slices 8..15), this thread's slice r0.  Only the occupied
 // 32-move layers run (nm of them): one packed pair for <= 2, a packed pair and the third layer alone for 3, two
-// packed pairs for 4; an empty slot in the last layer repeats a real move and is never written back.
+// packed pairs for 4; an empty slot in the last layer repeats a real move and is never written back.  The FP32
+// partial sums s2 are promoted into the float-float sums (hA, lA) after every group, so no partial sum holds more
+// than S / NSL <= 16 terms (the band's C_SUM).
 template <int NSL>
 __device__ __forceinline__ void tile_buffer(const float4 *tile, int cnt, int r0, int nm, const Mv2 (&mv)[MPT / 2],
-                                            f32x2 (&s2)[MPT / 2], f32x2 (&P2)[MPT / 2], float (&mA)[MPT])
+                                            f32x2 (&s2)[MPT / 2], f32x2 (&P2)[MPT / 2], float (&mA)[MPT],
+                                            float (&hA)[MPT], float (&lA)[MPT])
 {
-    const int nj = cnt * (S / NSL);
-    if (nm <= 2) {
+    constexpr int NJ = S / NSL;  // partners per thread per group
+    for (int gq = 0; gq < cnt; ++gq) {
+        const float4 *tg = tile + gq * S + r0;
+        if (nm <= 2) {
 #pragma unroll 8
-        for (int jj = 0; jj < nj; ++jj) pair_far2(mv[0], tile[jj * NSL + r0], s2[0], P2[0], mA[0], mA[1]);
-    } else if (nm == 3) {
-        float s3, s3b, p3, p3b;
-        upk2(s2[1], s3, s3b);
-        upk2(P2[1], p3, p3b);
+            for (int jj = 0; jj < NJ; ++jj) pair_far2(mv[0], tg[jj * NSL], s2[0], P2[0], mA[0], mA[1]);
+        } else if (nm == 3) {
+            float s3, s3b, p3, p3b;
+            upk2(s2[1], s3, s3b);
+            upk2(P2[1], p3, p3b);
 #pragma unroll 8
-        for (int jj = 0; jj < nj; ++jj) {
-            const float4 y = tile[jj * NSL + r0];
-            pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
-            pair_far1(mv[1], y, s3, p3, mA[2]);
+            for (int jj = 0; jj < NJ; ++jj) {
+                const float4 y = tg[jj * NSL];
+                pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
+                pair_far1(mv[1], y, s3, p3, mA[2]);
+            }
+            s2[1] = pk2(s3, s3b);
+            P2[1] = pk2(p3, p3b);
+        } else {
+#pragma unroll 8
+            for (int jj = 0; jj < NJ; ++jj) {
+                const float4 y = tg[jj * NSL];
+                pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
+                pair_far2(mv[1], y, s2[1], P2[1], mA[2], mA[3]);
+            }
         }
-        s2[1] = pk2(s3, s3b);
-        P2[1] = pk2(p3, p3b);
-    } else {
-#pragma unroll 8
-        for (int jj = 0; jj < nj; ++jj) {
-            const float4 y = tile[jj * NSL + r0];
-            pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
-            pair_far2(mv[1], y, s2[1], P2[1], mA[2], mA[3]);
+#pragma unroll
+        for (int pp = 0; pp < MPT / 2; ++pp) {  // promote this group's partial sums
+            float v[2];
+            upk2(s2[pp], v[0], v[1]);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                float t2, e;
+                two_sum(hA[2 * pp + u], v[u], t2, e);
+                hA[2 * pp + u] = t2;
+                lA[2 * pp + u] += e;
+            }
+            s2[pp] = pk2(0.f, 0.f);
         }
     }
 }
 
-// The packed move data of thread row p (move slots p + 32 m) from the staged positions.
+// The packed move data of thread row p (move slots p + 32 m) from the staged positions: old positions, the
+// displacements and their negatives.
 __device__ __forceinline__ void tile_moves(const Smem &sm, int p, int ns, int (&km)[MPT], Mv2 (&mv)[MPT / 2])
 {
     float3 b3[MPT], d3[MPT];
@@ -1199,21 +1231,8 @@ __device__ void helper_loop(Smem &sm)
             const int cnt = sm.tcnt[cur];
             const int hz = sm.hzs[cur];
             const int in = i + cnt;
-            const int pn = (in < ntl && in <= hz) ? ((in + 1 < ntl && in + 1 <= hz) ? 2 : 1) : 0;
-            tile_buffer<2 * SL>(sm.tile[cur], cnt, SL + r, nm, mv, s2, P2, mA);
-#pragma unroll
-            for (int pp = 0; pp < MPT / 2; ++pp) {
-                float v[2];
-                upk2(s2[pp], v[0], v[1]);
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    float t2, e;
-                    two_sum(hA[2 * pp + u], v[u], t2, e);
-                    hA[2 * pp + u] = t2;
-                    lA[2 * pp + u] += e;
-                }
-                s2[pp] = pk2(0.f, 0.f);
-            }
+            const int pn = next_groups(in, ntl, hz);
+            tile_buffer<2 * SL>(sm.tile[cur], cnt, SL + r, nm, mv, s2, P2, mA, hA, lA);
             bar_all();  // the iteration's barrier
             if (in < ntl && pn == 0) {
                 bar_all();  // the next tile has been waited for
@@ -1662,12 +1681,16 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (lane == 0) {
                 sm.ok = ok;
                 sm.hzs[0] = hz0;
-                sm.tcnt[0] = (hz0 >= 1 && ntl > 1) ? 2 : 1;
+                sm.tcnt[0] = next_groups(0, ntl, hz0);
             }
         }
         bar_main();
         if (!sm.ok) return false;
-        if (tid < sm.tcnt[0] * S) sm.tile[0][tid] = __ldcg(&tile_src(tile_J(tid >> 7))[tid & (S - 1)]);
+#pragma unroll
+        for (int u = 0; u < TG * S / T; ++u) {
+            const int q = u * T + tid;
+            if (q < sm.tcnt[0] * S) sm.tile[0][q] = __ldcg(&tile_src(tile_J(q >> 7))[q & (S - 1)]);
+        }
         bar_main();
     }
     // the tiles run two moves per packed FP32x2 instruction (slots (0,1) and (2,3)); their |t| sum is bounded
@@ -1689,21 +1712,6 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         s2[pp] = pk2(sA[m0], sA[m1]);
         P2[pp] = pk2(PA[m0], PA[m1]);
     }
-    auto promote2 = [&]() {
-#pragma unroll
-        for (int pp = 0; pp < MPT / 2; ++pp) {
-            float v[2];
-            upk2(s2[pp], v[0], v[1]);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                float t2, e;
-                two_sum(hA[2 * pp + u], v[u], t2, e);
-                hA[2 * pp + u] = t2;
-                lA[2 * pp + u] += e;
-            }
-            s2[pp] = pk2(0.f, 0.f);
-        }
-    };
     // with helper warps: hand the tile pass over (they wait at barrier 2); they take column slices 8..15
     const bool tiles_run = ntl > 0 && ns > 0;
     if (HELP) {
@@ -1724,15 +1732,20 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const int cnt = sm.tcnt[cur];
         const int hz = sm.hzs[cur];
         const int in = i + cnt;  // first group of the next buffer
-        const int pn = (in < ntl && in <= hz) ? ((in + 1 < ntl && in + 1 <= hz) ? 2 : 1) : 0;  // groups prefetched
-        float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (tid < pn * S) pre = __ldcg(&tile_src(tile_J(in + (tid >> 7)))[tid & (S - 1)]);
+        const int pn = next_groups(in, ntl, hz);  // groups prefetched
+        float4 pre[TG * S / T];
+#pragma unroll
+        for (int u = 0; u < TG * S / T; ++u) {
+            const int q = u * T + tid;
+            pre[u] = (q < pn * S) ? __ldcg(&tile_src(tile_J(in + (q >> 7)))[q & (S - 1)]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         // occupied 32-move layers only (all of them for a plain chain)
-        tile_buffer<HELP ? 2 * SL : SL>(sm.tile[cur], cnt, r, nm, mv, s2, P2, mA);
-        promote2();
-        if (tid < pn * S) sm.tile[cur ^ 1][tid] = pre;
+        tile_buffer<HELP ? 2 * SL : SL>(sm.tile[cur], cnt, r, nm, mv, s2, P2, mA, hA, lA);
+#pragma unroll
+        for (int u = 0; u < TG * S / T; ++u)
+            if (u * T + tid < pn * S) sm.tile[cur ^ 1][u * T + tid] = pre[u];
         if (warp == 0) {
-            const int nh = (hz < in + 8 && hz < ntl - 1) ? advance_horizon(hz) : hz;
+            const int nh = (hz < in + 4 * TG && hz < ntl - 1) ? advance_horizon(hz) : hz;
             if (lane == 0) {
                 sm.hzs[cur ^ 1] = nh;
                 sm.tcnt[cur ^ 1] = pn;
