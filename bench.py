@@ -311,13 +311,15 @@ def dE_error(pkg, ch, moves: int, threads: int) -> dict:
 
 
 def time_arm(pkg, chains, stream, flush, steps: int, warmup: int, sps: int, world: int, local: int,
-             surrogate=None, r_c: float = 4.0, W: int = 160, sampler=None) -> dict:
+             surrogate=None, r_c: float = 4.0, W: int = 160, sampler=None, pairs: int = -1) -> dict:
     """One arm: warm-up steps, then `steps` timed steps of `sps` sweeps each, CUDA events on the launch stream around
     every graph replay, L2 flushed between steps outside the events.  Returns times, counters and the system."""
     import torch
     with torch.cuda.stream(stream):
         sysm = pkg.System(chains)
         sysm.set_stream(stream.cuda_stream)
+        if pairs >= 0:
+            sysm.set_option(pkg.OPT_PAIRS, pairs)
         if surrogate is not None:
             for i in range(len(chains)):
                 sysm.set_surrogate(surrogate, r_c=r_c, W=W, chain=i)
@@ -428,17 +430,17 @@ def run_ours(args):
     arms = {}
     if mode in ("plain", "both"):
         arms["plain"] = time_arm(pkg, chains, stream, flush, args.steps, args.warmup, sps, world, local,
-                                 sampler=ClockSampler)
+                                 sampler=ClockSampler, pairs=args.pairs)
         if mode == "both":
             arms["plain"]["sys"].close()
     if mode == "both":
         arms["da_g0"] = time_arm(pkg, chains, stream, flush, args.steps, args.warmup, sps, world, local,
                                  surrogate=np.zeros(pkg.MLP_NP, np.uint16), r_c=args.r_c, W=args.da_W,
-                                 sampler=ClockSampler)
+                                 sampler=ClockSampler, pairs=args.pairs)
         arms["da_g0"]["sys"].close()
     if mode in ("da", "both"):
         arms["da"] = time_arm(pkg, chains, stream, flush, args.steps, args.warmup, sps, world, local,
-                              surrogate=w_da, r_c=args.r_c, W=args.da_W, sampler=ClockSampler)
+                              surrogate=w_da, r_c=args.r_c, W=args.da_W, sampler=ClockSampler, pairs=args.pairs)
     head_name = "da" if "da" in arms else "plain"
     head = arms[head_name]
     sysm = head["sys"]
@@ -571,6 +573,8 @@ def main():
     ap.add_argument("--mode", choices=["plain", "da", "both"], default=None,
                     help="plain exact path, delayed acceptance with a trained surrogate, or both (plain, g = 0 and "
                          "trained arms; default by workload)")
+    ap.add_argument("--pairs", type=int, choices=[-1, 0, 1], default=-1,
+                    help="pairs mode of the timed arms: -1 the library's automatic choice, 0 off, 1 on")
     ap.add_argument("--r-c", dest="r_c", type=float, default=4.0)
     ap.add_argument("--da-W", dest="da_W", type=int, default=160)
     ap.add_argument("--da-samples", dest="da_samples", type=int, default=2_000_000)

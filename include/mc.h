@@ -317,7 +317,7 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
  *                      delayed acceptance (default), 0 = they sweep plainly (the
  *                      surrogate stays set for mc_da_samples)
  *  MC_OPT_PAIRS        -1 = automatic (default: on for a single chain without a
- *                      surrogate of at most 4 x SMs groups when deep windows are
+ *                      surrogate of at most 2 x SMs groups when deep windows are
  *                      on), 0 = off, 1 = on:
  *                      thread-block clusters of two CTAs share each work item,
  *                      the second summing every other tile for the first.  The

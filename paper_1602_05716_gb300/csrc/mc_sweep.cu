@@ -1124,13 +1124,13 @@ __device__ __forceinline__ void tile_buffer(const float4 *tile, int cnt, int r0,
     for (int gq = 0; gq < cnt; ++gq) {
         const float4 *tg = tile + gq * S + r0;
         if (nm <= 2) {
-#pragma unroll 8
+#pragma unroll 4
             for (int jj = 0; jj < NJ; ++jj) pair_far2(mv[0], tg[jj * NSL], s2[0], P2[0], mA[0], mA[1]);
         } else if (nm == 3) {
             float s3, s3b, p3, p3b;
             upk2(s2[1], s3, s3b);
             upk2(P2[1], p3, p3b);
-#pragma unroll 8
+#pragma unroll 4
             for (int jj = 0; jj < NJ; ++jj) {
                 const float4 y = tg[jj * NSL];
                 pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
@@ -1139,7 +1139,7 @@ __device__ __forceinline__ void tile_buffer(const float4 *tile, int cnt, int r0,
             s2[1] = pk2(s3, s3b);
             P2[1] = pk2(p3, p3b);
         } else {
-#pragma unroll 8
+#pragma unroll 4
             for (int jj = 0; jj < NJ; ++jj) {
                 const float4 y = tg[jj * NSL];
                 pair_far2(mv[0], y, s2[0], P2[0], mA[0], mA[1]);
