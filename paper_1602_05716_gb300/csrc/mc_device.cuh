@@ -328,18 +328,22 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
     return r;
 }
 
-// Two moves (packed old positions b, displacements d, negated displacements nd) against one settled ion y.  Do, Dd
-// and Dn as in pair_far; then the term with two MUFU operations instead of three:
+// Two moves (packed old positions b, doubled displacements t = 2d and m = -|d|^2) against one settled ion y.  With
+// e = y - b:
+//   Do = |e|^2,   Dd = 2 d.e - |d|^2 = |b - y|^2 - |a - y|^2 (three FMAs on m),   Dn = Do - Dd,
+// then the term with two MUFU operations:
 //   s = rsqrt(Do Dn) = rn ro,   w = rsqrt(Do + Dn + 2 (Do Dn) s) = 1 / (sqrt(Do) + sqrt(Dn)) = rn ro / (rn + ro),
 //   t = (Dd s) w = Dd (rn ro)^2 / (rn + ro).
-// Relative error of t beyond Dd's own: with Do, Dn off by delta_o, delta_n (relative), s is within
-// (|delta_o| + |delta_n| + u) / 2 + 2^-22.9, sqrt(Do Dn) = (Do Dn) s within that + u, Do + Dn + 2 sqrt(Do Dn) (a sum
-// of positive terms) within max(|delta_o|, |delta_n|) + 4.7u, w within half of that + 2^-22.9, so t is within
-// |delta_o| + |delta_n| + 9.2u: below the rel(Dn) + 19u (|delta_o| <= 3u) of pair_far's per-term bound.  Without the
-// |t| sum (|t| <= dn rn ro exactly, so the bound takes dn P); P sums |q| s, which is within rel(Dn) / 2 + 5u of
-// rn ro, inside the bound's 2^-16 slack for the rounding of rn ro.
+// Dd's rounding: m = -fl(|d|^2) is within 3u |d|^2 and the FMA chain adds 3u (2 |d.e|_1 + |d|^2), so Dd is within
+// 6u dn (Ro + dn) of 2 d.e' - |d|^2 for the rounded e' (e's own rounding is the perturbation term of the bound, as
+// for pair_far's form).  Relative error of t beyond Dd's own: with Do, Dn off by delta_o, delta_n (relative), s is
+// within (|delta_o| + |delta_n| + u) / 2 + 2^-22.9, sqrt(Do Dn) = (Do Dn) s within that + u, Do + Dn + 2 sqrt(Do Dn)
+// (a sum of positive terms) within max(|delta_o|, |delta_n|) + 4.7u, w within half of that + 2^-22.9, so t is within
+// |delta_o| + |delta_n| + 9.2u: below the rel(Dn) + 19u (|delta_o| <= 3u) of the per-term bound far_coeffs uses.
+// Without the |t| sum (|t| <= dn rn ro exactly, so the bound takes dn P); P sums |q| s, which is within
+// rel(Dn) / 2 + 5u of rn ro, inside the bound's 2^-16 slack for the rounding of rn ro.
 struct Mv2 {
-    f32x2 bx, by, bz, dx, dy, dz, nx, ny, nz;
+    f32x2 bx, by, bz, tx, ty, tz, m;
 };
 
 __device__ __forceinline__ void pair_far2(const Mv2 &m, const float4 y, f32x2 &s, f32x2 &P, float &mn0, float &mn1)
@@ -347,8 +351,7 @@ __device__ __forceinline__ void pair_far2(const Mv2 &m, const float4 y, f32x2 &s
     const f32x2 two = pk2(2.0f, 2.0f);
     const f32x2 ex = sub2(pk2(y.x, y.x), m.bx), ey = sub2(pk2(y.y, y.y), m.by), ez = sub2(pk2(y.z, y.z), m.bz);
     const f32x2 Do = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
-    const f32x2 wx = fma2(two, ex, m.nx), wy = fma2(two, ey, m.ny), wz = fma2(two, ez, m.nz);
-    const f32x2 Dd = fma2(m.dz, wz, fma2(m.dy, wy, mul2(m.dx, wx)));
+    const f32x2 Dd = fma2(m.tz, ez, fma2(m.ty, ey, fma2(m.tx, ex, m.m)));
     const f32x2 Dn = sub2(Do, Dd);
     const f32x2 pd = mul2(Do, Dn);
     float p0, p1;
@@ -371,20 +374,17 @@ __device__ __forceinline__ void pair_far2(const Mv2 &m, const float4 y, f32x2 &s
 // rounds like the scalar operation), for a third occupied layer of 32 move slots.
 __device__ __forceinline__ void pair_far1(const Mv2 &m, const float4 y, float &s, float &P, float &mn)
 {
-    float bx, by, bz, dx, dy, dz, nx, ny, nz, u;
+    float bx, by, bz, tx, ty, tz, mm, u;
     upk2(m.bx, bx, u);
     upk2(m.by, by, u);
     upk2(m.bz, bz, u);
-    upk2(m.dx, dx, u);
-    upk2(m.dy, dy, u);
-    upk2(m.dz, dz, u);
-    upk2(m.nx, nx, u);
-    upk2(m.ny, ny, u);
-    upk2(m.nz, nz, u);
+    upk2(m.tx, tx, u);
+    upk2(m.ty, ty, u);
+    upk2(m.tz, tz, u);
+    upk2(m.m, mm, u);
     const float ex = __fsub_rn(y.x, bx), ey = __fsub_rn(y.y, by), ez = __fsub_rn(y.z, bz);
     const float Do = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
-    const float wx = __fmaf_rn(2.0f, ex, nx), wy = __fmaf_rn(2.0f, ey, ny), wz = __fmaf_rn(2.0f, ez, nz);
-    const float Dd = __fmaf_rn(dz, wz, __fmaf_rn(dy, wy, __fmul_rn(dx, wx)));
+    const float Dd = __fmaf_rn(tz, ez, __fmaf_rn(ty, ey, __fmaf_rn(tx, ex, mm)));
     const float Dn = __fsub_rn(Do, Dd);
     const float pd = __fmul_rn(Do, Dn);
     const float sr = rsqrt_ftz(pd);
@@ -395,6 +395,31 @@ __device__ __forceinline__ void pair_far1(const Mv2 &m, const float4 y, float &s
     P = __fmaf_rn(fabsf(y.w), sr, P);
     mn = fminf(mn, Dn);
 }
+
+// The packed move data of two moves (old positions b0, b1; displacements d0, d1 as FP32 differences a - b).
+__device__ __forceinline__ Mv2 make_mv2(const float3 b0, const float3 d0, const float3 b1, const float3 d1)
+{
+    Mv2 v;
+    v.bx = pk2(b0.x, b1.x);
+    v.by = pk2(b0.y, b1.y);
+    v.bz = pk2(b0.z, b1.z);
+    v.tx = pk2(2.0f * d0.x, 2.0f * d1.x);
+    v.ty = pk2(2.0f * d0.y, 2.0f * d1.y);
+    v.tz = pk2(2.0f * d0.z, 2.0f * d1.z);
+    v.m = pk2(-__fmaf_rn(d0.z, d0.z, __fmaf_rn(d0.y, d0.y, __fmul_rn(d0.x, d0.x))),
+              -__fmaf_rn(d1.z, d1.z, __fmaf_rn(d1.y, d1.y, __fmul_rn(d1.x, d1.x))));
+    return v;
+}
+
+// Asynchronous 16-byte copy global -> shared through L2 (cp.async.cg); cp_async_wait_all waits for all of this
+// thread's copies.  Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Error-free transformations in FP32 (Knuth's TwoSum, FMA-based TwoProduct).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)

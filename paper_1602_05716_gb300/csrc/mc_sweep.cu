@@ -318,23 +318,26 @@ __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsig
     }
 }
 
-// Bound coefficients of pair_far for a move of length at most dn when every settled ion is at least sp from
-// both the old and the trial position (x = dn / sp).  Following tier 2's per-term bound with
-// Ro <= Rn + dn, M <= dn (Rn + Ro) and rho >= (1 - x/2) min(Rn, Ro):
-//   per term  |err| <= u |q| (kT |t| + kP rn ro),   kT = kD + 20,  kP = (4 + k3) dn,
-//   kD = 3 (1+x)^2 + 4 (2x + x^2) + 1,   k3 = (1+x) (3/g^2 + 2x/g^3),  g = 1 - x/2;
-// the squared distance Dn is within u kO max(Dn, sigma^2) of |a - y|^2, kO = 5 (1+x)^2 + 14x + 8x^2 + 1.
+// Bound coefficients of the tiles' pair form (pair_far2) for a move of length at most dn when every settled ion
+// is at least sp from both the old and the trial position (x = dn / sp).  Following tier 2's per-term bound with
+// Ro <= Rn + dn and rho >= (1 - x/2) min(Rn, Ro):
+//   per term  |err| <= u |q| (kT |t| + kP rn ro),   kT = kD + 20,  kP = (6 (1 + x/2) + k3) dn,
+//   kD = 3 (1+x)^2 + 4 (2x + x^2) + 8x^2 + 1,   k3 = (1+x) (3/g^2 + 2x/g^3),  g = 1 - x/2;
+// the squared distance Dn is within u kO max(Dn, sigma^2) of |a - y|^2, kO = 5 (1+x)^2 + 14x + 16x^2 + 1.
+// pair_far2's three-FMA Dd is within 6u dn (Ro + dn), where tier 2's dot product is within 4u M <= 4u dn (Rn + Ro).
+// Relative to Dn that is at most u (6x + 12x^2) against u (8x + 4x^2): the 8x^2 added to kD and kO.  Through t's
+// factor (rn ro)^2 / (rn + ro) it is at most 6u (1 + x/2) dn rn ro against 4u dn rn ro: kP's 6 (1 + x/2).
 // Returns false for x >= 1.75, where the move is left to the FP64 tier.
 __device__ __forceinline__ bool far_coeffs(float dn, float sp, float &kT, float &kP, float &kO)
 {
     const float x = dn / sp * (1.0f + 0x1p-20f);
     if (!(x < 1.75f)) return false;
     const float x1 = 1.0f + x, g = 1.0f - 0.5f * x;
-    const float kD = 3.0f * x1 * x1 + 4.0f * x * (2.0f + x) + 1.0f;
+    const float kD = 3.0f * x1 * x1 + 4.0f * x * (2.0f + x) + 8.0f * x * x + 1.0f;
     const float k3 = x1 * (3.0f / (g * g) + 2.0f * x / (g * g * g));
     kT = (kD + 20.0f) * (1.0f + 0x1p-10f);
-    kP = (4.0f + k3) * dn * (1.0f + 0x1p-10f);
-    kO = (5.0f * x1 * x1 + x * (14.0f + 8.0f * x) + 1.0f) * (1.0f + 0x1p-4f);
+    kP = (6.0f * (1.0f + 0.5f * x) + k3) * dn * (1.0f + 0x1p-10f);
+    kO = (5.0f * x1 * x1 + x * (14.0f + 16.0f * x) + 1.0f) * (1.0f + 0x1p-4f);
     return true;
 }
 
@@ -1176,18 +1179,7 @@ __device__ __forceinline__ void tile_moves(const Smem &sm, int p, int ns, int (&
         d3[m] = make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
     }
 #pragma unroll
-    for (int pp = 0; pp < MPT / 2; ++pp) {
-        const int m0 = 2 * pp, m1 = 2 * pp + 1;
-        mv[pp].bx = pk2(b3[m0].x, b3[m1].x);
-        mv[pp].by = pk2(b3[m0].y, b3[m1].y);
-        mv[pp].bz = pk2(b3[m0].z, b3[m1].z);
-        mv[pp].dx = pk2(d3[m0].x, d3[m1].x);
-        mv[pp].dy = pk2(d3[m0].y, d3[m1].y);
-        mv[pp].dz = pk2(d3[m0].z, d3[m1].z);
-        mv[pp].nx = pk2(-d3[m0].x, -d3[m1].x);
-        mv[pp].ny = pk2(-d3[m0].y, -d3[m1].y);
-        mv[pp].nz = pk2(-d3[m0].z, -d3[m1].z);
-    }
+    for (int pp = 0; pp < MPT / 2; ++pp) mv[pp] = make_mv2(b3[2 * pp], d3[2 * pp], b3[2 * pp + 1], d3[2 * pp + 1]);
 }
 
 // The helper warps (threads T..2T-1 of the 2T-thread kernel): column slices 8..15 of every work item's tile pass,
@@ -1700,15 +1692,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
 #pragma unroll
     for (int pp = 0; pp < MPT / 2; ++pp) {
         const int m0 = 2 * pp, m1 = 2 * pp + 1;
-        mv[pp].bx = pk2(b3[m0].x, b3[m1].x);
-        mv[pp].by = pk2(b3[m0].y, b3[m1].y);
-        mv[pp].bz = pk2(b3[m0].z, b3[m1].z);
-        mv[pp].dx = pk2(d3[m0].x, d3[m1].x);
-        mv[pp].dy = pk2(d3[m0].y, d3[m1].y);
-        mv[pp].dz = pk2(d3[m0].z, d3[m1].z);
-        mv[pp].nx = pk2(-d3[m0].x, -d3[m1].x);
-        mv[pp].ny = pk2(-d3[m0].y, -d3[m1].y);
-        mv[pp].nz = pk2(-d3[m0].z, -d3[m1].z);
+        mv[pp] = make_mv2(b3[m0], d3[m0], b3[m1], d3[m1]);
         s2[pp] = pk2(sA[m0], sA[m1]);
         P2[pp] = pk2(PA[m0], PA[m1]);
     }
@@ -1733,17 +1717,16 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const int hz = sm.hzs[cur];
         const int in = i + cnt;  // first group of the next buffer
         const int pn = next_groups(in, ntl, hz);  // groups prefetched
-        float4 pre[TG * S / T];
+        // the next buffer's groups are copied into the other buffer (16 B per thread and copy, through L2) while
+        // this one runs; the copies complete before the barrier that ends the iteration
 #pragma unroll
         for (int u = 0; u < TG * S / T; ++u) {
             const int q = u * T + tid;
-            pre[u] = (q < pn * S) ? __ldcg(&tile_src(tile_J(in + (q >> 7)))[q & (S - 1)]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < pn * S) cp_async16(&sm.tile[cur ^ 1][q], &tile_src(tile_J(in + (q >> 7)))[q & (S - 1)]);
         }
         // occupied 32-move layers only (all of them for a plain chain)
         tile_buffer<HELP ? 2 * SL : SL>(sm.tile[cur], cnt, r, nm, mv, s2, P2, mA, hA, lA);
-#pragma unroll
-        for (int u = 0; u < TG * S / T; ++u)
-            if (u * T + tid < pn * S) sm.tile[cur ^ 1][u * T + tid] = pre[u];
+        cp_async_wait_all();
         if (warp == 0) {
             const int nh = (hz < in + 4 * TG && hz < ntl - 1) ? advance_horizon(hz) : hz;
             if (lane == 0) {
