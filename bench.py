@@ -311,7 +311,7 @@ def dE_error(pkg, ch, moves: int, threads: int) -> dict:
 
 
 def time_arm(pkg, chains, stream, flush, steps: int, warmup: int, sps: int, world: int, local: int,
-             surrogate=None, r_c: float = 4.0, W: int = 160, sampler=None, pairs: int = -1) -> dict:
+             surrogate=None, r_c: float = 4.0, W: int = 160, sampler=None, pairs: int = -1, prefilter: int = 0) -> dict:
     """One arm: warm-up steps, then `steps` timed steps of `sps` sweeps each, CUDA events on the launch stream around
     every graph replay, L2 flushed between steps outside the events.  Returns times, counters and the system."""
     import torch
@@ -323,6 +323,9 @@ def time_arm(pkg, chains, stream, flush, steps: int, warmup: int, sps: int, worl
         if surrogate is not None:
             for i in range(len(chains)):
                 sysm.set_surrogate(surrogate, r_c=r_c, W=W, chain=i)
+        if prefilter:
+            for i in range(len(chains)):
+                sysm.set_overlap_prefilter(prefilter, chain=i)
         tuned = sysm.autotune(2) if len(chains) > 1 else None
         for _ in range(warmup):
             flush.zero_()
@@ -370,7 +373,10 @@ def roofline(pairs_per_step: float, step_ms, info: dict, max_mhz: float, load_mh
             "kernel": kernel}
 
 
-def arm_summary(arm: dict, chains, sps: int, steps: int, info, max_mhz, load_mhz, traffic, da: bool, rates) -> dict:
+def arm_summary(arm: dict, chains, sps: int, steps: int, info, max_mhz, load_mhz, traffic, da: bool, rates,
+                prefilter: bool = False) -> dict:
+    """One arm's numbers.  With a stage 1 (delayed acceptance, or the overlap prefilter) only its survivors' pair
+    sums count as executed pair-evals; the plain-equivalent count is reported beside them."""
     n = sum(c.n for c in chains)
     d = arm["delta"]
     moves = n * sps * steps
@@ -379,7 +385,8 @@ def arm_summary(arm: dict, chains, sps: int, steps: int, info, max_mhz, load_mhz
     if da:
         surv = moves - d["da_rej1"] - d["da_ovl1"] - d["rej_wall"]
         executed = surv * (chains[0].n - 1) if len(chains) == 1 else plain_pairs * surv / max(1, moves)
-        kernel = "mcg::sweep_kernel with the surrogate stage (one launch per sweep), CUDA events on its stream"
+        kernel = ("mcg::sweep_kernel with the overlap prefilter" if prefilter else
+                  "mcg::sweep_kernel with the surrogate stage") + " (one launch per sweep), CUDA events on its stream"
     else:
         surv = moves
         executed = plain_pairs
@@ -433,6 +440,10 @@ def run_ours(args):
                                  sampler=ClockSampler, pairs=args.pairs)
         if mode == "both":
             arms["plain"]["sys"].close()
+    if mode == "both" and args.prefilter_W > 0:
+        arms["plain_pf"] = time_arm(pkg, chains, stream, flush, args.steps, args.warmup, sps, world, local,
+                                    sampler=ClockSampler, pairs=args.pairs, prefilter=args.prefilter_W)
+        arms["plain_pf"]["sys"].close()
     if mode == "both":
         arms["da_g0"] = time_arm(pkg, chains, stream, flush, args.steps, args.warmup, sps, world, local,
                                  surrogate=np.zeros(pkg.MLP_NP, np.uint16), r_c=args.r_c, W=args.da_W,
@@ -452,9 +463,10 @@ def run_ours(args):
     value = moves_total / t_max
     csum = head["clocks"] or {}
     load_mhz = csum.get("sm_mhz")
+    arm_file = {"plain": "plain", "plain_pf": "prefilter", "da_g0": "da", "da": "da"}
     summaries = {k: arm_summary(a, chains, sps, args.steps, info, max_mhz, (a["clocks"] or {}).get("sm_mhz"),
-                                measured_traffic(args.workload, "da" if k.startswith("da") else "plain"),
-                                k.startswith("da"), rates)
+                                measured_traffic(args.workload, arm_file[k]), k != "plain", rates,
+                                prefilter=(k == "plain_pf"))
                  for k, a in arms.items()}
     hs = summaries[head_name]
     energies = [sysm.energy(i) for i in range(len(chains))]
@@ -493,11 +505,14 @@ def run_ours(args):
         err = (rr["dE"] - rr["dEt"])[both]
         line["delayed_acceptance"]["surrogate_dE_error_rms_kT"] = float(np.sqrt(np.mean(err ** 2))) if err.size else None
         line["delayed_acceptance"]["surrogate_dE_error_mean_abs_kT"] = float(np.mean(np.abs(err))) if err.size else None
-        for k in ("plain", "da_g0"):
+        for k in ("plain", "plain_pf", "da_g0"):
             if k in summaries:
                 s = summaries[k]
-                line[{"plain": "plain_path_same_gpu", "da_g0": "da_g_zero_same_gpu"}[k]] = dict(
+                line[{"plain": "plain_path_same_gpu", "plain_pf": "plain_prefilter_same_gpu",
+                      "da_g0": "da_g_zero_same_gpu"}[k]] = dict(
                     s, speedup_of_trained=value / s["moves_per_s"] if world == 1 else None)
+        if "plain_pf" in summaries:
+            line["plain_prefilter_same_gpu"]["W_groups"] = args.prefilter_W
 
     # end to end through the C ABI with host buffers: upload positions, sweep, read positions + ledger back
     if not args.no_e2e:
@@ -575,6 +590,8 @@ def main():
                          "trained arms; default by workload)")
     ap.add_argument("--pairs", type=int, choices=[-1, 0, 1], default=-1,
                     help="pairs mode of the timed arms: -1 the library's automatic choice, 0 off, 1 on")
+    ap.add_argument("--prefilter-W", dest="prefilter_W", type=int, default=160,
+                    help="exclusion depth of the plain arm with the overlap prefilter (mode both; 0 = no such arm)")
     ap.add_argument("--r-c", dest="r_c", type=float, default=4.0)
     ap.add_argument("--da-W", dest="da_W", type=int, default=160)
     ap.add_argument("--da-samples", dest="da_samples", type=int, default=2_000_000)

@@ -407,6 +407,26 @@ int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t
  * sweep's start positions (no charge grid).                                  */
 int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W);
 
+/* Overlap prefilter (an exact speed-up of the plain chain; Sec. 2's rule that a
+ * trial overlapping another ion is rejected whatever its energy change).
+ * Before any pair sum, each work item rejects the moves whose trial position
+ * overlaps an ion it can already place: an ion more than W groups back in the
+ * sweep, or a later ion of its own group.  They are found through a cell list
+ * of the sweep's start positions (cells of edge at least (sigma + 2 sqrt(3)
+ * h) / 2, every listed position kept current as moves are accepted; a cell
+ * holds at most 64 ions and any beyond are simply not listed).  The plain
+ * chain rejects those moves as overlaps too, so decisions, positions and
+ * ledger are the plain chain's bit for bit; the surviving moves pay the O(N)
+ * sum and are decided by the plain rule (draw purpose 0, the same band and
+ * guard tiers).  Records of prefilter rejections carry tier 6.
+ * W >= 2 sets it (the launch then uses at most W - 1 persistent CTAs, as with
+ * a surrogate), W = 0 removes it.  Like a surrogate it makes sweeps run one
+ * per launch after the cell list is rebuilt, MC_OPT_DA = 0 suspends it, and
+ * it replaces a surrogate set on the chain (mc_set_surrogate replaces it in
+ * turn).  Device memory: at most 8 N cells (256 per axis) of up to 64 slots,
+ * 20 bytes each, plus 4 bytes per cell and per ion.                         */
+int mc_set_overlap_prefilter(mc_handle h, int chain, int W);
+
 /* Training samples from the chain as it stands: for each ion i, the trial move
  * the chain would make next (sweep counter unchanged, nothing moves), the
  * features v above at the old and the trial position (v_pairs: N x 66, old

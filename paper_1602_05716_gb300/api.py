@@ -113,6 +113,7 @@ def lib():
         "mc_unit_rates": ([vp], ci),
         "mc_total_energy_noalloc": ([vp, i64, dbl, vp, vp], ci),
         "mc_set_surrogate": ([vp, ci, vp, i64, dbl, ci], ci),
+        "mc_set_overlap_prefilter": ([vp, ci, ci], ci),
         "mc_da_samples": ([vp, ci, vp, vp, vp], ci),
         "mc_mlp_forward": ([vp, vp, i64, vp], ci),
         "mc_mlp_loss_grad": ([vp, vp, vp, i64, vp, vp], ci),
@@ -330,6 +331,10 @@ class System:
             return
         w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
         _check(lib().mc_set_surrogate(self._h, chain, w.ctypes.data, int(w.shape[0]), float(r_c), int(W)))
+
+    def set_overlap_prefilter(self, W: int = 160, chain: int = 0):
+        """The plain chain with its overlap test taken first through a cell list (identical decisions); 0 removes it."""
+        _check(lib().mc_set_overlap_prefilter(self._h, chain, int(W)))
 
     def da_samples(self, chain: int = 0):
         """Training samples of the chain's next trial moves: (v_pairs N x 66, y N, valid N)."""

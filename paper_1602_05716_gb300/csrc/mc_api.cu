@@ -39,6 +39,8 @@ cudaError_t log_test_launch(const double *u, int n, double *out, cudaStream_t st
 cudaError_t unit_rates(int sms, double *out);
 cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt, int *cellid,
                            int *start, int *fill, int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st);
+cudaError_t da_prep_bucket_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt,
+                                  int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st);
 cudaError_t da_sample_launch(const mcg::ChainDev *ch, const mcg::DADev *dd, int B, int grid, float *V, float *Y,
                              unsigned char *valid, cudaStream_t st);
 cudaError_t mlp_forward_launch(const unsigned short *w, const float *V, long long n, float *G, float *Z, cudaStream_t st);
@@ -128,6 +130,7 @@ struct Chain {
     float4 *cur() const { return pos[sweeps & 1]; }
     // delayed acceptance (mc_set_surrogate)
     bool da = false;
+    bool pf = false;              // the DA state is an overlap prefilter (mc_set_overlap_prefilter)
     mcg::DADev hda{};             // host copy of the device descriptor
     mcg::DADev *dda = nullptr;    // device descriptor
     unsigned short *d_w = nullptr;
@@ -285,6 +288,7 @@ mcg::ChainDev describe(const Chain &c)
     d.key1 = c.chain_id;
     d.ctr3 = (unsigned)(c.seed >> 32);
     d.da = nullptr;
+    d.pf = 0u;
     return d;
 }
 
@@ -293,7 +297,10 @@ int sync_descriptors(mc_system *h)
     h->h_chains.resize(h->chains.size());
     for (size_t i = 0; i < h->chains.size(); ++i) {
         h->h_chains[i] = describe(h->chains[i]);
-        if (h->chains[i].da && h->da_on) h->h_chains[i].da = h->chains[i].dda;
+        if (h->chains[i].da && h->da_on) {
+            h->h_chains[i].da = h->chains[i].dda;
+            h->h_chains[i].pf = h->chains[i].pf ? 1u : 0u;
+        }
     }
     CK(cudaMemcpy(h->d_chains, h->h_chains.data(), sizeof(mcg::ChainDev) * h->h_chains.size(), cudaMemcpyHostToDevice));
     return MC_OK;
@@ -558,8 +565,11 @@ cudaError_t enqueue_da(mc_system *h, long long n, int grid, const mcg::Ticket *s
         for (size_t ci = 0; ci < h->chains.size(); ++ci) {
             Chain &c = h->chains[ci];
             if (!c.da || e != cudaSuccess) continue;
-            e = mcg_host::da_prep_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid, c.d_cell_start,
-                                         c.d_fill, c.d_cell_ions, c.d_cell_pos, c.d_slot_of, h->stream);
+            e = c.pf ? mcg_host::da_prep_bucket_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cell_ions,
+                                                       c.d_cell_pos, c.d_slot_of, h->stream)
+                     : mcg_host::da_prep_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid,
+                                                c.d_cell_start, c.d_fill, c.d_cell_ions, c.d_cell_pos, c.d_slot_of,
+                                                h->stream);
         }
         if (e == cudaSuccess)
             e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), 1, h->stream,
@@ -1474,6 +1484,18 @@ int mc_autotune(mc_handle h, int64_t trial_sweeps, int64_t *best_policy, int64_t
 
 static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W);
 
+// Free the delayed-acceptance / prefilter arrays of a chain (the stream is idle).
+static void release_da(Chain &c)
+{
+    cudaFree(c.dda); cudaFree(c.d_w); cudaFree(c.d_w2n); cudaFree(c.d_cell_start); cudaFree(c.d_cell_ions);
+    cudaFree(c.d_slot_of); cudaFree(c.d_cnt); cudaFree(c.d_cellid); cudaFree(c.d_fill); cudaFree(c.d_cell_pos);
+    c.dda = nullptr; c.d_w = nullptr; c.d_w2n = nullptr; c.d_cell_start = nullptr; c.d_cell_ions = nullptr;
+    c.d_slot_of = nullptr; c.d_cnt = nullptr; c.d_cellid = nullptr; c.d_fill = nullptr; c.d_cell_pos = nullptr;
+    c.da = false;
+    c.pf = false;
+    c.ncell = 0;
+}
+
 int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w, double r_c, int W)
 {
     Range nv("mc_set_surrogate");
@@ -1489,6 +1511,7 @@ static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, in
     CK(cudaStreamSynchronize(h->stream));
     Chain &c = h->chains[chain];
     if (!w_bf16) {
+        if (c.pf) release_da(c);  // removing the surrogate never leaves a prefilter behind
         c.da = false;
         drop_graphs(h);
         return sync_descriptors(h);
@@ -1509,11 +1532,7 @@ static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, in
     const double reach = (r_c + 2.0 * std::sqrt(3.0) * 0.5 * D) * (1.0 + 0x1p-8) + 1e-6;
     const int G = std::max(1, std::min(64, (int)std::floor(2.0 * c.R / (0.5 * reach))));
     // (re)allocate
-    cudaFree(c.dda); cudaFree(c.d_w); cudaFree(c.d_w2n); cudaFree(c.d_cell_start); cudaFree(c.d_cell_ions);
-    cudaFree(c.d_slot_of); cudaFree(c.d_cnt); cudaFree(c.d_cellid); cudaFree(c.d_fill); cudaFree(c.d_cell_pos);
-    c.dda = nullptr; c.d_w = nullptr; c.d_w2n = nullptr; c.d_cell_start = nullptr; c.d_cell_ions = nullptr;
-    c.d_slot_of = nullptr; c.d_cnt = nullptr; c.d_cellid = nullptr; c.d_fill = nullptr; c.d_cell_pos = nullptr;
-    c.da = false;
+    release_da(c);
     c.ncell = G * G * G;
     const size_t N = (size_t)c.N;
     CK(cudaMalloc(&c.dda, sizeof(mcg::DADev)));
@@ -1571,6 +1590,71 @@ static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, in
     return sync_descriptors(h);
 }
 
+// The overlap prefilter (see include/mc.h): the delayed-acceptance machinery with stage 1 reduced to the overlap test
+// against counted ions, over a bucket cell list of edge >= half of sigma + the largest trial + the largest move
+// of a candidate.
+int mc_set_overlap_prefilter(mc_handle h, int chain, int W)
+{
+    Range nv("mc_set_overlap_prefilter");
+    int rc = check_chain(h, chain);
+    if (rc) return rc;
+    if (W != 0 && W < 2) return fail(MC_ERR_INVALID, "exclusion depth W = %d: 0 (off) or at least 2", W);
+    CK(cudaStreamSynchronize(h->stream));
+    Chain &c = h->chains[chain];
+    if (W == 0) {
+        if (c.pf) release_da(c);
+        drop_graphs(h);
+        rc = sync_descriptors(h);
+        if (rc == MC_OK && check(h) == MC_OK) write_ctl(h);
+        return rc;
+    }
+    release_da(c);
+    const double D = (double)(float)(2.0 * c.h);
+    const double mv = std::sqrt(3.0) * 0.5 * D;  // largest move of one ion (one per sweep)
+    const double reach = (c.sigma + 2.0 * mv) * (1.0 + 0x1p-8) + 1e-6;
+    // cells of edge >= reach / 2 (the 5^3 stencil covers the reach), at most 256 per axis and 8 per ion
+    const int gmax = std::min(256, std::max(1, (int)std::cbrt(8.0 * (double)c.N)));
+    const int G = std::max(1, std::min(gmax, (int)std::floor(2.0 * c.R / (0.5 * reach))));
+    const double edge = 2.0 * c.R / (double)G;
+    // slots per cell: m^3 sub-cubes of diagonal below sigma (with slack for the FP32 cell index) hold at most one
+    // ion each of a non-overlapping configuration
+    const int m = std::max(1, (int)std::ceil((edge * (1.0 + 0x1p-8) + 1e-4) * std::sqrt(3.0) / (c.sigma * (1.0 - 0x1p-16))));
+    const int cap = std::min(64, m * m * m);
+    c.ncell = G * G * G;
+    const size_t slots = (size_t)c.ncell * (size_t)cap, N = (size_t)c.N;
+    CK(cudaMalloc(&c.dda, sizeof(mcg::DADev)));
+    CK(cudaMalloc(&c.d_cnt, sizeof(int) * (size_t)c.ncell));
+    CK(cudaMalloc(&c.d_cell_ions, sizeof(int) * slots));
+    CK(cudaMalloc(&c.d_cell_pos, sizeof(float4) * slots));
+    CK(cudaMalloc(&c.d_slot_of, sizeof(int) * N));
+    mcg::DADev d{};
+    d.cell_ions = c.d_cell_ions;
+    d.cell_pos = c.d_cell_pos;
+    d.slot_of = c.d_slot_of;
+    d.cell_cnt = c.d_cnt;
+    d.R = c.R;
+    d.nf_scale = (float)((double)G / (2.0 * c.R));
+    d.nf_R = (float)c.R;
+    d.nf_edge = (float)edge;
+    d.reach2 = (float)(reach * reach * (1.0 + 0x1p-10));
+    const double orr = (c.sigma + mv) * (1.0 + 0x1p-8) + 1e-6;
+    d.ovl_reach2 = (float)(orr * orr * (1.0 + 0x1p-10));
+    d.Rr = (float)c.R;
+    d.nf_G = G;
+    d.W = W;
+    d.mlp_zero = 1;
+    d.cap = cap;
+    d.prefilter = 1;
+    c.hda = d;
+    CK(cudaMemcpy(c.dda, &d, sizeof d, cudaMemcpyHostToDevice));
+    c.da = true;
+    c.pf = true;
+    drop_graphs(h);
+    rc = sync_descriptors(h);
+    if (rc == MC_OK && check(h) == MC_OK) write_ctl(h);
+    return rc;
+}
+
 int mc_da_samples(mc_handle h, int chain, float *v_pairs, float *y, uint8_t *valid)
 {
     Range nv("mc_da_samples");
@@ -1578,7 +1662,7 @@ int mc_da_samples(mc_handle h, int chain, float *v_pairs, float *y, uint8_t *val
     if (rc) return rc;
     if (!v_pairs || !y || !valid) return fail(MC_ERR_INVALID, "NULL output");
     Chain &c = h->chains[chain];
-    if (!c.dda) return fail(MC_ERR_INVALID, "chain %d has no surrogate set (mc_set_surrogate)", chain);
+    if (!c.dda || c.pf) return fail(MC_ERR_INVALID, "chain %d has no surrogate set (mc_set_surrogate)", chain);
     CK(cudaStreamSynchronize(h->stream));
     const size_t N = (size_t)c.N;
     float *dV = nullptr, *dY = nullptr;

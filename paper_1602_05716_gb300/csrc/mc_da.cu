@@ -71,6 +71,29 @@ __global__ void da_prep_scatter(const ChainDev *__restrict__ chp, int N, const i
     slot_of[j] = slot;
 }
 
+// Overlap prefilter: bucket layout of the sweep's start positions (cell q: slots q cap .. q cap + cap - 1, filled
+// in arrival order; the order never matters, the prefilter only asks whether some listed ion overlaps).  cnt must
+// be zero on entry; it ends with the number of ions of each cell, possibly above cap (those past it are unlisted).
+__global__ void da_prep_bucket(const ChainDev *__restrict__ chp, int N, const DADev *__restrict__ dp, int *cnt,
+                               int *cell_ions, float4 *cell_pos, int *slot_of)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const DADev &d = *dp;
+    const float4 x = start_positions(*chp)[j];
+    const int G = d.nf_G;
+    const int c = (da_ncell_axis(d, x.x) * G + da_ncell_axis(d, x.y)) * G + da_ncell_axis(d, x.z);
+    const int t = atomicAdd(&cnt[c], 1);
+    if (t < d.cap) {
+        const int slot = c * d.cap + t;
+        cell_ions[slot] = j;
+        cell_pos[slot] = x;
+        slot_of[j] = slot;
+    } else {
+        slot_of[j] = -1;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Surrogate MLP (33-64-64-1, SiLU, BF16 weights, FP32 arithmetic).
 
@@ -372,6 +395,15 @@ cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd
     mcg::da_prep_count<<<(N + 255) / 256, 256, 0, st>>>(chd, N, dd, cnt, cellid);
     mcg::da_prep_scan<<<1, 1024, 0, st>>>(cnt, ncell, start, fill);
     mcg::da_prep_scatter<<<(N + 255) / 256, 256, 0, st>>>(chd, N, cellid, fill, cell_ions, cell_pos, slot_of);
+    return cudaGetLastError();
+}
+
+cudaError_t da_prep_bucket_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt,
+                                  int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ncell, st)) != cudaSuccess) return e;
+    mcg::da_prep_bucket<<<(N + 255) / 256, 256, 0, st>>>(chd, N, dd, cnt, cell_ions, cell_pos, slot_of);
     return cudaGetLastError();
 }
 

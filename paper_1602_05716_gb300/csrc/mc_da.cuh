@@ -54,6 +54,13 @@ struct DADev {
     int nf_G;                      // near-field cells per axis
     int W;                         // exclusion depth in groups
     int mlp_zero;                  // every weight is +-0, so g = 0 exactly: the FP32 MLP pass is skipped
+    // overlap prefilter (mc_set_overlap_prefilter): no surrogate and no stage-1 Metropolis test, stage 1 only
+    // rejects trials that overlap a counted ion.  Bucket layout: cell q holds ions in slots q cap ..
+    // q cap + min(cell_cnt[q], cap) - 1; an ion that finds its cell full has slot_of -1 and is not listed.
+    const int *cell_cnt;
+    float ovl_reach2;              // (sigma + the largest move of a candidate since the sweep's start)^2, with slack
+    int cap;                       // slots per cell
+    int prefilter;                 // 1: the prefilter, 0: delayed acceptance
 };
 
 __device__ __forceinline__ int da_ncell_axis(const DADev &d, float x)
@@ -353,6 +360,47 @@ __device__ inline NearOut da_near_warp(const DADev &d, int g, int B, int Wg, int
     o.nt = nt;
     o.ovl = ovl;
     return o;
+}
+
+// Overlap prefilter: does the trial position a of ion i (old position x) overlap a counted ion?  Warp-collective
+// over the 5 x 5 x 5 cells around x's cell (edge >= half the reach, so they hold every ion that can lie within
+// sigma of a at any time of the sweep); each lane takes up to four cells and their listed ions.  An ion left out
+// of a full cell is only a missed rejection: the exact pass finds every overlap.  Returns the same value in every
+// lane: 1 when some counted ion certainly overlaps (FP32 squared distance below lo2, or the reference FP64 test
+// inside the band).
+__device__ inline int da_ovl_warp(const DADev &d, int g, int B, int Wg, int i, float4 x, float4 a, float lo2, float hi2,
+                                  double sig2)
+{
+    const int lane = threadIdx.x & 31;
+    const int G = d.nf_G;
+    const int cx = da_ncell_axis(d, x.x), cy = da_ncell_axis(d, x.y), cz = da_ncell_axis(d, x.z);
+    int ovl = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = lane + 32 * u;
+        if (c >= NF_ST) continue;
+        const int ax = cx + c / 25 - 2, ay = cy + (c / 5) % 5 - 2, az = cz + c % 5 - 2;
+        if (ax < 0 || ay < 0 || az < 0 || ax >= G || ay >= G || az >= G) continue;
+        const float bx = -d.nf_R + (float)ax * d.nf_edge, by = -d.nf_R + (float)ay * d.nf_edge,
+                    bz = -d.nf_R + (float)az * d.nf_edge;
+        const float ex = fmaxf(fmaxf(bx - a.x, a.x - (bx + d.nf_edge)), 0.f);
+        const float ey = fmaxf(fmaxf(by - a.y, a.y - (by + d.nf_edge)), 0.f);
+        const float ez = fmaxf(fmaxf(bz - a.z, a.z - (bz + d.nf_edge)), 0.f);
+        if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) > d.ovl_reach2) continue;
+        const int q = (ax * G + ay) * G + az;
+        const int n = min(__ldg(&d.cell_cnt[q]), d.cap);
+        for (int t = 0; t < n && !ovl; ++t) {
+            const int slot = q * d.cap + t;
+            const int j = __ldg(&d.cell_ions[slot]);
+            if (!da_counted(i, g, B, Wg, j)) continue;
+            const float4 y = __ldcg(&d.cell_pos[slot]);
+            const float dx = a.x - y.x, dy = a.y - y.y, dz = a.z - y.z;
+            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (d2 < lo2) ovl = 1;
+            else if (!(d2 > hi2) && d2_fp64(a.x, a.y, a.z, y.x, y.y, y.z) < sig2) ovl = 1;
+        }
+    }
+    return __any_sync(0xffffffffu, ovl) ? 1 : 0;
 }
 
 }  // namespace mcg

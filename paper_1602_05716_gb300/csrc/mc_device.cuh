@@ -84,7 +84,7 @@ struct ChainDev {
     double lB;                    // Bjerrum length
     double Rc2;                   // (R - sigma/2)^2
     unsigned key0, key1, ctr3;    // Philox key (seed_lo, chain_id), counter word 3 (seed_hi)
-    unsigned pad;
+    unsigned pf;                  // 1: da is an overlap prefilter (the plain chain's decisions), 0 otherwise
     const struct DADev *da;       // delayed-acceptance state, nullptr for the plain chain
 };
 

@@ -1098,6 +1098,61 @@ __device__ bool da_stage1(Smem &sm, const Ctx &c, Ctl *ctl, int mode, int &n_fp6
     return true;
 }
 
+// Stage 1 of the overlap prefilter (a chain without a surrogate whose DADev is a prefilter): the moves whose trial
+// overlaps a counted ion are rejected as overlaps (the reference chain rejects them too, whatever their energy
+// change), the others are listed as survivors and decided by the plain chain's rule on their exact dE: the
+// acceptance draw, threshold and band of step 1 are left as they are.
+__device__ bool prefilter_stage1(Smem &sm, const Ctx &c, Ctl *ctl)
+{
+    const ChainDev &ch = *c.ch;
+    const DADev &d = *ch.da;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nk = c.nk, Wg = min(d.W, c.B - 1);
+    if (tid == 0) {
+        const unsigned long long need = c.s * (unsigned long long)c.B + (unsigned long long)max(c.g - Wg, 0);
+        sm.ok = wait_ledger(ch, need, ctl) ? 1 : 0;
+        sm.namb = 0;
+    }
+    if (tid < WORDS) sm.d64w[tid] = 0u;
+    if (tid < S) {
+        sm.dEt32[tid] = __int_as_float(0x7fc00000);
+        sm.dEtB[tid] = 0.f;
+        sm.dEt64[tid] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    bar_main();
+    if (!sm.ok) return false;
+    const auto active = [&](int k) { return k < nk && !(sm.st[k] & (ST_INACTIVE | ST_WALL)); };
+    for (int k = warp; k < nk; k += T / 32) {  // warp per move
+        if (!active(k)) continue;
+        const int o = da_ovl_warp(d, c.g, c.B, Wg, c.k0 + k, sm.own[k], sm.trial[k], ch.sig2_lo, ch.sig2_hi, ch.sig2);
+        if (lane == 0 && o) {
+            sm.outcome[k] = (signed char)OUT_OVERLAP;
+            sm.tier[k] = 6;
+            sm.st[k] = (unsigned char)(sm.st[k] | ST_DA_DONE);
+        }
+    }
+    bar_main();
+    bool sv = false;
+    if (tid < S) {
+        sv = active(tid) && !(sm.st[tid] & ST_DA_DONE);
+        const unsigned bal = __ballot_sync(FULL, sv);
+        if (lane == 0) sm.redf[warp] = __int_as_float(__popc(bal));
+    }
+    bar_main();
+    if (tid < S) {
+        const int k = tid, w = k >> 5;
+        int before = 0;
+        for (int q = 0; q < w; ++q) before += __float_as_int(sm.redf[q]);
+        const unsigned bal = __ballot_sync(FULL, sv);
+        const int n = before + __popc(bal & ((1u << lane) - 1u));
+        if (sv) sm.surv[n] = (unsigned char)k;
+        sm.slot[k] = sv ? (unsigned char)n : (unsigned char)255;
+        if (k == S - 1) sm.ns = before + __popc(bal);
+    }
+    bar_main();
+    return true;
+}
+
 // One work item: the S moves of group g of chain `tk.chain` at sweep s.
 // role 0: the whole work item (the cluster's leader in pairs mode: even tiles); role 1: the pairs-mode helper,
 // which sums the odd tiles for the leader and decides nothing.
@@ -1409,7 +1464,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     long long da_part[4] = {0, 0, 0, 0};
     const long long cyc_da0 = clock64();
     if (ch.da) {
-        if (!da_stage1(sm, c, ctl, mode, n_dfp64, da_part)) return false;
+        if (!(ch.pf ? prefilter_stage1(sm, c, ctl) : da_stage1(sm, c, ctl, mode, n_dfp64, da_part))) return false;
     } else {
         if (tid < S) {
             sm.surv[tid] = (unsigned char)tid;
@@ -1916,7 +1971,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             float bnd = (mode == 1 || mode == 3 || kT < 0.f)
                             ? finf()
                             : (mode == 2 ? 0.f : lqa * (U32 * (sm.Qs[k] * infl) + 0x1p-40f * ch.a_max));
-            if (ch.da && mode == 0) bnd += sm.dEtB[k];  // stage 2 compares dE with L(u2) + dEt
+            if (ch.da && !ch.pf && mode == 0) bnd += sm.dEtB[k];  // stage 2 compares dE with L(u2) + dEt
             sm.bnd[k] = bnd;
         }
         if (trc) gt_ph[1] = globaltimer();
@@ -2105,7 +2160,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             const int k = first;
             const unsigned stv = sm.st[k];
             // the acceptance draw of this decision: purpose 0, or purpose 1 for delayed acceptance's stage 2
-            const bool isda = ch.da != nullptr;
+            const bool isda = ch.da != nullptr && !ch.pf;
             const unsigned ua =
                 move_draws(ch, s * (unsigned long long)N + (unsigned long long)(k0 + k), isda ? 1u : 0u).w >> 8;
             const double L64 = (ua == 0u) ? 0.0 : -series_log((double)ua * 0x1p-24);
@@ -2203,9 +2258,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         const bool acc = bit(sm.accw, tid);
         __stcg(&ch.pos[(s + 1) & 1][k0 + tid], acc ? sm.trial[tid] : sm.own[tid]);
         if (ch.da && acc && publish) {
-            // delayed acceptance: the near-field cell list holds current positions
+            // delayed acceptance and the prefilter: the near-field cell list holds current positions (an ion
+            // left out of a full prefilter cell has no slot)
             const DADev &dd = *ch.da;
-            __stcg(&dd.cell_pos[__ldg(&dd.slot_of[k0 + tid])], sm.trial[tid]);
+            const int sl = __ldg(&dd.slot_of[k0 + tid]);
+            if (sl >= 0) __stcg(&dd.cell_pos[sl], sm.trial[tid]);
         }
     }
     bar_main();
