@@ -459,8 +459,9 @@ int mc_mlp_train(const float *v_pairs, const float *y, int64_t n, const uint16_t
  * device memory belongs to a pool they may not bypass).
  * pos_q_dev: device array of n float4 (x, y, z, valence), 16-byte aligned;
  * energy_dev: device double receiving the result; stream: a cudaStream_t as
- * void* (NULL = the default stream).  Same kernels and arithmetic as the
- * recomputed energy of mc_energy (FP32 pair terms, FP64 row sums).
+ * void* (NULL = the default stream).  FP32 pair terms with FP64 row sums
+ * (about 1e-7 of sum |q_i q_j| / r_ij; mc_energy's recomputed value uses
+ * float-float terms and is about a million times closer).
  * The row sums live in one fixed device array of 1,048,576 doubles (8 MiB)
  * that the library's module carries on every GPU that loads it, until the
  * process exits; n > 1,048,576 returns MC_ERR_INVALID.  The first call on a
