@@ -76,7 +76,8 @@ def _compare_records(gr, orc, N, lB_q_tol=1e-6):
 
 @pytest.mark.parametrize("n,two_one,phi,sweeps", [(2, False, 0.05, 30), (3, True, 0.05, 30), (33, False, 0.1, 20),
                                                   (128, False, 0.15, 10), (129, True, 0.15, 10),
-                                                  (257, False, 0.2, 8), (300, True, 0.25, 6), (700, False, 0.2, 3)])
+                                                  (208, True, 0.2, 6), (257, False, 0.2, 8), (300, True, 0.25, 6),
+                                                  (700, False, 0.2, 3)])
 def test_trajectory_bit_identical_small(pkg, n, two_one, phi, sweeps):
     """Several tiles and a ragged tail: decisions, positions and counters identical to the oracle."""
     ch = inputs.small_chain(n, phi=phi, seed=100 + n, two_one=two_one, half_width=0.4)
