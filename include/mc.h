@@ -343,7 +343,14 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
  *                      budget, while the first 256 run the work items as
  *                      before.  The trajectory is identical either way;
  *                      reading it returns whether the form is in effect.
- *                      The autotuner tries it. */
+ *                      The autotuner tries it.
+ *  MC_OPT_DA_SWEEPS    sweeps per launch of chains with a surrogate or the
+ *                      overlap prefilter (1 by default, at most 64): the cell
+ *                      list is rebuilt at the start of each launch, so its
+ *                      cells are sized for this many moves of every ion.
+ *                      Set it before mc_set_surrogate / mc_set_overlap_prefilter
+ *                      (MC_ERR_INVALID while a chain holds a cell list built
+ *                      for another value).  The trajectory is unchanged. */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3
@@ -355,6 +362,7 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
 #define MC_OPT_DEEP_WINDOWS 9
 #define MC_OPT_DRIFT_EVERY 10
 #define MC_OPT_HELPERS 11
+#define MC_OPT_DA_SWEEPS 12
 int mc_set_option(mc_handle h, int option, int64_t value);
 int mc_get_option(mc_handle h, int option, int64_t *value);
 

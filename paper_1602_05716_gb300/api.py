@@ -13,6 +13,7 @@ OPT_GUARD_MODE, OPT_TIMEOUT_MS, OPT_CTAS, OPT_SKIP_PUBLISH, OPT_USE_GRAPH, OPT_P
 OPT_DEEP_WINDOWS = 9
 OPT_DRIFT_EVERY = 10
 OPT_HELPERS = 11
+OPT_DA_SWEEPS = 12
 MLP_NIN, MLP_H = 33, 64
 MLP_NP = MLP_H * MLP_NIN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1  # layout W1, b1, W2, b2, W3, b3
 

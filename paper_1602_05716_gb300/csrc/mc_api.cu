@@ -131,6 +131,7 @@ struct Chain {
     // delayed acceptance (mc_set_surrogate)
     bool da = false;
     bool pf = false;              // the DA state is an overlap prefilter (mc_set_overlap_prefilter)
+    int da_k = 1;                 // sweeps per launch its cell list was sized for
     mcg::DADev hda{};             // host copy of the device descriptor
     mcg::DADev *dda = nullptr;    // device descriptor
     unsigned short *d_w = nullptr;
@@ -178,6 +179,7 @@ struct mc_system {
     int deep_opt = 1;                   // MC_OPT_DEEP_WINDOWS: 1 on (default), 0 off
     long long drift_every = 0;          // MC_OPT_DRIFT_EVERY: accurate energy and drift check every K sweeps (0 off)
     int helpers_opt = 0;                // MC_OPT_HELPERS: 0 off (default), 1 on
+    int da_sweeps = 1;                  // MC_OPT_DA_SWEEPS: sweeps per launch of chains with a cell list
     int occ_h = 0;                      // resident CTAs per SM of the helper-warp kernel (0: unavailable)
     int max_clusters = 0;               // resident clusters of two CTAs (0: pairs mode unavailable)
     mcg::PairBox *d_box = nullptr;      // one hand-over box per cluster
@@ -554,14 +556,20 @@ cudaError_t enqueue_drift(mc_system *h)
     return e;
 }
 
-// Delayed acceptance: one sweep per launch, each preceded by the preparation of every surrogate chain
-// (near-field cell list and feature grid of the sweep's start positions).  The control block is copied
-// once; later launches only reset its ticket counter, so an error or abort stays visible.
-cudaError_t enqueue_da(mc_system *h, long long n, int grid, const mcg::Ticket *sched, int count)
+// Chains with a cell list (delayed acceptance, the overlap prefilter): launches of at most MC_OPT_DA_SWEEPS sweeps,
+// each preceded by the preparation of every such chain's cell list from the launch's start positions, and cut at
+// the drift check's period.  The control block is copied once; later launches only reset its ticket counter, so an
+// error or abort stays visible.
+cudaError_t enqueue_da(mc_system *h, long long n, int grid)
 {
     cudaError_t e = cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(mcg::Ctl), cudaMemcpyHostToDevice, h->stream);
-    for (long long t = 0; t < n && e == cudaSuccess; ++t) {
-        if (t > 0) e = cudaMemsetAsync(&h->d_ctl->ticket, 0, sizeof(unsigned), h->stream);
+    for (long long done = 0; done < n && e == cudaSuccess;) {
+        long long m = std::min<long long>(h->da_sweeps, n - done);
+        if (h->drift_every > 0) m = std::min(m, h->drift_every - done % h->drift_every);
+        mcg::Ticket *sched = nullptr;
+        int count = 0;
+        if (schedule_for(h, m, &sched, &count) != MC_OK) return cudaErrorInvalidValue;
+        if (done > 0) e = cudaMemsetAsync(&h->d_ctl->ticket, 0, sizeof(unsigned), h->stream);
         for (size_t ci = 0; ci < h->chains.size(); ++ci) {
             Chain &c = h->chains[ci];
             if (!c.da || e != cudaSuccess) continue;
@@ -572,9 +580,10 @@ cudaError_t enqueue_da(mc_system *h, long long n, int grid, const mcg::Ticket *s
                                                 h->stream);
         }
         if (e == cudaSuccess)
-            e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), 1, h->stream,
+            e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), m, h->stream,
                                        false, helpers_on(h));
-        if (e == cudaSuccess && h->drift_every > 0 && (t + 1) % h->drift_every == 0) e = enqueue_drift(h);
+        done += m;
+        if (e == cudaSuccess && h->drift_every > 0 && done % h->drift_every == 0) e = enqueue_drift(h);
     }
     return e;
 }
@@ -605,9 +614,27 @@ int enqueue_sweeps(mc_system *h, long long n)
     mcg::Ticket *sched = nullptr;
     int count = 0;
     const bool da = any_da(h);
-    const long long per = da ? 1 : (h->drift_every > 0 ? std::min<long long>(n, h->drift_every) : n);
+    const long long per = da ? std::min<long long>(n, h->da_sweeps)
+                             : (h->drift_every > 0 ? std::min<long long>(n, h->drift_every) : n);
     int rc = schedule_for(h, per, &sched, &count);
     if (rc) return rc;
+    if (da) {  // every launch length enqueue_da will use, before any capture (schedules are allocated once)
+        long long seen[4] = {per, 0, 0, 0};
+        int ns = 1;
+        for (long long done = 0; done < n;) {
+            long long m = std::min<long long>(h->da_sweeps, n - done);
+            if (h->drift_every > 0) m = std::min(m, h->drift_every - done % h->drift_every);
+            bool have = false;
+            for (int q = 0; q < ns; ++q) have |= seen[q] == m;
+            if (!have) {
+                mcg::Ticket *s2 = nullptr;
+                int c2 = 0;
+                if ((rc = schedule_for(h, m, &s2, &c2))) return rc;
+                if (ns < 4) seen[ns++] = m;
+            }
+            done += m;
+        }
+    }
     if (!da && h->drift_every > 0 && n > h->drift_every) {  // the schedule of the last, shorter launch
         mcg::Ticket *s2 = nullptr;
         int c2 = 0;
@@ -625,7 +652,7 @@ int enqueue_sweeps(mc_system *h, long long n)
             CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
             if (da) {
-                e2 = enqueue_da(h, n, grid, sched, count);
+                e2 = enqueue_da(h, n, grid);
             } else {
                 e2 = enqueue_plain(h, n, grid, pr);
             }
@@ -643,7 +670,7 @@ int enqueue_sweeps(mc_system *h, long long n)
         }
         CK(cudaGraphLaunch(it->second, h->stream));
     } else if (da) {
-        CK(enqueue_da(h, n, grid, sched, count));
+        CK(enqueue_da(h, n, grid));
     } else {
         CK(enqueue_plain(h, n, grid, pr));
     }
@@ -1323,6 +1350,15 @@ static int set_option(mc_handle h, int option, int64_t value)
         if (value < 0) return fail(MC_ERR_INVALID, "drift check period %lld", (long long)value);
         h->drift_every = value;
         return MC_OK;
+    case MC_OPT_DA_SWEEPS:
+        if (value < 1 || value > 64) return fail(MC_ERR_INVALID, "sweeps per launch %lld", (long long)value);
+        for (auto &c : h->chains)
+            if (c.dda && c.da_k != value)
+                return fail(MC_ERR_INVALID, "a chain's cell list is sized for %d sweeps per launch: set the option "
+                                            "before mc_set_surrogate / mc_set_overlap_prefilter", c.da_k);
+        h->da_sweeps = (int)value;
+        drop_graphs(h);
+        return MC_OK;
     case MC_OPT_HELPERS:
         if (value < 0 || value > 1) return fail(MC_ERR_INVALID, "helpers %lld", (long long)value);
         if (value == 1 && h->occ_h < 1) return fail(MC_ERR_INVALID, "the helper-warp kernel does not fit an SM");
@@ -1361,6 +1397,7 @@ int mc_get_option(mc_handle h, int option, int64_t *value)
     case MC_OPT_DEEP_WINDOWS: *value = h->deep_opt; return MC_OK;
     case MC_OPT_DRIFT_EVERY: *value = h->drift_every; return MC_OK;
     case MC_OPT_HELPERS: *value = helpers_on(h) ? 1 : 0; return MC_OK;
+    case MC_OPT_DA_SWEEPS: *value = h->da_sweeps; return MC_OK;
     default: return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
 }
@@ -1526,10 +1563,10 @@ static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, in
         if (!std::isfinite(wf[k])) return fail(MC_ERR_INVALID, "weight %d is not finite", k);
     }
     // near-field reach: r_c plus the largest trial displacement plus the largest move of a candidate since the
-    // sweep's start (one per sweep); cells of edge >= reach / 2, so the cells within two of an ion's start cell
-    // hold every ion within r_c of its old or trial position at any time of the sweep
+    // launch's start (one per sweep, MC_OPT_DA_SWEEPS sweeps); cells of edge >= reach / 2, so the cells within two
+    // of an ion's start cell hold every ion within r_c of its old or trial position at any time of the launch
     const double D = (double)(float)(2.0 * c.h);
-    const double reach = (r_c + 2.0 * std::sqrt(3.0) * 0.5 * D) * (1.0 + 0x1p-8) + 1e-6;
+    const double reach = (r_c + (1.0 + h->da_sweeps) * std::sqrt(3.0) * 0.5 * D) * (1.0 + 0x1p-8) + 1e-6;
     const int G = std::max(1, std::min(64, (int)std::floor(2.0 * c.R / (0.5 * reach))));
     // (re)allocate
     release_da(c);
@@ -1586,6 +1623,7 @@ static int set_surrogate_impl(mc_handle h, int chain, const uint16_t *w_bf16, in
     c.hda = d;
     CK(cudaMemcpy(c.dda, &d, sizeof d, cudaMemcpyHostToDevice));
     c.da = true;
+    c.da_k = h->da_sweeps;
     drop_graphs(h);
     return sync_descriptors(h);
 }
@@ -1611,7 +1649,8 @@ int mc_set_overlap_prefilter(mc_handle h, int chain, int W)
     release_da(c);
     const double D = (double)(float)(2.0 * c.h);
     const double mv = std::sqrt(3.0) * 0.5 * D;  // largest move of one ion (one per sweep)
-    const double reach = (c.sigma + 2.0 * mv) * (1.0 + 0x1p-8) + 1e-6;
+    const int K = h->da_sweeps;                   // sweeps per launch (one cell list per launch)
+    const double reach = (c.sigma + (1.0 + K) * mv) * (1.0 + 0x1p-8) + 1e-6;
     // cells of edge >= reach / 2 (the 5^3 stencil covers the reach), at most 256 per axis and 8 per ion
     const int gmax = std::min(256, std::max(1, (int)std::cbrt(8.0 * (double)c.N)));
     const int G = std::max(1, std::min(gmax, (int)std::floor(2.0 * c.R / (0.5 * reach))));
@@ -1637,7 +1676,7 @@ int mc_set_overlap_prefilter(mc_handle h, int chain, int W)
     d.nf_R = (float)c.R;
     d.nf_edge = (float)edge;
     d.reach2 = (float)(reach * reach * (1.0 + 0x1p-10));
-    const double orr = (c.sigma + mv) * (1.0 + 0x1p-8) + 1e-6;
+    const double orr = (c.sigma + K * mv) * (1.0 + 0x1p-8) + 1e-6;
     d.ovl_reach2 = (float)(orr * orr * (1.0 + 0x1p-10));
     d.Rr = (float)c.R;
     d.nf_G = G;
@@ -1649,6 +1688,7 @@ int mc_set_overlap_prefilter(mc_handle h, int chain, int W)
     CK(cudaMemcpy(c.dda, &d, sizeof d, cudaMemcpyHostToDevice));
     c.da = true;
     c.pf = true;
+    c.da_k = K;
     drop_graphs(h);
     rc = sync_descriptors(h);
     if (rc == MC_OK && check(h) == MC_OK) write_ctl(h);

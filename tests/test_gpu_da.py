@@ -70,10 +70,11 @@ def test_mlp_gradient_matches_oracle(pkg):
     assert err.max() <= 2e-4 * scale, (err.max(), scale, int(err.argmax()))
 
 
-def _da_pair(ch, w, W, r_c=4.0, ctas=3):
+def _da_pair(ch, w, W, r_c=4.0, ctas=3, per_launch=1):
     import paper_1602_05716_gb300 as p
     g = p.System([ch])
     g.set_option(p.OPT_CTAS, ctas)
+    g.set_option(p.OPT_DA_SWEEPS, per_launch)
     g.set_surrogate(w, r_c=r_c, W=W)
     o = oracle.OracleChain.from_chain(ch, threads=THREADS)
     o.set_surrogate(w, r_c=r_c, W=W)
@@ -153,6 +154,29 @@ def test_da_trajectory_bit_identical(pkg, n, W, two_one, seed):
     assert sd["rej1"] > 0 and sd["rej2"] + sg["accepts"] > 0
     led_g, rec_g = g.energy()
     assert abs(led_g - rec_g) < 1e-5 * max(1.0, abs(rec_g))
+
+
+@pytest.mark.parametrize("per_launch", [2, 3])
+def test_da_several_sweeps_per_launch(pkg, per_launch):
+    """Several delayed-acceptance sweeps in one launch (one cell list for the launch, cells sized for that many
+    moves): the same trajectory as the oracle's, sweep after sweep; the option cannot change under a built list."""
+    ch = inputs.small_chain(1500, phi=0.25, seed=44, two_one=True, half_width=0.35)
+    w = _random_bf16(44, scale=1.0, radial=2.0)
+    g, o = _da_pair(ch, w, 3, ctas=2, per_launch=per_launch)
+    sweeps = 2 * per_launch + 1
+    g.record_enable(sweeps * ch.n)
+    o.da_record(sweeps * ch.n)
+    g.sweep(sweeps)  # launches of per_launch sweeps and a shorter last one
+    o.da_sweep(sweeps)
+    assert (g.positions() == o.positions()).all()
+    gr, orc = g.records(), o.da_records()
+    assert (gr["outcome"] == orc["outcome"]).all(), np.nonzero(gr["outcome"] != orc["outcome"])[0][:10]
+    sg, so = g.stats(), o.stats()
+    assert sg["accepts"] == so["accept"] and sg["rej_overlap"] == so["rej_overlap"]
+    import paper_1602_05716_gb300 as p
+    with pytest.raises(p.MCError):
+        g.set_option(p.OPT_DA_SWEEPS, per_launch + 1)
+    g.close()
 
 
 def test_da_guard_mode_fp64_identical(pkg):

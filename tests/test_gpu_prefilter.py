@@ -59,6 +59,23 @@ def test_prefilter_trajectory_bit_identical(pkg, n, two_one, phi, sweeps, W):
     g.close()
 
 
+def test_prefilter_several_sweeps_per_launch(pkg):
+    """Four prefilter sweeps per launch (cells sized for four moves of every ion): the oracle's trajectory."""
+    ch = inputs.small_chain(2000, phi=0.25, seed=901, two_one=True, half_width=0.3)
+    g = pkg.System([ch])
+    g.set_option(pkg.OPT_DA_SWEEPS, 4)
+    g.set_overlap_prefilter(4)
+    o = oracle.OracleChain.from_chain(ch, threads=THREADS)
+    g.record_enable(9 * ch.n)
+    o.record(9 * ch.n)
+    g.sweep(9)
+    o.sweep(9)
+    assert (g.positions() == o.positions()).all()
+    _compare_records(g.records(), o.records(), ch.n)
+    assert g.stats()["da_ovl1"] > 0
+    g.close()
+
+
 def test_prefilter_batch_and_removal(pkg):
     """A batch with the prefilter on one chain equals the chains run alone; W = 0 restores the plain launches with
     the same trajectory; mc_set_surrogate replaces the prefilter; the training-sample call refuses it."""
