@@ -160,8 +160,13 @@ int mc_energy(mc_handle h, int chain, double *ledger, double *recomputed);
  * centres, so counts are exact integers.                                     */
 int mc_gr_histogram(mc_handle h, int chain, int n_bins, double r_max, double wall_margin, uint64_t *counts);
 
-/* Copy chain positions to / from a caller buffer of n*3 floats.  Setting
- * validates like mc_create (MC_ERR_OVERLAP_INIT).                           */
+/* Copy chain positions to / from a caller buffer of n*3 floats (pinned host
+ * memory makes the copies direct).  Setting validates like mc_create
+ * (MC_ERR_OVERLAP_INIT), with the same FP64 rule applied on the device (the
+ * wall, and every pair closer than sigma found through a grid of cells of
+ * edge >= sigma); on failure the chain keeps its positions.  The ledger is
+ * kept as it is.  The first call allocates the chain's staging and grid
+ * (12 n bytes, and up to 4 n cells of a few slots each).                    */
 int mc_get_positions(mc_handle h, int chain, float *pos_xyz);
 int mc_set_positions(mc_handle h, int chain, const float *pos_xyz);
 

@@ -37,6 +37,10 @@ cudaError_t philox_test_launch(const uint4 *ctr, const uint2 *key, int n, uint4 
                                cudaStream_t st);
 cudaError_t log_test_launch(const double *u, int n, double *out, cudaStream_t st);
 cudaError_t unit_rates(int sms, double *out);
+cudaError_t pos_check_launch(const float *xyz, int N, double Rc, double edge, int m, int cap, double s2, int *cnt,
+                             int *ids, unsigned long long *err, cudaStream_t st);
+cudaError_t pos_pack_launch(const float *xyz, int N, float4 *dst, cudaStream_t st);
+cudaError_t pos_unpack_launch(const float4 *src, int N, float *xyz, cudaStream_t st);
 cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt, int *cellid,
                            int *start, int *fill, int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st);
 cudaError_t da_prep_bucket_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt,
@@ -139,6 +143,11 @@ struct Chain {
     int *d_cell_start = nullptr, *d_cell_ions = nullptr, *d_slot_of = nullptr, *d_cnt = nullptr, *d_cellid = nullptr;
     int *d_fill = nullptr;
     float4 *d_cell_pos = nullptr;
+    // mc_set_positions / mc_get_positions on the device: xyz staging (3N floats), the check's bucket grid, its key
+    float *d_xyz = nullptr;
+    int *d_vcnt = nullptr, *d_vids = nullptr;
+    unsigned long long *d_verr = nullptr;
+    int vm = 0, vcap = 0;
     int ncell = 0;
 };
 
@@ -363,6 +372,10 @@ void free_chain(Chain &c)
 {
     cudaFree(c.pos[0]);
     cudaFree(c.pos[1]);
+    cudaFree(c.d_xyz);
+    cudaFree(c.d_vcnt);
+    cudaFree(c.d_vids);
+    cudaFree(c.d_verr);
     cudaFree(c.flags);
     cudaFree(c.bits);
     cudaFree(c.slab);
@@ -831,6 +844,26 @@ int mc_gr_histogram(mc_handle h, int chain, int n_bins, double r_max, double wal
     return MC_OK;
 }
 
+// Device staging of host positions and the grid of their check (allocated on first use, kept with the chain).
+static int ensure_pos_scratch(Chain &c)
+{
+    if (c.d_xyz) return MC_OK;
+    const double Rc = c.R - 0.5 * c.sigma;
+    // cells of edge >= sigma, at most 4 per ion and 600 per axis; cap = k^3 sub-cubes of diagonal below sigma
+    long long m = (long long)std::floor(2.0 * Rc / c.sigma);
+    m = std::min(m, std::min(600LL, (long long)std::cbrt(4.0 * (double)c.N) + 1));
+    m = std::max(1LL, m);
+    const double edge = 2.0 * Rc / (double)m;
+    const int k = (int)std::floor(edge * std::sqrt(3.0) / c.sigma * (1.0 + 1e-9)) + 1;
+    c.vm = (int)m;
+    c.vcap = std::min(1000, k * k * k);
+    CK(cudaMalloc(&c.d_xyz, sizeof(float) * 3 * (size_t)c.N));
+    CK(cudaMalloc(&c.d_vcnt, sizeof(int) * (size_t)(m * m * m)));
+    CK(cudaMalloc(&c.d_vids, sizeof(int) * (size_t)(m * m * m) * (size_t)c.vcap));
+    CK(cudaMalloc(&c.d_verr, sizeof(unsigned long long)));
+    return MC_OK;
+}
+
 int mc_get_positions(mc_handle h, int chain, float *pos_xyz)
 {
     Range nv("mc_get_positions");
@@ -838,17 +871,15 @@ int mc_get_positions(mc_handle h, int chain, float *pos_xyz)
     if (rc) return rc;
     if (!pos_xyz) return fail(MC_ERR_INVALID, "NULL buffer");
     Chain &c = h->chains[chain];
-    std::vector<float4> buf((size_t)c.N);
+    if ((rc = ensure_pos_scratch(c))) return rc;
+    CK(mcg_host::pos_unpack_launch(c.cur(), c.N, c.d_xyz, h->stream));
+    CK(cudaMemcpyAsync(pos_xyz, c.d_xyz, sizeof(float) * 3 * (size_t)c.N, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    CK(cudaMemcpy(buf.data(), c.cur(), sizeof(float4) * buf.size(), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < c.N; ++i) {
-        pos_xyz[3 * i] = buf[i].x;
-        pos_xyz[3 * i + 1] = buf[i].y;
-        pos_xyz[3 * i + 2] = buf[i].z;
-    }
     return MC_OK;
 }
 
+// The positions are copied to the device, checked there by the validation rule (FP64, every pair within sigma
+// through a bucket grid) and packed into the current buffer only if they pass; the valences stay.
 int mc_set_positions(mc_handle h, int chain, const float *pos_xyz)
 {
     Range nv("mc_set_positions");
@@ -856,11 +887,25 @@ int mc_set_positions(mc_handle h, int chain, const float *pos_xyz)
     if (rc) return rc;
     if (!pos_xyz) return fail(MC_ERR_INVALID, "NULL buffer");
     Chain &c = h->chains[chain];
-    rc = validate(pos_xyz, c.N, c.sigma, c.R);
-    if (rc) return rc;
+    if ((rc = ensure_pos_scratch(c))) return rc;
+    const double Rc = c.R - 0.5 * c.sigma;
+    CK(cudaMemcpyAsync(c.d_xyz, pos_xyz, sizeof(float) * 3 * (size_t)c.N, cudaMemcpyHostToDevice, h->stream));
+    CK(mcg_host::pos_check_launch(c.d_xyz, c.N, Rc, 2.0 * Rc / (double)c.vm, c.vm, c.vcap, c.sigma * c.sigma,
+                                  c.d_vcnt, c.d_vids, c.d_verr, h->stream));
+    unsigned long long key = 0;
+    CK(cudaMemcpyAsync(&key, c.d_verr, sizeof key, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    rc = upload_positions(h, c, pos_xyz, h->stream);
-    if (rc) return rc;
+    if (key != ~0ull) {
+        const unsigned kind = (unsigned)(key >> 62);
+        if (kind == 1) return fail(MC_ERR_OVERLAP_INIT, "ion %lld lies outside the wall", (long long)(key & 0x7fffffffull));
+        if (kind == 2)
+            return fail(MC_ERR_OVERLAP_INIT, "ions %lld and %lld overlap", (long long)(key & 0x7fffffffull),
+                        (long long)((key >> 31) & 0x7fffffffull));
+        return fail(MC_ERR_OVERLAP_INIT, "ions overlap (more than %d in a cell of edge %.6g)", c.vcap, 2.0 * Rc / c.vm);
+    }
+    CK(mcg_host::pos_pack_launch(c.d_xyz, c.N, c.cur(), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    c.sweep_base = c.sweeps;
     return sync_descriptors(h);
 }
 

@@ -337,9 +337,107 @@ __global__ void log_test(const double *__restrict__ u, int n, double *__restrict
     if (t < n) out[t] = series_log(u[t]);
 }
 
+// ---------------------------------------------------------------------------
+// Positions from the host (mc_set_positions) checked and packed on the device.  The checks are the library's
+// validation rule in FP64, operation for operation (no contraction): |r|^2 = (x^2 + y^2) + z^2 <= Rc^2 for the wall,
+// d^2 = (dx^2 + dy^2) + dz^2 >= sigma^2 for every pair.  Pairs are found through a bucket grid of m^3 cells of edge
+// >= sigma (the 27 cells around an ion's cell hold every ion closer than sigma); a cell holds at most cap ions,
+// cap = k^3 for sub-cubes of diagonal below sigma, so a full cell proves an overlap by itself.  err is a 64-bit
+// key: all ones for none, (1 << 62) | i for ion i outside the wall, (2 << 62) | (i << 31) | j for the pair (j < i), the
+// smallest key found; (3 << 62) for a full cell.
+
+__device__ __forceinline__ long long vcell(double v, double Rc, double edge, long long m)
+{
+    long long c = (long long)floor(__ddiv_rn(__dadd_rn(v, Rc), edge));
+    return c < 0 ? 0 : (c >= m ? m - 1 : c);
+}
+
+__global__ void pos_bin(const float *__restrict__ xyz, int N, double Rc, double edge, int m, int cap, int *cnt,
+                        int *ids, unsigned long long *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+    if (!(r2 <= __dmul_rn(Rc, Rc))) atomicMin(err, (1ull << 62) | (unsigned long long)i);
+    const long long c = (vcell(x, Rc, edge, m) * m + vcell(y, Rc, edge, m)) * m + vcell(z, Rc, edge, m);
+    const int t = atomicAdd(&cnt[c], 1);
+    if (t < cap) ids[c * cap + t] = i;
+    else atomicMin(err, 3ull << 62);
+}
+
+__global__ void pos_pairs(const float *__restrict__ xyz, int N, double Rc, double edge, int m, int cap, double s2,
+                          const int *__restrict__ cnt, const int *__restrict__ ids, unsigned long long *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    const long long cx = vcell(x, Rc, edge, m), cy = vcell(y, Rc, edge, m), cz = vcell(z, Rc, edge, m);
+    for (long long ax = cx - 1; ax <= cx + 1; ++ax)
+        for (long long ay = cy - 1; ay <= cy + 1; ++ay)
+            for (long long az = cz - 1; az <= cz + 1; ++az) {
+                if (ax < 0 || ay < 0 || az < 0 || ax >= m || ay >= m || az >= m) continue;
+                const long long c = (ax * m + ay) * m + az;
+                const int n = min(cnt[c], cap);
+                for (int t = 0; t < n; ++t) {
+                    const int j = ids[c * cap + t];
+                    if (j >= i) continue;  // each pair once, from its larger index
+                    const double dx = __dsub_rn((double)xyz[3 * i], (double)xyz[3 * j]);
+                    const double dy = __dsub_rn((double)xyz[3 * i + 1], (double)xyz[3 * j + 1]);
+                    const double dz = __dsub_rn((double)xyz[3 * i + 2], (double)xyz[3 * j + 2]);
+                    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                    if (d2 < s2) atomicMin(err, (2ull << 62) | ((unsigned long long)i << 31) | (unsigned long long)j);
+                }
+            }
+}
+
+// Packed positions: (x, y, z) from xyz and the valence kept in the fourth word of dst.
+__global__ void pos_pack(const float *__restrict__ xyz, int N, float4 *dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) dst[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], dst[i].w);
+}
+
+__global__ void pos_unpack(const float4 *__restrict__ src, int N, float *xyz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 v = src[i];
+    xyz[3 * i] = v.x;
+    xyz[3 * i + 1] = v.y;
+    xyz[3 * i + 2] = v.z;
+}
+
 }  // namespace mcg
 
 namespace mcg_host {
+
+// The device-side check of N host positions already copied to xyz (see pos_bin); err receives the key.
+cudaError_t pos_check_launch(const float *xyz, int N, double Rc, double edge, int m, int cap, double s2, int *cnt,
+                             int *ids, unsigned long long *err, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)m * m * m, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0xff, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || N <= 0) return e;
+    const int nb = (N + 255) / 256;
+    mcg::pos_bin<<<nb, 256, 0, st>>>(xyz, N, Rc, edge, m, cap, cnt, ids, err);
+    mcg::pos_pairs<<<nb, 256, 0, st>>>(xyz, N, Rc, edge, m, cap, s2, cnt, ids, err);
+    return cudaGetLastError();
+}
+
+cudaError_t pos_pack_launch(const float *xyz, int N, float4 *dst, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    mcg::pos_pack<<<(N + 255) / 256, 256, 0, st>>>(xyz, N, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t pos_unpack_launch(const float4 *src, int N, float *xyz, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    mcg::pos_unpack<<<(N + 255) / 256, 256, 0, st>>>(src, N, xyz);
+    return cudaGetLastError();
+}
 
 cudaError_t energy_launch(const float4 *pos, int N, double lB, double *rows, double *out, cudaStream_t st)
 {
