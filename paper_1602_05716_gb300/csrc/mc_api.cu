@@ -25,7 +25,7 @@ size_t sweep_smem_bytes();
 cudaError_t sweep_configure();
 cudaError_t sweep_occupancy(int *blocks_per_sm);
 cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticket *sched, int n_tickets, mcg::Ctl *ctl,
-                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs, bool help);
+                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs, bool help, bool da);
 cudaError_t sweep_occupancy_h(int *blocks_per_sm);
 cudaError_t sweep_max_clusters(int *n);
 int energy_ff_parts(int N);
@@ -594,7 +594,7 @@ cudaError_t enqueue_da(mc_system *h, long long n, int grid)
         }
         if (e == cudaSuccess)
             e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, (int)h->chains.size(), m, h->stream,
-                                       false, helpers_on(h));
+                                       false, helpers_on(h), true);
         done += m;
         if (e == cudaSuccess && h->drift_every > 0 && done % h->drift_every == 0) e = enqueue_drift(h);
     }
@@ -615,7 +615,8 @@ cudaError_t enqueue_plain(mc_system *h, long long n, int grid, bool pr)
         if (schedule_for(h, m, &sched, &count) != MC_OK) return cudaErrorInvalidValue;
         if (done > 0) e = cudaMemsetAsync(&h->d_ctl->ticket, 0, sizeof(unsigned), h->stream);
         if (e == cudaSuccess)
-            e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, m, h->stream, pr, !pr && helpers_on(h));
+            e = mcg_host::sweep_launch(grid, h->d_chains, sched, count, h->d_ctl, nch, m, h->stream, pr, !pr && helpers_on(h),
+                                       false);
         done += m;
         if (e == cudaSuccess && h->drift_every > 0 && m == K) e = enqueue_drift(h);
     }

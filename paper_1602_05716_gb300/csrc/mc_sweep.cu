@@ -1220,6 +1220,43 @@ __device__ __forceinline__ void tile_buffer(const float4 *tile, int cnt, int r0,
     }
 }
 
+// One buffer for a group of 65..72 occupied move slots ("excess" mode): the first 64 slots as two
+// layers (mv0: slots p and p + 32 of thread row p, column slices of SL, as tile_buffer), and the e = ns - 64
+// excess moves by rows of XR = T / XS threads, XS column slices each: row q < e runs excess move 64 + q (mx, lane 0)
+// against ions rx, rx + XS, ... of each group.  The excess sums are promoted after every group like the others
+// (S / XS <= 16 terms per partial sum) and handed over through shared memory after the tiles.
+template <int XS>
+__device__ __forceinline__ void tile_buffer_x(const float4 *tile, int cnt, int r0, const Mv2 &mv0, f32x2 &s20,
+                                              f32x2 &P20, float &mA0, float &mA1, float &hA0, float &lA0, float &hA1,
+                                              float &lA1, bool xact, int rx, const Mv2 &mx, float &sx, float &Px,
+                                              float &mnx, float &hx, float &lx)
+{
+    constexpr int NJ = S / SL, NX = S / XS;
+    for (int gq = 0; gq < cnt; ++gq) {
+        const float4 *tg = tile + gq * S;
+#pragma unroll 4
+        for (int jj = 0; jj < NJ; ++jj) pair_far2(mv0, tg[r0 + jj * SL], s20, P20, mA0, mA1);
+        if (xact) {
+#pragma unroll
+            for (int jj = 0; jj < NX; ++jj) pair_far1(mx, tg[rx + jj * XS], sx, Px, mnx);
+            float t2, e;
+            two_sum(hx, sx, t2, e);
+            hx = t2;
+            lx += e;
+            sx = 0.f;
+        }
+        float v0, v1, t2, e;
+        upk2(s20, v0, v1);
+        two_sum(hA0, v0, t2, e);
+        hA0 = t2;
+        lA0 += e;
+        two_sum(hA1, v1, t2, e);
+        hA1 = t2;
+        lA1 += e;
+        s20 = pk2(0.f, 0.f);
+    }
+}
+
 // The packed move data of thread row p (move slots p + 32 m) from the staged positions: old positions, the
 // displacements and their negatives.
 __device__ __forceinline__ void tile_moves(const Smem &sm, int p, int ns, int (&km)[MPT], Mv2 (&mv)[MPT / 2])
@@ -1322,7 +1359,7 @@ __device__ void helper_loop(Smem &sm)
     }
 }
 
-template <bool HELP>
+template <bool HELP, bool DA>
 __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, const Ticket tk, int ticket, Ctl *ctl,
                               int role, int &hseq)
 {
@@ -1463,7 +1500,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     int n_dfp64 = 0;
     long long da_part[4] = {0, 0, 0, 0};
     const long long cyc_da0 = clock64();
-    if (ch.da) {
+    if (DA && ch.da) {
         if (!(ch.pf ? prefilter_stage1(sm, c, ctl) : da_stage1(sm, c, ctl, mode, n_dfp64, da_part))) return false;
     } else {
         if (tid < S) {
@@ -1751,6 +1788,21 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         s2[pp] = pk2(sA[m0], sA[m1]);
         P2[pp] = pk2(PA[m0], PA[m1]);
     }
+    // excess mode (65..72 occupied slots, delayed acceptance or the prefilter, no helper warps, no pairs): two layers
+    // as usual and the e = ns - 64 excess moves by 8 rows of 32 threads (tile_buffer_x), instead of a third layer of
+    // 32 move slots that would cost half as much again as the two
+    const int nex = ns - 64;
+    const int XS = (DA && !HELP && !pairs && nex > 0 && nex <= 8) ? 32 : 0;
+    const int qx = XS ? tid / XS : 0, rx = XS ? tid % XS : 0;
+    const bool xact = XS && qx < nex;
+    Mv2 mx;
+    float sx = 0.f, Px = 0.f, mnx = finf(), hx = 0.f, lx = 0.f;
+    {
+        const int kx = (int)sm.surv[xact ? 64 + qx : 0];
+        const float4 ax = sm.trial[kx], bx = sm.own[kx];
+        const float3 bx3 = make_float3(bx.x, bx.y, bx.z), dx3 = make_float3(ax.x - bx.x, ax.y - bx.y, ax.z - bx.z);
+        mx = make_mv2(bx3, dx3, bx3, dx3);
+    }
     // with helper warps: hand the tile pass over (they wait at barrier 2); they take column slices 8..15
     const bool tiles_run = ntl > 0 && ns > 0;
     if (HELP) {
@@ -1780,7 +1832,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (q < pn * S) cp_async16(&sm.tile[cur ^ 1][q], &tile_src(tile_J(in + (q >> 7)))[q & (S - 1)]);
         }
         // occupied 32-move layers only (all of them for a plain chain)
-        tile_buffer<HELP ? 2 * SL : SL>(sm.tile[cur], cnt, r, nm, mv, s2, P2, mA, hA, lA);
+        if (XS == 32)
+            tile_buffer_x<32>(sm.tile[cur], cnt, r, mv[0], s2[0], P2[0], mA[0], mA[1], hA[0], lA[0], hA[1], lA[1], xact,
+                              rx, mx, sx, Px, mnx, hx, lx);
+        else
+            tile_buffer<HELP ? 2 * SL : SL>(sm.tile[cur], cnt, r, nm, mv, s2, P2, mA, hA, lA);
         cp_async_wait_all();
         if (warp == 0) {
             const int nh = (hz < in + 4 * TG && hz < ntl - 1) ? advance_horizon(hz) : hz;
@@ -1810,6 +1866,25 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         i = in;
     }
     if (HELP && tiles_run) bar_all();  // the helpers' per-move sums are in shared memory
+    if (XS) {  // excess moves: combine each row's XS slices (a warp or half a warp) and hand the sums over
+        for (int o = 1; o < XS; o <<= 1) {
+            const float h2 = __shfl_xor_sync(FULL, hx, o), l2 = __shfl_xor_sync(FULL, lx, o);
+            float t2, e;
+            two_sum(hx, h2, t2, e);
+            hx = t2;
+            lx = lx + l2 + e;
+            Px += __shfl_xor_sync(FULL, Px, o);
+            mnx = fminf(mnx, __shfl_xor_sync(FULL, mnx, o));
+        }
+        if (xact && rx == 0) {
+            const int kx = sm.surv[64 + qx];
+            help_h(sm)[kx] = hx;
+            help_l(sm)[kx] = lx;
+            help_p(sm)[kx] = Px;
+            help_m(sm)[kx] = mnx;
+        }
+        bar_main();
+    }
     cyc_tiles = clock64() - cyc_t0;
     if (trc) gt_tiles = globaltimer();
 #pragma unroll
@@ -1899,7 +1974,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 qv += sm.kPs[kv] * __ldcg(&box->p[kv]);
                 mv = fminf(mv, __ldcg(&box->m[kv]));
             }
-            if (HELP && tiles_run) {  // the helper warps' column slices
+            if ((HELP && tiles_run) || (XS && r == 2)) {  // the helper warps' column slices, or the excess rows
                 float s2, e;
                 two_sum(hv, help_h(sm)[kv], s2, e);
                 hv = s2;
@@ -1971,7 +2046,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             float bnd = (mode == 1 || mode == 3 || kT < 0.f)
                             ? finf()
                             : (mode == 2 ? 0.f : lqa * (U32 * (sm.Qs[k] * infl) + 0x1p-40f * ch.a_max));
-            if (ch.da && !ch.pf && mode == 0) bnd += sm.dEtB[k];  // stage 2 compares dE with L(u2) + dEt
+            if (DA && ch.da && !ch.pf && mode == 0) bnd += sm.dEtB[k];  // stage 2 compares dE with L(u2) + dEt
             sm.bnd[k] = bnd;
         }
         if (trc) gt_ph[1] = globaltimer();
@@ -2160,7 +2235,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             const int k = first;
             const unsigned stv = sm.st[k];
             // the acceptance draw of this decision: purpose 0, or purpose 1 for delayed acceptance's stage 2
-            const bool isda = ch.da != nullptr && !ch.pf;
+            const bool isda = DA && ch.da != nullptr && !ch.pf;
             const unsigned ua =
                 move_draws(ch, s * (unsigned long long)N + (unsigned long long)(k0 + k), isda ? 1u : 0u).w >> 8;
             const double L64 = (ua == 0u) ? 0.0 : -series_log((double)ua * 0x1p-24);
@@ -2257,7 +2332,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     if (tid < nk) {
         const bool acc = bit(sm.accw, tid);
         __stcg(&ch.pos[(s + 1) & 1][k0 + tid], acc ? sm.trial[tid] : sm.own[tid]);
-        if (ch.da && acc && publish) {
+        if (DA && ch.da && acc && publish) {
             // delayed acceptance and the prefilter: the near-field cell list holds current positions (an ion
             // left out of a full prefilter cell has no slot)
             const DADev &dd = *ch.da;
@@ -2395,7 +2470,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 atomicAdd(&ch.stats[CNT_OVL_SCAN], (unsigned long long)n_scan);
                 atomicAdd(&ch.stats[CNT_CYC_OVL], (unsigned long long)cyc_ovl);
             }
-            if (ch.da) {
+            if (DA && ch.da) {
                 atomicAdd(&ch.stats[CNT_DA_REJ1], (unsigned long long)cnt[9]);
                 atomicAdd(&ch.stats[CNT_DA_OVL1], (unsigned long long)cnt[10]);
                 atomicAdd(&ch.stats[CNT_DA_FP64], (unsigned long long)n_dfp64);
@@ -2415,7 +2490,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             rc.tier = sm.tier[k];
             rc.pad = 0;
             rc.bound = (double)sm.bnd[k];
-            rc.dEt = !ch.da ? __longlong_as_double(0x7ff8000000000000ll)
+            rc.dEt = !(DA && ch.da) ? __longlong_as_double(0x7ff8000000000000ll)
                             : (bit(sm.d64w, k) ? sm.dEt64[k] : (double)sm.dEt32[k]);
             const int out = sm.outcome[k];
             const bool ev = out == OUT_ACCEPT || out == OUT_METROPOLIS;
@@ -2428,8 +2503,11 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     return sm.ok != 0;
 }
 
-__global__ void __launch_bounds__(T, 1)
-sweep_kernel(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sched, int n_tickets, Ctl *ctl)
+// The persistent loop of one CTA (T threads); DA: the chains may carry a cell list (delayed acceptance, the
+// prefilter).  Plain launches use the instance without it, so its code and registers are the plain path's alone.
+template <bool DA>
+__device__ __forceinline__ void sweep_body(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sched,
+                                           int n_tickets, Ctl *ctl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
@@ -2459,13 +2537,25 @@ sweep_kernel(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sch
         if (t < 0) break;
         int hseq = 0;
         // uniform: every failure exit follows a barrier
-        if (!process_group<false>(sm, chains, sched[t], t, ctl, role, hseq)) break;
+        if (!process_group<false, DA>(sm, chains, sched[t], t, ctl, role, hseq)) break;
     }
     // every exit path releases the TMEM columns before the CTA ends
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
     if (threadIdx.x < 32) tmem_dealloc(sm.tmem);
+}
+
+__global__ void __launch_bounds__(T, 1)
+sweep_kernel(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sched, int n_tickets, Ctl *ctl)
+{
+    sweep_body<false>(chains, sched, n_tickets, ctl);
+}
+
+__global__ void __launch_bounds__(T, 1)
+sweep_kernel_da(const ChainDev *__restrict__ chains, const Ticket *__restrict__ sched, int n_tickets, Ctl *ctl)
+{
+    sweep_body<true>(chains, sched, n_tickets, ctl);
 }
 
 // The same persistent loop with helper warps: 2T threads, one CTA per SM.  Warpgroups 0-1 (threads < T) run the
@@ -2502,7 +2592,7 @@ sweep_kernel_h(const ChainDev *__restrict__ chains, const Ticket *__restrict__ s
             const int t = sm.ticket;
             bar_main();
             if (t < 0) break;
-            if (!process_group<true>(sm, chains, sched[t], t, ctl, 0, hseq)) break;
+            if (!process_group<true, true>(sm, chains, sched[t], t, ctl, 0, hseq)) break;
         }
         // release the helper warps (they wait at the next hand-over)
         if (threadIdx.x == 0) sm.hcmd[hseq & 1] = HC_EXIT;
@@ -2537,6 +2627,8 @@ cudaError_t sweep_configure()
     cudaError_t e = cudaFuncSetAttribute(mcg::sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(mcg::Smem));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(mcg::sweep_kernel_da, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(mcg::Smem));
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(mcg::sweep_kernel_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(mcg::Smem));
 }
 
@@ -2570,7 +2662,7 @@ cudaError_t sweep_max_clusters(int *n)
 }
 
 cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticket *sched, int n_tickets, mcg::Ctl *ctl,
-                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs, bool help)
+                         int n_chains, long long n_sweeps, cudaStream_t st, bool pairs, bool help, bool da)
 {
     if (help && !pairs) {
         mcg::sweep_kernel_h<<<grid, 2 * mcg::T, sizeof(mcg::Smem), st>>>(chains, sched, n_tickets, ctl);
@@ -2589,6 +2681,8 @@ cudaError_t sweep_launch(int grid, const mcg::ChainDev *chains, const mcg::Ticke
         cfg.numAttrs = 1;
         cudaError_t e = cudaLaunchKernelEx(&cfg, mcg::sweep_kernel, chains, sched, n_tickets, ctl);
         if (e != cudaSuccess) return e;
+    } else if (da) {
+        mcg::sweep_kernel_da<<<grid, mcg::T, sizeof(mcg::Smem), st>>>(chains, sched, n_tickets, ctl);
     } else {
         mcg::sweep_kernel<<<grid, mcg::T, sizeof(mcg::Smem), st>>>(chains, sched, n_tickets, ctl);
     }
