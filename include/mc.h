@@ -436,8 +436,9 @@ int mc_set_surrogate(mc_handle h, int chain, const uint16_t *w_bf16, int64_t n_w
  * a surrogate), W = 0 removes it.  Like a surrogate it makes sweeps run one
  * per launch after the cell list is rebuilt, MC_OPT_DA = 0 suspends it, and
  * it replaces a surrogate set on the chain (mc_set_surrogate replaces it in
- * turn).  Device memory: at most 8 N cells (256 per axis) of up to 64 slots,
- * 20 bytes each, plus 4 bytes per cell and per ion.                         */
+ * turn).  Device memory: at most 8 N cells (256 per axis) of 4 slots (up to
+ * 64 for cells of edge above 0.894 sigma), 16 bytes each, plus 4 bytes per
+ * cell and per ion.  "Sweeps per launch" (MC_OPT_DA_SWEEPS) apply to it.    */
 int mc_set_overlap_prefilter(mc_handle h, int chain, int W);
 
 /* Training samples from the chain as it stands: for each ion i, the trial move

@@ -44,7 +44,7 @@ cudaError_t pos_unpack_launch(const float4 *src, int N, float *xyz, cudaStream_t
 cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt, int *cellid,
                            int *start, int *fill, int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st);
 cudaError_t da_prep_bucket_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt,
-                                  int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st);
+                                  float4 *cell_pos, int *slot_of, cudaStream_t st);
 cudaError_t da_sample_launch(const mcg::ChainDev *ch, const mcg::DADev *dd, int B, int grid, float *V, float *Y,
                              unsigned char *valid, cudaStream_t st);
 cudaError_t mlp_forward_launch(const unsigned short *w, const float *V, long long n, float *G, float *Z, cudaStream_t st);
@@ -586,8 +586,8 @@ cudaError_t enqueue_da(mc_system *h, long long n, int grid)
         for (size_t ci = 0; ci < h->chains.size(); ++ci) {
             Chain &c = h->chains[ci];
             if (!c.da || e != cudaSuccess) continue;
-            e = c.pf ? mcg_host::da_prep_bucket_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cell_ions,
-                                                       c.d_cell_pos, c.d_slot_of, h->stream)
+            e = c.pf ? mcg_host::da_prep_bucket_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cell_pos,
+                                                       c.d_slot_of, h->stream)
                      : mcg_host::da_prep_launch(h->d_chains + ci, c.N, c.dda, c.ncell, c.d_cnt, c.d_cellid,
                                                 c.d_cell_start, c.d_fill, c.d_cell_ions, c.d_cell_pos, c.d_slot_of,
                                                 h->stream);
@@ -1704,16 +1704,16 @@ int mc_set_overlap_prefilter(mc_handle h, int chain, int W)
     // slots per cell: m^3 sub-cubes of diagonal below sigma (with slack for the FP32 cell index) hold at most one
     // ion each of a non-overlapping configuration
     const int m = std::max(1, (int)std::ceil((edge * (1.0 + 0x1p-8) + 1e-4) * std::sqrt(3.0) / (c.sigma * (1.0 - 0x1p-16))));
-    const int cap = std::min(64, m * m * m);
+    // five ions at least sigma apart do not fit a cube of edge below 0.894 sigma (sqrt(5)/2 is the largest least
+    // distance of five points in a unit cube); an ion past a full cell is only left out of the list anyway
+    const int cap = (edge * (1.0 + 0x1p-8) + 1e-4 < 0.894 * c.sigma) ? 4 : std::min(64, m * m * m);
     c.ncell = G * G * G;
     const size_t slots = (size_t)c.ncell * (size_t)cap, N = (size_t)c.N;
     CK(cudaMalloc(&c.dda, sizeof(mcg::DADev)));
     CK(cudaMalloc(&c.d_cnt, sizeof(int) * (size_t)c.ncell));
-    CK(cudaMalloc(&c.d_cell_ions, sizeof(int) * slots));
     CK(cudaMalloc(&c.d_cell_pos, sizeof(float4) * slots));
     CK(cudaMalloc(&c.d_slot_of, sizeof(int) * N));
     mcg::DADev d{};
-    d.cell_ions = c.d_cell_ions;
     d.cell_pos = c.d_cell_pos;
     d.slot_of = c.d_slot_of;
     d.cell_cnt = c.d_cnt;

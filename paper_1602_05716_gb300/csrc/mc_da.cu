@@ -71,11 +71,11 @@ __global__ void da_prep_scatter(const ChainDev *__restrict__ chp, int N, const i
     slot_of[j] = slot;
 }
 
-// Overlap prefilter: bucket layout of the sweep's start positions (cell q: slots q cap .. q cap + cap - 1, filled
-// in arrival order; the order never matters, the prefilter only asks whether some listed ion overlaps).  cnt must
+// Overlap prefilter: bucket layout of the sweep's start positions (cell q: slots q cap .. q cap + cap - 1, each the
+// position with the ion's index in place of its valence, filled in arrival order; the order never matters, the prefilter only asks whether some listed ion overlaps).  cnt must
 // be zero on entry; it ends with the number of ions of each cell, possibly above cap (those past it are unlisted).
 __global__ void da_prep_bucket(const ChainDev *__restrict__ chp, int N, const DADev *__restrict__ dp, int *cnt,
-                               int *cell_ions, float4 *cell_pos, int *slot_of)
+                               float4 *cell_pos, int *slot_of)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -86,8 +86,7 @@ __global__ void da_prep_bucket(const ChainDev *__restrict__ chp, int N, const DA
     const int t = atomicAdd(&cnt[c], 1);
     if (t < d.cap) {
         const int slot = c * d.cap + t;
-        cell_ions[slot] = j;
-        cell_pos[slot] = x;
+        cell_pos[slot] = make_float4(x.x, x.y, x.z, __int_as_float(j));  // the ion's index in the fourth word
         slot_of[j] = slot;
     } else {
         slot_of[j] = -1;
@@ -399,11 +398,11 @@ cudaError_t da_prep_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd
 }
 
 cudaError_t da_prep_bucket_launch(const mcg::ChainDev *chd, int N, const mcg::DADev *dd, int ncell, int *cnt,
-                                  int *cell_ions, float4 *cell_pos, int *slot_of, cudaStream_t st)
+                                  float4 *cell_pos, int *slot_of, cudaStream_t st)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ncell, st)) != cudaSuccess) return e;
-    mcg::da_prep_bucket<<<(N + 255) / 256, 256, 0, st>>>(chd, N, dd, cnt, cell_ions, cell_pos, slot_of);
+    mcg::da_prep_bucket<<<(N + 255) / 256, 256, 0, st>>>(chd, N, dd, cnt, cell_pos, slot_of);
     return cudaGetLastError();
 }
 

@@ -56,7 +56,8 @@ struct DADev {
     int mlp_zero;                  // every weight is +-0, so g = 0 exactly: the FP32 MLP pass is skipped
     // overlap prefilter (mc_set_overlap_prefilter): no surrogate and no stage-1 Metropolis test, stage 1 only
     // rejects trials that overlap a counted ion.  Bucket layout: cell q holds ions in slots q cap ..
-    // q cap + min(cell_cnt[q], cap) - 1; an ion that finds its cell full has slot_of -1 and is not listed.
+    // q cap + min(cell_cnt[q], cap) - 1, each the position with the ion's index as the fourth word; an ion that
+    // finds its cell full has slot_of -1 and is not listed.
     const int *cell_cnt;
     float ovl_reach2;              // (sigma + the largest move of a candidate since the sweep's start)^2, with slack
     int cap;                       // slots per cell
@@ -390,10 +391,8 @@ __device__ inline int da_ovl_warp(const DADev &d, int g, int B, int Wg, int i, f
         const int q = (ax * G + ay) * G + az;
         const int n = min(__ldg(&d.cell_cnt[q]), d.cap);
         for (int t = 0; t < n && !ovl; ++t) {
-            const int slot = q * d.cap + t;
-            const int j = __ldg(&d.cell_ions[slot]);
-            if (!da_counted(i, g, B, Wg, j)) continue;
-            const float4 y = __ldcg(&d.cell_pos[slot]);
+            const float4 y = __ldcg(&d.cell_pos[q * d.cap + t]);  // fourth word: the ion's index
+            if (!da_counted(i, g, B, Wg, __float_as_int(y.w))) continue;
             const float dx = a.x - y.x, dy = a.y - y.y, dz = a.z - y.z;
             const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             if (d2 < lo2) ovl = 1;

@@ -2337,7 +2337,8 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             // left out of a full prefilter cell has no slot)
             const DADev &dd = *ch.da;
             const int sl = __ldg(&dd.slot_of[k0 + tid]);
-            if (sl >= 0) __stcg(&dd.cell_pos[sl], sm.trial[tid]);
+            const float4 tv = sm.trial[tid];
+            if (sl >= 0) __stcg(&dd.cell_pos[sl], ch.pf ? make_float4(tv.x, tv.y, tv.z, __int_as_float(k0 + tid)) : tv);
         }
     }
     bar_main();
