@@ -492,6 +492,8 @@ def run_ours(args):
             "energy": {"ledger": led, "recomputed": rec, "drift": led - rec,
                        "max_abs_drift_over_chains": max(abs(a - b) for a, b in energies)},
             "wall_s": head["wall"]}
+    # per step: delayed acceptance runs the cell-list preparation (count, scan, scatter), the sweep and the sweep
+    # counter per sweep; a plain step one sweep launch and the counter
     kernels_per_step = (5 * sps) if head_name == "da" else 2
     line["gpu_launches"] = kernels_per_step * args.steps
     if head_name == "da":
@@ -546,7 +548,8 @@ def run_ours(args):
         line["e2e"] = {"value": mv / t_e2e, "unit": "moves/s", "h2d_bytes_per_step": 16 * npad,
                        "d2h_bytes_per_step": 16 * n + 8 * len(chains),
                        "path": "mc_set_positions(pinned host) + mc_sweep + mc_get_positions + mc_energy per step"}
-        line["gpu_launches"] += kernels_per_step * args.steps
+        # ... and each end-to-end step adds the device-side position check (2), pack and unpack
+        line["gpu_launches"] += (kernels_per_step + 4 * len(chains)) * args.steps
     sysm.close()
 
     threads = os.cpu_count() or 1
