@@ -106,12 +106,13 @@ def test_prefilter_batch_and_removal(pkg):
 
 def test_prefilter_large_n1048576_prefix(pkg):
     """The 2^20-ion workload with the prefilter at its production depth (W = 160) in the production launch: the
-    first 1024 moves of the first sweep against the oracle move by move, then the invariants of the whole
+    first 4096 moves of the first sweep against the oracle move by move (among their 32 groups some have 65..72
+    survivors, the groups whose excess moves run on rows of threads), then the invariants of the whole
     configuration after the sweep (inside the wall, no overlap, ledger equal to the recomputed energy)."""
     ch = inputs.workload("large_n1048576").chains[0]
     g = pkg.System([ch])
     g.set_overlap_prefilter(160)
-    k = 1024
+    k = 4096
     g.record_enable(k)
     g.sweep(1)
     o = oracle.OracleChain.from_chain(ch, threads=THREADS)
@@ -122,6 +123,8 @@ def test_prefilter_large_n1048576_prefix(pkg):
     pg = g.positions()
     assert (pg[:k] == o.positions()[:k]).all()
     _compare_records(gr, orc, ch.n)
+    surv = ((gr["tier"] != 6) & (gr["outcome"] != oracle.REJECT_WALL)).reshape(-1, 128).sum(1)
+    assert ((surv > 64) & (surv <= 72)).any(), surv
     st = g.stats()
     assert st["da_ovl1"] > 0.5 * st["rej_overlap"]  # most overlaps are caught before any pair sum
     Rc = ch.R - 0.5
