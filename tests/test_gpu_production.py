@@ -5,6 +5,10 @@
    counted ion's position is final when a work item starts (W >= grid + 1) is what the parity rests on.  The first
    2048 moves of sweep 0 (records, outcome counts, positions) against the oracle's delayed-acceptance chain.
  * The same at N = 2^20 (the large workload), first 1024 moves.
+ * The N = 65536 delayed-acceptance workload, in the launch the bench times for it: one whole sweep move by move,
+   for delayed acceptance (W = 160, so the counted-ion rule wraps around the sweep's end: ions of later groups
+   are counted from their previous sweep's positions) and for the plain and prefilter launches against one
+   plain oracle sweep.
  * The 64-chain batch with deep windows and pairs mode at their defaults, run as back-to-back 10-sweep launches
    for 120 sweeps (the launch pattern that once exposed a resolve-round race): sweep 0 of four chains against the
    oracle move by move, then for every chain no overlap, every ion inside the wall and the ledger equal to the
@@ -97,6 +101,52 @@ def test_da_large_n1048576_prefix(pkg):
     led, rec = g.energy()
     assert abs(led - rec) < 1e-6 * abs(rec), (led, rec)
     g.close()
+
+
+def test_da_n65536_full_sweep(pkg):
+    """Delayed acceptance at N = 65536 (1:1, phi 0.30, h 0.2; 512 groups, W = 160) in the bench's launch: every
+    move of sweep 0 against the oracle's delayed-acceptance chain (decisions, positions, stage-1 values where
+    both sides took the exact FP64 path), then the invariants of the configuration."""
+    ch = inputs.workload("da_n65536").chains[0]
+    w = _random_bf16(73)
+    g, grid, counts = _da_prefix(pkg, ch, w, 160, ch.n)
+    assert counts[4] > 0 and counts[0] > 0
+    st = g.stats()
+    assert st["sweeps"] == 1
+    _no_overlap_inside(g.positions(), ch.R)
+    led, rec = g.energy()
+    assert abs(led - rec) < 1e-6 * abs(rec), (led, rec)
+    g.close()
+
+
+def test_plain_and_prefilter_n65536_full_sweep(pkg):
+    """The same chain's plain launch and its prefilter launch (W = 160) against one plain oracle sweep: both
+    bit-identical in every decision and position, with the FP32 values inside their bands."""
+    from test_gpu_parity import _compare_records
+    ch = inputs.workload("da_n65536").chains[0]
+    n = ch.n
+    o = oracle.OracleChain.from_chain(ch, threads=THREADS)
+    o.record(n)
+    o.sweep(1)
+    orc, pos_o = o.records(), o.positions()
+    so = o.stats()
+    o.close()
+    for W in (0, 160):
+        g = pkg.System([ch])
+        if W:
+            g.set_overlap_prefilter(W)
+        g.record_enable(n)
+        g.sweep(1)
+        gr = g.records()
+        _compare_records(gr, orc, n)
+        assert (g.positions() == pos_o).all()
+        sg = g.stats()
+        for k_g, k_o in [("accepts", "accept"), ("rej_metropolis", "rej_metropolis"), ("rej_overlap", "rej_overlap"),
+                         ("rej_wall", "rej_wall")]:
+            assert sg[k_g] == so[k_o], (W, k_g, sg, so)
+        if W:
+            assert sg["da_ovl1"] == int((gr["tier"] == 6).sum()) > 0.5 * sg["rej_overlap"]
+        g.close()
 
 
 def test_batch64_back_to_back_regression(pkg):
