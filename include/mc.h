@@ -355,7 +355,19 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
  *                      cells are sized for this many moves of every ion.
  *                      Set it before mc_set_surrogate / mc_set_overlap_prefilter
  *                      (MC_ERR_INVALID while a chain holds a cell list built
- *                      for another value).  The trajectory is unchanged. */
+ *                      for another value).  The trajectory is unchanged.
+ *  MC_OPT_SHARED_GUARD 1 = on (default), 0 = off.  In launches of chains
+ *                      with a surrogate or the overlap prefilter, a move
+ *                      whose FP32 value falls inside its error band is
+ *                      recomputed (guard tiers 2 and 3) by its work item's
+ *                      warps together with every warp of the launch that
+ *                      waits at that moment, in chunks of 4096 partners,
+ *                      instead of by its work item's CTA alone; one such
+ *                      move at a time (others run on their own CTA).
+ *                      Launches of plain chains only keep the tiers on the
+ *                      work item's CTA.  Decisions and the trajectory are
+ *                      unchanged; the dE recorded for a tier-2 or tier-3
+ *                      move may differ in its last FP64 bits. */
 #define MC_OPT_GUARD_MODE 1
 #define MC_OPT_TIMEOUT_MS 2
 #define MC_OPT_CTAS 3
@@ -368,6 +380,7 @@ int mc_reduction_run(const mc_chain_desc *desc, int64_t n_sweeps, int scheme, fl
 #define MC_OPT_DRIFT_EVERY 10
 #define MC_OPT_HELPERS 11
 #define MC_OPT_DA_SWEEPS 12
+#define MC_OPT_SHARED_GUARD 13
 int mc_set_option(mc_handle h, int option, int64_t value);
 int mc_get_option(mc_handle h, int option, int64_t *value);
 

@@ -14,6 +14,7 @@ OPT_DEEP_WINDOWS = 9
 OPT_DRIFT_EVERY = 10
 OPT_HELPERS = 11
 OPT_DA_SWEEPS = 12
+OPT_SHARED_GUARD = 13
 MLP_NIN, MLP_H = 33, 64
 MLP_NP = MLP_H * MLP_NIN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1  # layout W1, b1, W2, b2, W3, b3
 

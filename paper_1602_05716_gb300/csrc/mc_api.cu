@@ -192,6 +192,8 @@ struct mc_system {
     int occ_h = 0;                      // resident CTAs per SM of the helper-warp kernel (0: unavailable)
     int max_clusters = 0;               // resident clusters of two CTAs (0: pairs mode unavailable)
     mcg::PairBox *d_box = nullptr;      // one hand-over box per cluster
+    mcg::GuardBoard *d_gb = nullptr;    // the shared guard's board (and its per-chunk sums after it)
+    int gb_opt = 1;                     // MC_OPT_SHARED_GUARD
     int da_on = 1;  // chains with a surrogate sweep with delayed acceptance (MC_OPT_DA)
     std::map<std::pair<long long, int>, std::pair<mcg::Ticket *, int>> scheds;  // (n_sweeps, policy) -> schedule
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -424,6 +426,7 @@ int create_common(const mc_chain_desc *descs, int n_chains, mc_handle *out)
         for (auto &c : h->chains) free_chain(c);
         cudaFree(h->d_chains);
         cudaFree(h->d_ctl);
+        cudaFree(h->d_gb);
         cudaFree(h->d_box);
         if (h->h_ctl) cudaFreeHost(h->h_ctl);
         if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -460,6 +463,23 @@ int create_common(const mc_chain_desc *descs, int n_chains, mc_handle *out)
         cudaMallocHost(&h->h_ctl, sizeof(mcg::Ctl)) != cudaSuccess ||
         cudaMalloc(&h->d_box, sizeof(mcg::PairBox) * (size_t)std::max(1, h->sm_count)) != cudaSuccess)
         return bail(fail(MC_ERR_OOM, "allocation of launch state failed"));
+    {
+        // the shared guard's board: the request, then the sums of every chunk of the largest chain
+        long long nmax = 1;
+        for (const auto &c : h->chains) nmax = std::max(nmax, ((long long)c.N + mcg::GB_CHUNK - 1) / mcg::GB_CHUNK);
+        if (nmax <= 0xffff) {
+            const size_t off = (sizeof(mcg::GuardBoard) + 255) & ~(size_t)255;
+            char *p = nullptr;
+            if (cudaMalloc(&p, off + 2 * sizeof(double) * (size_t)nmax) != cudaSuccess)
+                return bail(fail(MC_ERR_OOM, "allocation of the guard board failed"));
+            h->d_gb = reinterpret_cast<mcg::GuardBoard *>(p);
+            mcg::GuardBoard gb{};
+            gb.part = reinterpret_cast<double *>(p + off);
+            gb.bpart = gb.part + nmax;
+            if (cudaMemcpy(h->d_gb, &gb, sizeof gb, cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(MC_ERR_CUDA, "guard board setup failed"));
+        }
+    }
     int rc = sync_descriptors(h);
     if (rc) return bail(rc);
     write_ctl(h);
@@ -717,6 +737,7 @@ void write_ctl(mc_system *h)
     c->pairs = pairs_on(h) ? 1 : 0;
     c->deep = h->deep_opt;
     c->box = h->d_box;
+    c->gb = h->gb_opt ? h->d_gb : nullptr;
 }
 
 int finish(mc_system *h)
@@ -1405,6 +1426,11 @@ static int set_option(mc_handle h, int option, int64_t value)
         h->da_sweeps = (int)value;
         drop_graphs(h);
         return MC_OK;
+    case MC_OPT_SHARED_GUARD:
+        if (value < 0 || value > 1) return fail(MC_ERR_INVALID, "shared guard %lld", (long long)value);
+        h->gb_opt = (int)value;
+        drop_graphs(h);
+        return MC_OK;
     case MC_OPT_HELPERS:
         if (value < 0 || value > 1) return fail(MC_ERR_INVALID, "helpers %lld", (long long)value);
         if (value == 1 && h->occ_h < 1) return fail(MC_ERR_INVALID, "the helper-warp kernel does not fit an SM");
@@ -1444,6 +1470,7 @@ int mc_get_option(mc_handle h, int option, int64_t *value)
     case MC_OPT_DRIFT_EVERY: *value = h->drift_every; return MC_OK;
     case MC_OPT_HELPERS: *value = helpers_on(h) ? 1 : 0; return MC_OK;
     case MC_OPT_DA_SWEEPS: *value = h->da_sweeps; return MC_OK;
+    case MC_OPT_SHARED_GUARD: *value = (h->gb_opt && h->d_gb) ? 1 : 0; return MC_OK;
     default: return fail(MC_ERR_INVALID, "unknown option %d", option);
     }
 }
@@ -1928,6 +1955,7 @@ void mc_destroy(mc_handle h)
     for (auto &c : h->chains) free_chain(c);
     cudaFree(h->d_chains);
     cudaFree(h->d_ctl);
+    cudaFree(h->d_gb);
     cudaFree(h->d_box);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);

@@ -106,6 +106,29 @@ struct Ctl {
     int pairs;                    // 1: clusters of two CTAs share each work item's tiles (leader even, helper odd)
     int deep;                     // 1: deep windows (groups g-2.. both ways, corrections in tensor memory)
     struct PairBox *box;          // per cluster: the work item and the helper's per-move tile sums
+    // shared guard: a work item whose move needs an accurate recomputation posts it on the board, and every warp
+    // that waits in wait_words takes chunks of its pair sum
+    struct GuardBoard *gb;        // nullptr: every guard tier runs on its own work item's CTA
+    unsigned long long gnext;     // (request id << 32) | (chunks << 16) | next chunk to take
+    unsigned gdone;               // chunks of the current request finished
+    unsigned glock;               // 1 while a work item holds the board
+};
+
+// The posted guard request: the move (ion i of group g, old position b, trial a), where its partners' positions
+// are published, and the groups whose positions it sees from its work item's shared memory (GB_SLOTS of them:
+// its own group, the window, the deep windows; group -1 for an unused slot).  part / bpart: per chunk of
+// GB_CHUNK ions, the sum of the pair terms and of their error bounds.
+constexpr int GB_CHUNK = 4096, GB_SLOTS = 5;
+struct GuardBoard {
+    int tier, N, g, i;
+    float dn, rho0;               // tier 2: bound of the move's length, smallest partner distance to [b, a]
+    int pad0[2];
+    float4 a, b;
+    const float4 *Pprev, *Pcur;
+    int slotJ[GB_SLOTS];
+    int pad[3];
+    float4 ovl[GB_SLOTS][128];
+    double *part, *bpart;
 };
 
 // Hand-over from a cluster's helper CTA to its leader (global memory, ordered by the cluster barriers).

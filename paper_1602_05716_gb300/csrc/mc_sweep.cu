@@ -58,6 +58,7 @@ constexpr int TG = 4;              // groups per tile-ring buffer (one barrier p
 constexpr int SL = T / (S / MPT);  // column slices (8)
 constexpr int HALF = S / 2;
 constexpr int DW = 3;              // deep windows: the groups g-2 .. g-1-DW, both positions, matrices in TMEM
+static_assert(DW + 2 <= GB_SLOTS, "the guard board holds this group, the window and the deep windows");
 constexpr unsigned TMEM_COLS = 512;  // power of two >= S * DW
 static_assert(S == 128 && T == 256 && S * DW <= (int)TMEM_COLS && TMEM_COLS <= 512, "TMEM layout");
 
@@ -274,11 +275,42 @@ __device__ __forceinline__ void bar_all()
 // Tile-pass hand-over to the helper warps (Smem::hcmd).
 constexpr int HC_SKIP = 0, HC_RUN = 1, HC_EXIT = 2;
 
+// ---------------------------------------------------------------------------
+// The shared guard (Ctl::gb).  Tiers 2 and 3 of a move sum N terms; while one work item decides its group, most
+// of the launch's work items wait for that group's outcome.  So a work item whose move needs tier 2 or 3 posts
+// the move on the board, and its own warps take chunks of GB_CHUNK partners together with every warp that waits
+// in wait_words meanwhile.  Per chunk: the tier's own per-pair terms and error bounds, summed per lane
+// (compensated, as in the tier) and over the warp in FP64.  The poster adds the chunk sums in chunk order with a
+// compensated FP64 sum, so the sum and the bound are the tier's up to FP64 roundings far inside the tier's margin,
+// and the decision rule is the tier's.  One request at a time: a work item that finds the board taken (another
+// chain of a batch) runs the tier on its own CTA, and so does every work item after a wait on the board gave up.
+
+__device__ __forceinline__ unsigned ld_acquire32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Warp: take chunks of the posted request until none is left (defined with the guard tiers).
+__device__ __noinline__ void gb_help(Ctl *ctl);
+
+// Is a posted request waiting for warps?  (Every lane gets the answer.)
+__device__ __forceinline__ bool gb_open(Ctl *ctl)
+{
+    int w = 0;
+    if ((threadIdx.x & 31) == 0 && ctl->gb) {
+        const unsigned long long v = ld_relaxed(&ctl->gnext);
+        w = ((unsigned)v & 0xffffu) < (((unsigned)(v >> 16)) & 0xffffu);
+    }
+    return __shfl_sync(FULL, w, 0) != 0;
+}
+
 // Warp 0 waits until the sweep tags of the nw words of group J lie in [lo, hi]
 // (acquire).  Returns false on timeout, protocol error or abort.  bits (lane w)
 // gets word w's accept bits.
 __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsigned hi, Ctl *ctl, unsigned &bits,
-                           bool sleep = true, bool outcome_words = false)
+                           bool sleep = true, bool outcome_words = false, bool help = false)
 {
     const unsigned long long *words = outcome_words ? ch.bits : ch.flags;
     const int lane = threadIdx.x & 31;
@@ -301,6 +333,7 @@ __device__ bool wait_words(const ChainDev &ch, int J, int nw, unsigned lo, unsig
         }
         if (__all_sync(FULL, done)) return true;
         ++spins;
+        if (help && (spins & 7) == 0 && gb_open(ctl)) gb_help(ctl);
         if (spins > 16 && sleep) __nanosleep(32);
         if ((spins & 31) == 0 && *(volatile int *)&ctl->abort) return false;
         if ((spins & 63) == 0) {
@@ -499,6 +532,48 @@ __device__ __forceinline__ void block_sum(Smem &sm, double v, float bb, double &
 // |delta| / r^2 instead of 1/r.  Per-term bound:
 // |q| [ |t| (rel(Dn) + 19u) + 4u M (rn ro)^2/(rn+ro) + u |delta| (2 Ro + rho)/rho^3 ]
 // with rho a lower bound of the distance from y to the segment [b, a].
+constexpr double T2_KB = 1.25, T2_KR = 0x1p-40, T3_KB = 1.01 * 0x1p-38, T3_KR = 0x1p-48;
+
+// A guard tier's outcome: dE = lq tot against the threshold L64 with the margin kb |lq| bt (bt the sum of the
+// terms' error bounds) plus kr (|dE| + |L64|) for the final roundings and xs: 0 accept, 1 reject, -1 undecided.
+__device__ __forceinline__ int guard_outcome(double lq, double tot, double bt, double kb, double kr, double L64,
+                                             double xs, double &dE)
+{
+    dE = lq * tot;
+    const double Bm = fabs(lq) * bt * kb + kr * (fabs(dE) + fabs(L64)) + xs + 1e-300;
+    return (dE < L64 - Bm) ? 0 : ((dE > L64 + Bm) ? 1 : -1);
+}
+
+// Tier 2's term for partner y (old position b, displacement (dx, dy, dz) of length at most dn, rho0 the
+// smallest distance from a partner to the segment [b, a] that the overlap rule allows) added to the compensated
+// sum (hi, lo), and its error bound to bsum.
+__device__ __forceinline__ void t2_pair(const float4 b, float dx, float dy, float dz, float dn, float rho0,
+                                        const float4 y, float &hi, float &lo, float &bsum)
+{
+    const float ex = y.x - b.x, ey = y.y - b.y, ez = y.z - b.z;
+    const float Do = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+    const float wx = fmaf(2.0f, ex, -dx), wy = fmaf(2.0f, ey, -dy), wz = fmaf(2.0f, ez, -dz);
+    const float Dd = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
+    const float M = fabsf(dx * wx) + fabsf(dy * wy) + fabsf(dz * wz);
+    const float Dn = Do - Dd;
+    const float ro = rsqrt_approx(Do), rn = rsqrt_approx(Dn);
+    const float pr = rn * ro, inv = rcp_approx(rn + ro);
+    const float t = Dd * pr * pr * inv;
+    const float term = y.w * t;
+    float e, s;
+    two_sum(hi, term, s, e);
+    hi = s;
+    lo += e;
+    const float relDn = fmaf(3.0f * U32, Do, 4.0f * U32 * M) * rn * rn + U32;
+    const float Ro = Do * ro * (1.0f + 0x1p-18f), Rn = Dn * rn;
+    const float rho = fmaxf(fminf(Rn, Ro) * (1.0f - 0x1p-18f) - 0.5f * dn, rho0);
+    const float ir = rcp_approx(rho);
+    const float E1 = fabsf(t) * (relDn + 19.0f * U32);
+    const float E2 = 4.0f * U32 * M * pr * pr * inv;
+    const float E3 = U32 * dn * (2.0f * Ro + rho) * ir * ir * ir;
+    bsum += fabsf(y.w) * (E1 + E2 + E3);
+}
+
 __device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double xs, double &dE_out)
 {
     const int tid = threadIdx.x;
@@ -516,39 +591,15 @@ __device__ int tier2(Smem &sm, const Ctx &c, int k, double L64, double xs, doubl
       for (int u = 0; u < GSTAGE / T; ++u) {
         const int j = j0 + u * T + tid;
         if (j >= c.N || j == i) continue;
-        const float4 y = buf[u * T + tid];
-        const float ex = y.x - b.x, ey = y.y - b.y, ez = y.z - b.z;
-        const float Do = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-        const float wx = fmaf(2.0f, ex, -dx), wy = fmaf(2.0f, ey, -dy), wz = fmaf(2.0f, ez, -dz);
-        const float Dd = fmaf(dz, wz, fmaf(dy, wy, dx * wx));
-        const float M = fabsf(dx * wx) + fabsf(dy * wy) + fabsf(dz * wz);
-        const float Dn = Do - Dd;
-        const float ro = rsqrt_approx(Do), rn = rsqrt_approx(Dn);
-        const float pr = rn * ro, inv = rcp_approx(rn + ro);
-        const float t = Dd * pr * pr * inv;
-        const float term = y.w * t;
-        float e, s;
-        two_sum(hi, term, s, e);
-        hi = s;
-        lo += e;
-        const float relDn = fmaf(3.0f * U32, Do, 4.0f * U32 * M) * rn * rn + U32;
-        const float Ro = Do * ro * (1.0f + 0x1p-18f), Rn = Dn * rn;
-        const float rho = fmaxf(fminf(Rn, Ro) * (1.0f - 0x1p-18f) - 0.5f * dn, rho0);
-        const float ir = rcp_approx(rho);
-        const float E1 = fabsf(t) * (relDn + 19.0f * U32);
-        const float E2 = 4.0f * U32 * M * pr * pr * inv;
-        const float E3 = U32 * dn * (2.0f * Ro + rho) * ir * ir * ir;
-        bsum += fabsf(y.w) * (E1 + E2 + E3);
+        t2_pair(b, dx, dy, dz, dn, rho0, buf[u * T + tid], hi, lo, bsum);
       }
     }
     double tot, bt;
     block_sum(sm, (double)hi + (double)lo, bsum, tot, bt);
     if (tid == 0) {
-        const double lq = c.ch->lB * (double)a.w;
-        const double dE = lq * tot;
-        const double B2 = fabs(lq) * bt * 1.25 + 0x1p-40 * (fabs(dE) + fabs(L64)) + xs + 1e-300;
+        double dE;
+        sm.guard_k = guard_outcome(c.ch->lB * (double)a.w, tot, bt, T2_KB, T2_KR, L64, xs, dE);
         sm.redd[16] = dE;
-        sm.guard_k = (dE < L64 - B2) ? 0 : ((dE > L64 + B2) ? 1 : -1);
     }
     bar_main();
     const int out = sm.guard_k;
@@ -590,6 +641,148 @@ __device__ __forceinline__ void df_rsqrt(float dh, float dl, float &rh, float &r
     rl = corr - (rh - r0);
 }
 
+// Tier 3's term for partner y in double-single, added to (hh, hl); |q_y| (1/r' + 1/r) added to absum.
+__device__ __forceinline__ void t3_pair(const float4 a, const float4 b, const float4 y, float &hh, float &hl,
+                                        float &absum)
+{
+    float Dn_h = 0.f, Dn_l = 0.f, Do_h = 0.f, Do_l = 0.f;
+    const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, yv[3] = {y.x, y.y, y.z};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float eh, el, sh, sl;
+        two_sum(av[q], -yv[q], eh, el);  // exact a - y
+        df_mul(eh, el, eh, el, sh, sl);
+        df_add(Dn_h, Dn_l, sh, sl, Dn_h, Dn_l);
+        two_sum(bv[q], -yv[q], eh, el);  // exact b - y
+        df_mul(eh, el, eh, el, sh, sl);
+        df_add(Do_h, Do_l, sh, sl, Do_h, Do_l);
+    }
+    float rnh, rnl, roh, rol, th, tl, qh, ql;
+    df_rsqrt(Dn_h, Dn_l, rnh, rnl);
+    df_rsqrt(Do_h, Do_l, roh, rol);
+    df_add(rnh, rnl, -roh, -rol, th, tl);
+    df_mul(th, tl, y.w, 0.0f, qh, ql);
+    df_add(hh, hl, qh, ql, hh, hl);
+    absum += fabsf(y.w) * (rnh + roh);
+}
+
+// One chunk of the posted request (whole warp); lane 0 stores the chunk's sums.  The request is read through L2:
+// it was written by another SM after this SM may have cached an older one.  A waiting warp often runs alone on
+// its SM, so the positions are loaded GQ ions per lane ahead of their use.
+constexpr int GQ = 4;
+__device__ __forceinline__ void gb_chunk(GuardBoard *gb, int q)
+{
+    const int lane = threadIdx.x & 31;
+    const int tier = __ldcg(&gb->tier), N = __ldcg(&gb->N), g = __ldcg(&gb->g), i = __ldcg(&gb->i);
+    const float4 a = __ldcg(&gb->a), b = __ldcg(&gb->b);
+    const float4 *Pp = (const float4 *)__ldcg((const unsigned long long *)&gb->Pprev);
+    const float4 *Pc = (const float4 *)__ldcg((const unsigned long long *)&gb->Pcur);
+    int sJ[GB_SLOTS];
+#pragma unroll
+    for (int u = 0; u < GB_SLOTS; ++u) sJ[u] = __ldcg(&gb->slotJ[u]);
+    const int j0 = q * GB_CHUNK, j1 = min(N, j0 + GB_CHUNK);
+    // the address of partner j's position: the request's copy for the groups it holds, else the published arrays
+    auto src = [&](int j) -> const float4 * {
+        const int J = j / S;
+        const float4 *p = &(J > g ? Pp : Pc)[j];
+#pragma unroll
+        for (int u = GB_SLOTS - 1; u >= 0; --u)
+            if (sJ[u] == J) p = &gb->ovl[u][j - J * S];
+        return p;
+    };
+    auto fetch = [&](float4(&dst)[GQ], int base) {
+#pragma unroll
+        for (int u = 0; u < GQ; ++u) {
+            const int j = base + 32 * u;
+            dst[u] = (j < j1) ? __ldcg(src(j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    // two batches of GQ partners per lane: one in flight while the other is summed
+    auto sweep2 = [&](auto &&sum8) {
+        float4 yA[GQ], yB[GQ];
+        fetch(yA, j0 + lane);
+        for (int base = j0 + lane; base < j1; base += 64 * GQ) {
+            const int bB = base + 32 * GQ;
+            if (bB < j1) fetch(yB, bB);
+            sum8(yA, base);
+            if (bB < j1) {
+                if (bB + 32 * GQ < j1) fetch(yA, bB + 32 * GQ);
+                sum8(yB, bB);
+            }
+        }
+    };
+    double v;
+    float bb;
+    if (tier == 2) {
+        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const float dn = __ldcg(&gb->dn), rho0 = __ldcg(&gb->rho0);
+        float hi = 0.f, lo = 0.f, bsum = 0.f;
+        sweep2([&](const float4(&yy)[GQ], int base) {
+#pragma unroll
+            for (int u = 0; u < GQ; ++u) {
+                const int j = base + 32 * u;
+                if (j < j1 && j != i) t2_pair(b, dx, dy, dz, dn, rho0, yy[u], hi, lo, bsum);
+            }
+        });
+        v = (double)hi + (double)lo;
+        bb = bsum;
+    } else {
+        float hh = 0.f, hl = 0.f, absum = 0.f;
+        sweep2([&](const float4(&yy)[GQ], int base) {
+#pragma unroll
+            for (int u = 0; u < GQ; ++u) {
+                const int j = base + 32 * u;
+                if (j < j1 && j != i) t3_pair(a, b, yy[u], hh, hl, absum);
+            }
+        });
+        v = (double)hh + (double)hl;
+        bb = absum;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(FULL, v, o);
+        bb += __shfl_xor_sync(FULL, bb, o);
+    }
+    if (lane == 0) {
+        gb->part[q] = v;
+        gb->bpart[q] = (double)bb;
+    }
+}
+
+// A warp takes a chunk is taken by a compare-and-swap on the
+// whole (request, chunks, next) word, so a warp that read an older request takes nothing from a newer one.
+__device__ __noinline__ void gb_help(Ctl *ctl)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long v = 0;
+        int got = 0;
+        if (lane == 0) {
+            v = ld_relaxed(&ctl->gnext);
+            for (int tries = 0; tries < 4096; ++tries) {  // every failed swap is another warp's progress
+                const unsigned n = (unsigned)(v >> 16) & 0xffffu, nx = (unsigned)v & 0xffffu;
+                if (nx >= n) break;
+                const unsigned long long w = atomicCAS(&ctl->gnext, v, v + 1ull);
+                if (w == v) {
+                    got = 1;
+                    break;
+                }
+                v = w;
+            }
+        }
+        if (!__shfl_sync(FULL, got, 0)) return;
+        v = __shfl_sync(FULL, v, 0);
+        fence_acq_rel();  // the request was written before it was posted
+        gb_chunk(ctl->gb, (int)(v & 0xffffull));
+        __syncwarp();
+        if (lane == 0) {
+            fence_acq_rel();  // the chunk's sums before its count
+            atomicAdd(&ctl->gdone, 1u);
+        }
+        __syncwarp();
+    }
+}
+
 // Tier 3: every pair term in double-single arithmetic (distances from exact
 // FP32 differences); bound 2^-38 l_B |q_i| sum_j |q_j| (1/r' + 1/r).
 __device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double xs, double &dE_out)
@@ -604,36 +797,108 @@ __device__ int tier3(Smem &sm, const Ctx &c, int k, double L64, double xs, doubl
       for (int u = 0; u < GSTAGE / T; ++u) {
         const int j = j0 + u * T + tid;
         if (j >= c.N || j == i) continue;
-        const float4 y = buf[u * T + tid];
-        float Dn_h = 0.f, Dn_l = 0.f, Do_h = 0.f, Do_l = 0.f;
-        const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, yv[3] = {y.x, y.y, y.z};
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            float eh, el, sh, sl;
-            two_sum(av[q], -yv[q], eh, el);  // exact a - y
-            df_mul(eh, el, eh, el, sh, sl);
-            df_add(Dn_h, Dn_l, sh, sl, Dn_h, Dn_l);
-            two_sum(bv[q], -yv[q], eh, el);  // exact b - y
-            df_mul(eh, el, eh, el, sh, sl);
-            df_add(Do_h, Do_l, sh, sl, Do_h, Do_l);
-        }
-        float rnh, rnl, roh, rol, th, tl, qh, ql;
-        df_rsqrt(Dn_h, Dn_l, rnh, rnl);
-        df_rsqrt(Do_h, Do_l, roh, rol);
-        df_add(rnh, rnl, -roh, -rol, th, tl);
-        df_mul(th, tl, y.w, 0.0f, qh, ql);
-        df_add(hh, hl, qh, ql, hh, hl);
-        absum += fabsf(y.w) * (rnh + roh);
+        t3_pair(a, b, buf[u * T + tid], hh, hl, absum);
       }
     }
     double tot, bt;
     block_sum(sm, (double)hh + (double)hl, absum, tot, bt);
     if (tid == 0) {
-        const double lq = c.ch->lB * (double)a.w;
-        const double dE = lq * tot;
-        const double B3 = fabs(lq) * bt * 1.01 * 0x1p-38 + 0x1p-48 * (fabs(dE) + fabs(L64)) + xs + 1e-300;
+        double dE;
+        sm.guard_k = guard_outcome(c.ch->lB * (double)a.w, tot, bt, T3_KB, T3_KR, L64, xs, dE);
         sm.redd[16] = dE;
-        sm.guard_k = (dE < L64 - B3) ? 0 : ((dE > L64 + B3) ? 1 : -1);
+    }
+    bar_main();
+    const int out = sm.guard_k;
+    dE_out = sm.redd[16];
+    bar_main();
+    return out;
+}
+
+// Tier 2 or 3 of move k through the board (whole CTA).  Returns 0 accept, 1 reject, -1 undecided, or -2 when
+// the board is taken (the caller runs the tier on its own CTA).  The request holds the positions the move sees
+// from shared memory: its own group (moves before k decided), the window and the deep windows.
+__device__ int gb_tier(Smem &sm, const Ctx &c, Ctl *ctl, int k, int tier, double L64, double xs, double &dE_out)
+{
+    const int tid = threadIdx.x;
+    GuardBoard *gb = ctl->gb;
+    const unsigned n = (unsigned)((c.N + GB_CHUNK - 1) / GB_CHUNK);
+    if (tid == 0) sm.guard_k = (gb && n <= 0xffffu && atomicCAS(&ctl->glock, 0u, 1u) == 0u) ? 1 : 0;
+    bar_main();
+    const bool mine = sm.guard_k != 0;
+    bar_main();
+    if (!mine) return -2;
+    const float4 a = sm.trial[k], b = sm.own[k];
+    for (int q = tid; q < GB_SLOTS * S; q += T) {
+        const int u = q / S, l = q - u * S;
+        int J = -1;
+        if (u == 0) J = c.g;
+        else if (u == 1) J = c.win ? c.Jw : -1;
+        else if (u - 2 < c.nd) J = c.g - u;  // deep window u - 2: group g - 2 - (u - 2)
+        gb->ovl[u][l] = (J >= 0) ? position_of(sm, c, k, J * S + l) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (l == 0) gb->slotJ[u] = J;
+    }
+    if (tid == 0) {
+        gb->tier = tier;
+        gb->N = c.N;
+        gb->g = c.g;
+        gb->i = c.k0 + k;
+        gb->a = a;
+        gb->b = b;
+        gb->Pprev = c.Pprev;
+        gb->Pcur = c.Pcur;
+        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const float dn = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) * (1.0f + 0x1p-18f);
+        const float s2 = (float)c.ch->sig2;
+        gb->dn = dn;
+        gb->rho0 = sqrtf(fmaxf(s2 * (1.0f - 0x1p-18f) - 0.25f * dn * dn, 0.0f)) * (1.0f - 0x1p-18f);
+    }
+    fence_acq_rel();
+    bar_main();
+    if (tid == 0) {
+        atomicExch(&ctl->gdone, 0u);
+        const unsigned long long id = (ld_relaxed(&ctl->gnext) >> 32) + 1ull;
+        fence_acq_rel();
+        atomicExch(&ctl->gnext, (id << 32) | ((unsigned long long)n << 16));
+    }
+    bar_main();
+    gb_help(ctl);  // this work item's warps take chunks too
+    if (tid == 0) {
+        // the chunks taken by other warps: each is a bounded computation
+        bool ok = true;
+        unsigned long long t0 = 0;
+        for (unsigned spins = 1; ld_acquire32(&ctl->gdone) < n; ++spins) {
+            if ((spins & 63) == 0) {
+                const unsigned long long now = globaltimer();
+                if (t0 == 0) t0 = now;
+                else if ((long long)(now - t0) > ctl->timeout_ns) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        int out = -1;
+        double dE = 0.0;
+        if (ok) {
+            double sh = 0.0, sl = 0.0, bt = 0.0;
+            for (unsigned q = 0; q < n; ++q) {  // compensated, in chunk order
+                const double p = __ldcg(&gb->part[q]);
+                const double t = sh + p, bp = t - sh;
+                sl += (sh - (t - bp)) + (p - bp);
+                sh = t;
+                bt += __ldcg(&gb->bpart[q]);
+            }
+            out = guard_outcome(c.ch->lB * (double)a.w, sh + sl, bt, tier == 2 ? T2_KB : T3_KB,
+                                tier == 2 ? T2_KR : T3_KR, L64, xs, dE);
+            fence_acq_rel();
+            atomicExch(&ctl->glock, 0u);
+        } else {
+            // a chunk never arrived: the board stays taken (its late writes land on no newer request), the launch
+            // ends with the error, and this move goes on to tier 4
+            if (atomicCAS(&ctl->err, 0, KERR_TIMEOUT) == 0) ctl->err_info = 0xffffffffull;
+            atomicExch(&ctl->abort, 1);
+        }
+        sm.guard_k = out;
+        sm.redd[16] = dE;
     }
     bar_main();
     const int out = sm.guard_k;
@@ -1366,6 +1631,9 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const bool pairs = ctl->pairs != 0, helper = role == 1;
+    // the shared guard: in the instance for chains with a cell list only (on the plain instance the board's code
+    // measured slower, through the register allocation of the tile loop)
+    constexpr bool SHG = DA && !HELP;
     const ChainDev &ch = chains[tk.chain];
     Ctx c;
     c.ch = &ch;
@@ -1416,10 +1684,10 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
     // 1. own positions (version s-1) and, if active, the window's old positions (version sw-1)
     if (warp == 0) {
         unsigned bits;
-        bool ok = wait_words(ch, g, (nk + 31) / 32, tag_prev, tag_prev, ctl, bits);
-        if (ok && c.win) ok = wait_words(ch, c.Jw, (c.nwk + 31) / 32, (unsigned)sw, (unsigned)(sw + 1), ctl, bits);
+        bool ok = wait_words(ch, g, (nk + 31) / 32, tag_prev, tag_prev, ctl, bits, true, false, SHG);
+        if (ok && c.win) ok = wait_words(ch, c.Jw, (c.nwk + 31) / 32, (unsigned)sw, (unsigned)(sw + 1), ctl, bits, true, false, SHG);
         for (int d = 0; ok && d < c.nd; ++d)  // deep windows: version s-1 (their version s may be out already)
-            ok = wait_words(ch, g - 2 - d, WORDS, tag_prev, tag_cur, ctl, bits);
+            ok = wait_words(ch, g - 2 - d, WORDS, tag_prev, tag_cur, ctl, bits, true, false, SHG);
         if (lane == 0) sm.ok = ok;
     }
     bar_main();
@@ -1759,7 +2027,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             if (hz0 < 0) {  // the oldest tile is not published yet: wait for it
                 const int J0 = tile_J(0);
                 unsigned bits;
-                ok = wait_words(ch, J0, tile_words(J0), tile_tag(J0), tile_tag(J0), ctl, bits);
+                ok = wait_words(ch, J0, tile_words(J0), tile_tag(J0), tile_tag(J0), ctl, bits, true, false, SHG);
                 hz0 = 0;
             }
             if (lane == 0) {
@@ -1850,7 +2118,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
             const int Jn = tile_J(in);
             if (warp == 0) {
                 unsigned bits;
-                const bool ok = wait_words(ch, Jn, tile_words(Jn), tile_tag(Jn), tile_tag(Jn), ctl, bits);
+                const bool ok = wait_words(ch, Jn, tile_words(Jn), tile_tag(Jn), tile_tag(Jn), ctl, bits, true, false, SHG);
                 if (lane == 0) {
                     sm.ok = ok;
                     sm.hzs[cur ^ 1] = max(sm.hzs[cur ^ 1], in);
@@ -1992,7 +2260,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         if (warp == 0) {
             unsigned bits;
             const int nw = (c.nd - 1) * WORDS;
-            const bool ok = wait_words(ch, g - 1 - c.nd, nw, tag_cur, tag_cur, ctl, bits, false, true);
+            const bool ok = wait_words(ch, g - 1 - c.nd, nw, tag_cur, tag_cur, ctl, bits, false, true, SHG);
             if (lane < nw) sm.dacc[c.nd - 1 - lane / WORDS][lane % WORDS] = bits;
             if (lane == 0) sm.ok = ok;
         }
@@ -2093,7 +2361,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         // sums from TMEM and its exact overlap
         if (warp == 0) {
             unsigned bits;
-            const bool ok = wait_words(ch, g - 2, WORDS, tag_cur, tag_cur, ctl, bits, false, true);
+            const bool ok = wait_words(ch, g - 2, WORDS, tag_cur, tag_cur, ctl, bits, false, true, SHG);
             if (lane < WORDS) sm.dacc[0][lane] = bits;
             if (lane == 0) sm.ok = ok;
         }
@@ -2132,7 +2400,7 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
         if (warp == 0) {
             unsigned bits;
             const int nw = (c.nwk + 31) / 32;
-            const bool ok = wait_words(ch, c.Jw, nw, (unsigned)(sw + 1), (unsigned)(sw + 1), ctl, bits, false, true);
+            const bool ok = wait_words(ch, c.Jw, nw, (unsigned)(sw + 1), (unsigned)(sw + 1), ctl, bits, false, true, SHG);
             if (lane < WORDS) sm.winacc[lane] = (lane < nw) ? bits : 0u;
             if (lane == 0) sm.ok = ok;
         }
@@ -2275,12 +2543,14 @@ __device__ bool process_group(Smem &sm, const ChainDev *__restrict__ chains, con
                 }
                 if (!(stv & ST_OVL_AMBIG) && mode != 1) {
                     long long q0 = clock64();
-                    res = tier2(sm, c, k, thr, xs, dE);
+                    res = SHG ? gb_tier(sm, c, ctl, k, 2, thr, xs, dE) : -2;
+                    if (res == -2) res = tier2(sm, c, k, thr, xs, dE);
                     cyc_t[0] += clock64() - q0;
                     if (res < 0) {
                         tier = 3;
                         q0 = clock64();
-                        res = tier3(sm, c, k, thr, xs, dE);
+                        res = SHG ? gb_tier(sm, c, ctl, k, 3, thr, xs, dE) : -2;
+                        if (res == -2) res = tier3(sm, c, k, thr, xs, dE);
                         cyc_t[1] += clock64() - q0;
                     }
                 }

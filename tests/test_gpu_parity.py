@@ -150,6 +150,42 @@ def test_guard_modes(pkg, mode):
         assert diff <= 3, diff
 
 
+def test_shared_guard_every_move(pkg):
+    """Guard mode 3 at N = 20000 (every evaluated move through tiers 2 and 3): each recomputation is posted on the
+    shared board and summed in five chunks of 4096 partners by the warps that take them.  Decisions and positions
+    equal the oracle's and those of the same chain with the board off; the tier values keep their accuracy."""
+    ch = inputs.small_chain(20000, phi=0.2, seed=17, two_one=True, half_width=0.3)
+    n = ch.n
+    runs = {}
+    for shared in (1, 0):
+        gs = pkg.System([ch])
+        assert gs.get_option(pkg.OPT_SHARED_GUARD) == 1
+        gs.set_option(pkg.OPT_SHARED_GUARD, shared)
+        assert gs.get_option(pkg.OPT_SHARED_GUARD) == shared
+        gs.set_option(pkg.OPT_GUARD_MODE, 3)
+        gs.record_enable(n)
+        gs.sweep(1)
+        runs[shared] = (gs.records(), gs.positions(), gs.stats())
+        gs.close()
+    oc = oracle.OracleChain.from_chain(ch, threads=THREADS)
+    oc.record(n)
+    oc.sweep(1)
+    orc = oc.records()
+    for shared, (gr, pos, st) in runs.items():
+        assert (pos == oc.positions()).all(), shared
+        assert (gr["outcome"] == orc["outcome"]).all(), shared
+        ev = (orc["outcome"] == 0) | (orc["outcome"] == 1)
+        tiers = gr["tier"][ev]
+        assert (tiers >= 2).all() and (tiers == 2).sum() > 0.9 * ev.sum()
+        err = np.abs(gr["dE"][ev] - orc["dE"][ev]) / orc["scale"][ev]
+        assert err[tiers == 2].max() <= 1e-7, (shared, err[tiers == 2].max())
+        if (tiers == 3).any():
+            assert err[tiers == 3].max() <= 1e-10
+        assert (err[tiers == 4] == 0).all()
+    assert (runs[1][0]["tier"] == runs[0][0]["tier"]).mean() > 0.999
+    oc.close()
+
+
 def test_large_chain_prefix(pkg):
     """The N=16383 2:1 workload (phi 0.20, h 0.3): the first two sweeps bit-identical, in the production launch."""
     ch = inputs.workload("plain_n16383").chains[0]
