@@ -32,6 +32,16 @@ def test_library_exports_every_declared_symbol():
             assert hasattr(L, name), f"{name} declared in {header} but not exported"
 
 
+def test_option_constants_match_the_header():
+    """Every MC_OPT_* value of include/mc.h is the binding's OPT_* constant of the same name."""
+    import paper_1602_05716_gb300 as pkg
+    src = open(os.path.join(ROOT, "include", "mc.h")).read()
+    defs = dict(re.findall(r"^#define MC_(OPT_[A-Z0-9_]+)\s+(\d+)", src, flags=re.M))
+    assert "OPT_SHARED_GUARD" in defs and len(defs) >= 13
+    for name, value in defs.items():
+        assert getattr(pkg, name) == int(value), name
+
+
 def test_binding_loads_without_gpu():
     import paper_1602_05716_gb300 as pkg
     pkg.build()
