@@ -1,0 +1,198 @@
+"""The FP32 error bounds behind the bit-identical decisions, checked in exact arithmetic on the CPU.
+
+The sweep kernel decides a move in FP32 only when the FP32 energy change is further from the threshold than a
+proven bound; that bound is a sum of per-pair bounds.  These tests restate the kernel's per-pair arithmetic
+operation by operation in 24-bit binary arithmetic (mpmath, round to nearest even, FMA rounded once), give
+its approximate reciprocal square roots the worst error the PTX ISA allows them (2^-22.9 relative, both
+signs), and compare with the exact value of the pair's energy change 1/|a - y| - 1/|b - y| for the same FP32
+coordinates:
+
+ * the tiles' settled form (t = Dd rsqrt(Do Dn) rsqrt(Do + Dn + 2 sqrt(Do Dn)), Dd by three FMAs from 2d and
+   -|d|^2) against u (kT |t| + kP / (r_n r_o)) with the kernel's coefficients for x = dn / sp, sp the pair's
+   own smaller distance; and its squared distance Dn against u kO max(Dn, sigma^2);
+ * guard tier 2's term against its own per-term bound E1 + E2 + E3.
+
+Configurations: old positions anywhere in a 2^20-ion confinement (|b| up to 75 sigma), displacements of
+half-width 0.2 and 0.5 sigma, partners from contact (r = sigma) to 140 sigma, trial positions that overlap
+nothing (the only ones whose value matters).
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+mpmath = pytest.importorskip("mpmath")
+mp = mpmath.mp
+
+U = 2.0 ** -24
+EPS_RSQRT = 2.0 ** -22.9
+
+
+def f32(v):
+    return float(np.float32(v))
+
+
+def r24(v):
+    """Round an mpf to the nearest binary32 value (the operands here stay in the normal range)."""
+    return mp.mpf(mpmath.fadd(v, 0, prec=24, rounding="n"))
+
+
+def add(a, b):
+    return mpmath.fadd(a, b, prec=24, rounding="n")
+
+
+def sub(a, b):
+    return mpmath.fsub(a, b, prec=24, rounding="n")
+
+
+def mul(a, b):
+    return mpmath.fmul(a, b, prec=24, rounding="n")
+
+
+def fma(a, b, c):
+    return mpmath.fadd(mpmath.fmul(a, b, exact=True), c, prec=24, rounding="n")
+
+
+def rsqrt_approx(v, e):
+    with mp.workprec(80):
+        exact = 1 / mpmath.sqrt(v)
+    return r24(exact * (1 + e))
+
+
+def far_coeffs(dn, sp):
+    """The kernel's coefficients (FP32 there; here in FP64, inside their 2^-10 slack)."""
+    x = dn / sp * (1.0 + 2.0 ** -20)
+    assert x < 1.75
+    x1, g = 1.0 + x, 1.0 - 0.5 * x
+    kD = 3.0 * x1 * x1 + 4.0 * x * (2.0 + x) + 8.0 * x * x + 1.0
+    k3 = x1 * (3.0 / (g * g) + 2.0 * x / (g * g * g))
+    kT = (kD + 20.0) * (1.0 + 2.0 ** -10)
+    kP = (6.0 * (1.0 + 0.5 * x) + k3) * dn * (1.0 + 2.0 ** -10)
+    kO = (5.0 * x1 * x1 + x * (14.0 + 16.0 * x) + 1.0) * (1.0 + 2.0 ** -4)
+    return kT, kP, kO
+
+
+def settled_term(b, a, y, e1, e2):
+    """The tiles' pair form for old position b, trial a, partner y (FP32 inputs), rsqrt errors e1, e2."""
+    d = [sub(a[q], b[q]) for q in range(3)]
+    t = [mul(2, d[q]) for q in range(3)]  # exact doubling
+    m = -fma(d[2], d[2], fma(d[1], d[1], mul(d[0], d[0])))
+    ex, ey, ez = (sub(y[q], b[q]) for q in range(3))
+    Do = fma(ez, ez, fma(ey, ey, mul(ex, ex)))
+    Dd = fma(t[2], ez, fma(t[1], ey, fma(t[0], ex, m)))
+    Dn = sub(Do, Dd)
+    pd = mul(Do, Dn)
+    sr = rsqrt_approx(pd, e1)
+    c2 = fma(2, mul(pd, sr), add(Do, Dn))
+    w = rsqrt_approx(c2, e2)
+    return mul(mul(Dd, sr), w), Dn, d
+
+
+def tier2_term(b, a, y, e1, e2, e3, e4, sig2=1.0):
+    """Guard tier 2's term and its per-term bound (charge 1), errors e1..e4 of its approximate functions."""
+    dx, dy, dz = (sub(a[q], b[q]) for q in range(3))
+    with mp.workprec(24):
+        dn = mul(r24(mpmath.sqrt(fma(dz, dz, fma(dy, dy, mul(dx, dx))))), f32(1.0 + 2.0 ** -18))
+    s2 = mp.mpf(f32(sig2))
+    inner = sub(mul(s2, f32(1.0 - 2.0 ** -18)), mul(mul(0.25, dn), dn))
+    rho0 = mul(r24(mpmath.sqrt(max(inner, 0))), f32(1.0 - 2.0 ** -18)) if inner > 0 else mp.mpf(0)
+    ex, ey, ez = (sub(y[q], b[q]) for q in range(3))
+    Do = fma(ez, ez, fma(ey, ey, mul(ex, ex)))
+    wx, wy, wz = fma(2, ex, -dx), fma(2, ey, -dy), fma(2, ez, -dz)
+    Dd = fma(dz, wz, fma(dy, wy, mul(dx, wx)))
+    M = add(add(abs(mul(dx, wx)), abs(mul(dy, wy))), abs(mul(dz, wz)))
+    Dn = sub(Do, Dd)
+    ro, rn = rsqrt_approx(Do, e1), rsqrt_approx(Dn, e2)
+    pr = mul(rn, ro)
+    inv = r24(1 / add(rn, ro) * (1 + e3))
+    t = mul(mul(mul(Dd, pr), pr), inv)
+    u = mp.mpf(U)
+    relDn = add(mul(mul(fma(3 * u, Do, mul(4 * u, M)), rn), rn), u)
+    Ro = mul(mul(Do, ro), f32(1.0 + 2.0 ** -18))
+    Rn = mul(Dn, rn)
+    rho = max(sub(mul(min(Rn, Ro), f32(1.0 - 2.0 ** -18)), mul(0.5, dn)), rho0)
+    ir = r24(1 / rho * (1 + e4))
+    E1 = mul(abs(t), add(relDn, mul(19, u)))
+    E2 = mul(mul(mul(mul(4 * u, M), pr), pr), inv)
+    E3 = mul(mul(mul(mul(mul(u, dn), add(mul(2, Ro), rho)), ir), ir), ir)
+    return t, add(add(E1, E2), E3)
+
+
+def configurations(n, seed):
+    rng = random.Random(seed)
+    out = []
+    while len(out) < n:
+        h = rng.choice([0.2, 0.5])
+        b = [f32(rng.uniform(-43.0, 43.0)) for _ in range(3)]  # |b| up to 75
+        a = [f32(b[q] + rng.uniform(-h, h)) for q in range(3)]
+        kind = rng.random()
+        r = (1.0 + 1e-3 * rng.random() if kind < 0.25 else rng.uniform(1.0, 3.0) if kind < 0.5
+             else rng.uniform(3.0, 20.0) if kind < 0.75 else rng.uniform(20.0, 140.0))
+        v = [rng.gauss(0, 1) for _ in range(3)]
+        nv = math.sqrt(sum(c * c for c in v))
+        y = [f32(b[q] + r * v[q] / nv) for q in range(3)]
+        with mp.workprec(200):
+            ro = mpmath.sqrt(sum((mp.mpf(y[q]) - mp.mpf(b[q])) ** 2 for q in range(3)))
+            rn = mpmath.sqrt(sum((mp.mpf(y[q]) - mp.mpf(a[q])) ** 2 for q in range(3)))
+        if ro < 1 or rn < 1:
+            continue  # an overlapping configuration: no energy is evaluated for it
+        out.append((b, a, y, ro, rn))
+    return out
+
+
+SIGNS = [(s1 * EPS_RSQRT, s2 * EPS_RSQRT) for s1 in (-1, 1) for s2 in (-1, 1)]
+
+
+def test_settled_form_within_its_bound():
+    worst_t = worst_d = 0.0
+    for b, a, y, ro, rn in configurations(600, 11):
+        with mp.workprec(200):
+            t_ex = 1 / rn - 1 / ro
+            D_ex = rn * rn
+        for e1, e2 in SIGNS:
+            t, Dn, d = settled_term(b, a, y, e1, e2)
+            dn = f32(math.sqrt(f32(f32(float(d[2]) ** 2) + f32(float(d[1]) ** 2) + f32(float(d[0]) ** 2)))) \
+                * (1.0 + 2.0 ** -17)  # a bound of the FP32 |d| with the kernel's slack and a little more
+            sp = float(min(ro, rn))
+            kT, kP, kO = far_coeffs(dn, sp)
+            with mp.workprec(200):
+                bound_t = U * (kT * abs(t_ex) + kP / (ro * rn))
+                err_t = abs(t - t_ex)
+                bound_d = U * kO * max(D_ex, 1)
+                err_d = abs(Dn - D_ex)
+            assert err_t <= bound_t, (b, a, y, float(err_t), float(bound_t))
+            assert err_d <= bound_d, (b, a, y, float(err_d), float(bound_d))
+            worst_t = max(worst_t, float(err_t / bound_t))
+            worst_d = max(worst_d, float(err_d / bound_d))
+    # the bounds are not vacuous: some configurations use a good part of them
+    assert worst_t > 1e-3 and worst_d > 1e-3, (worst_t, worst_d)
+
+
+def test_tier2_term_within_its_bound():
+    worst = 0.0
+    for b, a, y, ro, rn in configurations(300, 12):
+        with mp.workprec(200):
+            t_ex = 1 / rn - 1 / ro
+        for e1, e2 in SIGNS:
+            for e3, e4 in ((EPS_RSQRT, -EPS_RSQRT), (-EPS_RSQRT, EPS_RSQRT)):
+                t, E = tier2_term(b, a, y, e1, e2, e3, e4)
+                with mp.workprec(200):
+                    err = abs(t - t_ex)
+                assert err <= E, (b, a, y, float(err), float(E))
+                worst = max(worst, float(err / E))
+    assert worst > 1e-3, worst
+
+
+def test_planted_error_is_caught():
+    """The check itself can fail: an rsqrt error of 2^-16, far beyond the documented one, breaks the bound."""
+    fails = 0
+    for b, a, y, ro, rn in configurations(80, 13):
+        with mp.workprec(200):
+            t_ex = 1 / rn - 1 / ro
+        t, Dn, d = settled_term(b, a, y, 2.0 ** -16, 2.0 ** -16)
+        dn = f32(math.sqrt(float(d[0]) ** 2 + float(d[1]) ** 2 + float(d[2]) ** 2)) * (1.0 + 2.0 ** -17)
+        kT, kP, kO = far_coeffs(dn, float(min(ro, rn)))
+        with mp.workprec(200):
+            fails += abs(t - t_ex) > U * (kT * abs(t_ex) + kP / (ro * rn))
+    assert fails > 10, fails
