@@ -10,6 +10,8 @@ coordinates:
  * the tiles' settled form (t = Dd rsqrt(Do Dn) rsqrt(Do + Dn + 2 sqrt(Do Dn)), Dd by three FMAs from 2d and
    -|d|^2) against u (kT |t| + kP / (r_n r_o)) with the kernel's coefficients for x = dn / sp, sp the pair's
    own smaller distance; and its squared distance Dn against u kO max(Dn, sigma^2);
+ * the direct form 1/r' - 1/r of the ions seen at both positions (this group, the windows) against its 10 u
+   (1/r' + 1/r);
  * guard tier 2's term against its own per-term bound E1 + E2 + E3.
 
 Configurations: old positions anywhere in a 2^20-ion confinement (|b| up to 75 sigma), displacements of
@@ -167,6 +169,29 @@ def test_settled_form_within_its_bound():
             worst_d = max(worst_d, float(err_d / bound_d))
     # the bounds are not vacuous: some configurations use a good part of them
     assert worst_t > 1e-3 and worst_d > 1e-3, (worst_t, worst_d)
+
+
+def direct_term(b, a, y, e1, e2):
+    """The both-position ions' direct form: rsqrt of each FP32 squared distance, then the difference."""
+    dn = [sub(a[q], y[q]) for q in range(3)]
+    do = [sub(b[q], y[q]) for q in range(3)]
+    d2n = fma(dn[2], dn[2], fma(dn[1], dn[1], mul(dn[0], dn[0])))
+    d2o = fma(do[2], do[2], fma(do[1], do[1], mul(do[0], do[0])))
+    return sub(rsqrt_approx(d2n, e1), rsqrt_approx(d2o, e2))
+
+
+def test_direct_form_within_its_bound():
+    worst = 0.0
+    for b, a, y, ro, rn in configurations(400, 14):
+        with mp.workprec(200):
+            t_ex = 1 / rn - 1 / ro
+            bound = 10 * U * (1 / rn + 1 / ro)
+        for e1, e2 in SIGNS:
+            with mp.workprec(200):
+                err = abs(direct_term(b, a, y, e1, e2) - t_ex)
+            assert err <= bound, (b, a, y, float(err), float(bound))
+            worst = max(worst, float(err / bound))
+    assert worst > 0.05, worst
 
 
 def test_tier2_term_within_its_bound():
