@@ -12,7 +12,8 @@ coordinates:
    own smaller distance; and its squared distance Dn against u kO max(Dn, sigma^2);
  * the direct form 1/r' - 1/r of the ions seen at both positions (this group, the windows) against its 10 u
    (1/r' + 1/r);
- * guard tier 2's term against its own per-term bound E1 + E2 + E3.
+ * guard tier 2's term against its own per-term bound E1 + E2 + E3;
+ * guard tier 3's double-single term against its 2^-38 (1/r' + 1/r).
 
 Configurations: old positions anywhere in a 2^20-ion confinement (|b| up to 75 sigma), displacements of
 half-width 0.2 and 0.5 sigma, partners from contact (r = sigma) to 140 sigma, trial positions that overlap
@@ -207,6 +208,70 @@ def test_tier2_term_within_its_bound():
                 assert err <= E, (b, a, y, float(err), float(E))
                 worst = max(worst, float(err / E))
     assert worst > 1e-3, worst
+
+
+def two_sum(a, b):
+    s_ = add(a, b)
+    bb = sub(s_, a)
+    return s_, add(sub(a, sub(s_, bb)), sub(b, bb))
+
+
+def two_prod(a, b):
+    p = mul(a, b)
+    return p, fma(a, b, -p)
+
+
+def df_add(ah, al, bh, bl):
+    s_, e = two_sum(ah, bh)
+    e = add(e, add(al, bl))
+    sh = add(s_, e)
+    return sh, sub(e, sub(sh, s_))
+
+
+def df_mul(ah, al, bh, bl):
+    p, e = two_prod(ah, bh)
+    e = fma(ah, bl, fma(al, bh, e))
+    ph = add(p, e)
+    return ph, sub(e, sub(ph, p))
+
+
+def df_rsqrt(dh, dl, e):
+    r0 = rsqrt_approx(dh, e)
+    ph, pl = two_prod(r0, r0)
+    xh, xl = df_mul(dh, dl, ph, pl)
+    res = sub(sub(1, xh), xl)
+    corr = mul(mul(0.5, r0), res)
+    rh = add(r0, corr)
+    return rh, sub(corr, sub(rh, r0))
+
+
+def tier3_term(b, a, y, e1, e2):
+    """Guard tier 3's term (charge 1): exact differences, double-single squares and sums, Newton-refined rsqrt."""
+    Dn = (mp.mpf(0), mp.mpf(0))
+    Do = (mp.mpf(0), mp.mpf(0))
+    for q in range(3):
+        eh, el = two_sum(a[q], -y[q])
+        Dn = df_add(*Dn, *df_mul(eh, el, eh, el))
+        eh, el = two_sum(b[q], -y[q])
+        Do = df_add(*Do, *df_mul(eh, el, eh, el))
+    rnh, rnl = df_rsqrt(*Dn, e1)
+    roh, rol = df_rsqrt(*Do, e2)
+    th, tl = df_add(rnh, rnl, -roh, -rol)
+    return th + tl
+
+
+def test_tier3_term_within_its_bound():
+    worst = 0.0
+    for b, a, y, ro, rn in configurations(300, 15):
+        with mp.workprec(200):
+            t_ex = 1 / rn - 1 / ro
+            bound = 2.0 ** -38 * (1 / rn + 1 / ro)
+        for e1, e2 in SIGNS:
+            with mp.workprec(200):
+                err = abs(tier3_term(b, a, y, e1, e2) - t_ex)
+            assert err <= bound, (b, a, y, float(err), float(bound))
+            worst = max(worst, float(err / bound))
+    assert worst > 1e-4, worst
 
 
 def test_planted_error_is_caught():
