@@ -286,3 +286,65 @@ def test_planted_error_is_caught():
         with mp.workprec(200):
             fails += abs(t - t_ex) > U * (kT * abs(t_ex) + kP / (ro * rn))
     assert fails > 10, fails
+
+
+def _two_sum_lanes(hi, lo, term):
+    """Per-lane compensated accumulation in FP32 (numpy float32 arrays): the tiers' (hi, lo) update."""
+    s_ = (hi + term).astype(np.float32)
+    bb = (s_ - hi).astype(np.float32)
+    e = ((hi - (s_ - bb)) + (term - bb)).astype(np.float32)
+    return s_, (lo + e).astype(np.float32)
+
+
+def test_tier_sum_partitions_within_the_margin():
+    """Tier 2 sums 2^20 FP32 terms either on one CTA (256 lanes of 4096 terms, FP64 block sum) or on the shared
+    board (chunks of 4096 partners: 32 lanes of 128 terms, FP64 warp sums, chunk sums added with a compensated
+    FP64 sum).  Either way the error of the summation itself, against the exact sum of the same FP32 terms, stays
+    far inside the quarter of the per-term bound sum that tier 2 keeps as margin (bt x 1.25)."""
+    import fractions
+    rng = np.random.default_rng(16)
+    n = 1 << 20
+    r = rng.uniform(1.0, 140.0, n)
+    q = rng.choice([-1.0, 2.0], n)
+    dn = 0.3
+    terms = (q * dn * rng.uniform(-1, 1, n) / (r * r)).astype(np.float32)  # |t| ~ dn / r^2 like the tiles
+    exact = float(sum(fractions.Fraction(float(t)) for t in terms))
+    margin = 0.25 * 19 * U * float(np.abs(terms.astype(np.float64)).sum())  # 0.25 x (the 19u |t| part of bt)
+
+    def lanes(grid):  # grid: (lanes, terms per lane), accumulated in order along axis 1
+        hi = np.zeros(grid.shape[0], np.float32)
+        lo = np.zeros(grid.shape[0], np.float32)
+        for k in range(grid.shape[1]):
+            hi, lo = _two_sum_lanes(hi, lo, grid[:, k])
+        return hi.astype(np.float64) + lo.astype(np.float64)
+
+    # one CTA: thread t takes terms t, t + 256, ...
+    cta = lanes(terms.reshape(-1, 256).T)
+    cta_sum = 0.0
+    for w in range(8):
+        v = cta[32 * w:32 * w + 32].copy()
+        for o in (16, 8, 4, 2, 1):  # xor-shuffle tree
+            v = v + v[np.arange(32) ^ o]
+        cta_sum += v[0]
+    # the board: chunk c, lane l takes terms c * 4096 + l, + 32, ...
+    ch = terms.reshape(-1, 128, 32).transpose(0, 2, 1).reshape(-1, 128)
+    lane_sums = lanes(ch).reshape(-1, 32)
+    sh = sl = 0.0
+    for row in lane_sums:
+        v = row.copy()
+        for o in (16, 8, 4, 2, 1):
+            v = v + v[np.arange(32) ^ o]
+        p = v[0]
+        t = sh + p
+        bp = t - sh
+        sl += (sh - (t - bp)) + (p - bp)
+        sh = t
+    board_sum = sh + sl
+    for got in (cta_sum, board_sum):
+        assert abs(got - exact) <= 1e-3 * margin, (got, exact, margin)
+    # the check has teeth: the same partitions without the compensation miss that threshold
+    for grid in (terms.reshape(-1, 256).T, ch):
+        acc = np.zeros(grid.shape[0], np.float32)
+        for k in range(grid.shape[1]):
+            acc = (acc + grid[:, k]).astype(np.float32)
+        assert abs(float(acc.astype(np.float64).sum()) - exact) > 1e-3 * margin
