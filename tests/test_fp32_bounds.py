@@ -13,7 +13,9 @@ coordinates:
  * the direct form 1/r' - 1/r of the ions seen at both positions (this group, the windows) against its 10 u
    (1/r' + 1/r);
  * guard tier 2's term against its own per-term bound E1 + E2 + E3;
- * guard tier 3's double-single term against its 2^-38 (1/r' + 1/r).
+ * guard tier 3's double-single term against its 2^-38 (1/r' + 1/r);
+ * the surrogate MLP's FP32 forward pass (delayed acceptance's stage 1) against its bound eg of |g32 - g64|,
+   g64 the oracle's FP64 forward pass on the same BF16 weights, with expf given its documented 2 ulp.
 
 Configurations: old positions anywhere in a 2^20-ion confinement (|b| up to 75 sigma), displacements of
 half-width 0.2 and 0.5 sigma, partners from contact (r = sigma) to 140 sigma, trial positions that overlap
@@ -272,6 +274,92 @@ def test_tier3_term_within_its_bound():
             assert err <= bound, (b, a, y, float(err), float(bound))
             worst = max(worst, float(err / bound))
     assert worst > 1e-4, worst
+
+
+def mlp32(wf, v, e_exp):
+    """The stage-1 MLP in FP32, operation by operation (the kernel's FMA chains, silu = z / (1 + expf(-z)) with
+    expf off by the relative error e_exp), and its bound eg."""
+    H, NIN = 64, 33
+    W1, b1 = wf[:H * NIN], wf[H * NIN:H * NIN + H]
+    W2 = wf[H * NIN + H:H * NIN + H + H * H]
+    b2 = wf[H * NIN + H + H * H:H * NIN + 2 * H + H * H]
+    W3, b3 = wf[H * NIN + 2 * H + H * H:H * NIN + 3 * H + H * H], wf[-1]
+    u = mp.mpf(U)
+
+    def silu(z):
+        with mp.workprec(80):
+            ex = mpmath.exp(-z)
+        ex = r24(ex * (1 + e_exp))
+        return mpmath.fdiv(z, add(1, ex), prec=24, rounding="n")
+
+    ev32 = mul(4 * u, abs(v[32]))
+    h1, mh, me = [], mp.mpf(0), mp.mpf(0)
+    for o in range(H):
+        z0, z1, M = b1[o], mp.mpf(0), abs(b1[o])
+        for i in range(0, 32, 2):
+            z0 = fma(W1[o * NIN + i], v[i], z0)
+            z1 = fma(W1[o * NIN + i + 1], v[i + 1], z1)
+            M = fma(abs(W1[o * NIN + i]), abs(v[i]), M)
+            M = fma(abs(W1[o * NIN + i + 1]), abs(v[i + 1]), M)
+        z0 = fma(W1[o * NIN + 32], v[32], z0)
+        M = fma(abs(W1[o * NIN + 32]), abs(v[32]), M)
+        z = add(z0, z1)
+        ez = add(mul(mul(36, u), M), mul(abs(W1[o * NIN + 32]), ev32))
+        h = silu(z)
+        h1.append(h)
+        mh = max(mh, abs(h))
+        me = max(me, add(add(mul(1.1, ez), mul(4 * u, abs(h))), mul(2 * u, abs(z))))
+    gs, Mg, eacc = b3, abs(b3), mp.mpf(0)
+    for o in range(H):
+        row = W2[o * H:(o + 1) * H]
+        w2n = mp.mpf(float(np.nextafter(np.float32(float(sum(abs(x) for x in row))), np.float32(np.inf))))
+        zz = [b2[o], mp.mpf(0), mp.mpf(0), mp.mpf(0)]
+        for i in range(0, H, 4):
+            for k in range(4):
+                zz[k] = fma(row[i + k], h1[i + k], zz[k])
+        z = add(add(zz[0], zz[1]), add(zz[2], zz[3]))
+        ez = add(mul(mul(68, u), add(abs(b2[o]), mul(w2n, mh))), mul(w2n, me))
+        h = silu(z)
+        eh = add(add(mul(1.1, ez), mul(4 * u, abs(h))), mul(2 * u, abs(z)))
+        gs = fma(W3[o], h, gs)
+        Mg = fma(abs(W3[o]), abs(h), Mg)
+        eacc = fma(abs(W3[o]), eh, eacc)
+    eg = mul(add(mul(mul(66, u), Mg), eacc), 1 + 2.0 ** -8)
+    return gs, eg
+
+
+def _mlp_cases(n, seed):
+    import oracle
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n):
+        scale = [0.5, 1.0, 3.0][c % 3]
+        H, NIN = 64, 33
+        parts = [rng.normal(0, scale / math.sqrt(NIN), H * NIN), rng.normal(0, 0.1 * scale, H),
+                 rng.normal(0, scale / math.sqrt(H), H * H), rng.normal(0, 0.1 * scale, H),
+                 rng.normal(0, scale / math.sqrt(H), H), rng.normal(0, 0.1, 1)]
+        w64 = oracle.bf16_to_f64(oracle.f64_to_bf16(np.concatenate(parts)))
+        v = np.concatenate([rng.integers(-24, 25, 32) * 0.25, [f32(rng.uniform(0, 1))]])
+        out.append((w64, v, oracle.mlp_forward(w64, v)))
+    return out
+
+
+def test_mlp32_within_its_bound():
+    """The bound holds with expf at its documented worst (and it is a worst case: the errors seen use 2e-4 of it
+    at most), while an expf off by 2^-5 breaks it for most networks."""
+    worst, planted = 0.0, 0
+    for w64, v, g64 in _mlp_cases(12, 17):
+        wf = [mp.mpf(float(x)) for x in w64]
+        vv = [mp.mpf(float(x)) for x in v]
+        for sign in (1, -1):
+            g32, eg = mlp32(wf, vv, sign * 2.0 ** -22)
+            err = abs(g32 - mp.mpf(g64))
+            assert err <= eg, (float(err), float(eg))
+            worst = max(worst, float(err / eg))
+        g32, eg = mlp32(wf, vv, 2.0 ** -5)
+        planted += abs(g32 - mp.mpf(g64)) > eg
+    assert worst > 1e-5, worst
+    assert planted >= 4, planted
 
 
 def test_planted_error_is_caught():
