@@ -15,7 +15,8 @@ coordinates:
  * guard tier 2's term against its own per-term bound E1 + E2 + E3;
  * guard tier 3's double-single term against its 2^-38 (1/r' + 1/r);
  * the surrogate MLP's FP32 forward pass (delayed acceptance's stage 1) against its bound eg of |g32 - g64|,
-   g64 the oracle's FP64 forward pass on the same BF16 weights, with expf given its documented 2 ulp.
+   g64 the oracle's FP64 forward pass on the same BF16 weights, with expf given its documented 2 ulp;
+ * stage 1's near-field term q s(d) / d (the C1 taper s beyond r_s = r_c / 2) against its 34 u |q| / d.
 
 Configurations: old positions anywhere in a 2^20-ion confinement (|b| up to 75 sigma), displacements of
 half-width 0.2 and 0.5 sigma, partners from contact (r = sigma) to 140 sigma, trial positions that overlap
@@ -360,6 +361,48 @@ def test_mlp32_within_its_bound():
         planted += abs(g32 - mp.mpf(g64)) > eg
     assert worst > 1e-5, worst
     assert planted >= 4, planted
+
+
+def near_term(x, y, q, e, r_c=4.0):
+    """Stage 1's near-field term in FP32 as the kernel forms it: q s(d) rounded, times rsqrt(d^2)."""
+    tw = 0.5 * r_c
+    rs_f, itw_f = mp.mpf(f32(r_c - tw)), mp.mpf(f32(1.0 / tw))
+    dx, dy, dz = (sub(x[k], y[k]) for k in range(3))
+    d2 = fma(dz, dz, fma(dy, dy, mul(dx, dx)))
+    r = rsqrt_approx(d2, e)
+    dist = mul(d2, r)
+    if dist > rs_f:
+        t = mul(sub(dist, rs_f), itw_f)
+        taper = sub(1, mul(mul(t, t), sub(3, mul(2, t))))
+    else:
+        taper = mp.mpf(1)
+    return mul(mul(q, taper), r)
+
+
+def test_near_field_term_within_its_bound():
+    rng = random.Random(18)
+    worst = 0.0
+    for _ in range(1500):
+        x = [f32(rng.uniform(-60.0, 60.0)) for _ in range(3)]
+        dist = rng.uniform(1.0, 3.999)
+        v = [rng.gauss(0, 1) for _ in range(3)]
+        nv = math.sqrt(sum(c * c for c in v))
+        y = [f32(x[k] + dist * v[k] / nv) for k in range(3)]
+        q = rng.choice([-1.0, 2.0])
+        with mp.workprec(200):
+            d = mpmath.sqrt(sum((mp.mpf(x[k]) - mp.mpf(y[k])) ** 2 for k in range(3)))
+            if d >= 4:
+                continue
+            tt = (d - 2) / 2
+            sd = 1 - tt * tt * (3 - 2 * tt) if d > 2 else mp.mpf(1)
+            exact = q * sd / d
+            bound = 34 * U * abs(q) / d
+        for e in (EPS_RSQRT, -EPS_RSQRT):
+            with mp.workprec(200):
+                err = abs(near_term(x, y, q, e) - exact)
+            assert err <= bound, (x, y, q, float(err), float(bound))
+            worst = max(worst, float(err / bound))
+    assert worst > 0.01, worst
 
 
 def test_planted_error_is_caught():
